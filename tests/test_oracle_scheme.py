@@ -1,0 +1,289 @@
+"""Pins of the oracle's scheme: encryption, CRT, tensor, key switching,
+ModDown, rescale, the network blocks and graph evaluation (Alg. firing)."""
+import numpy as np
+import pytest
+
+from oracle import ckks, core
+from paper_2110_13638_gb300 import workloads as W
+import golden_io
+
+BITS4 = [60, 40, 40, 40, 60]
+
+
+@pytest.fixture(scope="module")
+def ctx16():
+    c = ckks.Context(16, BITS4)
+    c.keygen(3)
+    return c
+
+
+@pytest.fixture(scope="module")
+def ctx64():
+    c = ckks.Context(64, BITS4)
+    c.keygen(0)
+    return c
+
+
+def _schoolbook_z(a, b):
+    """negacyclic product over the integers (lists of Python ints)"""
+    N = len(a)
+    c = [0] * N
+    for i in range(N):
+        for j in range(N):
+            if i + j < N:
+                c[i + j] += a[i] * b[j]
+            else:
+                c[i + j - N] -= a[i] * b[j]
+    return c
+
+
+def _crt(ctx, res, primes):
+    """residues [len(primes)][N] -> list of integers in [0, prod)"""
+    Q = 1
+    for p in primes:
+        Q *= p
+    out = []
+    for k in range(res.shape[1]):
+        x = 0
+        for r, p in enumerate(primes):
+            Qr = Q // p
+            x += int(res[r, k]) * Qr * pow(Qr, -1, p)
+        out.append(x % Q)
+    return out, Q
+
+
+def _centre(x, Q):
+    return x - Q if x > (Q - 1) // 2 else x
+
+
+def _s_int(ctx):
+    return [int(v) for v in ctx.s_int]
+
+
+def _phase(ctx, c, level):
+    """c0 + c1 s (+ c2 s^2) over the integers mod Q_level, centred."""
+    primes = ctx.q[:level]
+    s = _s_int(ctx)
+    comps = [_crt(ctx, c[k], primes)[0] for k in range(c.shape[0])]
+    Q = 1
+    for p in primes:
+        Q *= p
+    acc = list(comps[0])
+    spow = s
+    for k in range(1, c.shape[0]):
+        prod = _schoolbook_z(comps[k], spow)
+        acc = [a + b for a, b in zip(acc, prod)]
+        spow = _schoolbook_z(spow, s)
+    return [_centre(a % Q, Q) for a in acc]
+
+
+# ---------------------------------------------------------------- keys / enc
+def test_keys_have_the_stated_form(ctx16):
+    """pk0 + pk1 s is small (the Gaussian e); ksk_j[0] + ksk_j[1] s is
+    e_j + P s^2 in residue j and e_j elsewhere."""
+    ctx = ctx16
+    N = ctx.N
+    s = _s_int(ctx)
+    for r in range(ctx.L_top):
+        q = ctx.q[r]
+        v = [(int(a) + b) % q for a, b in zip(ctx.pk[0, r], _schoolbook_z([int(x) for x in ctx.pk[1, r]], s))]
+        v = [_centre(x, q) for x in v]
+        assert max(abs(x) for x in v) <= 19
+    s2 = _schoolbook_z(s, s)
+    for j in range(ctx.L_top):
+        for r, p in enumerate(ctx.key_primes):
+            v = [(int(a) + b) % p for a, b in zip(ctx.ksk[j, 0, r], _schoolbook_z([int(x) for x in ctx.ksk[j, 1, r]], s))]
+            if r == j:
+                v = [(x - ctx.P * t) % p for x, t in zip(v, s2)]
+            v = [_centre(x, p) for x in v]
+            assert max(abs(x) for x in v) <= 19, (j, r)
+
+
+def test_encrypt_decrypt_roundtrip(ctx64):
+    ctx = ctx64
+    N = ctx.N
+    z = np.random.default_rng(0).uniform(-1, 1, N // 2)
+    m = ctx.encode(z)
+    ct = ctx.encrypt(m, 17)
+    d = ctx.decrypt(ct, check_crt=True)
+    bound = 2 * 19 * N + 19          # |u e| + |e1 s| + |e0|
+    assert np.max(np.abs(d - m)) <= bound
+    assert np.max(np.abs(d - m)) > 0   # noise is present
+    assert np.max(np.abs(ctx.decode(d, ct.scale) - z)) < bound / ctx.delta + N / ctx.delta
+
+
+def test_encryptions_differ_by_ct_id(ctx16):
+    m = np.zeros(16, dtype=np.int64)
+    a = ctx16.encrypt(m, 1).c
+    b = ctx16.encrypt(m, 2).c
+    assert not np.array_equal(a, b)
+    assert np.array_equal(a, ctx16.encrypt(m, 1).c)
+
+
+# ---------------------------------------------------------------- tensor
+def test_tensor_phase_is_product_of_phases(ctx16):
+    ctx = ctx16
+    rng = np.random.default_rng(1)
+    L = 3
+    a = ckks.Ciphertext(np.stack([np.stack([rng.integers(0, q, 16, dtype=np.uint64) for q in ctx.q[:L]]) for _ in range(2)]), L, 1.0)
+    b = ckks.Ciphertext(np.stack([np.stack([rng.integers(0, q, 16, dtype=np.uint64) for q in ctx.q[:L]]) for _ in range(2)]), L, 1.0)
+    d = ctx.tensor(a, b)
+    Q = ctx.q[0] * ctx.q[1] * ctx.q[2]
+    pa, pb, pd = _phase(ctx, a.c, L), _phase(ctx, b.c, L), _phase(ctx, d.c, L)
+    want = [_centre(x % Q, Q) for x in _schoolbook_z(pa, pb)]
+    assert pd == want
+
+
+# ---------------------------------------------------------------- rescale
+def test_rescale_is_rounded_division(ctx16):
+    ctx = ctx16
+    rng = np.random.default_rng(2)
+    L = 4
+    c = np.stack([np.stack([rng.integers(0, q, 16, dtype=np.uint64) for q in ctx.q[:L]]) for _ in range(2)])
+    out = ctx.rescale(ckks.Ciphertext(c, L, 2.0 ** 80))
+    ql = ctx.q[L - 1]
+    for k in range(2):
+        X, Q = _crt(ctx, c[k], ctx.q[:L])
+        for i in range(L - 1):
+            for n in range(16):
+                want = ((X[n] + ql // 2) // ql) % ctx.q[i]     # round(X / q_{L-1}), no ties
+                assert int(out.c[k, i, n]) == want
+    assert out.level == L - 1 and out.scale == 2.0 ** 80 / float(ql)
+
+
+def test_mod_down_is_rounded_division(ctx16):
+    ctx = ctx16
+    rng = np.random.default_rng(3)
+    L = 3
+    primes = ctx.q[:L] + [ctx.P]
+    acc = np.stack([np.stack([rng.integers(0, p, 16, dtype=np.uint64) for p in primes]) for _ in range(2)])
+    out = ctx.mod_down(acc, L)
+    P = ctx.P
+    for k in range(2):
+        X, _ = _crt(ctx, acc[k], primes)
+        for t in range(L):
+            for n in range(16):
+                assert int(out[k, t, n]) == ((X[n] + P // 2) // P) % ctx.q[t]
+
+
+def test_keyswitch_accumulator_definition(ctx16):
+    """acc_k = sum_j [d2]_{q_j} ksk_j[k] in every prime (schoolbook)."""
+    ctx = ctx16
+    rng = np.random.default_rng(4)
+    L = 2
+    d2 = np.stack([rng.integers(0, q, 16, dtype=np.uint64) for q in ctx.q[:L]])
+    acc = ctx.keyswitch_accumulate(d2, L)
+    for ti, kr in enumerate(list(range(L)) + [ctx.L_top]):
+        p = ctx.key_primes[kr]
+        for k in range(2):
+            want = [0] * 16
+            for j in range(L):
+                prod = _schoolbook_z([int(x) for x in d2[j]], [int(x) for x in ctx.ksk[j, k, kr]])
+                want = [a + b for a, b in zip(want, prod)]
+            assert [int(x) for x in acc[k, ti]] == [w % p for w in want]
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+def test_relinearise_preserves_phase(ctx16, L):
+    """decrypt(relin(d0, d1, d2)) = d0 + d1 s + d2 s^2 up to the key-switching
+    noise: rounding (<= 1/2 per coefficient of each component, times |s|)
+    plus sum_j |digit_j| |e_j| N / P."""
+    ctx = ctx16
+    N = 16
+    rng = np.random.default_rng(5 + L)
+    d = np.stack([np.stack([rng.integers(0, q, N, dtype=np.uint64) for q in ctx.q[:L]]) for _ in range(3)])
+    before = _phase(ctx, d, L)
+    r = ctx.relinearise(ckks.Ciphertext(d, L, 1.0))
+    after = _phase(ctx, r.c, L)
+    bound = 0.5 + 0.5 * N + L * max(ctx.q) * 19 * N / ctx.P + 1
+    assert max(abs(a - b) for a, b in zip(after, before)) <= bound
+
+
+# ---------------------------------------------------------------- blocks
+def test_linear_block(ctx64):
+    ctx = ctx64
+    N = ctx.N
+    rng = np.random.default_rng(7)
+    xs = rng.uniform(-1, 1, size=(3, N // 2))
+    cts = [ctx.encrypt(ctx.encode(x), 100 + i) for i, x in enumerate(xs)]
+    Wt = rng.normal(0, 0.5, size=(2, 3))
+    b = np.array([0.3, -0.2])
+    rows = [(np.arange(3), Wt[o]) for o in range(2)]
+    ys = ctx.linear(cts, rows, b)
+    for o in range(2):
+        assert ys[o].level == ctx.L_top - 1
+        assert ys[o].scale == ctx.delta
+        got = ctx.decode(ctx.decrypt(ys[o]), ys[o].scale)
+        assert np.max(np.abs(got - (Wt[o] @ xs + b[o]))) < 1e-6
+
+
+def test_square_and_poly3_blocks(ctx64):
+    ctx = ctx64
+    N = ctx.N
+    z = np.random.default_rng(8).uniform(-4, 4, N // 2)
+    ct = ctx.encrypt(ctx.encode(z), 5)
+    sq = ctx.square(ct)
+    assert sq.level == ctx.L_top - 1
+    assert np.max(np.abs(ctx.decode(ctx.decrypt(sq), sq.scale) - z * z)) < 1e-6
+    a = [0.5, 0.2, 0.01, -0.004]
+    y = ctx.poly3(ct, a)
+    assert y.level == ctx.L_top - 2
+    assert abs(y.scale / ctx.delta - 1) < 1e-9
+    ref = a[0] + a[1] * z + a[2] * z * z + a[3] * z ** 3
+    assert np.max(np.abs(ctx.decode(ctx.decrypt(y), y.scale) - ref)) < 1e-6
+
+
+def test_sigmoid_fit_reproduces_printed_coefficients():
+    got = W.sigmoid_fit()
+    want = golden_io.sigmoid_coeffs()
+    # the paper prints three decimals
+    for g, w in zip(got, want):
+        assert abs(g - w) < 1.5e-3
+    assert abs(got[1] - want[1]) > 1e-4       # a1 really is 0.198..., not 0.197
+
+
+# ---------------------------------------------------------------- graphs
+def test_graph_eval_mini_cnn_matches_fp64():
+    g, x = W.mini_cnn(n_slots=32)
+    assert ckks.graph_depth(g, W.input_nodes(g)) == 7
+    ctx = ckks.Context(64, [60] + [40] * 7 + [60])
+    ctx.keygen(0)
+    cts = [ctx.encrypt(ctx.encode(v), i) for i, v in enumerate(x)]
+    out = ckks.eval_graph(ctx, g, W.input_nodes(g), [cts])
+    ref = ckks.forward_fp64(g, W.input_nodes(g), [x])
+    (o, ys), = out.items()
+    assert len(ys) == ref[o].shape[0] == 3
+    for y, r in zip(ys, ref[o]):
+        assert y.level == 1
+        assert np.max(np.abs(ctx.decode(ctx.decrypt(y), y.scale) - r)) < 1e-4
+
+
+def test_graph_eval_branches_level_match():
+    g, xs = W.branch_graph(n_slots=32)
+    ins = W.input_nodes(g)
+    ctx = ckks.Context(64, [60, 40, 40, 40, 60])
+    ctx.keygen(1)
+    sig = [[ctx.encrypt(ctx.encode(v), 10 * k + i) for i, v in enumerate(x)] for k, x in enumerate(xs)]
+    out = ckks.eval_graph(ctx, g, ins, sig)
+    ref = ckks.forward_fp64(g, ins, xs)
+    (o, ys), = out.items()
+    assert len(ys) == 4
+    for y, r in zip(ys, ref[o]):
+        assert y.level == 1
+        assert np.max(np.abs(ctx.decode(ctx.decrypt(y), y.scale) - r)) < 1e-5
+
+
+def test_firing_waits_for_all_inbound_edges():
+    order = []
+    nodes = [{"kind": "input"}, {"kind": "input"}, {"kind": "add"}, {"kind": "output"}]
+    g = {"nodes": nodes, "edges": [(0, 2), (1, 2), (2, 3)]}
+
+    def apply_fn(n, node, s):
+        order.append(n)
+        if isinstance(s, dict):
+            return sum(s["edges"])
+        return s
+
+    out = ckks.fire(g, [0, 1], [5, 7], apply_fn, lambda sigs: {"edges": sigs})
+    assert order == [0, 1, 2, 3]          # node 2 fired only after input 1 arrived
+    assert out == {3: 12}
