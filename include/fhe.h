@@ -1,0 +1,231 @@
+/*
+ * fhe.h -- C ABI of libfhe: RNS-CKKS evaluation of neural-network graphs on one
+ * NVIDIA GB300 (sm_103a), after arXiv 2110.13638 ("EDLaaS: Fully Homomorphic
+ * Encryption Over Neural Network Graphs").
+ *
+ * Conventions (every entry point):
+ *   - returns int: FHE_OK (0) or a negative FHE_E* code; fhe_last_error()
+ *     then holds a message for the calling thread;
+ *   - handles (fhe_ctx, fhe_graph) are opaque, owned by the library and freed
+ *     by their *_destroy call;
+ *   - pointers named d_* are DEVICE pointers owned by the caller (e.g. the
+ *     storage of a PyTorch tensor); the library never frees them.  Pointers
+ *     named h_* or plain arrays are HOST memory owned by the caller and read
+ *     only during the call;
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream); device work is
+ *     enqueued on it and the call returns without waiting unless stated;
+ *   - one context must not be used from two streams or threads at once (its
+ *     workspace is shared by the calls made on it).
+ *
+ * Data layout:
+ *   residue polynomial  : N u64 words, every word < its prime
+ *   ciphertext batch    : u64 [n_ct][2][L][N], NTT form (bit-reversed order),
+ *                         residue r belongs to prime q_r; L = level
+ *   plaintext batch     : u64 [n_ct][L][N], NTT form
+ *   coefficient export  : same shapes in coefficient (natural) order
+ *   slots               : double [n_ct][N/2] (real slots, batch-in-slots)
+ *   decrypted poly      : int64 [n_ct][N], centred coefficients mod q_0
+ */
+#ifndef FHE_H
+#define FHE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FHE_OK 0
+#define FHE_EINVAL (-1)       /* bad argument, shape or graph */
+#define FHE_ENOMEM (-2)       /* device or host allocation failed */
+#define FHE_ELEVEL (-3)       /* not enough primes left for the operation */
+#define FHE_ESCALE (-4)       /* operands' nominal scales disagree */
+#define FHE_ECUDA (-5)        /* a CUDA runtime call failed */
+#define FHE_ETIMEOUT (-6)     /* a bounded device wait gave up */
+#define FHE_EUNSUPPORTED (-7) /* valid request this build does not implement */
+#define FHE_ENOKEY (-8)       /* fhe_keygen has not run on this context */
+
+typedef struct fhe_ctx fhe_ctx;
+typedef struct fhe_graph fhe_graph;
+
+/* Context facts (fhe_ctx_query). */
+typedef struct {
+    uint32_t N;          /* ring degree */
+    uint32_t slots;      /* N / 2 */
+    uint32_t L_top;      /* data primes q_0 .. q_{L_top-1} */
+    uint32_t log_scale;  /* scale = 2^log_scale */
+    uint64_t primes[64]; /* q_0 .. q_{L_top-1}, then the special prime P */
+    uint64_t key_bytes;  /* device bytes held for keys and tables */
+} fhe_ctx_info;
+
+/* Per-ciphertext metadata returned by graph evaluation. */
+typedef struct {
+    uint32_t level;      /* number of primes held */
+    double scale;        /* nominal scale (FP64) */
+} fhe_ct_meta;
+
+/* ---- graph description (host arrays, copied by fhe_graph_create) ---------
+ * Sec. 3 graph rules: nodes are blocks (layers); an edge carries a list of
+ * ciphertexts; a node with several in-edges sees them stacked in edge order
+ * (FHE_NODE_ADD sums them element by element instead); a node fires once all
+ * in-edges carry data; its output goes to every out-edge. */
+enum {
+    FHE_NODE_INPUT = 0,  /* source: encrypted input signal (type of concern) */
+    FHE_NODE_LINEAR = 1, /* y_o = sum_e w_e x_{col_e} + b_o (dense or conv), cost 1 */
+    FHE_NODE_POLY = 2,   /* a0 + a1 x + a2 x^2 + a3 x^3 per ciphertext, cost 2 */
+    FHE_NODE_SQUARE = 3, /* x^2 per ciphertext, cost 1 */
+    FHE_NODE_ADD = 4,    /* element-wise sum of the in-edge lists, cost 0 */
+    FHE_NODE_OUTPUT = 5  /* sink: result handed to the client (type of concern) */
+};
+
+typedef struct {
+    uint32_t kind;            /* FHE_NODE_* */
+    uint32_t n_out;           /* LINEAR: outputs; INPUT: ciphertexts it receives */
+    const uint32_t* row_ptr;  /* LINEAR: CSR row pointers, n_out + 1 entries */
+    const uint32_t* col_idx;  /* LINEAR: CSR column = index into the stacked input */
+    const double* weight;     /* LINEAR: CSR values (FP64) */
+    const double* bias;       /* LINEAR: n_out biases (FP64), may be NULL = 0 */
+    double coeffs[4];         /* POLY: a0..a3 */
+} fhe_node_desc;
+
+typedef struct {
+    uint32_t n_nodes;
+    const fhe_node_desc* nodes;
+    uint32_t n_edges;
+    const uint32_t* edge_src;   /* edge e goes edge_src[e] -> edge_dst[e] */
+    const uint32_t* edge_dst;
+} fhe_graph_desc;
+
+/* ---- parameters (Sec. 3.1) ---------------------------------------------- */
+
+/* Alg. parameterise: multiplicative cost c -> ring degree N and the
+ * coefficient-modulus bit list m (first and last entries int(s * p); the last
+ * one is the special prime).  bits must hold c + 2 entries.  Host only. */
+int fhe_parameterise(uint32_t cost, uint32_t log_scale, double special_mult,
+                     uint32_t* N, uint32_t* bits, uint32_t bits_cap, uint32_t* n_bits);
+
+/* Alg. autoHE / autoHE_discover over a graph: parameter groups of the input
+ * nodes and each group's largest cost.  group_of[i] receives the group of the
+ * i-th INPUT node (in node order); group_cost[g] the cost of group g.  Host only. */
+int fhe_autohe(const fhe_graph_desc* g, uint32_t* group_of, uint32_t group_of_cap,
+               uint32_t* group_cost, uint32_t group_cost_cap, uint32_t* n_groups);
+
+/* Prime chain for (N, bits): q > 2^b, q = 1 mod 2N, increasing per size.
+ * out receives n_bits primes (last = special prime).  Host only. */
+int fhe_prime_chain(uint32_t N, const uint32_t* bits, uint32_t n_bits, uint64_t* out);
+
+/* Discrete-Gaussian cumulative table used by the samplers (38 thresholds,
+ * support [-19, 19], sigma 3.2).  Host only. */
+int fhe_gauss_table(uint64_t* out38);
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Build the context on the current CUDA device: primes, NTT tables and
+ * encoder tables resident in HBM.  bits: coefficient-modulus bit sizes, the
+ * last one being the special prime; log_scale: scale 2^log_scale.
+ * N must be a power of two in [16, 16384]. */
+int fhe_ctx_create(uint32_t N, const uint32_t* bits, uint32_t n_bits,
+                   uint32_t log_scale, fhe_ctx** out);
+int fhe_ctx_destroy(fhe_ctx* ctx);
+int fhe_ctx_query(const fhe_ctx* ctx, fhe_ctx_info* out);
+
+/* Secret key s (ternary), public key and relinearisation keys (per-prime
+ * digits, special prime P), sampled on the device from `seed`; resident in
+ * HBM until the context is destroyed.  Synchronises `stream` at the end. */
+int fhe_keygen(fhe_ctx* ctx, uint64_t seed, void* stream);
+
+/* Device copy of the secret key (NTT form) [L_top + 1][N], for tests. */
+int fhe_export_secret(fhe_ctx* ctx, uint64_t* d_out, void* stream);
+
+/* ---- encode / encrypt / decrypt / decode -------------------------------- */
+
+/* CKKS canonical-embedding encode: d_slots [n_ct][N/2] real -> plaintext
+ * [n_ct][level][N] (NTT form); m_k = round(scale * sigma^{-1}(z)_k), half
+ * away from zero, in double-double arithmetic. */
+int fhe_encode(fhe_ctx* ctx, const double* d_slots, uint32_t n_ct, uint32_t level,
+               double scale, uint64_t* d_pt, void* stream);
+
+/* Public-key encryption at the top level: ct = (u pk0 + e0 + m, u pk1 + e1),
+ * u ternary and e0, e1 Gaussian drawn from (keygen seed, ct id), ct id =
+ * first_ct_id + k.  d_pt [n_ct][L_top][N] -> d_ct [n_ct][2][L_top][N]. */
+int fhe_encrypt(fhe_ctx* ctx, const uint64_t* d_pt, uint32_t n_ct, uint64_t first_ct_id,
+                uint64_t* d_ct, void* stream);
+
+/* Decrypt at `level`: m = c0 + c1 s, dropped to q_0, centred lift -> d_m
+ * int64 [n_ct][N] (coefficient form). */
+int fhe_decrypt(fhe_ctx* ctx, const uint64_t* d_ct, uint32_t n_ct, uint32_t level,
+                int64_t* d_m, void* stream);
+
+/* Decode: d_m int64 [n_ct][N] -> d_slots [n_ct][N/2] real parts, divided by
+ * scale (FP64 FFT). */
+int fhe_decode(fhe_ctx* ctx, const int64_t* d_m, uint32_t n_ct, double scale,
+               double* d_slots, void* stream);
+
+/* ---- layout conversion (parity export / import) ------------------------- */
+
+/* n_poly residue polynomials [n_poly][rows][N]: rows-th row r belongs to
+ * prime index r (0..L_top, L_top = P).  forward = coefficient -> NTT form. */
+int fhe_ntt(fhe_ctx* ctx, uint64_t* d_poly, uint32_t n_poly, uint32_t rows, int forward, void* stream);
+
+/* ciphertexts [n_ct][2][level][N]: NTT form -> coefficient form (to_coeff = 1)
+ * or back (to_coeff = 0); in and out may alias. */
+int fhe_ct_convert(fhe_ctx* ctx, const uint64_t* d_in, uint32_t n_ct, uint32_t level,
+                   int to_coeff, uint64_t* d_out, void* stream);
+
+/* ---- homomorphic operations (batched; all at one level) ----------------- */
+
+/* d_out = d_a + d_b */
+int fhe_add(fhe_ctx* ctx, const uint64_t* d_a, const uint64_t* d_b, uint32_t n_ct, uint32_t level,
+            uint64_t* d_out, void* stream);
+
+/* tensor: d_out [n_ct][3][level][N] = (a0 b0, a0 b1 + a1 b0, a1 b1) */
+int fhe_tensor(fhe_ctx* ctx, const uint64_t* d_a, const uint64_t* d_b, uint32_t n_ct, uint32_t level,
+               uint64_t* d_out, void* stream);
+
+/* relinearise: d3 [n_ct][3][level][N] -> d_out [n_ct][2][level][N] by RNS key
+ * switching of the third component (per-prime digits, ModDown by P). */
+int fhe_relinearise(fhe_ctx* ctx, const uint64_t* d3, uint32_t n_ct, uint32_t level,
+                    uint64_t* d_out, void* stream);
+
+/* rescale: d_in [n_ct][comps][level][N] -> d_out [n_ct][comps][level-1][N],
+ * division by q_{level-1} with the centred remainder. */
+int fhe_rescale(fhe_ctx* ctx, const uint64_t* d_in, uint32_t n_ct, uint32_t comps, uint32_t level,
+                uint64_t* d_out, void* stream);
+
+/* ct-mult + relinearise + rescale for n_ct pairs at `level`:
+ * d_out [n_ct][2][level-1][N] = rescale(relin(a (x) b)). */
+int fhe_mul_relin_rescale(fhe_ctx* ctx, const uint64_t* d_a, const uint64_t* d_b, uint32_t n_ct,
+                          uint32_t level, uint64_t* d_out, void* stream);
+
+/* multiply by integer constants: ct_k *= C_k (one signed constant per
+ * ciphertext, host array) ; and add integer constants to the constant term. */
+int fhe_mul_const(fhe_ctx* ctx, const uint64_t* d_in, const int64_t* h_c, uint32_t n_ct, uint32_t level,
+                  uint64_t* d_out, void* stream);
+int fhe_add_const(fhe_ctx* ctx, uint64_t* d_ct, const int64_t* h_c, uint32_t n_ct, uint32_t level,
+                  void* stream);
+
+/* ---- graphs ------------------------------------------------------------- */
+
+/* Copy a graph description (weights included) into a library-owned graph. */
+int fhe_graph_create(const fhe_graph_desc* desc, fhe_graph** out);
+int fhe_graph_destroy(fhe_graph* g);
+
+/* Number of ciphertexts each OUTPUT node produces and their level, once the
+ * graph is evaluated on a context whose inputs enter at L_top. */
+int fhe_graph_outputs(fhe_ctx* ctx, const fhe_graph* g, uint32_t* n_out_cts, uint32_t* out_level);
+
+/* Evaluate the graph (Alg. firing): d_in[i] holds the ciphertexts of the
+ * i-th INPUT node ([n][2][L_top][N], scale 2^log_scale); the outputs of all
+ * OUTPUT nodes, in node order, are written to d_out [n_out][2][out_level][N]
+ * with one fhe_ct_meta each. */
+int fhe_eval_graph(fhe_ctx* ctx, const fhe_graph* g, const uint64_t* const* d_in, uint32_t n_inputs,
+                   uint64_t* d_out, fhe_ct_meta* out_meta, uint32_t out_cap, void* stream);
+
+const char* fhe_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FHE_H */

@@ -1,0 +1,579 @@
+// capi.cu -- the extern "C" entry points of libfhe (include/fhe.h): context
+// and key management, batched homomorphic operations, and graph evaluation
+// (the neuronal-firing traversal of arXiv 2110.13638, Sec. 3, Alg. firing /
+// signal_carrier / get_inbound_signal / apply_signal / set_outbound_signals),
+// whose node receptors launch the kernels of kernels.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/fhe.h"
+#include "ctx.h"
+#include "host_math.h"
+
+using namespace fhe;
+
+namespace fhe {
+
+static thread_local std::string g_err;
+
+int fail(int code, const std::string& msg)
+{
+    g_err = msg;
+    return code;
+}
+
+int cuda_check(cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return FHE_OK;
+    return fail(e == cudaErrorMemoryAllocation ? FHE_ENOMEM : FHE_ECUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int ws_reserve(fhe_ctx* c, size_t bytes, Arena* a)
+{
+    if (bytes == 0) bytes = 256;
+    if (c->ws_bytes < bytes) {
+        if (c->ws) {
+            cudaDeviceSynchronize();
+            cudaFree(c->ws);
+            c->ws = nullptr;
+            c->ws_bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&c->ws, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return cuda_check(e, "workspace cudaMalloc");
+        }
+        c->ws_bytes = bytes;
+    }
+    a->base = (char*)c->ws;
+    a->cap = c->ws_bytes;
+    a->used = 0;
+    return FHE_OK;
+}
+
+// llround of a double: round half away from zero (C semantics)
+static int64_t dround(double x) { return (int64_t)std::llround(x); }
+
+static u64 mod_signed(int64_t v, u64 q)
+{
+    if (v >= 0) return (u64)v % q;
+    u64 r = (u64)(-(v + 1)) % q;            // |v| - 1 mod q
+    r = (r + 1) % q;
+    return r == 0 ? 0 : q - r;
+}
+
+}  // namespace fhe
+
+#define CHECK_CTX(c)                                                         \
+    do {                                                                     \
+        if (!(c)) return fail(FHE_EINVAL, "null context");                  \
+    } while (0)
+#define CHECK_KEYS(c)                                                        \
+    do {                                                                     \
+        if (!(c)->has_keys) return fail(FHE_ENOKEY, "fhe_keygen has not run"); \
+    } while (0)
+#define CUDA_LAST(what)                                                      \
+    do {                                                                     \
+        cudaError_t _e = cudaGetLastError();                                 \
+        if (_e != cudaSuccess) return cuda_check(_e, what);                  \
+    } while (0)
+
+extern "C" {
+
+const char* fhe_last_error(void) { return g_err.c_str(); }
+
+// ---------------------------------------------------------------- parameters
+int fhe_parameterise(uint32_t cost, uint32_t log_scale, double special_mult, uint32_t* N, uint32_t* bits,
+                     uint32_t bits_cap, uint32_t* n_bits)
+{
+    if (!N || !bits || !n_bits) return fail(FHE_EINVAL, "null output");
+    std::vector<uint32_t> b;
+    parameterise(cost, log_scale, special_mult, N, b);
+    *n_bits = (uint32_t)b.size();
+    if (b.size() > bits_cap) return fail(FHE_EINVAL, "bits_cap too small");
+    for (size_t i = 0; i < b.size(); ++i) bits[i] = b[i];
+    return FHE_OK;
+}
+
+int fhe_prime_chain(uint32_t N, const uint32_t* bits, uint32_t n_bits, uint64_t* out)
+{
+    if (!bits || !out || n_bits == 0) return fail(FHE_EINVAL, "bad arguments");
+    if (N < 2 || (N & (N - 1))) return fail(FHE_EINVAL, "N must be a power of two");
+    std::vector<u64> ch;
+    if (!prime_chain(N, bits, n_bits, ch)) return fail(FHE_EINVAL, "bit size out of range [20, 61]");
+    for (uint32_t i = 0; i < n_bits; ++i) out[i] = ch[i];
+    return FHE_OK;
+}
+
+int fhe_gauss_table(uint64_t* out38)
+{
+    if (!out38) return fail(FHE_EINVAL, "null output");
+    std::vector<u64> t = gauss_cdt();
+    for (size_t i = 0; i < t.size(); ++i) out38[i] = t[i];
+    return FHE_OK;
+}
+
+// Alg. autoHE_discover: largest accumulated cost from source s at every node;
+// a node of the concern type (input / output) reached from another source
+// restarts discovery as its own source with cost 0.
+static uint32_t node_cost(uint32_t kind)
+{
+    switch (kind) {
+    case FHE_NODE_LINEAR: return 1;
+    case FHE_NODE_SQUARE: return 1;
+    case FHE_NODE_POLY: return 2;
+    default: return 0;
+    }
+}
+
+static bool is_concern(uint32_t kind) { return kind == FHE_NODE_INPUT || kind == FHE_NODE_OUTPUT; }
+
+struct Discover {
+    const fhe_graph_desc* g;
+    std::vector<std::map<uint32_t, uint32_t>> sources;   // node -> {source: cost}
+    std::vector<std::vector<uint32_t>> succ;
+    int depth = 0;
+    bool overflow = false;
+    void run(uint32_t n, uint32_t s, uint32_t c)
+    {
+        if (++depth > 100000) { overflow = true; --depth; return; }
+        auto& d = sources[n];
+        if (s != n) {
+            auto it = d.find(s);
+            if (it == d.end() || it->second < c) d[s] = c;
+        }
+        if (is_concern(g->nodes[n].kind) && s != n) {
+            run(n, n, 0);
+        } else {
+            for (uint32_t i : succ[n]) run(i, s, c + node_cost(g->nodes[i].kind));
+        }
+        --depth;
+    }
+};
+
+int fhe_autohe(const fhe_graph_desc* g, uint32_t* group_of, uint32_t group_of_cap, uint32_t* group_cost,
+               uint32_t group_cost_cap, uint32_t* n_groups)
+{
+    if (!g || !g->nodes || !n_groups) return fail(FHE_EINVAL, "null graph");
+    Discover D;
+    D.g = g;
+    D.sources.resize(g->n_nodes);
+    D.succ.resize(g->n_nodes);
+    for (uint32_t e = 0; e < g->n_edges; ++e) {
+        uint32_t a = g->edge_src[e], b = g->edge_dst[e];
+        if (a >= g->n_nodes || b >= g->n_nodes) return fail(FHE_EINVAL, "edge out of range");
+        auto& v = D.succ[a];
+        if (std::find(v.begin(), v.end(), b) == v.end()) v.push_back(b);
+    }
+    std::vector<uint32_t> inputs;
+    for (uint32_t i = 0; i < g->n_nodes; ++i)
+        if (g->nodes[i].kind == FHE_NODE_INPUT) inputs.push_back(i);
+    for (uint32_t i : inputs) D.run(i, i, 0);
+    if (D.overflow) return fail(FHE_EINVAL, "graph traversal too deep (cycle without a concern node?)");
+    std::map<uint32_t, uint32_t> gof;
+    std::vector<uint32_t> gcost;
+    for (uint32_t i : inputs) {
+        if (!gof.count(i)) {
+            gof[i] = (uint32_t)gcost.size();
+            gcost.push_back(0);
+        }
+        for (uint32_t j = 0; j < g->n_nodes; ++j) {
+            const auto& src = D.sources[j];
+            if (!src.count(i)) continue;
+            for (const auto& kv : src) {
+                gof[kv.first] = gof[i];
+                if (kv.second > gcost[gof[i]]) gcost[gof[i]] = kv.second;
+            }
+        }
+    }
+    *n_groups = (uint32_t)gcost.size();
+    if (group_of) {
+        if (inputs.size() > group_of_cap) return fail(FHE_EINVAL, "group_of_cap too small");
+        for (size_t k = 0; k < inputs.size(); ++k) group_of[k] = gof[inputs[k]];
+    }
+    if (group_cost) {
+        if (gcost.size() > group_cost_cap) return fail(FHE_EINVAL, "group_cost_cap too small");
+        for (size_t k = 0; k < gcost.size(); ++k) group_cost[k] = gcost[k];
+    }
+    return FHE_OK;
+}
+
+// ---------------------------------------------------------------- context
+static void free_ctx(fhe_ctx* c)
+{
+    cudaFree(c->d_pc);
+    cudaFree(c->d_tw_fwd);
+    cudaFree(c->d_tw_inv);
+    cudaFree(c->d_cdt);
+    cudaFree(c->d_enc_tw);
+    cudaFree(c->d_enc_twist);
+    cudaFree(c->d_slot_of);
+    cudaFree(c->d_s);
+    cudaFree(c->d_pk);
+    cudaFree(c->d_ksk);
+    cudaFree(c->ws);
+    delete c;
+}
+
+int fhe_ctx_create(uint32_t N, const uint32_t* bits, uint32_t n_bits, uint32_t log_scale, fhe_ctx** out)
+{
+    if (!out || !bits) return fail(FHE_EINVAL, "null argument");
+    *out = nullptr;
+    if (N < 16 || N > 16384 || (N & (N - 1))) return fail(FHE_EUNSUPPORTED, "N must be a power of two in [16, 16384]");
+    if (n_bits < 2 || n_bits > 33) return fail(FHE_EINVAL, "need 2..33 coefficient-modulus entries");
+    if (log_scale < 1 || log_scale > 60) return fail(FHE_EINVAL, "log_scale out of range");
+    std::vector<u64> ch;
+    if (!prime_chain(N, bits, n_bits, ch)) return fail(FHE_EINVAL, "bit size out of range [20, 61]");
+
+    fhe_ctx* c = new fhe_ctx();
+    c->N = N;
+    c->logN = 0;
+    while ((1u << c->logN) < N) ++c->logN;
+    c->L_top = n_bits - 1;
+    c->log_scale = log_scale;
+    c->primes = ch;
+    c->delta = std::ldexp(1.0, (int)log_scale);
+    cudaGetDevice(&c->device);
+
+    const uint32_t np = n_bits;
+    c->pc.resize(np);
+    std::vector<ulonglong2> twf((size_t)np * N), twi((size_t)np * N);
+    for (uint32_t r = 0; r < np; ++r) {
+        const u64 q = ch[r];
+        PrimeC& P = c->pc[r];
+        P.q = q;
+        P.q2 = 2 * q;
+        P.mu = (u64)(((u128)1 << 64) / q);
+        P.r64 = (u64)(((u128)1 << 64) % q);
+        P.r64s = shoup(P.r64, q);
+        P.ninv = hinv(N, q);
+        P.ninvs = shoup(P.ninv, q);
+        P.half = (q - 1) / 2;
+        P.ub = (u64)((((u128)1 << 64) / q) * q);
+        const u64 psi = primitive_root_2n(q, N);
+        const u64 psi_inv = hinv(psi, q);
+        for (uint32_t i = 0; i < N; ++i) {
+            const uint32_t br = bitrev(i, (int)c->logN);
+            const u64 w = hpow(psi, br, q), wi = hpow(psi_inv, br, q);
+            twf[(size_t)r * N + i] = make_ulonglong2(w, shoup(w, q));
+            twi[(size_t)r * N + i] = make_ulonglong2(wi, shoup(wi, q));
+        }
+    }
+    std::vector<u64> cdt = gauss_cdt();
+    // encoder tables: zeta^{-4k} (k < N/4), zeta^{-k} (k < N/2), slot positions
+    std::vector<double4> etw(N / 4), etwist(N / 2);
+    for (uint32_t k = 0; k < N / 4; ++k) {
+        cdd z = zeta_pow_dd(-4 * (int64_t)k, N);
+        etw[k] = make_double4(z.re.hi, z.re.lo, z.im.hi, z.im.lo);
+    }
+    for (uint32_t k = 0; k < N / 2; ++k) {
+        cdd z = zeta_pow_dd(-(int64_t)k, N);
+        etwist[k] = make_double4(z.re.hi, z.re.lo, z.im.hi, z.im.lo);
+    }
+    std::vector<uint32_t> slot_of(N / 2);
+    u64 e = 1;
+    for (uint32_t j = 0; j < N / 2; ++j) {
+        slot_of[(e - 1) / 4] = j;
+        e = (e * 5) % (2ull * N);
+    }
+
+    int rc = FHE_OK;
+    auto up = [&](void** dst, const void* src, size_t bytes) {
+        if (rc != FHE_OK) return;
+        cudaError_t err = cudaMalloc(dst, bytes);
+        if (err == cudaSuccess) err = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+        if (err != cudaSuccess) {
+            cudaGetLastError();
+            rc = cuda_check(err, "fhe_ctx_create upload");
+        }
+    };
+    up((void**)&c->d_pc, c->pc.data(), np * sizeof(PrimeC));
+    up((void**)&c->d_tw_fwd, twf.data(), twf.size() * sizeof(ulonglong2));
+    up((void**)&c->d_tw_inv, twi.data(), twi.size() * sizeof(ulonglong2));
+    up((void**)&c->d_cdt, cdt.data(), cdt.size() * sizeof(u64));
+    up((void**)&c->d_enc_tw, etw.data(), etw.size() * sizeof(double4));
+    up((void**)&c->d_enc_twist, etwist.data(), etwist.size() * sizeof(double4));
+    up((void**)&c->d_slot_of, slot_of.data(), slot_of.size() * sizeof(uint32_t));
+    if (rc != FHE_OK) {
+        free_ctx(c);
+        return rc;
+    }
+    c->key_bytes = np * sizeof(PrimeC) + 2 * twf.size() * sizeof(ulonglong2) + cdt.size() * 8 +
+                   (etw.size() + etwist.size()) * sizeof(double4) + slot_of.size() * 4;
+    *out = c;
+    return FHE_OK;
+}
+
+int fhe_ctx_destroy(fhe_ctx* c)
+{
+    if (!c) return FHE_OK;
+    cudaDeviceSynchronize();
+    free_ctx(c);
+    return FHE_OK;
+}
+
+int fhe_ctx_query(const fhe_ctx* c, fhe_ctx_info* out)
+{
+    CHECK_CTX(c);
+    if (!out) return fail(FHE_EINVAL, "null output");
+    std::memset(out, 0, sizeof(*out));
+    out->N = c->N;
+    out->slots = c->N / 2;
+    out->L_top = c->L_top;
+    out->log_scale = c->log_scale;
+    for (size_t i = 0; i < c->primes.size() && i < 64; ++i) out->primes[i] = c->primes[i];
+    out->key_bytes = c->key_bytes;
+    return FHE_OK;
+}
+
+int fhe_keygen(fhe_ctx* c, uint64_t seed, void* stream)
+{
+    CHECK_CTX(c);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t N = c->N, Lt = c->L_top;
+    if (!c->d_s) {
+        size_t bs = (Lt + 1) * N * 8, bp = 2 * Lt * N * 8, bk = Lt * 2 * (Lt + 1) * N * 8;
+        cudaError_t e = cudaMalloc((void**)&c->d_s, bs);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_pk, bp);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_ksk, bk);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return cuda_check(e, "key allocation");
+        }
+        c->key_bytes += bs + bp + bk;
+    }
+    c->seed = seed;
+    k_keygen(c, st);
+    CUDA_LAST("keygen launch");
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_check(e, "keygen");
+    c->has_keys = true;
+    return FHE_OK;
+}
+
+int fhe_export_secret(fhe_ctx* c, uint64_t* d_out, void* stream)
+{
+    CHECK_CTX(c);
+    CHECK_KEYS(c);
+    if (!d_out) return fail(FHE_EINVAL, "null output");
+    return cuda_check(cudaMemcpyAsync(d_out, c->d_s, (size_t)(c->L_top + 1) * c->N * 8, cudaMemcpyDeviceToDevice,
+                                      (cudaStream_t)stream),
+                      "export secret");
+}
+
+// ---------------------------------------------------------------- encode etc.
+int fhe_encode(fhe_ctx* c, const double* d_slots, uint32_t n_ct, uint32_t level, double scale, uint64_t* d_pt,
+               void* stream)
+{
+    CHECK_CTX(c);
+    if (n_ct == 0) return FHE_OK;
+    if (!d_slots || !d_pt) return fail(FHE_EINVAL, "null buffer");
+    if (level < 1 || level > c->L_top) return fail(FHE_ELEVEL, "level out of range");
+    if (!(scale > 0.0) || !std::isfinite(scale)) return fail(FHE_EINVAL, "bad scale");
+    Arena ar;
+    int rc = ws_reserve(c, encode_scratch_bytes(c, n_ct), &ar);
+    if (rc) return rc;
+    k_encode(c, d_slots, n_ct, level, scale, (u64*)d_pt, ar.take(encode_scratch_bytes(c, n_ct)), (cudaStream_t)stream);
+    CUDA_LAST("encode launch");
+    return FHE_OK;
+}
+
+int fhe_encrypt(fhe_ctx* c, const uint64_t* d_pt, uint32_t n_ct, uint64_t first_ct_id, uint64_t* d_ct, void* stream)
+{
+    CHECK_CTX(c);
+    CHECK_KEYS(c);
+    if (n_ct == 0) return FHE_OK;
+    if (!d_pt || !d_ct) return fail(FHE_EINVAL, "null buffer");
+    k_encrypt(c, (const u64*)d_pt, n_ct, first_ct_id, (u64*)d_ct, (cudaStream_t)stream);
+    CUDA_LAST("encrypt launch");
+    return FHE_OK;
+}
+
+int fhe_decrypt(fhe_ctx* c, const uint64_t* d_ct, uint32_t n_ct, uint32_t level, int64_t* d_m, void* stream)
+{
+    CHECK_CTX(c);
+    CHECK_KEYS(c);
+    if (n_ct == 0) return FHE_OK;
+    if (!d_ct || !d_m) return fail(FHE_EINVAL, "null buffer");
+    if (level < 1 || level > c->L_top) return fail(FHE_ELEVEL, "level out of range");
+    k_decrypt(c, (const u64*)d_ct, n_ct, level, (i64*)d_m, (cudaStream_t)stream);
+    CUDA_LAST("decrypt launch");
+    return FHE_OK;
+}
+
+int fhe_decode(fhe_ctx* c, const int64_t* d_m, uint32_t n_ct, double scale, double* d_slots, void* stream)
+{
+    CHECK_CTX(c);
+    if (n_ct == 0) return FHE_OK;
+    if (!d_m || !d_slots) return fail(FHE_EINVAL, "null buffer");
+    if (!(scale > 0.0) || !std::isfinite(scale)) return fail(FHE_EINVAL, "bad scale");
+    k_decode(c, (const i64*)d_m, n_ct, scale, d_slots, (cudaStream_t)stream);
+    CUDA_LAST("decode launch");
+    return FHE_OK;
+}
+
+int fhe_ntt(fhe_ctx* c, uint64_t* d_poly, uint32_t n_poly, uint32_t rows, int forward, void* stream)
+{
+    CHECK_CTX(c);
+    if (n_poly == 0) return FHE_OK;
+    if (!d_poly) return fail(FHE_EINVAL, "null buffer");
+    if (rows < 1 || rows > c->L_top + 1) return fail(FHE_EINVAL, "rows out of range");
+    uint8_t pm[64];
+    for (uint32_t r = 0; r < rows; ++r) pm[r] = (uint8_t)r;
+    k_ntt_rows(c, (u64*)d_poly, n_poly, rows, pm, forward != 0, (cudaStream_t)stream);
+    CUDA_LAST("ntt launch");
+    return FHE_OK;
+}
+
+int fhe_ct_convert(fhe_ctx* c, const uint64_t* d_in, uint32_t n_ct, uint32_t level, int to_coeff, uint64_t* d_out,
+                   void* stream)
+{
+    CHECK_CTX(c);
+    if (n_ct == 0) return FHE_OK;
+    if (!d_in || !d_out) return fail(FHE_EINVAL, "null buffer");
+    if (level < 1 || level > c->L_top) return fail(FHE_ELEVEL, "level out of range");
+    k_ct_to_coeff(c, (const u64*)d_in, (u64*)d_out, n_ct, 2, level, to_coeff != 0, (cudaStream_t)stream);
+    CUDA_LAST("convert launch");
+    return FHE_OK;
+}
+
+// ---------------------------------------------------------------- ops
+#define CHECK_LEVEL(c, L, lo)                                                  \
+    do {                                                                       \
+        if ((L) < (lo) || (L) > (c)->L_top) return fail(FHE_ELEVEL, "level out of range"); \
+    } while (0)
+
+int fhe_add(fhe_ctx* c, const uint64_t* a, const uint64_t* b, uint32_t n_ct, uint32_t level, uint64_t* out,
+            void* stream)
+{
+    CHECK_CTX(c);
+    CHECK_LEVEL(c, level, 1);
+    if (n_ct == 0) return FHE_OK;
+    if (!a || !b || !out) return fail(FHE_EINVAL, "null buffer");
+    k_add(c, (const u64*)a, (const u64*)b, (u64*)out, n_ct, 2, level, (cudaStream_t)stream);
+    CUDA_LAST("add launch");
+    return FHE_OK;
+}
+
+int fhe_tensor(fhe_ctx* c, const uint64_t* a, const uint64_t* b, uint32_t n_ct, uint32_t level, uint64_t* out,
+               void* stream)
+{
+    CHECK_CTX(c);
+    CHECK_LEVEL(c, level, 1);
+    if (n_ct == 0) return FHE_OK;
+    if (!a || !b || !out) return fail(FHE_EINVAL, "null buffer");
+    k_tensor(c, (const u64*)a, (const u64*)b, (u64*)out, n_ct, level, (cudaStream_t)stream);
+    CUDA_LAST("tensor launch");
+    return FHE_OK;
+}
+
+int fhe_relinearise(fhe_ctx* c, const uint64_t* d3, uint32_t n_ct, uint32_t level, uint64_t* out, void* stream)
+{
+    CHECK_CTX(c);
+    CHECK_KEYS(c);
+    CHECK_LEVEL(c, level, 1);
+    if (n_ct == 0) return FHE_OK;
+    if (!d3 || !out) return fail(FHE_EINVAL, "null buffer");
+    Arena ar;
+    size_t need = relin_scratch_bytes(c, n_ct, level);
+    int rc = ws_reserve(c, need, &ar);
+    if (rc) return rc;
+    k_relin(c, (const u64*)d3, (u64*)out, n_ct, level, ar.take(need), (cudaStream_t)stream);
+    CUDA_LAST("relinearise launch");
+    return FHE_OK;
+}
+
+int fhe_rescale(fhe_ctx* c, const uint64_t* in, uint32_t n_ct, uint32_t comps, uint32_t level, uint64_t* out,
+                void* stream)
+{
+    CHECK_CTX(c);
+    CHECK_LEVEL(c, level, 2);
+    if (n_ct == 0) return FHE_OK;
+    if (!in || !out) return fail(FHE_EINVAL, "null buffer");
+    if (comps < 1 || comps > 3) return fail(FHE_EINVAL, "comps must be 1..3");
+    Arena ar;
+    size_t need = rescale_scratch_bytes(c, n_ct, comps);
+    int rc = ws_reserve(c, need, &ar);
+    if (rc) return rc;
+    k_rescale(c, (const u64*)in, (u64*)out, n_ct, comps, level, nullptr, 0, ar.take(need), (cudaStream_t)stream);
+    CUDA_LAST("rescale launch");
+    return FHE_OK;
+}
+
+int fhe_mul_relin_rescale(fhe_ctx* c, const uint64_t* a, const uint64_t* b, uint32_t n_ct, uint32_t level,
+                          uint64_t* out, void* stream)
+{
+    CHECK_CTX(c);
+    CHECK_KEYS(c);
+    CHECK_LEVEL(c, level, 2);
+    if (n_ct == 0) return FHE_OK;
+    if (!a || !b || !out) return fail(FHE_EINVAL, "null buffer");
+    const size_t N = c->N;
+    const size_t b3 = (size_t)n_ct * 3 * level * N * 8, b2 = (size_t)n_ct * 2 * level * N * 8;
+    const size_t br = relin_scratch_bytes(c, n_ct, level), bs = rescale_scratch_bytes(c, n_ct, 2);
+    Arena ar;
+    int rc = ws_reserve(c, arena_need({b3, b2, br, bs}), &ar);
+    if (rc) return rc;
+    u64* t3 = (u64*)ar.take(b3);
+    u64* t2 = (u64*)ar.take(b2);
+    void* sr = ar.take(br);
+    void* ss = ar.take(bs);
+    cudaStream_t st = (cudaStream_t)stream;
+    k_tensor(c, (const u64*)a, (const u64*)b, t3, n_ct, level, st);
+    k_relin(c, t3, t2, n_ct, level, sr, st);
+    k_rescale(c, t2, (u64*)out, n_ct, 2, level, nullptr, 0, ss, st);
+    CUDA_LAST("mul_relin_rescale launch");
+    return FHE_OK;
+}
+
+static int upload_const_residues(fhe_ctx* c, const int64_t* h, uint32_t n_ct, uint32_t level, Arena* ar, u64** dres,
+                                 cudaStream_t st)
+{
+    std::vector<u64> res((size_t)n_ct * level);
+    for (uint32_t k = 0; k < n_ct; ++k)
+        for (uint32_t r = 0; r < level; ++r) res[(size_t)k * level + r] = mod_signed(h[k], c->primes[r]);
+    *dres = (u64*)ar->take(res.size() * 8);
+    return cuda_check(cudaMemcpyAsync(*dres, res.data(), res.size() * 8, cudaMemcpyHostToDevice, st), "const upload");
+}
+
+int fhe_mul_const(fhe_ctx* c, const uint64_t* in, const int64_t* h_c, uint32_t n_ct, uint32_t level, uint64_t* out,
+                  void* stream)
+{
+    CHECK_CTX(c);
+    CHECK_LEVEL(c, level, 1);
+    if (n_ct == 0) return FHE_OK;
+    if (!in || !out || !h_c) return fail(FHE_EINVAL, "null buffer");
+    Arena ar;
+    int rc = ws_reserve(c, (size_t)n_ct * level * 8 + 256, &ar);
+    if (rc) return rc;
+    u64* dres;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = upload_const_residues(c, h_c, n_ct, level, &ar, &dres, st))) return rc;
+    k_mul_const(c, (const u64*)in, (u64*)out, n_ct, 2, level, level, dres, level, st);
+    CUDA_LAST("mul_const launch");
+    return cuda_check(cudaStreamSynchronize(st), "mul_const");
+}
+
+int fhe_add_const(fhe_ctx* c, uint64_t* ct, const int64_t* h_c, uint32_t n_ct, uint32_t level, void* stream)
+{
+    CHECK_CTX(c);
+    CHECK_LEVEL(c, level, 1);
+    if (n_ct == 0) return FHE_OK;
+    if (!ct || !h_c) return fail(FHE_EINVAL, "null buffer");
+    Arena ar;
+    int rc = ws_reserve(c, (size_t)n_ct * level * 8 + 256, &ar);
+    if (rc) return rc;
+    u64* dres;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = upload_const_residues(c, h_c, n_ct, level, &ar, &dres, st))) return rc;
+    k_add_const(c, (u64*)ct, n_ct, level, dres, level, st);
+    CUDA_LAST("add_const launch");
+    return cuda_check(cudaStreamSynchronize(st), "add_const");
+}
+
+}  // extern "C"

@@ -1,0 +1,150 @@
+// ctx.h -- internal context of libfhe (not part of the C ABI).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "fhe_device.cuh"
+
+struct fhe_ctx {
+    uint32_t N = 0, logN = 0, L_top = 0, log_scale = 0;
+    std::vector<u64> primes;       // q_0 .. q_{L_top-1}, P (index L_top)
+    std::vector<PrimeC> pc;        // host copy of the per-prime constants
+    double delta = 0.0;
+    int device = 0;
+
+    // resident tables
+    PrimeC* d_pc = nullptr;
+    ulonglong2* d_tw_fwd = nullptr;
+    ulonglong2* d_tw_inv = nullptr;
+    u64* d_cdt = nullptr;          // 38 Gaussian thresholds
+    double4* d_enc_tw = nullptr;   // [N/4] zeta^{-4k} as (re.hi, re.lo, im.hi, im.lo)
+    double4* d_enc_twist = nullptr;// [N/2] zeta^{-k}
+    uint32_t* d_slot_of = nullptr; // [N/2] FFT position l -> slot j
+
+    // keys (NTT form)
+    bool has_keys = false;
+    uint64_t seed = 0;
+    u64* d_s = nullptr;            // [L_top + 1][N]
+    u64* d_pk = nullptr;           // [2][L_top][N]
+    u64* d_ksk = nullptr;          // [L_top][2][L_top + 1][N]
+    size_t key_bytes = 0;
+
+    // call workspace (grows on demand)
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+
+    NttTables tabs() const
+    {
+        NttTables t;
+        t.tw_fwd = d_tw_fwd;
+        t.tw_inv = d_tw_inv;
+        t.pc = d_pc;
+        t.logN = (int)logN;
+        return t;
+    }
+};
+
+struct fhe_graph_node {
+    uint32_t kind = 0;
+    uint32_t n_out = 0;
+    std::vector<uint32_t> row_ptr, col_idx;
+    std::vector<double> weight, bias;
+    double coeffs[4] = {0, 0, 0, 0};
+};
+
+// device constants of one node at its planned level (built on first use)
+struct fhe_node_const {
+    uint32_t L = 0;            // input level the constants were made for
+    double s_in = 0.0;         // input nominal scale they were made for
+    void* buf = nullptr;       // one device allocation holding the arrays below
+    uint32_t* row_ptr = nullptr;
+    uint32_t* col = nullptr;
+    u64* W = nullptr;          // LINEAR: [nnz][L] weight residues
+    u64* bias = nullptr;       // LINEAR: [n_out][L-1] bias residues
+    u64* c3 = nullptr;         // POLY: constant residues (shared by all ciphertexts)
+    u64* c2 = nullptr;
+    u64* c1 = nullptr;
+    u64* c0 = nullptr;
+};
+
+struct fhe_graph {
+    std::vector<fhe_graph_node> nodes;
+    std::vector<uint32_t> esrc, edst;
+    const fhe_ctx* cache_ctx = nullptr;
+    std::vector<fhe_node_const> cache;
+};
+
+namespace fhe {
+
+// error reporting (thread-local message)
+int fail(int code, const std::string& msg);
+int cuda_check(cudaError_t e, const char* what);
+
+// ---- workspace arena -----------------------------------------------------
+struct Arena {
+    char* base = nullptr;
+    size_t cap = 0, used = 0;
+    void* take(size_t bytes)
+    {
+        size_t a = (used + 255) & ~(size_t)255;
+        if (a + bytes > cap) return nullptr;
+        used = a + bytes;
+        return base + a;
+    }
+};
+int ws_reserve(fhe_ctx* c, size_t bytes, Arena* a);
+inline size_t arena_need(std::initializer_list<size_t> parts)
+{
+    size_t s = 0;
+    for (size_t p : parts) s += ((p + 255) & ~(size_t)255);
+    return s;
+}
+
+// ---- per-level constants (host-computed, passed by value) ------------------
+struct DivC {           // division by one prime p into primes q_0..q_{n-1}
+    u64 p, p_half;
+    u64 inv[32], invs[32];    // p^{-1} mod q_i and its Shoup quotient
+    u64 pmod[32];             // p mod q_i
+};
+DivC make_divc(const fhe_ctx* c, uint32_t p_index, uint32_t n_targets);
+
+// ---- kernels (kernels.cu); all enqueue on `st` -------------------------
+void k_ntt_rows(const fhe_ctx* c, u64* d, uint32_t n_poly, uint32_t rows, const uint8_t* row_prime,
+                bool forward, cudaStream_t st);
+void k_ct_to_coeff(const fhe_ctx* c, const u64* in, u64* out, uint32_t n_ct, uint32_t comps, uint32_t L,
+                   bool to_coeff, cudaStream_t st);
+void k_add(const fhe_ctx* c, const u64* a, const u64* b, u64* out, uint32_t n_ct, uint32_t comps, uint32_t L,
+           cudaStream_t st);
+void k_tensor(const fhe_ctx* c, const u64* a, const u64* b, u64* out3, uint32_t n_ct, uint32_t L, cudaStream_t st);
+// scratch: relin_scratch_bytes(n_ct, L)
+size_t relin_scratch_bytes(const fhe_ctx* c, uint32_t n_ct, uint32_t L);
+void k_relin(const fhe_ctx* c, const u64* d3, u64* out2, uint32_t n_ct, uint32_t L, void* scratch, cudaStream_t st);
+// scratch: rescale_scratch_bytes; addc: optional constants (device residues,
+// addc[ct * addc_stride + i]) added to comp 0 of the result
+size_t rescale_scratch_bytes(const fhe_ctx* c, uint32_t n_ct, uint32_t comps);
+void k_rescale(const fhe_ctx* c, const u64* in, u64* out, uint32_t n_ct, uint32_t comps, uint32_t L,
+               const u64* addc, uint32_t addc_stride, void* scratch, cudaStream_t st);
+// constants C (device residues cres[ct * cstride + r]) multiply every component;
+// reads residues r < L_out of an input stored with L_in residues
+void k_mul_const(const fhe_ctx* c, const u64* in, u64* out, uint32_t n_ct, uint32_t comps, uint32_t L_in,
+                 uint32_t L_out, const u64* cres, uint32_t cstride, cudaStream_t st);
+void k_add_const(const fhe_ctx* c, u64* ct, uint32_t n_ct, uint32_t L, const u64* cres, uint32_t cstride,
+                 cudaStream_t st);
+// gather-MAC: Y[o][k][r] = sum_e W[e][r] X[col[e]][k][r] over CSR row o (all at level L)
+void k_linear_mac(const fhe_ctx* c, const u64* X, uint32_t n_in, const uint32_t* row_ptr, const uint32_t* col,
+                  const u64* Wres, uint32_t n_out, uint32_t L, u64* Y, cudaStream_t st);
+
+void k_keygen(fhe_ctx* c, cudaStream_t st);
+void k_encrypt(const fhe_ctx* c, const u64* pt, uint32_t n_ct, uint64_t first_id, u64* ct, cudaStream_t st);
+void k_decrypt(const fhe_ctx* c, const u64* ct, uint32_t n_ct, uint32_t L, i64* m, cudaStream_t st);
+size_t encode_scratch_bytes(const fhe_ctx* c, uint32_t n_ct);
+void k_encode(const fhe_ctx* c, const double* slots, uint32_t n_ct, uint32_t L, double scale, u64* pt,
+              void* scratch, cudaStream_t st);
+void k_decode(const fhe_ctx* c, const i64* m, uint32_t n_ct, double scale, double* slots, cudaStream_t st);
+
+uint64_t stream_key(uint64_t seed, uint64_t domain, uint64_t object);
+
+}  // namespace fhe

@@ -1,0 +1,593 @@
+// graph.cu -- graph objects and encrypted graph evaluation.
+//
+// Traversal follows Alg. firing / signal_carrier of arXiv 2110.13638 (Sec. 3):
+// each input node is stimulated in turn; a node fires once every in-edge
+// carries a signal (its inputs stacked in edge order, or summed for ADD);
+// its output is set on every out-edge, then each successor is visited.
+// Receptors (apply_signal) are the block schedules below; each is a fixed
+// sequence of batched kernel launches on the caller's stream:
+//   LINEAR  y_o = rescale(sum_e llround(w_e q_{L-1}) x_{col_e}) + llround(b_o s_y)
+//   SQUARE  rescale(relin(x (x) x))
+//   POLY    x2 = rescale(relin(x (x) x));  w = rescale(x * llround(a3 s3));
+//           T = relin(x2 (x) w) + x2 * llround(a2 s_2) + drop(x) * llround(a1 q');
+//           y = rescale(T) + llround(a0 s_y)
+//           (s3 = q' q / s2, s_2 = s q' / s2, s2 = s s / q; q = q_{L-1}, q' = q_{L-2})
+// Nominal scales are FP64 values updated in exactly this order.
+// A dry run with the same allocation sequence sizes the workspace first.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "../../include/fhe.h"
+#include "ctx.h"
+#include "host_math.h"
+
+using namespace fhe;
+
+namespace {
+
+struct Sig {
+    u64* p = nullptr;
+    uint32_t n = 0, L = 0;
+    double scale = 0.0;
+    bool set = false;
+};
+
+static u64 mod_signed(int64_t v, u64 q)
+{
+    if (v >= 0) return (u64)v % q;
+    u64 r = (u64)(-(v + 1)) % q;
+    r = (r + 1) % q;
+    return r == 0 ? 0 : q - r;
+}
+
+static size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct Exec {
+    fhe_ctx* c;
+    fhe_graph* g;
+    cudaStream_t st;
+    bool dry;
+    Arena ar;
+    size_t need = 0;
+    int rc = FHE_OK;
+    std::vector<Sig> edge;
+    std::vector<char> fired;
+    std::vector<Sig> outputs;            // per node (OUTPUT nodes only)
+    std::vector<std::vector<uint32_t>> in_e, out_e;
+
+    void* take(size_t bytes)
+    {
+        if (dry) {
+            need += al(bytes);
+            return nullptr;
+        }
+        void* p = ar.take(bytes);
+        if (!p && rc == FHE_OK) rc = fail(FHE_ENOMEM, "graph workspace exhausted");
+        return p;
+    }
+    size_t cts(uint32_t n, uint32_t comps, uint32_t L) const { return (size_t)n * comps * L * c->N * 8; }
+    bool ok() const { return rc == FHE_OK; }
+    int err(int code, const char* m)
+    {
+        if (rc == FHE_OK) rc = fail(code, m);
+        return rc;
+    }
+
+    // ------------------------------------------------ constants cache
+    fhe_node_const* node_const(uint32_t i, uint32_t L, double s_in)
+    {
+        fhe_node_const& nc = g->cache[i];
+        if (nc.buf && nc.L == L && nc.s_in == s_in) return &nc;
+        if (nc.buf) {
+            cudaStreamSynchronize(st);
+            cudaFree(nc.buf);
+            nc = fhe_node_const();
+        }
+        const fhe_graph_node& nd = g->nodes[i];
+        std::vector<char> host;
+        auto put = [&](const void* src, size_t bytes) {
+            size_t off = host.size();
+            host.resize(off + al(bytes));
+            std::memcpy(host.data() + off, src, bytes);
+            return off;
+        };
+        size_t o_rp = 0, o_col = 0, o_W = 0, o_b = 0, o_c3 = 0, o_c2 = 0, o_c1 = 0, o_c0 = 0;
+        if (nd.kind == FHE_NODE_LINEAR) {
+            const double qd = (double)c->primes[L - 1];
+            const size_t nnz = nd.col_idx.size();
+            std::vector<u64> W(nnz * L);
+            for (size_t e = 0; e < nnz; ++e) {
+                const int64_t w = (int64_t)std::llround(nd.weight[e] * qd);
+                for (uint32_t r = 0; r < L; ++r) W[e * L + r] = mod_signed(w, c->primes[r]);
+            }
+            const double s_out = (s_in * qd) / qd;
+            std::vector<u64> B((size_t)nd.n_out * (L - 1));
+            for (uint32_t o = 0; o < nd.n_out; ++o) {
+                const int64_t b = (int64_t)std::llround(nd.bias[o] * s_out);
+                for (uint32_t r = 0; r + 1 < L; ++r) B[(size_t)o * (L - 1) + r] = mod_signed(b, c->primes[r]);
+            }
+            o_rp = put(nd.row_ptr.data(), nd.row_ptr.size() * 4);
+            o_col = put(nd.col_idx.data(), std::max<size_t>(1, nd.col_idx.size()) * 4);
+            o_W = put(W.data(), std::max<size_t>(1, W.size()) * 8);
+            o_b = put(B.data(), std::max<size_t>(1, B.size()) * 8);
+        } else if (nd.kind == FHE_NODE_POLY) {
+            PolyK k = poly_constants(nd, L, s_in);
+            std::vector<u64> r3(L), r2(L - 1), r1(L - 1), r0(L - 2);
+            for (uint32_t r = 0; r < L; ++r) r3[r] = mod_signed(k.C3, c->primes[r]);
+            for (uint32_t r = 0; r + 1 < L; ++r) {
+                r2[r] = mod_signed(k.C2, c->primes[r]);
+                r1[r] = mod_signed(k.C1, c->primes[r]);
+            }
+            for (uint32_t r = 0; r + 2 < L; ++r) r0[r] = mod_signed(k.C0, c->primes[r]);
+            o_c3 = put(r3.data(), r3.size() * 8);
+            o_c2 = put(r2.data(), r2.size() * 8);
+            o_c1 = put(r1.data(), r1.size() * 8);
+            o_c0 = put(r0.data(), std::max<size_t>(1, r0.size()) * 8);
+        } else {
+            return nullptr;
+        }
+        cudaError_t e = cudaMalloc(&nc.buf, host.size());
+        if (e == cudaSuccess) e = cudaMemcpy(nc.buf, host.data(), host.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            rc = cuda_check(e, "graph constants");
+            return nullptr;
+        }
+        char* b = (char*)nc.buf;
+        nc.L = L;
+        nc.s_in = s_in;
+        if (nd.kind == FHE_NODE_LINEAR) {
+            nc.row_ptr = (uint32_t*)(b + o_rp);
+            nc.col = (uint32_t*)(b + o_col);
+            nc.W = (u64*)(b + o_W);
+            nc.bias = (u64*)(b + o_b);
+        } else {
+            nc.c3 = (u64*)(b + o_c3);
+            nc.c2 = (u64*)(b + o_c2);
+            nc.c1 = (u64*)(b + o_c1);
+            nc.c0 = (u64*)(b + o_c0);
+        }
+        return &nc;
+    }
+
+    // ------------------------------------------------ scale schedule of POLY
+    struct PolyK {
+        int64_t C3, C2, C1, C0;
+        double s_x2, s_w, s_t1, s_t2, s_t3, s_y;
+    };
+    PolyK poly_constants(const fhe_graph_node& nd, uint32_t L, double s) const
+    {
+        PolyK k;
+        const double q = (double)c->primes[L - 1];
+        const double qp = (double)c->primes[L - 2];
+        const double s2 = (s * s) / q;
+        k.s_x2 = (s * s) / q;
+        const double s3 = (qp * q) / s2;
+        k.C3 = (int64_t)std::llround(nd.coeffs[3] * s3);
+        k.s_w = (s * s3) / q;
+        k.s_t1 = k.s_x2 * k.s_w;
+        const double sg2 = (s * qp) / s2;
+        k.C2 = (int64_t)std::llround(nd.coeffs[2] * sg2);
+        k.s_t2 = k.s_x2 * sg2;
+        k.C1 = (int64_t)std::llround(nd.coeffs[1] * qp);
+        k.s_t3 = s * qp;
+        k.s_y = k.s_t1 / qp;
+        k.C0 = (int64_t)std::llround(nd.coeffs[0] * k.s_y);
+        return k;
+    }
+
+    static bool scale_match(double a, double b) { return std::fabs(a - b) <= std::fabs(a) * std::ldexp(1.0, -40); }
+
+    // ------------------------------------------------ receptors
+    Sig linear(uint32_t i, const Sig& x)
+    {
+        const fhe_graph_node& nd = g->nodes[i];
+        Sig y;
+        const uint32_t L = x.L;
+        if (L < 2) { err(FHE_ELEVEL, "linear node needs two primes"); return y; }
+        if (nd.n_out == 0) { err(FHE_EINVAL, "linear node without outputs"); return y; }
+        for (uint32_t col : nd.col_idx)
+            if (col >= x.n) { err(FHE_EINVAL, "linear column index beyond the stacked input"); return y; }
+        const double qd = (double)c->primes[L - 1];
+        u64* Y = (u64*)take(cts(nd.n_out, 2, L));
+        u64* out = (u64*)take(cts(nd.n_out, 2, L - 1));
+        void* sc = take(rescale_scratch_bytes(c, nd.n_out, 2));
+        if (!dry && ok()) {
+            fhe_node_const* k = node_const(i, L, x.scale);
+            if (!k) return y;
+            k_linear_mac(c, x.p, x.n, k->row_ptr, k->col, k->W, nd.n_out, L, Y, st);
+            k_rescale(c, Y, out, nd.n_out, 2, L, k->bias, L - 1, sc, st);
+        }
+        y.p = out;
+        y.n = nd.n_out;
+        y.L = L - 1;
+        y.scale = (x.scale * qd) / qd;
+        y.set = true;
+        return y;
+    }
+
+    Sig square(const Sig& x)
+    {
+        Sig y;
+        const uint32_t L = x.L;
+        if (L < 2) { err(FHE_ELEVEL, "square needs two primes"); return y; }
+        u64* T3 = (u64*)take(cts(x.n, 3, L));
+        u64* R = (u64*)take(cts(x.n, 2, L));
+        void* rs = take(relin_scratch_bytes(c, x.n, L));
+        void* ss = take(rescale_scratch_bytes(c, x.n, 2));
+        u64* out = (u64*)take(cts(x.n, 2, L - 1));
+        if (!dry && ok()) {
+            k_tensor(c, x.p, x.p, T3, x.n, L, st);
+            k_relin(c, T3, R, x.n, L, rs, st);
+            k_rescale(c, R, out, x.n, 2, L, nullptr, 0, ss, st);
+        }
+        y.p = out;
+        y.n = x.n;
+        y.L = L - 1;
+        y.scale = (x.scale * x.scale) / (double)c->primes[L - 1];
+        y.set = true;
+        return y;
+    }
+
+    Sig poly(uint32_t i, const Sig& x)
+    {
+        Sig y;
+        const uint32_t L = x.L, n = x.n;
+        if (L < 3) { err(FHE_ELEVEL, "a degree-3 activation needs three primes"); return y; }
+        const PolyK k = poly_constants(g->nodes[i], L, x.scale);
+        if (!scale_match(k.s_t1, k.s_t2) || !scale_match(k.s_t1, k.s_t3)) {
+            err(FHE_ESCALE, "polynomial terms disagree in scale");
+            return y;
+        }
+        u64* T3 = (u64*)take(cts(n, 3, L));
+        u64* R = (u64*)take(cts(n, 2, L));
+        void* rs = take(relin_scratch_bytes(c, n, L));
+        void* ss = take(rescale_scratch_bytes(c, n, 2));
+        u64* x2 = (u64*)take(cts(n, 2, L - 1));
+        u64* xa = (u64*)take(cts(n, 2, L));
+        u64* w = (u64*)take(cts(n, 2, L - 1));
+        u64* T3b = (u64*)take(cts(n, 3, L - 1));
+        u64* t1 = (u64*)take(cts(n, 2, L - 1));
+        u64* t2 = (u64*)take(cts(n, 2, L - 1));
+        u64* t3 = (u64*)take(cts(n, 2, L - 1));
+        u64* out = (u64*)take(cts(n, 2, L - 2));
+        if (!dry && ok()) {
+            fhe_node_const* kc = node_const(i, L, x.scale);
+            if (!kc) return y;
+            k_tensor(c, x.p, x.p, T3, n, L, st);
+            k_relin(c, T3, R, n, L, rs, st);
+            k_rescale(c, R, x2, n, 2, L, nullptr, 0, ss, st);
+            k_mul_const(c, x.p, xa, n, 2, L, L, kc->c3, 0, st);
+            k_rescale(c, xa, w, n, 2, L, nullptr, 0, ss, st);
+            k_tensor(c, x2, w, T3b, n, L - 1, st);
+            k_relin(c, T3b, t1, n, L - 1, rs, st);
+            k_mul_const(c, x2, t2, n, 2, L - 1, L - 1, kc->c2, 0, st);
+            k_mul_const(c, x.p, t3, n, 2, L, L - 1, kc->c1, 0, st);
+            k_add(c, t1, t2, t1, n, 2, L - 1, st);
+            k_add(c, t1, t3, t1, n, 2, L - 1, st);
+            k_rescale(c, t1, out, n, 2, L - 1, kc->c0, 0, ss, st);
+        }
+        y.p = out;
+        y.n = n;
+        y.L = L - 2;
+        y.scale = k.s_y;
+        y.set = true;
+        return y;
+    }
+
+    // level-match a list of signals by mod-drop (copy of the first L residues)
+    Sig drop_to(const Sig& s, uint32_t L)
+    {
+        if (s.L == L) return s;
+        Sig d = s;
+        d.L = L;
+        d.p = (u64*)take(cts(s.n, 2, L));
+        if (!dry && ok()) {
+            const size_t w = (size_t)L * c->N * 8, sp = (size_t)s.L * c->N * 8;
+            cudaError_t e = cudaMemcpy2DAsync(d.p, w, s.p, sp, w, (size_t)s.n * 2, cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) rc = cuda_check(e, "mod-drop copy");
+        }
+        return d;
+    }
+
+    Sig stack(const std::vector<Sig>& in, bool sum)
+    {
+        Sig y;
+        uint32_t Lmin = in[0].L;
+        for (const Sig& s : in) Lmin = std::min(Lmin, s.L);
+        std::vector<Sig> m;
+        for (const Sig& s : in) m.push_back(drop_to(s, Lmin));
+        for (const Sig& s : m)
+            if (!scale_match(m[0].scale, s.scale)) { err(FHE_ESCALE, "stacked inputs disagree in scale"); return y; }
+        if (sum) {
+            for (const Sig& s : m)
+                if (s.n != m[0].n) { err(FHE_EINVAL, "add node inputs differ in length"); return y; }
+            u64* out = (u64*)take(cts(m[0].n, 2, Lmin));
+            if (!dry && ok()) {
+                k_add(c, m[0].p, m[1].p, out, m[0].n, 2, Lmin, st);
+                for (size_t k = 2; k < m.size(); ++k) k_add(c, out, m[k].p, out, m[0].n, 2, Lmin, st);
+            }
+            y.p = out;
+            y.n = m[0].n;
+        } else {
+            uint32_t n = 0;
+            for (const Sig& s : m) n += s.n;
+            u64* out = (u64*)take(cts(n, 2, Lmin));
+            if (!dry && ok()) {
+                size_t off = 0;
+                for (const Sig& s : m) {
+                    cudaError_t e = cudaMemcpyAsync(out + off, s.p, cts(s.n, 2, Lmin), cudaMemcpyDeviceToDevice, st);
+                    if (e != cudaSuccess) rc = cuda_check(e, "stack copy");
+                    off += cts(s.n, 2, Lmin) / 8;
+                }
+            }
+            y.p = out;
+            y.n = n;
+        }
+        y.L = Lmin;
+        y.scale = m[0].scale;
+        y.set = true;
+        return y;
+    }
+
+    // ------------------------------------------------ Alg. firing
+    bool inbound(uint32_t n, const Sig* bootstrap, Sig* s)
+    {
+        if (bootstrap) {
+            *s = *bootstrap;
+            return true;
+        }
+        std::vector<Sig> in;
+        for (uint32_t e : in_e[n]) {
+            if (!edge[e].set) return false;
+            in.push_back(edge[e]);
+        }
+        if (in.empty()) return false;
+        if (in.size() == 1) {
+            *s = in[0];
+            return true;
+        }
+        *s = stack(in, g->nodes[n].kind == FHE_NODE_ADD);
+        return s->set;
+    }
+
+    Sig apply(uint32_t n, const Sig& s)
+    {
+        switch (g->nodes[n].kind) {
+        case FHE_NODE_INPUT:
+        case FHE_NODE_OUTPUT:
+        case FHE_NODE_ADD: return s;
+        case FHE_NODE_LINEAR: return linear(n, s);
+        case FHE_NODE_SQUARE: return square(s);
+        case FHE_NODE_POLY: return poly(n, s);
+        default: err(FHE_EINVAL, "unknown node kind"); return Sig();
+        }
+    }
+
+    void carrier(uint32_t n, const Sig* bootstrap, int depth)
+    {
+        if (!ok() || fired[n]) return;
+        if (depth > 10000) { err(FHE_EINVAL, "graph too deep"); return; }
+        Sig s;
+        if (!inbound(n, bootstrap, &s)) return;
+        s = apply(n, s);
+        if (!ok() || !s.set) return;
+        fired[n] = 1;
+        if (g->nodes[n].kind == FHE_NODE_OUTPUT) outputs[n] = s;
+        for (uint32_t e : out_e[n]) edge[e] = s;
+        std::vector<uint32_t> seen;
+        for (uint32_t e : out_e[n]) {
+            const uint32_t b = g->edst[e];
+            if (std::find(seen.begin(), seen.end(), b) != seen.end()) continue;
+            seen.push_back(b);
+            carrier(b, nullptr, depth + 1);
+        }
+    }
+
+    void run(const uint64_t* const* d_in, uint32_t n_inputs)
+    {
+        const uint32_t nn = (uint32_t)g->nodes.size();
+        edge.assign(g->esrc.size(), Sig());
+        fired.assign(nn, 0);
+        outputs.assign(nn, Sig());
+        in_e.assign(nn, {});
+        out_e.assign(nn, {});
+        for (uint32_t e = 0; e < g->esrc.size(); ++e) {
+            out_e[g->esrc[e]].push_back(e);
+            in_e[g->edst[e]].push_back(e);
+        }
+        uint32_t k = 0;
+        for (uint32_t n = 0; n < nn && ok(); ++n) {
+            if (g->nodes[n].kind != FHE_NODE_INPUT) continue;
+            if (k >= n_inputs) { err(FHE_EINVAL, "fewer input buffers than input nodes"); return; }
+            Sig s;
+            s.p = d_in ? (u64*)d_in[k] : nullptr;
+            s.n = g->nodes[n].n_out;
+            s.L = c->L_top;
+            s.scale = c->delta;
+            s.set = true;
+            ++k;
+            carrier(n, &s, 0);
+        }
+        if (ok() && k != n_inputs) err(FHE_EINVAL, "more input buffers than input nodes");
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+int fhe_graph_create(const fhe_graph_desc* d, fhe_graph** out)
+{
+    if (!d || !out || (!d->nodes && d->n_nodes)) return fail(FHE_EINVAL, "null graph description");
+    *out = nullptr;
+    fhe_graph* g = new fhe_graph();
+    for (uint32_t i = 0; i < d->n_nodes; ++i) {
+        const fhe_node_desc& s = d->nodes[i];
+        fhe_graph_node n;
+        n.kind = s.kind;
+        n.n_out = s.n_out;
+        if (s.kind > FHE_NODE_OUTPUT) {
+            delete g;
+            return fail(FHE_EINVAL, "unknown node kind");
+        }
+        if (s.kind == FHE_NODE_LINEAR) {
+            if (!s.row_ptr || (s.n_out && (!s.col_idx || !s.weight))) {
+                delete g;
+                return fail(FHE_EINVAL, "linear node without CSR arrays");
+            }
+            n.row_ptr.assign(s.row_ptr, s.row_ptr + s.n_out + 1);
+            const uint32_t nnz = n.row_ptr.back();
+            if (n.row_ptr[0] != 0) {
+                delete g;
+                return fail(FHE_EINVAL, "row_ptr[0] must be 0");
+            }
+            for (uint32_t o = 0; o < s.n_out; ++o)
+                if (n.row_ptr[o + 1] < n.row_ptr[o]) {
+                    delete g;
+                    return fail(FHE_EINVAL, "row_ptr must be non-decreasing");
+                }
+            n.col_idx.assign(s.col_idx, s.col_idx + nnz);
+            n.weight.assign(s.weight, s.weight + nnz);
+            if (s.bias) n.bias.assign(s.bias, s.bias + s.n_out);
+            else n.bias.assign(s.n_out, 0.0);
+            for (double w : n.weight)
+                if (!std::isfinite(w)) {
+                    delete g;
+                    return fail(FHE_EINVAL, "non-finite weight");
+                }
+        }
+        for (int k = 0; k < 4; ++k) n.coeffs[k] = s.coeffs[k];
+        g->nodes.push_back(n);
+    }
+    for (uint32_t e = 0; e < d->n_edges; ++e) {
+        if (d->edge_src[e] >= d->n_nodes || d->edge_dst[e] >= d->n_nodes) {
+            delete g;
+            return fail(FHE_EINVAL, "edge endpoint out of range");
+        }
+        g->esrc.push_back(d->edge_src[e]);
+        g->edst.push_back(d->edge_dst[e]);
+    }
+    g->cache.resize(g->nodes.size());
+    *out = g;
+    return FHE_OK;
+}
+
+int fhe_graph_destroy(fhe_graph* g)
+{
+    if (!g) return FHE_OK;
+    bool any = false;
+    for (auto& nc : g->cache) any |= (nc.buf != nullptr);
+    if (any) cudaDeviceSynchronize();
+    for (auto& nc : g->cache) cudaFree(nc.buf);
+    delete g;
+    return FHE_OK;
+}
+
+static int dry_run(fhe_ctx* c, fhe_graph* g, uint32_t n_inputs, Exec* X)
+{
+    X->c = c;
+    X->g = g;
+    X->st = nullptr;
+    X->dry = true;
+    X->run(nullptr, n_inputs);
+    return X->rc;
+}
+
+static int count_inputs(const fhe_graph* g)
+{
+    int k = 0;
+    for (const auto& n : g->nodes) k += (n.kind == FHE_NODE_INPUT);
+    return k;
+}
+
+int fhe_graph_outputs(fhe_ctx* c, const fhe_graph* gc, uint32_t* n_out_cts, uint32_t* out_level)
+{
+    if (!c || !gc) return fail(FHE_EINVAL, "null argument");
+    fhe_graph* g = const_cast<fhe_graph*>(gc);
+    Exec X;
+    int rc = dry_run(c, g, (uint32_t)count_inputs(g), &X);
+    if (rc) return rc;
+    uint32_t n = 0, L = 0;
+    bool first = true;
+    for (size_t i = 0; i < g->nodes.size(); ++i) {
+        if (g->nodes[i].kind != FHE_NODE_OUTPUT) continue;
+        if (!X.outputs[i].set) return fail(FHE_EINVAL, "an output node never fires");
+        n += X.outputs[i].n;
+        L = first ? X.outputs[i].L : std::min(L, X.outputs[i].L);
+        first = false;
+    }
+    if (n_out_cts) *n_out_cts = n;
+    if (out_level) *out_level = L;
+    return FHE_OK;
+}
+
+int fhe_eval_graph(fhe_ctx* c, const fhe_graph* gc, const uint64_t* const* d_in, uint32_t n_inputs, uint64_t* d_out,
+                   fhe_ct_meta* out_meta, uint32_t out_cap, void* stream)
+{
+    if (!c || !gc || !d_in || !d_out) return fail(FHE_EINVAL, "null argument");
+    if (!c->has_keys) return fail(FHE_ENOKEY, "fhe_keygen has not run");
+    fhe_graph* g = const_cast<fhe_graph*>(gc);
+    if (g->cache_ctx != c) {
+        bool any = false;
+        for (auto& nc : g->cache) any |= (nc.buf != nullptr);
+        if (any) cudaDeviceSynchronize();
+        for (auto& nc : g->cache) {
+            cudaFree(nc.buf);
+            nc = fhe_node_const();
+        }
+        g->cache_ctx = c;
+    }
+    for (uint32_t i = 0; i < n_inputs; ++i)
+        if (!d_in[i]) return fail(FHE_EINVAL, "null input buffer");
+    Exec D;
+    int rc = dry_run(c, g, n_inputs, &D);
+    if (rc) return rc;
+    uint32_t n_out = 0, Lout = 0;
+    bool first = true;
+    for (size_t i = 0; i < g->nodes.size(); ++i) {
+        if (g->nodes[i].kind != FHE_NODE_OUTPUT) continue;
+        if (!D.outputs[i].set) return fail(FHE_EINVAL, "an output node never fires");
+        n_out += D.outputs[i].n;
+        Lout = first ? D.outputs[i].L : std::min(Lout, D.outputs[i].L);
+        first = false;
+    }
+    if (n_out > out_cap) return fail(FHE_EINVAL, "out_cap smaller than the number of output ciphertexts");
+
+    Exec X;
+    X.c = c;
+    X.g = g;
+    X.st = (cudaStream_t)stream;
+    X.dry = false;
+    rc = ws_reserve(c, D.need, &X.ar);
+    if (rc) return rc;
+    X.run(d_in, n_inputs);
+    if (X.rc) return X.rc;
+    size_t off = 0;
+    const size_t N = c->N;
+    for (size_t i = 0; i < g->nodes.size(); ++i) {
+        if (g->nodes[i].kind != FHE_NODE_OUTPUT) continue;
+        const Sig& s = X.outputs[i];
+        const size_t w = (size_t)Lout * N * 8, sp = (size_t)s.L * N * 8;
+        cudaError_t e = cudaMemcpy2DAsync((char*)d_out + off, w, s.p, sp, w, (size_t)s.n * 2, cudaMemcpyDeviceToDevice,
+                                          X.st);
+        if (e != cudaSuccess) return cuda_check(e, "output copy");
+        off += (size_t)s.n * 2 * w;
+        if (out_meta) {
+            size_t base = 0;
+            for (size_t j = 0; j < i; ++j)
+                if (g->nodes[j].kind == FHE_NODE_OUTPUT) base += X.outputs[j].n;
+            for (uint32_t k = 0; k < s.n; ++k) {
+                out_meta[base + k].level = Lout;
+                out_meta[base + k].scale = s.scale;
+            }
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(e, "graph launch");
+    return FHE_OK;
+}
+
+}  // extern "C"

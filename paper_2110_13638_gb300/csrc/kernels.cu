@@ -1,0 +1,873 @@
+// kernels.cu -- sm_103a kernels of the RNS-CKKS path.
+//
+// Every transform-bearing step is one launch of k_ntt_op (fhe_device.cuh)
+// with a step-specific Op whose load() is the fused prologue (sampling,
+// base conversion, pointwise products) and whose store() is the fused
+// epilogue (key products, ModDown / rescale combination, encryption sums).
+// The remaining kernels are element-wise (coalesced, grid-stride), the
+// gather multiply-accumulate of dense / convolution layers, and the
+// double-double / FP64 canonical-embedding FFTs of encode / decode.
+#include <algorithm>
+#include <cstdio>
+
+#include "ctx.h"
+#include "host_math.h"
+
+namespace fhe {
+
+static constexpr int kLogR = 4;      // radix-16 register passes
+static constexpr int kMaxT = 512;    // threads per transform block (128 registers each)
+static constexpr u64 kGamma = 0x9E3779B97F4A7C15ull;
+
+// ---------------------------------------------------------------- PRNG
+// SplitMix64 (Steele, Lea, Flood 2014): output i of the generator started in
+// state s is mix(s + (i + 1) * gamma).  Draw index = coef | residue << 16 | retry << 24.
+__host__ __device__ __forceinline__ u64 mix64(u64 z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__host__ __device__ __forceinline__ u64 sm_out(u64 s, u64 i) { return mix64(s + (i + 1) * kGamma); }
+
+uint64_t stream_key(uint64_t seed, uint64_t domain, uint64_t object)
+{
+    return sm_out(sm_out(seed, domain), object);
+}
+
+__device__ __forceinline__ i64 draw_ternary(u64 s0, int j)
+{
+    const u64 bound = 0xFFFFFFFFFFFFFFFFull;     // 3 * floor(2^64 / 3) = 2^64 - 1
+    for (u64 t = 0;; ++t) {
+        u64 u = sm_out(s0, (u64)j | (t << 24));
+        if (u < bound) return (i64)(u % 3ull) - 1;
+    }
+}
+
+__device__ __forceinline__ i64 draw_gauss(u64 s0, int j, const u64* __restrict__ cdt)
+{
+    u64 u = sm_out(s0, (u64)j);
+    i64 e = -19;
+#pragma unroll
+    for (int i = 0; i < 38; ++i) e += (u >= __ldg(&cdt[i])) ? 1 : 0;
+    return e;
+}
+
+__device__ __forceinline__ u64 draw_uniform(u64 s0, int j, int r, const PrimeC& P)
+{
+    for (u64 t = 0;; ++t) {
+        u64 u = sm_out(s0, (u64)j | ((u64)r << 16) | (t << 24));
+        if (u < P.ub) return reduce64(u, P);
+    }
+}
+
+// ---------------------------------------------------------------- launch
+template <bool INV, class Op>
+static void launch_ntt(const fhe_ctx* c, const Op& op, cudaStream_t st)
+{
+    const int count = op.count();
+    if (count <= 0) return;
+    const int N = (int)c->N;
+    int thr = N / 16;
+    thr = thr < 32 ? 32 : (thr > kMaxT ? kMaxT : thr);
+    const size_t smem = (size_t)ntt_smem_words(N) * sizeof(u64);
+    auto fn = k_ntt_op<INV, kLogR, kMaxT, Op>;
+    static size_t configured = 0;        // per instantiation
+    if (configured < smem) {
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        configured = smem;
+    }
+    fn<<<count, thr, smem, st>>>(op, c->tabs());
+}
+
+// ---------------------------------------------------------------- ops
+// in-place / out-of-place transform of rows of polynomials
+struct OpRows {
+    const u64* src;
+    u64* dst;
+    int n, rows, N;
+    uint8_t pmap[64];
+    __device__ int count() const { return n; }
+    __device__ int nsub(int) const { return 1; }
+    __device__ int prime(int p, int) const { return pmap[p % rows]; }
+    __device__ bool direct(int, int) const { return false; }
+    __device__ u64 load(int p, int, int j, const PrimeC&) const { return src[(size_t)p * N + j]; }
+    __device__ void store(int p, int, int j, u64 v, const PrimeC&) const { dst[(size_t)p * N + j] = v; }
+};
+
+void k_ntt_rows(const fhe_ctx* c, u64* d, uint32_t n_poly, uint32_t rows, const uint8_t* row_prime, bool forward,
+                cudaStream_t st)
+{
+    OpRows op;
+    op.src = d;
+    op.dst = d;
+    op.n = (int)(n_poly * rows);
+    op.rows = (int)rows;
+    op.N = (int)c->N;
+    for (uint32_t r = 0; r < rows && r < 64; ++r) op.pmap[r] = row_prime[r];
+    if (forward) launch_ntt<false>(c, op, st);
+    else launch_ntt<true>(c, op, st);
+}
+
+void k_ct_to_coeff(const fhe_ctx* c, const u64* in, u64* out, uint32_t n_ct, uint32_t comps, uint32_t L, bool to_coeff,
+                   cudaStream_t st)
+{
+    OpRows op;
+    op.src = in;
+    op.dst = out;
+    op.n = (int)(n_ct * comps * L);
+    op.rows = (int)L;
+    op.N = (int)c->N;
+    for (uint32_t r = 0; r < L; ++r) op.pmap[r] = (uint8_t)r;
+    if (to_coeff) launch_ntt<true>(c, op, st);
+    else launch_ntt<false>(c, op, st);
+}
+
+// ---------------------------------------------------------------- element-wise
+// per-prime constants for element-wise kernels come from the resident table
+__global__ void k_add_kernel(const u64* __restrict__ a, const u64* __restrict__ b, u64* __restrict__ out,
+                             size_t total, int L, int logN, const PrimeC* __restrict__ pc)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)((i >> logN) % L);
+        const u64 q = pc[r].q;
+        out[i] = add_mod(a[i], b[i], q);
+    }
+}
+
+static int ew_grid(size_t total)
+{
+    size_t g = (total + 255) / 256;
+    return (int)std::min<size_t>(g, 152 * 32);
+}
+
+void k_add(const fhe_ctx* c, const u64* a, const u64* b, u64* out, uint32_t n_ct, uint32_t comps, uint32_t L,
+           cudaStream_t st)
+{
+    size_t total = (size_t)n_ct * comps * L * c->N;
+    if (!total) return;
+    k_add_kernel<<<ew_grid(total), 256, 0, st>>>(a, b, out, total, (int)L, (int)c->logN, c->d_pc);
+}
+
+__global__ void k_tensor_kernel(const u64* __restrict__ a, const u64* __restrict__ b, u64* __restrict__ out,
+                                size_t per_comp, int n_ct, int L, int logN, const PrimeC* __restrict__ pc)
+{
+    // per_comp = L * N; thread covers (ct, r, j)
+    const size_t total = (size_t)n_ct * per_comp;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t ct = i / per_comp, w = i % per_comp;
+        const int r = (int)(w >> logN);
+        const PrimeC P = pc[r];
+        const u64* A = a + ct * 2 * per_comp;
+        const u64* B = b + ct * 2 * per_comp;
+        const u64 a0 = A[w], a1 = A[per_comp + w], b0 = B[w], b1 = B[per_comp + w];
+        u64* O = out + ct * 3 * per_comp;
+        O[w] = mul_mod(a0, b0, P);
+        O[per_comp + w] = add_mod(mul_mod(a0, b1, P), mul_mod(a1, b0, P), P.q);
+        O[2 * per_comp + w] = mul_mod(a1, b1, P);
+    }
+}
+
+void k_tensor(const fhe_ctx* c, const u64* a, const u64* b, u64* out3, uint32_t n_ct, uint32_t L, cudaStream_t st)
+{
+    const size_t per_comp = (size_t)L * c->N;
+    const size_t total = (size_t)n_ct * per_comp;
+    if (!total) return;
+    k_tensor_kernel<<<ew_grid(total), 256, 0, st>>>(a, b, out3, per_comp, (int)n_ct, (int)L, (int)c->logN, c->d_pc);
+}
+
+// cres[ct * cstride + r]: residues of one integer constant per ciphertext
+// (cstride = 0: one constant for all).  Reads residues r < L_out of an input
+// stored with L_in residues (L_out < L_in is a mod-drop on the fly).
+__global__ void k_mul_const_kernel(const u64* __restrict__ in, u64* __restrict__ out, size_t total, int comps, int L_in,
+                                   int L_out, int logN, const u64* __restrict__ cres, int cstride,
+                                   const PrimeC* __restrict__ pc)
+{
+    const size_t Nm = ((size_t)1 << logN) - 1;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = i >> logN;            // (ct, comp, r) with r < L_out
+        const int r = (int)(row % L_out);
+        const size_t poly = row / L_out;
+        const size_t ct = poly / comps;
+        const PrimeC P = pc[r];
+        const u64 x = in[((poly * L_in + r) << logN) + (i & Nm)];
+        out[i] = mul_mod(x, cres[ct * cstride + r], P);
+    }
+}
+
+void k_mul_const(const fhe_ctx* c, const u64* in, u64* out, uint32_t n_ct, uint32_t comps, uint32_t L_in, uint32_t L_out,
+                 const u64* cres, uint32_t cstride, cudaStream_t st)
+{
+    size_t total = (size_t)n_ct * comps * L_out * c->N;
+    if (!total) return;
+    k_mul_const_kernel<<<ew_grid(total), 256, 0, st>>>(in, out, total, (int)comps, (int)L_in, (int)L_out, (int)c->logN,
+                                                       cres, (int)cstride, c->d_pc);
+}
+
+// constant polynomial (C, 0, ..., 0) is C at every NTT point: add to comp 0
+__global__ void k_add_const_kernel(u64* __restrict__ ct, size_t total, int L, int logN, const u64* __restrict__ cres,
+                                   int cstride, const PrimeC* __restrict__ pc)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = i >> logN;                // (ct, r) over comp 0 only
+        const size_t n = row / L;
+        const int r = (int)(row % L);
+        const size_t idx = (n * 2 * L + r) * ((size_t)1 << logN) + (i & (((size_t)1 << logN) - 1));
+        ct[idx] = add_mod(ct[idx], cres[n * cstride + r], pc[r].q);
+    }
+}
+
+void k_add_const(const fhe_ctx* c, u64* ct, uint32_t n_ct, uint32_t L, const u64* cres, uint32_t cstride, cudaStream_t st)
+{
+    size_t total = (size_t)n_ct * L * c->N;
+    if (!total) return;
+    k_add_const_kernel<<<ew_grid(total), 256, 0, st>>>(ct, total, (int)L, (int)c->logN, cres, (int)cstride, c->d_pc);
+}
+
+// ---------------------------------------------------------------- rescale
+DivC make_divc(const fhe_ctx* c, uint32_t p_index, uint32_t n_targets)
+{
+    DivC d;
+    const u64 p = c->primes[p_index];
+    d.p = p;
+    d.p_half = (p - 1) / 2;
+    for (uint32_t i = 0; i < n_targets && i < 32; ++i) {
+        const u64 q = c->primes[i];
+        d.inv[i] = hinv(p % q, q);
+        d.invs[i] = shoup(d.inv[i], q);
+        d.pmod[i] = p % q;
+    }
+    return d;
+}
+
+// INTT of one residue row per (ct, comp) into scratch V (coefficient form)
+struct OpTakeRowInv {
+    const u64* in;
+    u64* V;
+    int n, L, row, N, pidx;
+    __device__ int count() const { return n; }
+    __device__ int nsub(int) const { return 1; }
+    __device__ int prime(int, int) const { return pidx; }
+    __device__ bool direct(int, int) const { return false; }
+    __device__ u64 load(int p, int, int j, const PrimeC&) const { return in[((size_t)p * L + row) * N + j]; }
+    __device__ void store(int p, int, int j, u64 v, const PrimeC&) const { V[(size_t)p * N + j] = v; }
+};
+
+// out_i = (in_i - NTT([v]_{q_i})) * p^{-1} (+ addc on comp 0)
+struct OpDivFwd {
+    const u64* in;      // [n_poly][L_in][N]
+    const u64* V;       // [n_poly][N]  coefficient form mod p
+    u64* out;           // [n_poly][L_out][N]
+    const u64* addc;    // optional: residues of a constant added to comp 0, [n_ct][addc_stride]
+    int n_poly, comps, L_in, L_out, N, addc_stride;
+    DivC d;
+    __device__ int count() const { return n_poly * L_out; }
+    __device__ int nsub(int) const { return 1; }
+    __device__ int prime(int p, int) const { return p % L_out; }
+    __device__ bool direct(int, int) const { return false; }
+    __device__ u64 load(int p, int, int j, const PrimeC& Q) const
+    {
+        const int poly = p / L_out, i = p % L_out;
+        return centred_to(V[(size_t)poly * N + j], d.p, d.p_half, d.pmod[i], Q);
+    }
+    __device__ void store(int p, int, int j, u64 v, const PrimeC& Q) const
+    {
+        const int poly = p / L_out, i = p % L_out;
+        const u64 x = in[((size_t)poly * L_in + i) * N + j];
+        u64 r = mul_shoup(sub_mod(x, v, Q.q), d.inv[i], d.invs[i], Q.q);
+        if (addc && (poly % comps) == 0) r = add_mod(r, addc[(size_t)(poly / comps) * addc_stride + i], Q.q);
+        out[((size_t)poly * L_out + i) * N + j] = r;
+    }
+};
+
+size_t rescale_scratch_bytes(const fhe_ctx* c, uint32_t n_ct, uint32_t comps)
+{
+    return (size_t)n_ct * comps * c->N * sizeof(u64);
+}
+
+void k_rescale(const fhe_ctx* c, const u64* in, u64* out, uint32_t n_ct, uint32_t comps, uint32_t L, const u64* addc,
+               uint32_t addc_stride, void* scratch, cudaStream_t st)
+{
+    if (n_ct == 0) return;
+    u64* V = (u64*)scratch;
+    OpTakeRowInv a;
+    a.in = in;
+    a.V = V;
+    a.n = (int)(n_ct * comps);
+    a.L = (int)L;
+    a.row = (int)L - 1;
+    a.N = (int)c->N;
+    a.pidx = (int)L - 1;
+    launch_ntt<true>(c, a, st);
+    OpDivFwd b;
+    b.in = in;
+    b.V = V;
+    b.out = out;
+    b.addc = addc;
+    b.addc_stride = (int)addc_stride;
+    b.n_poly = (int)(n_ct * comps);
+    b.comps = (int)comps;
+    b.L_in = (int)L;
+    b.L_out = (int)L - 1;
+    b.N = (int)c->N;
+    b.d = make_divc(c, L - 1, L - 1);
+    launch_ntt<false>(c, b, st);
+}
+
+// ---------------------------------------------------------------- relinearise
+// step 1: digits D_j = INTT(d2_j) in [0, q_j)
+struct OpDigitsInv {
+    const u64* d3;      // [n][3][L][N]
+    u64* D;             // [n][L][N]
+    int n, L, N;
+    __device__ int count() const { return n * L; }
+    __device__ int nsub(int) const { return 1; }
+    __device__ int prime(int p, int) const { return p % L; }
+    __device__ bool direct(int, int) const { return false; }
+    __device__ u64 load(int p, int, int j, const PrimeC&) const
+    {
+        const int ct = p / L, r = p % L;
+        return d3[(((size_t)ct * 3 + 2) * L + r) * N + j];
+    }
+    __device__ void store(int p, int, int j, u64 v, const PrimeC&) const { D[(size_t)p * N + j] = v; }
+};
+
+// step 2: per (ct, target t in 0..L, t = L meaning P): for every digit u,
+// NTT(D_u mod q_t) * ksk_u[k][t], accumulated over u into acc[ct][k][t]
+struct OpModUpMac {
+    const u64* d3;
+    const u64* D;
+    const u64* ksk;     // [L_top][2][L_top+1][N]
+    u64* acc;           // [n][2][L+1][N]
+    int n, L, N, Ltop;
+    __device__ int count() const { return n * (L + 1); }
+    __device__ int nsub(int) const { return L; }
+    __device__ int prime(int p, int) const
+    {
+        const int t = p % (L + 1);
+        return t == L ? Ltop : t;
+    }
+    __device__ bool direct(int p, int u) const { return (p % (L + 1)) == u; }
+    __device__ u64 load(int p, int u, int j, const PrimeC& Q) const
+    {
+        const int ct = p / (L + 1);
+        return reduce64(D[((size_t)ct * L + u) * N + j], Q);
+    }
+    __device__ void store(int p, int u, int j, u64 v, const PrimeC& Q) const
+    {
+        const int ct = p / (L + 1), t = p % (L + 1);
+        const int tk = t == L ? Ltop : t;
+        if (t == u) v = d3[(((size_t)ct * 3 + 2) * L + t) * N + j];    // NTT(d2_t) is d2_t
+        const u64* k0 = ksk + (((size_t)u * 2 + 0) * (Ltop + 1) + tk) * N;
+        const u64* k1 = ksk + (((size_t)u * 2 + 1) * (Ltop + 1) + tk) * N;
+        u64* a0 = acc + (((size_t)ct * 2 + 0) * (L + 1) + t) * N;
+        u64* a1 = acc + (((size_t)ct * 2 + 1) * (L + 1) + t) * N;
+        const u64 p0 = mul_mod(v, k0[j], Q), p1 = mul_mod(v, k1[j], Q);
+        if (u == 0) {
+            a0[j] = p0;
+            a1[j] = p1;
+        } else {
+            a0[j] = add_mod(a0[j], p0, Q.q);
+            a1[j] = add_mod(a1[j], p1, Q.q);
+        }
+    }
+};
+
+// step 3: INTT of the P residue of both accumulators
+struct OpAccPInv {
+    const u64* acc;
+    u64* Vp;            // [n][2][N]
+    int n, L, N, Ltop;
+    __device__ int count() const { return n * 2; }
+    __device__ int nsub(int) const { return 1; }
+    __device__ int prime(int, int) const { return Ltop; }
+    __device__ bool direct(int, int) const { return false; }
+    __device__ u64 load(int p, int, int j, const PrimeC&) const { return acc[((size_t)p * (L + 1) + L) * N + j]; }
+    __device__ void store(int p, int, int j, u64 v, const PrimeC&) const { Vp[(size_t)p * N + j] = v; }
+};
+
+// step 4: ModDown + add: out_k,t = d_k,t + (acc_k,t - NTT([v]_{q_t})) * P^{-1}
+struct OpModDown {
+    const u64* d3;
+    const u64* acc;
+    const u64* Vp;
+    u64* out;           // [n][2][L][N]
+    int n, L, N;
+    DivC d;
+    __device__ int count() const { return n * 2 * L; }
+    __device__ int nsub(int) const { return 1; }
+    __device__ int prime(int p, int) const { return p % L; }
+    __device__ bool direct(int, int) const { return false; }
+    __device__ u64 load(int p, int, int j, const PrimeC& Q) const
+    {
+        const int poly = p / L, t = p % L;             // poly = ct*2 + k
+        return centred_to(Vp[(size_t)poly * N + j], d.p, d.p_half, d.pmod[t], Q);
+    }
+    __device__ void store(int p, int, int j, u64 v, const PrimeC& Q) const
+    {
+        const int poly = p / L, t = p % L;
+        const int ct = poly >> 1, k = poly & 1;
+        const u64 a = acc[((size_t)poly * (L + 1) + t) * N + j];
+        const u64 ks = mul_shoup(sub_mod(a, v, Q.q), d.inv[t], d.invs[t], Q.q);
+        const u64 dk = d3[(((size_t)ct * 3 + k) * L + t) * N + j];
+        out[(((size_t)ct * 2 + k) * L + t) * N + j] = add_mod(dk, ks, Q.q);
+    }
+};
+
+size_t relin_scratch_bytes(const fhe_ctx* c, uint32_t n_ct, uint32_t L)
+{
+    const size_t N = c->N;
+    return arena_need({(size_t)n_ct * L * N * 8, (size_t)n_ct * 2 * (L + 1) * N * 8, (size_t)n_ct * 2 * N * 8});
+}
+
+void k_relin(const fhe_ctx* c, const u64* d3, u64* out2, uint32_t n_ct, uint32_t L, void* scratch, cudaStream_t st)
+{
+    if (n_ct == 0) return;
+    const size_t N = c->N;
+    Arena ar;
+    ar.base = (char*)scratch;
+    ar.cap = relin_scratch_bytes(c, n_ct, L);
+    u64* D = (u64*)ar.take((size_t)n_ct * L * N * 8);
+    u64* acc = (u64*)ar.take((size_t)n_ct * 2 * (L + 1) * N * 8);
+    u64* Vp = (u64*)ar.take((size_t)n_ct * 2 * N * 8);
+
+    OpDigitsInv s1{d3, D, (int)n_ct, (int)L, (int)N};
+    launch_ntt<true>(c, s1, st);
+    OpModUpMac s2{d3, D, c->d_ksk, acc, (int)n_ct, (int)L, (int)N, (int)c->L_top};
+    launch_ntt<false>(c, s2, st);
+    OpAccPInv s3{acc, Vp, (int)n_ct, (int)L, (int)N, (int)c->L_top};
+    launch_ntt<true>(c, s3, st);
+    OpModDown s4;
+    s4.d3 = d3;
+    s4.acc = acc;
+    s4.Vp = Vp;
+    s4.out = out2;
+    s4.n = (int)n_ct;
+    s4.L = (int)L;
+    s4.N = (int)N;
+    s4.d = make_divc(c, c->L_top, L);
+    launch_ntt<false>(c, s4, st);
+}
+
+// ---------------------------------------------------------------- linear layers
+// Y[o][k][r][j] = sum_{e in row o} W[e][r] * X[col[e]][k][r][j]  (mod q_r)
+// grid: x = output o (fastest, so outputs sharing inputs run together and
+// reuse the input slice from L2), y = coefficient block, z = k * L + r.
+__global__ void __launch_bounds__(256) k_mac_kernel(const u64* __restrict__ X, const uint32_t* __restrict__ row_ptr,
+                                                     const uint32_t* __restrict__ col, const u64* __restrict__ W,
+                                                     u64* __restrict__ Y, int L, int N, const PrimeC* __restrict__ pc)
+{
+    const int o = blockIdx.x;
+    const int j = blockIdx.y * blockDim.x + threadIdx.x;
+    const int kr = blockIdx.z;
+    const int r = kr % L;
+    if (j >= N) return;
+    const PrimeC P = pc[r];
+    const size_t ct_stride = (size_t)2 * L * N;
+    const size_t off = (size_t)kr * N + j;
+    const uint32_t e0 = row_ptr[o], e1 = row_ptr[o + 1];
+    u64 lo = 0, hi = 0;
+    int cnt = 0;
+    for (uint32_t e = e0; e < e1; ++e) {
+        const u64 x = X[(size_t)col[e] * ct_stride + off];
+        const u64 w = W[(size_t)e * L + r];
+        const u64 pl = x * w, ph = __umul64hi(x, w);
+        lo += pl;
+        hi += ph + (lo < pl ? 1 : 0);
+        if (++cnt == 32) {              // hi < 32 * 2^58: fold before it can overflow
+            lo = reduce128(hi, lo, P);
+            hi = 0;
+            cnt = 0;
+        }
+    }
+    Y[(size_t)o * ct_stride + off] = reduce128(hi, lo, P);
+}
+
+void k_linear_mac(const fhe_ctx* c, const u64* X, uint32_t n_in, const uint32_t* row_ptr, const uint32_t* col,
+                  const u64* Wres, uint32_t n_out, uint32_t L, u64* Y, cudaStream_t st)
+{
+    (void)n_in;
+    if (n_out == 0) return;
+    const int N = (int)c->N;
+    const int tpb = N < 256 ? N : 256;
+    dim3 grid(n_out, (N + tpb - 1) / tpb, 2 * L);
+    k_mac_kernel<<<grid, tpb, 0, st>>>(X, row_ptr, col, Wres, Y, (int)L, N, c->d_pc);
+}
+
+// ---------------------------------------------------------------- keys
+enum { DOM_SECRET = 1, DOM_PK_A = 2, DOM_PK_E = 3, DOM_KSK_A = 4, DOM_KSK_E = 5,
+       DOM_ENC_U = 6, DOM_ENC_E0 = 7, DOM_ENC_E1 = 8 };
+
+// s (ternary) in every key prime
+struct OpSecret {
+    u64* s;
+    u64 s0;
+    int nprimes, N;
+    __device__ int count() const { return nprimes; }
+    __device__ int nsub(int) const { return 1; }
+    __device__ int prime(int p, int) const { return p; }
+    __device__ bool direct(int, int) const { return false; }
+    __device__ u64 load(int, int, int j, const PrimeC& P) const { return from_signed(draw_ternary(s0, j), P); }
+    __device__ void store(int p, int, int j, u64 v, const PrimeC&) const { s[(size_t)p * N + j] = v; }
+};
+
+// pk = (-a s + e, a) over the data primes: sub 0 = a (uniform), sub 1 = e
+struct OpPublicKey {
+    const u64* s;
+    u64* pk;            // [2][Ltop][N]
+    const u64* cdt;
+    u64 sa, se;
+    int Ltop, N;
+    __device__ int count() const { return Ltop; }
+    __device__ int nsub(int) const { return 2; }
+    __device__ int prime(int p, int) const { return p; }
+    __device__ bool direct(int, int) const { return false; }
+    __device__ u64 load(int p, int u, int j, const PrimeC& P) const
+    {
+        return u == 0 ? draw_uniform(sa, j, p, P) : from_signed(draw_gauss(se, j, cdt), P);
+    }
+    __device__ void store(int p, int u, int j, u64 v, const PrimeC& P) const
+    {
+        u64* b = pk + (size_t)p * N;
+        u64* a = pk + ((size_t)Ltop + p) * N;
+        if (u == 0) {
+            a[j] = v;
+            b[j] = sub_mod(0, mul_mod(v, s[(size_t)p * N + j], P), P.q);
+        } else {
+            b[j] = add_mod(b[j], v, P.q);
+        }
+    }
+};
+
+// ksk_j = (-a_j s + e_j + [r == j] P s^2, a_j) over every key prime r
+struct OpRelinKey {
+    const u64* s;
+    u64* ksk;           // [Ltop][2][Ltop+1][N]
+    const u64* cdt;
+    const u64* sa;      // per digit stream keys (device array [Ltop])
+    const u64* se;
+    u64 Pmod[33];       // P mod q_r
+    int Ltop, N;
+    __device__ int count() const { return Ltop * (Ltop + 1); }
+    __device__ int nsub(int) const { return 2; }
+    __device__ int prime(int p, int) const { return p % (Ltop + 1); }
+    __device__ bool direct(int, int) const { return false; }
+    __device__ u64 load(int p, int u, int j, const PrimeC& P) const
+    {
+        const int dj = p / (Ltop + 1), r = p % (Ltop + 1);
+        return u == 0 ? draw_uniform(sa[dj], j, r, P) : from_signed(draw_gauss(se[dj], j, cdt), P);
+    }
+    __device__ void store(int p, int u, int j, u64 v, const PrimeC& P) const
+    {
+        const int dj = p / (Ltop + 1), r = p % (Ltop + 1);
+        u64* b = ksk + (((size_t)dj * 2 + 0) * (Ltop + 1) + r) * N;
+        u64* a = ksk + (((size_t)dj * 2 + 1) * (Ltop + 1) + r) * N;
+        const u64 sr = s[(size_t)r * N + j];
+        if (u == 0) {
+            a[j] = v;
+            b[j] = sub_mod(0, mul_mod(v, sr, P), P.q);
+        } else {
+            u64 x = add_mod(b[j], v, P.q);
+            if (r == dj) x = add_mod(x, mul_mod(Pmod[r], mul_mod(sr, sr, P), P), P.q);
+            b[j] = x;
+        }
+    }
+};
+
+void k_keygen(fhe_ctx* c, cudaStream_t st)
+{
+    const int N = (int)c->N, Lt = (int)c->L_top;
+    OpSecret os{c->d_s, stream_key(c->seed, DOM_SECRET, 0), Lt + 1, N};
+    launch_ntt<false>(c, os, st);
+    OpPublicKey op{c->d_s, c->d_pk, c->d_cdt, stream_key(c->seed, DOM_PK_A, 0), stream_key(c->seed, DOM_PK_E, 0), Lt, N};
+    launch_ntt<false>(c, op, st);
+    std::vector<u64> h(2 * Lt);
+    for (int j = 0; j < Lt; ++j) {
+        h[j] = stream_key(c->seed, DOM_KSK_A, (u64)j);
+        h[Lt + j] = stream_key(c->seed, DOM_KSK_E, (u64)j);
+    }
+    u64* dkeys = nullptr;
+    cudaMallocAsync((void**)&dkeys, h.size() * 8, st);
+    cudaMemcpyAsync(dkeys, h.data(), h.size() * 8, cudaMemcpyHostToDevice, st);
+    OpRelinKey ok;
+    ok.s = c->d_s;
+    ok.ksk = c->d_ksk;
+    ok.cdt = c->d_cdt;
+    ok.sa = dkeys;
+    ok.se = dkeys + Lt;
+    for (int r = 0; r <= Lt && r < 33; ++r) ok.Pmod[r] = c->primes[Lt] % c->primes[r];
+    ok.Ltop = Lt;
+    ok.N = N;
+    launch_ntt<false>(c, ok, st);
+    cudaFreeAsync(dkeys, st);
+}
+
+// ---------------------------------------------------------------- encrypt
+// per (ct, r): sub 0 = u, sub 1 = e0, sub 2 = e1
+struct OpEncrypt {
+    const u64* pt;      // [n][Ltop][N]
+    const u64* pk;      // [2][Ltop][N]
+    u64* ct;            // [n][2][Ltop][N]
+    const u64* cdt;
+    u64 seed, first;
+    int n, Ltop, N;
+    __device__ int count() const { return n * Ltop; }
+    __device__ int nsub(int) const { return 3; }
+    __device__ int prime(int p, int) const { return p % Ltop; }
+    __device__ bool direct(int, int) const { return false; }
+    __device__ u64 key(int dom, int ct_i) const { return sm_out(sm_out(seed, (u64)dom), first + (u64)ct_i); }
+    __device__ u64 load(int p, int u, int j, const PrimeC& P) const
+    {
+        const int ci = p / Ltop;
+        if (u == 0) return from_signed(draw_ternary(key(DOM_ENC_U, ci), j), P);
+        return from_signed(draw_gauss(key(u == 1 ? DOM_ENC_E0 : DOM_ENC_E1, ci), j, cdt), P);
+    }
+    __device__ void store(int p, int u, int j, u64 v, const PrimeC& P) const
+    {
+        const int ci = p / Ltop, r = p % Ltop;
+        u64* c0 = ct + (((size_t)ci * 2 + 0) * Ltop + r) * N;
+        u64* c1 = ct + (((size_t)ci * 2 + 1) * Ltop + r) * N;
+        if (u == 0) {
+            const u64 m = pt[((size_t)ci * Ltop + r) * N + j];
+            c0[j] = add_mod(mul_mod(v, pk[(size_t)r * N + j], P), m, P.q);
+            c1[j] = mul_mod(v, pk[((size_t)Ltop + r) * N + j], P);
+        } else if (u == 1) {
+            c0[j] = add_mod(c0[j], v, P.q);
+        } else {
+            c1[j] = add_mod(c1[j], v, P.q);
+        }
+    }
+};
+
+void k_encrypt(const fhe_ctx* c, const u64* pt, uint32_t n_ct, uint64_t first_id, u64* ct, cudaStream_t st)
+{
+    OpEncrypt op{pt, c->d_pk, ct, c->d_cdt, c->seed, first_id, (int)n_ct, (int)c->L_top, (int)c->N};
+    launch_ntt<false>(c, op, st);
+}
+
+// ---------------------------------------------------------------- decrypt
+// prologue: c0 + c1 s at residue 0 (NTT form); INTT; centred lift
+struct OpDecrypt {
+    const u64* ct;
+    const u64* s;
+    i64* m;
+    int n, L, N;
+    __device__ int count() const { return n; }
+    __device__ int nsub(int) const { return 1; }
+    __device__ int prime(int, int) const { return 0; }
+    __device__ bool direct(int, int) const { return false; }
+    __device__ u64 load(int p, int, int j, const PrimeC& P) const
+    {
+        const u64 c0 = ct[(((size_t)p * 2 + 0) * L) * N + j];
+        const u64 c1 = ct[(((size_t)p * 2 + 1) * L) * N + j];
+        return add_mod(c0, mul_mod(c1, s[j], P), P.q);
+    }
+    __device__ void store(int p, int, int j, u64 v, const PrimeC& P) const
+    {
+        m[(size_t)p * N + j] = v > P.half ? (i64)v - (i64)P.q : (i64)v;
+    }
+};
+
+void k_decrypt(const fhe_ctx* c, const u64* ct, uint32_t n_ct, uint32_t L, i64* m, cudaStream_t st)
+{
+    OpDecrypt op{ct, c->d_s, m, (int)n_ct, (int)L, (int)c->N};
+    launch_ntt<true>(c, op, st);
+}
+
+// ---------------------------------------------------------------- encode
+// double-double helpers (explicit _rn intrinsics: never contracted)
+struct ddv { double hi, lo; };
+__device__ __forceinline__ ddv two_sum(double a, double b)
+{
+    double s = __dadd_rn(a, b);
+    double bb = __dsub_rn(s, a);
+    double e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ ddv fast_two_sum(double a, double b)
+{
+    double s = __dadd_rn(a, b);
+    return {s, __dsub_rn(b, __dsub_rn(s, a))};
+}
+__device__ __forceinline__ ddv dadd(ddv a, ddv b)
+{
+    ddv s = two_sum(a.hi, b.hi);
+    ddv t = two_sum(a.lo, b.lo);
+    s.lo = __dadd_rn(s.lo, t.hi);
+    s = fast_two_sum(s.hi, s.lo);
+    s.lo = __dadd_rn(s.lo, t.lo);
+    return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ ddv dneg(ddv a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ ddv dmul(ddv a, ddv b)
+{
+    double p = __dmul_rn(a.hi, b.hi);
+    double e = __fma_rn(a.hi, b.hi, -p);
+    e = __dadd_rn(e, __dadd_rn(__dmul_rn(a.hi, b.lo), __dmul_rn(a.lo, b.hi)));
+    return fast_two_sum(p, e);
+}
+struct cddv { ddv re, im; };
+__device__ __forceinline__ cddv cadd(cddv a, cddv b) { return {dadd(a.re, b.re), dadd(a.im, b.im)}; }
+__device__ __forceinline__ cddv csub(cddv a, cddv b) { return {dadd(a.re, dneg(b.re)), dadd(a.im, dneg(b.im))}; }
+__device__ __forceinline__ cddv cmul(cddv a, cddv b)
+{
+    return {dadd(dmul(a.re, b.re), dneg(dmul(a.im, b.im))), dadd(dmul(a.re, b.im), dmul(a.im, b.re))};
+}
+__device__ __forceinline__ cddv ld4(const double4& v) { return {{v.x, v.y}, {v.z, v.w}}; }
+
+// round half away from zero of a double-double to int64
+__device__ __forceinline__ i64 dd_round(ddv v)
+{
+    bool neg = v.hi < 0.0 || (v.hi == 0.0 && v.lo < 0.0);
+    if (neg) v = dneg(v);
+    double f = floor(v.hi);
+    double frac = __dadd_rn(__dsub_rn(v.hi, f), v.lo);
+    double add = floor(__dadd_rn(frac, 0.5));
+    i64 r = (i64)f + (i64)add;
+    return neg ? -r : r;
+}
+
+// One block per (ct, half h): the N/2-point inverse DFT of the slots (placed
+// at l(j) = (5^j mod 2N - 1)/4) is split by its first decimation-in-frequency
+// stage; half h runs the N/4-point DFT of its half in shared memory.
+// Output: m_k = round(scale * Re c_k), m_{k+N/2} = round(scale * Im c_k),
+// c_k = (2/N) zeta^{-k} X_k.
+__global__ void __launch_bounds__(512) k_encode_kernel(const double* __restrict__ slots, const uint32_t* __restrict__ slot_of,
+                                                        const double4* __restrict__ tw, const double4* __restrict__ twist,
+                                                        double scale_over_M, int N, i64* __restrict__ m)
+{
+    extern __shared__ double4 A[];       // N/4 complex dd values
+    const int M = N / 2, H = M / 2;
+    const int ct = blockIdx.x >> 1, h = blockIdx.x & 1;
+    const double* z = slots + (size_t)ct * M;
+    for (int l = threadIdx.x; l < H; l += blockDim.x) {
+        const double x0 = z[slot_of[l]], x1 = z[slot_of[l + H]];
+        cddv v;
+        if (h == 0) {
+            v.re = two_sum(x0, x1);
+            v.im = {0.0, 0.0};
+        } else {
+            ddv d = two_sum(x0, -x1);
+            const cddv w = ld4(tw[l]);                 // W^l, W = e^{-2 pi i / M}
+            v.re = dmul(d, w.re);
+            v.im = dmul(d, w.im);
+        }
+        A[l] = make_double4(v.re.hi, v.re.lo, v.im.hi, v.im.lo);
+    }
+    __syncthreads();
+    // H-point DIF, twiddle for offset o at half-size hs: W^{o * M / (2 hs)}
+    for (int hs = H / 2; hs >= 1; hs >>= 1) {
+        for (int b = threadIdx.x; b < H / 2; b += blockDim.x) {
+            const int blk = b / hs, o = b % hs;
+            const int i0 = blk * 2 * hs + o, i1 = i0 + hs;
+            const cddv x = ld4(A[i0]), y = ld4(A[i1]);
+            const cddv s = cadd(x, y);
+            const cddv d = cmul(csub(x, y), ld4(tw[o * (M / (2 * hs))]));
+            A[i0] = make_double4(s.re.hi, s.re.lo, s.im.hi, s.im.lo);
+            A[i1] = make_double4(d.re.hi, d.re.lo, d.im.hi, d.im.lo);
+        }
+        __syncthreads();
+    }
+    int lg = 0;
+    while ((1 << lg) < H) ++lg;
+    for (int p = threadIdx.x; p < H; p += blockDim.x) {
+        const int kp = (int)(__brev((unsigned)p) >> (32 - lg));
+        const int k = 2 * kp + h;                       // frequency index in [0, M)
+        const cddv X = ld4(A[p]);
+        cddv c = cmul(X, ld4(twist[k]));
+        const ddv s = {scale_over_M, 0.0};
+        m[(size_t)ct * N + k] = dd_round(dmul(c.re, s));
+        m[(size_t)ct * N + k + M] = dd_round(dmul(c.im, s));
+    }
+}
+
+struct OpSignedRows {
+    const i64* m;       // [n][N]
+    u64* out;           // [n][L][N]
+    int n, L, N;
+    __device__ int count() const { return n * L; }
+    __device__ int nsub(int) const { return 1; }
+    __device__ int prime(int p, int) const { return p % L; }
+    __device__ bool direct(int, int) const { return false; }
+    __device__ u64 load(int p, int, int j, const PrimeC& P) const { return from_signed(m[(size_t)(p / L) * N + j], P); }
+    __device__ void store(int p, int, int j, u64 v, const PrimeC&) const { out[(size_t)p * N + j] = v; }
+};
+
+size_t encode_scratch_bytes(const fhe_ctx* c, uint32_t n_ct) { return (size_t)n_ct * c->N * sizeof(i64); }
+
+void k_encode(const fhe_ctx* c, const double* slots, uint32_t n_ct, uint32_t L, double scale, u64* pt, void* scratch,
+              cudaStream_t st)
+{
+    if (n_ct == 0) return;
+    const int N = (int)c->N;
+    i64* m = (i64*)scratch;
+    const size_t smem = (size_t)(N / 4) * sizeof(double4);
+    static size_t configured = 0;
+    if (configured < smem) {
+        cudaFuncSetAttribute(k_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        configured = smem;
+    }
+    int thr = N / 8;
+    thr = thr < 32 ? 32 : (thr > 512 ? 512 : thr);
+    k_encode_kernel<<<2 * n_ct, thr, smem, st>>>(slots, c->d_slot_of, c->d_enc_tw, c->d_enc_twist,
+                                                 scale / (double)(N / 2), N, m);
+    OpSignedRows op{m, pt, (int)n_ct, (int)L, N};
+    launch_ntt<false>(c, op, st);
+}
+
+// ---------------------------------------------------------------- decode
+// z_j = Re Z_{l(j)} / scale, Z = DFT_{N/2}(c_k zeta^k) with e^{+2 pi i / M},
+// c_k = m_k + i m_{k+N/2}; FP64, one block per ciphertext.
+__global__ void __launch_bounds__(512) k_decode_kernel(const i64* __restrict__ m, const uint32_t* __restrict__ slot_of,
+                                                        const double4* __restrict__ tw, const double4* __restrict__ twist,
+                                                        double inv_scale, int N, double* __restrict__ slots)
+{
+    extern __shared__ double2 B[];       // N/2 complex doubles
+    const int M = N / 2;
+    const int ct = blockIdx.x;
+    const i64* mc = m + (size_t)ct * N;
+    for (int k = threadIdx.x; k < M; k += blockDim.x) {
+        const double a = (double)mc[k], b = (double)mc[k + M];
+        const double4 t = twist[k];                     // zeta^{-k}: use its conjugate
+        const double wr = t.x, wi = -t.z;
+        B[k] = make_double2(a * wr - b * wi, a * wi + b * wr);
+    }
+    __syncthreads();
+    for (int hs = M / 2; hs >= 1; hs >>= 1) {
+        for (int b = threadIdx.x; b < M / 2; b += blockDim.x) {
+            const int blk = b / hs, o = b % hs;
+            const int i0 = blk * 2 * hs + o, i1 = i0 + hs;
+            const double2 x = B[i0], y = B[i1];
+            const double4 w4 = tw[o * (M / (2 * hs))];  // W^e, W = e^{-2 pi i / M}: conjugate
+            const double wr = w4.x, wi = -w4.z;
+            const double dr = x.x - y.x, di = x.y - y.y;
+            B[i0] = make_double2(x.x + y.x, x.y + y.y);
+            B[i1] = make_double2(dr * wr - di * wi, dr * wi + di * wr);
+        }
+        __syncthreads();
+    }
+    int lg = 0;
+    while ((1 << lg) < M) ++lg;
+    for (int l = threadIdx.x; l < M; l += blockDim.x) {
+        const int p = (int)(__brev((unsigned)l) >> (32 - lg));
+        slots[(size_t)ct * M + slot_of[l]] = B[p].x * inv_scale;
+    }
+}
+
+void k_decode(const fhe_ctx* c, const i64* m, uint32_t n_ct, double scale, double* slots, cudaStream_t st)
+{
+    if (n_ct == 0) return;
+    const int N = (int)c->N;
+    const size_t smem = (size_t)(N / 2) * sizeof(double2);
+    static size_t configured = 0;
+    if (configured < smem) {
+        cudaFuncSetAttribute(k_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        configured = smem;
+    }
+    int thr = N / 4;
+    thr = thr < 32 ? 32 : (thr > 512 ? 512 : thr);
+    k_decode_kernel<<<n_ct, thr, smem, st>>>(m, c->d_slot_of, c->d_enc_tw, c->d_enc_twist, 1.0 / scale, N, slots);
+}
+
+}  // namespace fhe

@@ -1,0 +1,329 @@
+"""Python binding of libfhe (include/fhe.h): argument marshalling only.
+
+Every step of the encrypted path runs in the sm_103a CUDA library; this module
+converts PyTorch tensors to device pointers and host arrays to C arrays, and
+raises FheError on a non-zero return code.  There is no fallback: if the
+library is not built, the first call raises.
+
+Device buffers are torch tensors (dtype int64 holding raw 64-bit residues, or
+float64 slots) on the current CUDA device; work is enqueued on the current
+torch stream.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+SO_PATH = os.path.join(_HERE, "csrc", "_build", "libfhe.so")
+
+FHE_NODE_INPUT, FHE_NODE_LINEAR, FHE_NODE_POLY, FHE_NODE_SQUARE, FHE_NODE_ADD, FHE_NODE_OUTPUT = range(6)
+_KINDS = {"input": FHE_NODE_INPUT, "linear": FHE_NODE_LINEAR, "poly": FHE_NODE_POLY,
+          "square": FHE_NODE_SQUARE, "add": FHE_NODE_ADD, "output": FHE_NODE_OUTPUT}
+
+ERRORS = {-1: "FHE_EINVAL", -2: "FHE_ENOMEM", -3: "FHE_ELEVEL", -4: "FHE_ESCALE", -5: "FHE_ECUDA",
+          -6: "FHE_ETIMEOUT", -7: "FHE_EUNSUPPORTED", -8: "FHE_ENOKEY"}
+
+
+class FheError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class CtxInfo(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_uint32), ("slots", ctypes.c_uint32), ("L_top", ctypes.c_uint32),
+                ("log_scale", ctypes.c_uint32), ("primes", ctypes.c_uint64 * 64), ("key_bytes", ctypes.c_uint64)]
+
+
+class CtMeta(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_uint32), ("scale", ctypes.c_double)]
+
+
+class NodeDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_uint32), ("n_out", ctypes.c_uint32),
+                ("row_ptr", ctypes.POINTER(ctypes.c_uint32)), ("col_idx", ctypes.POINTER(ctypes.c_uint32)),
+                ("weight", ctypes.POINTER(ctypes.c_double)), ("bias", ctypes.POINTER(ctypes.c_double)),
+                ("coeffs", ctypes.c_double * 4)]
+
+
+class GraphDesc(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_uint32), ("nodes", ctypes.POINTER(NodeDesc)),
+                ("n_edges", ctypes.c_uint32), ("edge_src", ctypes.POINTER(ctypes.c_uint32)),
+                ("edge_dst", ctypes.POINTER(ctypes.c_uint32))]
+
+
+# exported symbols and their signatures (mirrors include/fhe.h)
+_P = ctypes.c_void_p
+_U32 = ctypes.c_uint32
+_U64 = ctypes.c_uint64
+_I = ctypes.c_int
+SIGNATURES = {
+    "fhe_parameterise": [_U32, _U32, ctypes.c_double, _P, _P, _U32, _P],
+    "fhe_autohe": [_P, _P, _U32, _P, _U32, _P],
+    "fhe_prime_chain": [_U32, _P, _U32, _P],
+    "fhe_gauss_table": [_P],
+    "fhe_ctx_create": [_U32, _P, _U32, _U32, _P],
+    "fhe_ctx_destroy": [_P],
+    "fhe_ctx_query": [_P, _P],
+    "fhe_keygen": [_P, _U64, _P],
+    "fhe_export_secret": [_P, _P, _P],
+    "fhe_encode": [_P, _P, _U32, _U32, ctypes.c_double, _P, _P],
+    "fhe_encrypt": [_P, _P, _U32, _U64, _P, _P],
+    "fhe_decrypt": [_P, _P, _U32, _U32, _P, _P],
+    "fhe_decode": [_P, _P, _U32, ctypes.c_double, _P, _P],
+    "fhe_ntt": [_P, _P, _U32, _U32, _I, _P],
+    "fhe_ct_convert": [_P, _P, _U32, _U32, _I, _P, _P],
+    "fhe_add": [_P, _P, _P, _U32, _U32, _P, _P],
+    "fhe_tensor": [_P, _P, _P, _U32, _U32, _P, _P],
+    "fhe_relinearise": [_P, _P, _U32, _U32, _P, _P],
+    "fhe_rescale": [_P, _P, _U32, _U32, _U32, _P, _P],
+    "fhe_mul_relin_rescale": [_P, _P, _P, _U32, _U32, _P, _P],
+    "fhe_mul_const": [_P, _P, _P, _U32, _U32, _P, _P],
+    "fhe_add_const": [_P, _P, _P, _U32, _U32, _P],
+    "fhe_graph_create": [_P, _P],
+    "fhe_graph_destroy": [_P],
+    "fhe_graph_outputs": [_P, _P, _P, _P],
+    "fhe_eval_graph": [_P, _P, _P, _U32, _P, _P, _U32, _P],
+    "fhe_last_error": [],
+}
+
+_lib = None
+
+
+def lib():
+    """Load libfhe.so; raises if it has not been built (no CPU fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(SO_PATH):
+            raise FheError(-7, "libfhe.so is not built (%s); run __graft_entry__.build()" % SO_PATH)
+        L = ctypes.CDLL(SO_PATH)
+        for name, args in SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_char_p if name == "fhe_last_error" else ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise FheError(rc, lib().fhe_last_error().decode(errors="replace"))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _arr(values, ctype):
+    a = (ctype * len(values))()
+    for i, v in enumerate(values):
+        a[i] = v
+    return a
+
+
+# ---------------------------------------------------------------- host-only
+def parameterise(cost, log_scale=40, special_mult=1.5):
+    N = ctypes.c_uint32()
+    bits = (ctypes.c_uint32 * 64)()
+    nb = ctypes.c_uint32()
+    _check(lib().fhe_parameterise(cost, log_scale, special_mult, ctypes.byref(N), bits, 64, ctypes.byref(nb)))
+    return N.value, [bits[i] for i in range(nb.value)]
+
+
+def prime_chain(N, bits):
+    out = (ctypes.c_uint64 * len(bits))()
+    _check(lib().fhe_prime_chain(N, _arr(bits, ctypes.c_uint32), len(bits), out))
+    return [int(v) for v in out]
+
+
+def gauss_table():
+    out = (ctypes.c_uint64 * 38)()
+    _check(lib().fhe_gauss_table(out))
+    return [int(v) for v in out]
+
+
+class _GraphArrays:
+    """Keeps the C arrays of a graph description alive while it is used."""
+
+    def __init__(self, graph):
+        nodes = graph["nodes"]
+        self.keep = []
+        self.nodes = (NodeDesc * len(nodes))()
+        for i, n in enumerate(nodes):
+            d = self.nodes[i]
+            d.kind = _KINDS[n["kind"]]
+            if n["kind"] == "linear":
+                rp = np.ascontiguousarray(n["row_ptr"], dtype=np.uint32)
+                ci = np.ascontiguousarray(n["col_idx"], dtype=np.uint32)
+                w = np.ascontiguousarray(n["weight"], dtype=np.float64)
+                b = np.ascontiguousarray(n["bias"], dtype=np.float64)
+                self.keep += [rp, ci, w, b]
+                d.n_out = len(rp) - 1
+                d.row_ptr = rp.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+                d.col_idx = ci.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+                d.weight = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+                d.bias = b.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            elif n["kind"] == "input":
+                d.n_out = int(n.get("n", 0))
+            if n["kind"] == "poly":
+                for k in range(4):
+                    d.coeffs[k] = float(n["coeffs"][k])
+        src = np.array([e[0] for e in graph["edges"]], dtype=np.uint32)
+        dst = np.array([e[1] for e in graph["edges"]], dtype=np.uint32)
+        self.keep += [src, dst]
+        self.desc = GraphDesc(len(nodes), self.nodes, len(src),
+                              src.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                              dst.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+
+
+def autohe(graph):
+    """(group of each input node in node order, cost of each group)."""
+    ga = _GraphArrays(graph)
+    n_in = sum(1 for n in graph["nodes"] if n["kind"] == "input")
+    gof = (ctypes.c_uint32 * max(1, n_in))()
+    gcost = (ctypes.c_uint32 * max(1, n_in))()
+    ng = ctypes.c_uint32()
+    _check(lib().fhe_autohe(ctypes.byref(ga.desc), gof, n_in, gcost, n_in, ctypes.byref(ng)))
+    return [gof[i] for i in range(n_in)], [gcost[i] for i in range(ng.value)]
+
+
+# ---------------------------------------------------------------- context
+class Context:
+    """An RNS-CKKS context on the current CUDA device (tables and keys in HBM)."""
+
+    def __init__(self, N, bits, log_scale=40):
+        h = ctypes.c_void_p()
+        _check(lib().fhe_ctx_create(N, _arr(bits, ctypes.c_uint32), len(bits), log_scale, ctypes.byref(h)))
+        self.h = h
+        info = CtxInfo()
+        _check(lib().fhe_ctx_query(self.h, ctypes.byref(info)))
+        self.N = info.N
+        self.slots = info.slots
+        self.L_top = info.L_top
+        self.log_scale = info.log_scale
+        self.primes = [int(info.primes[i]) for i in range(info.L_top + 1)]
+        self.key_bytes = int(info.key_bytes)
+        self.delta = float(2 ** log_scale)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().fhe_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- allocation helpers (torch device memory) --------------------------
+    def empty_ct(self, n, level, comps=2):
+        import torch
+        return torch.empty((n, comps, level, self.N), dtype=torch.int64, device="cuda")
+
+    def empty_pt(self, n, level):
+        import torch
+        return torch.empty((n, level, self.N), dtype=torch.int64, device="cuda")
+
+    # -- keys / encode / encrypt / decrypt / decode ------------------------
+    def keygen(self, seed, stream=None):
+        _check(lib().fhe_keygen(self.h, seed, _stream(stream)))
+
+    def export_secret(self, out, stream=None):
+        _check(lib().fhe_export_secret(self.h, _ptr(out), _stream(stream)))
+
+    def encode(self, slots, level, scale, out, stream=None):
+        _check(lib().fhe_encode(self.h, _ptr(slots), slots.shape[0], level, scale, _ptr(out), _stream(stream)))
+
+    def encrypt(self, pt, first_ct_id, out, stream=None):
+        _check(lib().fhe_encrypt(self.h, _ptr(pt), pt.shape[0], first_ct_id, _ptr(out), _stream(stream)))
+
+    def decrypt(self, ct, level, out, stream=None):
+        _check(lib().fhe_decrypt(self.h, _ptr(ct), ct.shape[0], level, _ptr(out), _stream(stream)))
+
+    def decode(self, m, scale, out, stream=None):
+        _check(lib().fhe_decode(self.h, _ptr(m), m.shape[0], scale, _ptr(out), _stream(stream)))
+
+    # -- layout ---------------------------------------------------------------
+    def ntt(self, polys, rows, forward, stream=None):
+        _check(lib().fhe_ntt(self.h, _ptr(polys), polys.shape[0], rows, 1 if forward else 0, _stream(stream)))
+
+    def ct_convert(self, ct, level, to_coeff, out, stream=None):
+        _check(lib().fhe_ct_convert(self.h, _ptr(ct), ct.shape[0], level, 1 if to_coeff else 0, _ptr(out),
+                                    _stream(stream)))
+
+    # -- operations -----------------------------------------------------------
+    def add(self, a, b, level, out, stream=None):
+        _check(lib().fhe_add(self.h, _ptr(a), _ptr(b), a.shape[0], level, _ptr(out), _stream(stream)))
+
+    def tensor(self, a, b, level, out, stream=None):
+        _check(lib().fhe_tensor(self.h, _ptr(a), _ptr(b), a.shape[0], level, _ptr(out), _stream(stream)))
+
+    def relinearise(self, d3, level, out, stream=None):
+        _check(lib().fhe_relinearise(self.h, _ptr(d3), d3.shape[0], level, _ptr(out), _stream(stream)))
+
+    def rescale(self, x, comps, level, out, stream=None):
+        _check(lib().fhe_rescale(self.h, _ptr(x), x.shape[0], comps, level, _ptr(out), _stream(stream)))
+
+    def mul_relin_rescale(self, a, b, level, out, stream=None):
+        _check(lib().fhe_mul_relin_rescale(self.h, _ptr(a), _ptr(b), a.shape[0], level, _ptr(out),
+                                           _stream(stream)))
+
+    def mul_const(self, x, consts, level, out, stream=None):
+        c = np.ascontiguousarray(consts, dtype=np.int64)
+        _check(lib().fhe_mul_const(self.h, _ptr(x), c.ctypes.data_as(ctypes.c_void_p), x.shape[0], level,
+                                   _ptr(out), _stream(stream)))
+
+    def add_const(self, x, consts, level, stream=None):
+        c = np.ascontiguousarray(consts, dtype=np.int64)
+        _check(lib().fhe_add_const(self.h, _ptr(x), c.ctypes.data_as(ctypes.c_void_p), x.shape[0], level,
+                                   _stream(stream)))
+
+
+class Graph:
+    """A network graph (workload dict) copied into the library."""
+
+    def __init__(self, graph):
+        self._arrays = _GraphArrays(graph)
+        h = ctypes.c_void_p()
+        _check(lib().fhe_graph_create(ctypes.byref(self._arrays.desc), ctypes.byref(h)))
+        self.h = h
+        self.n_inputs = sum(1 for n in graph["nodes"] if n["kind"] == "input")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().fhe_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def outputs(self, ctx):
+        n = ctypes.c_uint32()
+        L = ctypes.c_uint32()
+        _check(lib().fhe_graph_outputs(ctx.h, self.h, ctypes.byref(n), ctypes.byref(L)))
+        return n.value, L.value
+
+    def eval(self, ctx, inputs, out, stream=None):
+        """inputs: list of ciphertext tensors, one per input node; out: tensor
+        [n_out][2][out_level][N].  Returns a list of (level, scale)."""
+        arr = (ctypes.c_void_p * len(inputs))(*[t.data_ptr() for t in inputs])
+        cap = out.shape[0]
+        meta = (CtMeta * max(1, cap))()
+        _check(lib().fhe_eval_graph(ctx.h, self.h, arr, len(inputs), _ptr(out), meta, cap, _stream(stream)))
+        return [(meta[i].level, meta[i].scale) for i in range(cap)]
+
+
+def raw_u64(t):
+    """Device int64 tensor of raw residues -> host numpy uint64 array."""
+    return t.detach().cpu().numpy().view(np.uint64)

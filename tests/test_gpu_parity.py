@@ -1,0 +1,279 @@
+"""GPU parity: every step of the path through the C ABI against the CPU oracle.
+
+Ciphertext residues must be bit-exact (compared in coefficient form, so the
+device's internal NTT order and root choice do not matter).  Encoded
+coefficients may differ by 1 only where the oracle's unrounded value lies
+within 1e-6 of a rounding boundary.  Decoded slots are compared within the
+FP64 bound derived in the test."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import __graft_entry__
+from oracle import ckks
+from paper_2110_13638_gb300 import fhe, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+BITS5 = [60, 40, 40, 40, 40, 60]
+BITS9 = [60] + [40] * 7 + [60]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+_CTX = {}
+
+
+def pair(N, bits, seed=0):
+    key = (N, tuple(bits), seed)
+    if key not in _CTX:
+        g = fhe.Context(N, bits, 40)
+        g.keygen(seed)
+        o = ckks.Context(N, bits, 40)
+        o.keygen(seed)
+        _CTX[key] = (g, o)
+    return _CTX[key]
+
+
+def upload(ctx, arrs, level):
+    """oracle coefficient-form arrays [k][L][N] -> device NTT form [n][k][L][N]"""
+    a = np.stack(arrs).astype(np.uint64)
+    t = torch.from_numpy(a.view(np.int64).copy()).cuda()
+    comps = a.shape[1]
+    flat = t.view(-1, level, ctx.N)
+    ctx.ntt(flat, level, True)
+    return t
+
+
+def download(ctx, t, level):
+    """device NTT form [n][k][L][N] -> coefficient form uint64"""
+    c = t.clone()
+    ctx.ntt(c.view(-1, level, ctx.N), level, False)
+    torch.cuda.synchronize()
+    return fhe.raw_u64(c)
+
+
+def rand_ct(o, L, rng, comps=2):
+    return np.stack([np.stack([rng.integers(0, q, o.N, dtype=np.uint64) for q in o.q[:L]]) for _ in range(comps)])
+
+
+# ---------------------------------------------------------------- keys
+@pytest.mark.parametrize("N,bits", [(16, BITS5), (1024, BITS5), (16384, BITS9)])
+def test_secret_key_matches_oracle(N, bits):
+    g, o = pair(N, bits)
+    s = torch.empty((g.L_top + 1, N), dtype=torch.int64, device="cuda")
+    g.export_secret(s)
+    got = download(g, s.view(1, g.L_top + 1, N), g.L_top + 1)[0]
+    for r in range(g.L_top + 1):
+        assert np.array_equal(got[r], o.s[r]), r
+
+
+# ---------------------------------------------------------------- NTT / ring
+@pytest.mark.parametrize("N,bits,n", [(16, BITS5, 3), (256, BITS5, 5), (4096, BITS5, 2), (16384, BITS9, 2)])
+def test_ntt_roundtrip_and_tensor(N, bits, n):
+    g, o = pair(N, bits)
+    rng = np.random.default_rng(N + n)
+    L = g.L_top
+    A = [rand_ct(o, L, rng) for _ in range(n)]
+    B = [rand_ct(o, L, rng) for _ in range(n)]
+    ta, tb = upload(g, A, L), upload(g, B, L)
+    assert np.array_equal(download(g, ta, L), np.stack(A))
+    t3 = g.empty_ct(n, L, comps=3)
+    g.tensor(ta, tb, L, t3)
+    got = download(g, t3, L)
+    for k in range(n):
+        want = o.tensor(ckks.Ciphertext(A[k], L, 1.0), ckks.Ciphertext(B[k], L, 1.0)).c
+        assert np.array_equal(got[k], want), k
+
+
+# ---------------------------------------------------------------- encode
+def _encode_check(g, o, z, got_res, L):
+    """got_res: [n][L][N] coefficient-form residues of the device encoding"""
+    for i in range(z.shape[0]):
+        m, frac = o.encode(z[i], want_frac=True)
+        for r in range(L):
+            want = ckks.to_residue(m, o.q[r])
+            bad = np.nonzero(got_res[i, r] != want)[0]
+            for k in bad:
+                d = (int(got_res[i, r, k]) - int(want[k])) % o.q[r]
+                assert frac[k] < 1e-6 and d in (1, o.q[r] - 1), (i, r, k)
+
+
+@pytest.mark.parametrize("N,bits,n", [(16, BITS5, 3), (1024, BITS5, 3), (8192, [60, 40, 40, 60], 2),
+                                      (16384, BITS9, 2)])
+def test_encode_matches_oracle(N, bits, n):
+    g, o = pair(N, bits)
+    rng = np.random.default_rng(7)
+    z = rng.uniform(-1, 1, size=(n, N // 2))
+    z[0, :] = rng.uniform(0, 1, N // 2) * 50.0          # larger magnitudes
+    L = g.L_top
+    pt = g.empty_pt(n, L)
+    g.encode(torch.tensor(z, device="cuda"), L, g.delta, pt)
+    got = download(g, pt.view(n, 1, L, N), L)[:, 0]
+    _encode_check(g, o, z, got, L)
+
+
+# ---------------------------------------------------------------- encrypt / decrypt / decode
+@pytest.mark.parametrize("N,bits,n", [(16, BITS5, 2), (1024, BITS5, 3), (16384, BITS9, 2)])
+def test_encrypt_decrypt_decode(N, bits, n):
+    g, o = pair(N, bits)
+    rng = np.random.default_rng(11)
+    z = rng.uniform(-1, 1, size=(n, N // 2))
+    L = g.L_top
+    pt = g.empty_pt(n, L)
+    g.encode(torch.tensor(z, device="cuda"), L, g.delta, pt)
+    ct = g.empty_ct(n, L)
+    first = 1000
+    g.encrypt(pt, first, ct)
+    got = download(g, ct, L)
+    for i in range(n):
+        want = o.encrypt(o.encode(z[i]), first + i)
+        assert np.array_equal(got[i], want.c), i
+    # decrypt the oracle's own ciphertexts on the device
+    octs = [o.encrypt(o.encode(z[i]), 77 + i) for i in range(n)]
+    t = upload(g, [c.c for c in octs], L)
+    m = torch.empty((n, N), dtype=torch.int64, device="cuda")
+    g.decrypt(t, L, m)
+    md = m.cpu().numpy()
+    for i in range(n):
+        assert np.array_equal(md[i], o.decrypt(octs[i])), i
+    zs = torch.empty((n, N // 2), dtype=torch.float64, device="cuda")
+    g.decode(m, g.delta, zs)
+    zd = zs.cpu().numpy()
+    for i in range(n):
+        ref = o.decode(md[i], g.delta)
+        # FP64 FFT of integers < 2^62: error <= log2(N) * 2^-52 * sum|m| / scale
+        bound = np.log2(N) * 2.0 ** -52 * np.abs(md[i]).astype(np.float64).sum() / g.delta + 1e-15
+        assert np.max(np.abs(zd[i] - ref)) <= bound, i
+        assert np.max(np.abs(zd[i] - z[i])) < 1e-5
+
+
+# ---------------------------------------------------------------- key switching / rescale
+@pytest.mark.parametrize("N,bits,L,n", [(16, BITS5, 1, 2), (64, BITS5, 3, 3), (1024, BITS5, 5, 2),
+                                        (16384, BITS9, 8, 1)])
+def test_relinearise_bit_exact(N, bits, L, n):
+    g, o = pair(N, bits)
+    rng = np.random.default_rng(L * 100 + n)
+    D = [rand_ct(o, L, rng, comps=3) for _ in range(n)]
+    t3 = upload(g, D, L)
+    out = g.empty_ct(n, L)
+    g.relinearise(t3, L, out)
+    got = download(g, out, L)
+    for k in range(n):
+        assert np.array_equal(got[k], o.relinearise(ckks.Ciphertext(D[k], L, 1.0)).c), k
+
+
+@pytest.mark.parametrize("N,bits,L,comps,n", [(16, BITS5, 2, 2, 3), (1024, BITS5, 5, 3, 2), (16384, BITS9, 8, 2, 2)])
+def test_rescale_bit_exact(N, bits, L, comps, n):
+    g, o = pair(N, bits)
+    rng = np.random.default_rng(L + comps)
+    X = [rand_ct(o, L, rng, comps=comps) for _ in range(n)]
+    t = upload(g, X, L)
+    out = g.empty_ct(n, L - 1, comps=comps)
+    g.rescale(t, comps, L, out)
+    got = download(g, out, L - 1)
+    for k in range(n):
+        assert np.array_equal(got[k], o.rescale(ckks.Ciphertext(X[k], L, 1.0)).c), k
+
+
+@pytest.mark.parametrize("N,bits,L,n", [(1024, BITS5, 3, 3), (16384, BITS9, 8, 2), (16384, BITS9, 2, 1)])
+def test_mul_relin_rescale_bit_exact(N, bits, L, n):
+    g, o = pair(N, bits)
+    rng = np.random.default_rng(5 * L + n)
+    A = [rand_ct(o, L, rng) for _ in range(n)]
+    B = [rand_ct(o, L, rng) for _ in range(n)]
+    out = g.empty_ct(n, L - 1)
+    g.mul_relin_rescale(upload(g, A, L), upload(g, B, L), L, out)
+    got = download(g, out, L - 1)
+    for k in range(n):
+        a, b = ckks.Ciphertext(A[k], L, 1.0), ckks.Ciphertext(B[k], L, 1.0)
+        assert np.array_equal(got[k], o.rescale(o.relinearise(o.tensor(a, b))).c), k
+
+
+def test_const_ops_bit_exact():
+    g, o = pair(256, BITS5)
+    rng = np.random.default_rng(3)
+    L = 3
+    X = [rand_ct(o, L, rng) for _ in range(3)]
+    C = [123456789012, -987654321, 0]
+    t = upload(g, X, L)
+    out = g.empty_ct(3, L)
+    g.mul_const(t, C, L, out)
+    g.add_const(out, [5, -7, 2 ** 50], L)
+    got = download(g, out, L)
+    for k in range(3):
+        y = o.add_const(o.mul_const(ckks.Ciphertext(X[k], L, 1.0), C[k], 1.0), [5, -7, 2 ** 50][k])
+        assert np.array_equal(got[k], y.c), k
+
+
+def test_level_errors():
+    g, _ = pair(16, BITS5)
+    t = g.empty_ct(1, 1)
+    with pytest.raises(fhe.FheError) as e:
+        g.rescale(t, 2, 1, g.empty_ct(1, 1))
+    assert e.value.code == -3
+    with pytest.raises(fhe.FheError):
+        g.encode(torch.zeros((1, 8), dtype=torch.float64, device="cuda"), 9, g.delta, g.empty_pt(1, 4))
+
+
+# ---------------------------------------------------------------- graphs
+def _graph_parity(g, o, graph, xs, first_ids):
+    ins = W.input_nodes(graph)
+    N = g.N
+    L = g.L_top
+    dev_in, orc_in = [], []
+    for x, first in zip(xs, first_ids):
+        n = x.shape[0]
+        pt = g.empty_pt(n, L)
+        g.encode(torch.tensor(x, device="cuda"), L, g.delta, pt)
+        ct = g.empty_ct(n, L)
+        g.encrypt(pt, first, ct)
+        dev_in.append(ct)
+        orc_in.append([o.encrypt(o.encode(x[i]), first + i) for i in range(n)])
+    G = fhe.Graph(graph)
+    n_out, L_out = G.outputs(g)
+    out = g.empty_ct(n_out, L_out)
+    meta = G.eval(g, dev_in, out)
+    got = download(g, out, L_out)
+    res = ckks.eval_graph(o, graph, ins, orc_in)
+    want = [ct for node in sorted(res) for ct in res[node]]
+    assert len(want) == n_out
+    for k, y in enumerate(want):
+        assert y.level == L_out and meta[k][0] == L_out
+        assert meta[k][1] == y.scale
+        assert np.array_equal(got[k], y.c), k
+    m = torch.empty((n_out, N), dtype=torch.int64, device="cuda")
+    g.decrypt(out, L_out, m)
+    z = torch.empty((n_out, N // 2), dtype=torch.float64, device="cuda")
+    g.decode(m, meta[0][1], z)
+    ref = ckks.forward_fp64(graph, ins, xs)
+    refs = np.concatenate([ref[node] for node in sorted(ref)], axis=0)
+    return float(np.max(np.abs(z.cpu().numpy() - refs)))
+
+
+def test_graph_mini_cnn_bit_exact():
+    g, o = pair(1024, BITS9)
+    graph, x = W.mini_cnn(n_slots=512)
+    err = _graph_parity(g, o, graph, [x], [0])
+    assert err < 1e-4
+
+
+def test_graph_branches_bit_exact():
+    g, o = pair(256, [60, 40, 40, 40, 60])
+    graph, xs = W.branch_graph(n_slots=128)
+    err = _graph_parity(g, o, graph, xs, [0, 100])
+    assert err < 1e-4
+
+
+def test_graph_cfg0_full_size_bit_exact():
+    """Dense 8->4 then x^2 at N = 8192, [60,40,40,60], 4096 samples."""
+    N, bits = 8192, [60, 40, 40, 60]
+    g, o = pair(N, bits)
+    graph, x = W.cfg0()
+    err = _graph_parity(g, o, graph, [x], [0])
+    assert err < 1e-4
