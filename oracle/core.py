@@ -22,7 +22,10 @@ _lib = None
 def build(force=False):
     """Compile the C core with gcc (plain -O2, no fast-math, no FP contraction)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_SO)
+    stamp = os.path.join(_BUILD, "STAMP")
+    want = platform.machine()
+    same_machine = os.path.exists(stamp) and open(stamp).read().strip() == want
+    if (not force and same_machine and os.path.exists(_SO)
             and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
         return _SO
     libs = ["-lquadmath"] if platform.machine() == "x86_64" else ["-lm"]
@@ -31,6 +34,8 @@ def build(force=False):
            _SRC, "-o", tmp] + libs
     subprocess.check_call(cmd)
     os.replace(tmp, _SO)
+    with open(stamp, "w") as f:
+        f.write(want + "\n")
     return _SO
 
 

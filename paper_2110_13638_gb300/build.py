@@ -5,6 +5,7 @@ paper_2110_13638_gb300/csrc/_build/libfhe.so.  Host code is compiled with
 -ffp-contract=off so FP64 constant encodings round identically on every host.
 """
 import os
+import platform
 import subprocess
 import sys
 from concurrent.futures import ThreadPoolExecutor
@@ -40,8 +41,18 @@ def _stale(obj, src):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def _stamp_ok():
+    """Objects built on another machine (architecture) are never reused."""
+    stamp = os.path.join(BUILD, "STAMP")
+    want = platform.machine() + " " + " ".join(ARCH)
+    ok = os.path.exists(stamp) and open(stamp).read().strip() == want
+    return ok, stamp, want
+
+
 def build(force=False, verbose=False):
     os.makedirs(BUILD, exist_ok=True)
+    ok, stamp, want = _stamp_ok()
+    force = force or not ok
     cc = nvcc()
     jobs = []
     for s in SOURCES:
@@ -74,6 +85,8 @@ def build(force=False, verbose=False):
         if p.returncode != 0:
             raise RuntimeError("link failed:\n%s\n%s" % (p.stdout, p.stderr))
         os.replace(tmp, SO)
+    with open(stamp, "w") as f:
+        f.write(want + "\n")
     return SO
 
 

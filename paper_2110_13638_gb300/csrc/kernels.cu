@@ -88,7 +88,7 @@ struct OpRows {
     u64* dst;
     int n, rows, N;
     uint8_t pmap[64];
-    __device__ int count() const { return n; }
+    __host__ __device__ int count() const { return n; }
     __device__ int nsub(int) const { return 1; }
     __device__ int prime(int p, int) const { return pmap[p % rows]; }
     __device__ bool direct(int, int) const { return false; }
@@ -246,7 +246,7 @@ struct OpTakeRowInv {
     const u64* in;
     u64* V;
     int n, L, row, N, pidx;
-    __device__ int count() const { return n; }
+    __host__ __device__ int count() const { return n; }
     __device__ int nsub(int) const { return 1; }
     __device__ int prime(int, int) const { return pidx; }
     __device__ bool direct(int, int) const { return false; }
@@ -262,7 +262,7 @@ struct OpDivFwd {
     const u64* addc;    // optional: residues of a constant added to comp 0, [n_ct][addc_stride]
     int n_poly, comps, L_in, L_out, N, addc_stride;
     DivC d;
-    __device__ int count() const { return n_poly * L_out; }
+    __host__ __device__ int count() const { return n_poly * L_out; }
     __device__ int nsub(int) const { return 1; }
     __device__ int prime(int p, int) const { return p % L_out; }
     __device__ bool direct(int, int) const { return false; }
@@ -321,7 +321,7 @@ struct OpDigitsInv {
     const u64* d3;      // [n][3][L][N]
     u64* D;             // [n][L][N]
     int n, L, N;
-    __device__ int count() const { return n * L; }
+    __host__ __device__ int count() const { return n * L; }
     __device__ int nsub(int) const { return 1; }
     __device__ int prime(int p, int) const { return p % L; }
     __device__ bool direct(int, int) const { return false; }
@@ -341,7 +341,7 @@ struct OpModUpMac {
     const u64* ksk;     // [L_top][2][L_top+1][N]
     u64* acc;           // [n][2][L+1][N]
     int n, L, N, Ltop;
-    __device__ int count() const { return n * (L + 1); }
+    __host__ __device__ int count() const { return n * (L + 1); }
     __device__ int nsub(int) const { return L; }
     __device__ int prime(int p, int) const
     {
@@ -379,7 +379,7 @@ struct OpAccPInv {
     const u64* acc;
     u64* Vp;            // [n][2][N]
     int n, L, N, Ltop;
-    __device__ int count() const { return n * 2; }
+    __host__ __device__ int count() const { return n * 2; }
     __device__ int nsub(int) const { return 1; }
     __device__ int prime(int, int) const { return Ltop; }
     __device__ bool direct(int, int) const { return false; }
@@ -395,7 +395,7 @@ struct OpModDown {
     u64* out;           // [n][2][L][N]
     int n, L, N;
     DivC d;
-    __device__ int count() const { return n * 2 * L; }
+    __host__ __device__ int count() const { return n * 2 * L; }
     __device__ int nsub(int) const { return 1; }
     __device__ int prime(int p, int) const { return p % L; }
     __device__ bool direct(int, int) const { return false; }
@@ -504,7 +504,7 @@ struct OpSecret {
     u64* s;
     u64 s0;
     int nprimes, N;
-    __device__ int count() const { return nprimes; }
+    __host__ __device__ int count() const { return nprimes; }
     __device__ int nsub(int) const { return 1; }
     __device__ int prime(int p, int) const { return p; }
     __device__ bool direct(int, int) const { return false; }
@@ -519,7 +519,7 @@ struct OpPublicKey {
     const u64* cdt;
     u64 sa, se;
     int Ltop, N;
-    __device__ int count() const { return Ltop; }
+    __host__ __device__ int count() const { return Ltop; }
     __device__ int nsub(int) const { return 2; }
     __device__ int prime(int p, int) const { return p; }
     __device__ bool direct(int, int) const { return false; }
@@ -549,7 +549,7 @@ struct OpRelinKey {
     const u64* se;
     u64 Pmod[33];       // P mod q_r
     int Ltop, N;
-    __device__ int count() const { return Ltop * (Ltop + 1); }
+    __host__ __device__ int count() const { return Ltop * (Ltop + 1); }
     __device__ int nsub(int) const { return 2; }
     __device__ int prime(int p, int) const { return p % (Ltop + 1); }
     __device__ bool direct(int, int) const { return false; }
@@ -612,7 +612,7 @@ struct OpEncrypt {
     const u64* cdt;
     u64 seed, first;
     int n, Ltop, N;
-    __device__ int count() const { return n * Ltop; }
+    __host__ __device__ int count() const { return n * Ltop; }
     __device__ int nsub(int) const { return 3; }
     __device__ int prime(int p, int) const { return p % Ltop; }
     __device__ bool direct(int, int) const { return false; }
@@ -653,7 +653,7 @@ struct OpDecrypt {
     const u64* s;
     i64* m;
     int n, L, N;
-    __device__ int count() const { return n; }
+    __host__ __device__ int count() const { return n; }
     __device__ int nsub(int) const { return 1; }
     __device__ int prime(int, int) const { return 0; }
     __device__ bool direct(int, int) const { return false; }
@@ -786,7 +786,7 @@ struct OpSignedRows {
     const i64* m;       // [n][N]
     u64* out;           // [n][L][N]
     int n, L, N;
-    __device__ int count() const { return n * L; }
+    __host__ __device__ int count() const { return n * L; }
     __device__ int nsub(int) const { return 1; }
     __device__ int prime(int p, int) const { return p % L; }
     __device__ bool direct(int, int) const { return false; }
