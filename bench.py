@@ -1,0 +1,391 @@
+#!/usr/bin/env python3
+"""Throughput of encrypted inference on one GB300 (or N replicas).
+
+One step = one request of the encrypted CNN on 28x28x1 images with 8192
+samples in the slots (RNS-CKKS, N = 16384, coefficient modulus [60, 40 x 7, 60],
+scale 2^40, depth 7 from Alg. autoHE / parameterise): encode 784 slot vectors,
+encrypt them, evaluate the graph (conv 5x5x5 stride 2 -> degree-3 sigmoid fit ->
+dense 720->100 -> sigmoid fit -> dense 100->10), decrypt and decode the 10
+outputs.  Keys are generated once, outside the timed region.
+
+Prints one JSON line.  --impl reference times the CPU oracle instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "encrypted samples/s per net"
+UNIT = "samples/s"
+DOMINANT = "keyswitch_modup_mac"
+# GB300 figures used by the ALU roofline (recipe: 152 SMs, 2070 MHz max SM clock;
+# 64 INT32 multiply lanes per SM = 4 SMSPs x 16)
+SMS, SM_MHZ_MAX, MUL32_LANES = 152, 2070.0, 64
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def workload(name):
+    from paper_2110_13638_gb300 import workloads as W
+    if name == "cnn":
+        g, x = W.cfg1()
+        return g, x, "encrypted CNN 28x28x1, conv5x5x5/2 -> sigmoid3 -> 720x100 -> sigmoid3 -> 100x10"
+    if name == "mlp":
+        g, x = W.cfg2()
+        return g, x, "encrypted yield MLP 64 -> 128 -> sigmoid3 -> 32 -> sigmoid3 -> 1"
+    if name == "dense_square":
+        g, x = W.cfg0()
+        return g, x, "dense 8 -> 4 then x^2"
+    raise SystemExit("unknown workload " + name)
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def modup_mac_mul32(ctx, plan):
+    """Algorithmic 32-bit multiplies of the key-switching ModUp + key inner
+    product kernel over one request (see the design notes): per ciphertext at
+    level L, L*L forward transforms of (N/2) log2 N Shoup butterflies (10
+    multiplies each) and 2 L (L+1) N key products (mul_mod: 4 for the 128-bit
+    product + 14 for the 128-bit reduction)."""
+    import math
+    N = ctx.N
+    lg = int(math.log2(N))
+    tot = 0
+    for n_ct, L in plan:
+        bfly = L * L * (N // 2) * lg
+        prods = 2 * L * (L + 1) * N
+        tot += n_ct * (bfly * 10 + prods * 18)
+    return tot
+
+
+def run_ours(args):
+    import torch
+    import __graft_entry__
+    from paper_2110_13638_gb300 import fhe
+
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    __graft_entry__.build()
+    g, x, desc = workload(args.workload)
+    gof, gcost = fhe.autohe(g)
+    N, bits = fhe.parameterise(max(gcost), 40, 1.5)
+    ctx = fhe.Context(N, bits, 40)
+    ctx.keygen(0)
+    G = fhe.Graph(g)
+    n_out, L_out = G.outputs(ctx)
+    n_in = x.shape[0]
+    samples = x.shape[1]
+    dev = torch.device("cuda", local)
+    slots = torch.tensor(x, dtype=torch.float64, device=dev)
+    host_slots = torch.tensor(x, dtype=torch.float64).pin_memory()
+    host_out = torch.empty((n_out, N // 2), dtype=torch.float64).pin_memory()
+    pt = ctx.empty_pt(n_in, ctx.L_top)
+    ct = ctx.empty_ct(n_in, ctx.L_top)
+    out = ctx.empty_ct(n_out, L_out)
+    m = torch.empty((n_out, N), dtype=torch.int64, device=dev)
+    z = torch.empty((n_out, N // 2), dtype=torch.float64, device=dev)
+    meta = [None]
+
+    def step(k, src):
+        ctx.encode(src, ctx.L_top, ctx.delta, pt)
+        ctx.encrypt(pt, 1_000_000 * rank + k * n_in, ct)
+        meta[0] = G.eval(ctx, [ct], out)
+        ctx.decrypt(out, L_out, m)
+        ctx.decode(m, meta[0][0][1], z)
+
+    for k in range(args.warmup):
+        step(k, slots)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- timed region: inputs resident in HBM (1.6 GB of ciphertexts per step > L2)
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = fhe.launch_count()
+    ctx.profile_begin(args.profile_family, 1 << 16)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(args.steps):
+        step(args.warmup + k, slots)
+    e1.record()
+    barrier()
+    dev_ms = e0.elapsed_time(e1)
+    prof_ms, prof_n, prof_timed = ctx.profile_end()
+    launches = fhe.launch_count() - launches0
+    clk = clocks.stop()
+
+    # ---- end to end: pinned host slots in, decoded slots out, every step
+    barrier()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record()
+    for k in range(args.steps):
+        slots.copy_(host_slots, non_blocking=True)
+        step(10 * args.steps + k, slots)
+        host_out.copy_(z, non_blocking=True)
+    e3.record()
+    barrier()
+    e2e_ms = e2.elapsed_time(e3)
+
+    t = torch.tensor([dev_ms, e2e_ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev_ms, e2e_ms = float(t[0]), float(t[1])
+    total_samples = samples * args.steps * world
+    value = total_samples / (dev_ms / 1000.0)
+    e2e = total_samples / (e2e_ms / 1000.0)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    # roofline of the dominant kernel: key-switching ModUp + key products
+    plan = []   # (ciphertexts, level) of every relinearisation in one request
+    L = ctx.L_top
+    for node in g["nodes"]:
+        if node["kind"] == "linear":
+            L -= 1
+        elif node["kind"] == "poly":
+            n = n_out_prev
+            plan += [(n, L), (n, L - 1)]
+            L -= 2
+        elif node["kind"] == "square":
+            plan += [(n_out_prev, L)]
+            L -= 1
+        if node["kind"] == "linear":
+            n_out_prev = node["n_out"]
+        elif node["kind"] == "input":
+            n_out_prev = node["n"]
+    roof = None
+    if args.profile_family == DOMINANT and prof_timed:
+        work = modup_mac_mul32(ctx, plan) * args.steps
+        per_launch_ms = prof_ms / prof_timed
+        achieved = work / (prof_ms / 1000.0) / 1e12
+        peak = SMS * MUL32_LANES * SM_MHZ_MAX * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
+                "unit": "T int32-mul/s", "frac": round(achieved / peak, 4), "traffic": args.traffic,
+                "kernel": DOMINANT, "launches": prof_n, "avg_launch_ms": round(per_launch_ms, 4),
+                "share_of_step": round(prof_ms / dev_ms, 4),
+                "peak_source": "derived: 152 SMs x 64 INT32 multiply lanes x 2070 MHz"}
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dev_ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (seeded U[0,1] 28x28 images, He-normal weights; Fashion-MNIST not available)",
+        "config": {"workload": desc, "N": N, "coeff_modulus_bits": bits, "log_scale": 40,
+                   "samples_per_request": samples, "input_ciphertexts": n_in, "output_ciphertexts": n_out,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (1.6 GB of ciphertexts per step)"},
+        "e2e": {"value": round(e2e, 2), "unit": UNIT, "h2d_bytes_per_step": int(slots.numel() * 8),
+                "d2h_bytes_per_step": int(z.numel() * 8)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "roofline": roof,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = oracle_sample(args.workload)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_sample(name):
+    """The oracle as it stands, single-threaded, on a bounded sample of one
+    request: per-unit times of every stage (encode+encrypt one input, one conv
+    output, one degree-3 activation at each level, one dense output, one
+    decrypt+decode), extrapolated to the request's unit counts."""
+    import numpy as np
+    from oracle import ckks
+    g, x, desc = workload(name)
+    from oracle.params import autohe, parameterise
+    from paper_2110_13638_gb300 import workloads as W
+    cost = max(autohe(g, W.input_nodes(g))[1])
+    p = parameterise(cost)
+    N, bits = p["poly_modulus_degree"], p["coeff_modulus"]
+    o = ckks.Context(N, bits, 40)
+    t0 = time.perf_counter()
+    o.keygen(0)
+    t_keygen = time.perf_counter() - t0
+    rng = np.random.default_rng(0)
+
+    def rand_ct(L, scale):
+        c = np.stack([np.stack([rng.integers(0, q, N, dtype=np.uint64) for q in o.q[:L]]) for _ in range(2)])
+        return ckks.Ciphertext(c, L, scale)
+
+    total = 0.0
+    parts = []
+    L = o.L_top
+    nodes = g["nodes"]
+    n_prev = nodes[0]["n"]
+    # stage: encode + encrypt (per input ciphertext)
+    k = 2
+    t0 = time.perf_counter()
+    first = [o.encrypt(o.encode(x[i]), i) for i in range(k)]
+    t = (time.perf_counter() - t0) / k
+    total += t * n_prev
+    parts.append("encode+encrypt %.3fs x %d" % (t, n_prev))
+    for node in nodes[1:]:
+        kind = node["kind"]
+        if kind == "linear":
+            rows = ckks.csr_rows(node)
+            idx, ws = rows[0]
+            need = int(max(idx)) + 1
+            src = first[:need] if L == o.L_top else []
+            src = src + [rand_ct(L, o.delta) for _ in range(need - len(src))]
+            t0 = time.perf_counter()
+            o.linear(src, [rows[0]], [0.0])
+            t = time.perf_counter() - t0
+            total += t * node["n_out"]
+            parts.append("linear(%d terms, L=%d) %.3fs x %d" % (len(idx), L, t, node["n_out"]))
+            n_prev = node["n_out"]
+            L -= 1
+        elif kind == "poly":
+            t0 = time.perf_counter()
+            o.poly3(rand_ct(L, o.delta), node["coeffs"])
+            t = time.perf_counter() - t0
+            total += t * n_prev
+            parts.append("poly3(L=%d) %.3fs x %d" % (L, t, n_prev))
+            L -= 2
+        elif kind == "square":
+            t0 = time.perf_counter()
+            o.square(rand_ct(L, o.delta))
+            t = time.perf_counter() - t0
+            total += t * n_prev
+            parts.append("square(L=%d) %.3fs x %d" % (L, t, n_prev))
+            L -= 1
+    t0 = time.perf_counter()
+    o.decode(o.decrypt(rand_ct(L, o.delta)), o.delta)
+    t = time.perf_counter() - t0
+    total += t * n_prev
+    parts.append("decrypt+decode %.3fs x %d" % (t, n_prev))
+    samples = x.shape[1]
+    return {"value": round(samples / total, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one unit of every stage, extrapolated to one request (%.1f s est.): %s; keygen %.1fs not counted"
+                      % (total, "; ".join(parts), t_keygen),
+            "host": _host_desc()}
+
+
+def _host_desc():
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for l in f:
+                if l.lower().startswith(("model name", "cpu part", "hardware")):
+                    model = l.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu": model}
+
+
+def run_reference(args):
+    rank, world, local = _env_rank()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        pass           # the oracle has no warm state worth priming beyond one sample
+    vals = []
+    last = None
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        last = oracle_sample(args.workload)
+        vals.append(last["value"])
+    wall = time.perf_counter() - t0
+    value = statistics.median(vals)
+    g, x, desc = workload(args.workload)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(x.shape[1] / value * 1000.0, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": desc}, "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": last["sample"], "host": last["host"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": round(wall, 1)}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cnn", choices=["cnn", "mlp", "dense_square"])
+    ap.add_argument("--profile-family", default=DOMINANT)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu dram bytes per launch of the dominant kernel (from profiles/)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -222,6 +222,20 @@ int fhe_graph_outputs(fhe_ctx* ctx, const fhe_graph* g, uint32_t* n_out_cts, uin
 int fhe_eval_graph(fhe_ctx* ctx, const fhe_graph* g, const uint64_t* const* d_in, uint32_t n_inputs,
                    uint64_t* d_out, fhe_ct_meta* out_meta, uint32_t out_cap, void* stream);
 
+/* ---- measurement (no counterpart in the paper) ----------------------------
+ * fhe_profile_begin: from now on, every launch of the kernel family `family`
+ * made through this context ("keyswitch_modup_mac", "mac", "rescale_ntt", ...,
+ * the names fhe_profile_families lists) is bracketed by CUDA events recorded
+ * on its own stream (up to max_launches launches).  fhe_profile_end
+ * synchronises those events and returns the summed device time in ms, the
+ * number of launches and how many of them were timed; profiling then stops. */
+int fhe_profile_begin(fhe_ctx* ctx, const char* family, uint32_t max_launches);
+int fhe_profile_end(fhe_ctx* ctx, double* total_ms, uint64_t* launches, uint64_t* timed);
+/* Comma-separated list of the kernel family names (static string). */
+const char* fhe_profile_families(void);
+/* Number of kernels this library has launched in the process so far. */
+int fhe_launch_count(uint64_t* out);
+
 const char* fhe_last_error(void);
 
 #ifdef __cplusplus

@@ -206,6 +206,7 @@ int fhe_autohe(const fhe_graph_desc* g, uint32_t* group_of, uint32_t group_of_ca
 // ---------------------------------------------------------------- context
 static void free_ctx(fhe_ctx* c)
 {
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     cudaFree(c->d_pc);
     cudaFree(c->d_tw_fwd);
     cudaFree(c->d_tw_inv);
@@ -574,6 +575,60 @@ int fhe_add_const(fhe_ctx* c, uint64_t* ct, const int64_t* h_c, uint32_t n_ct, u
     k_add_const(c, (u64*)ct, n_ct, level, dres, level, st);
     CUDA_LAST("add_const launch");
     return cuda_check(cudaStreamSynchronize(st), "add_const");
+}
+
+// ---------------------------------------------------------------- measurement
+static const char* kFamilies =
+    "ntt,rescale_intt,rescale_ntt,keyswitch_intt,keyswitch_modup_mac,keyswitch_acc_intt,keyswitch_moddown,"
+    "keygen,encrypt,decrypt,encode_ntt,encode_fft,decode_fft,mac,tensor,elementwise";
+
+const char* fhe_profile_families(void) { return kFamilies; }
+
+int fhe_profile_begin(fhe_ctx* c, const char* family, uint32_t max_launches)
+{
+    CHECK_CTX(c);
+    if (!family || !*family) return fail(FHE_EINVAL, "empty family");
+    std::string f(family);
+    std::string all = std::string(",") + kFamilies + ",";
+    if (all.find("," + f + ",") == std::string::npos) return fail(FHE_EINVAL, "unknown kernel family " + f);
+    if (max_launches == 0) max_launches = 1;
+    while (c->prof_ev.size() < 2 * (size_t)max_launches) {
+        cudaEvent_t e;
+        cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) return cuda_check(err, "cudaEventCreate");
+        c->prof_ev.push_back(e);
+    }
+    c->prof_family = f;
+    c->prof_used = 0;
+    c->prof_launches = 0;
+    return FHE_OK;
+}
+
+int fhe_profile_end(fhe_ctx* c, double* total_ms, uint64_t* launches, uint64_t* timed)
+{
+    CHECK_CTX(c);
+    double tot = 0.0;
+    for (size_t i = 0; i + 1 < c->prof_used; i += 2) {
+        cudaError_t e = cudaEventSynchronize(c->prof_ev[i + 1]);
+        if (e != cudaSuccess) return cuda_check(e, "profile event");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->prof_ev[i], c->prof_ev[i + 1]);
+        tot += ms;
+    }
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = c->prof_launches;
+    if (timed) *timed = c->prof_used / 2;
+    c->prof_family.clear();
+    c->prof_used = 0;
+    c->prof_launches = 0;
+    return FHE_OK;
+}
+
+int fhe_launch_count(uint64_t* out)
+{
+    if (!out) return fail(FHE_EINVAL, "null output");
+    *out = launch_count();
+    return FHE_OK;
 }
 
 }  // extern "C"

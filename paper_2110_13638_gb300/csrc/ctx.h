@@ -36,6 +36,12 @@ struct fhe_ctx {
     void* ws = nullptr;
     size_t ws_bytes = 0;
 
+    // measurement hook: CUDA events around every launch of one kernel family
+    mutable std::string prof_family;
+    mutable std::vector<cudaEvent_t> prof_ev;   // pairs (start, stop)
+    mutable size_t prof_used = 0;
+    mutable uint64_t prof_launches = 0;
+
     NttTables tabs() const
     {
         NttTables t;
@@ -78,6 +84,17 @@ struct fhe_graph {
 };
 
 namespace fhe {
+
+// every kernel launch of the library goes through this scope: it counts the
+// launch and, when the context profiles that family, brackets it with events
+struct LaunchScope {
+    const fhe_ctx* c;
+    cudaStream_t st;
+    long idx = -1;
+    LaunchScope(const fhe_ctx* c, const char* family, cudaStream_t st);
+    ~LaunchScope();
+};
+uint64_t launch_count();
 
 // error reporting (thread-local message)
 int fail(int code, const std::string& msg);

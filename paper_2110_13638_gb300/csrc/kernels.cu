@@ -8,6 +8,7 @@
 // gather multiply-accumulate of dense / convolution layers, and the
 // double-double / FP64 canonical-embedding FFTs of encode / decode.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 
 #include "ctx.h"
@@ -63,6 +64,28 @@ __device__ __forceinline__ u64 draw_uniform(u64 s0, int j, int r, const PrimeC& 
 }
 
 // ---------------------------------------------------------------- launch
+static std::atomic<uint64_t> g_launches{0};
+
+uint64_t launch_count() { return g_launches.load(); }
+
+LaunchScope::LaunchScope(const fhe_ctx* ctx, const char* family, cudaStream_t s) : c(ctx), st(s)
+{
+    g_launches.fetch_add(1);
+    if (!c->prof_family.empty() && c->prof_family == family) {
+        c->prof_launches += 1;
+        if (c->prof_used + 2 <= c->prof_ev.size()) {
+            idx = (long)c->prof_used;
+            c->prof_used += 2;
+            cudaEventRecord(c->prof_ev[idx], st);
+        }
+    }
+}
+
+LaunchScope::~LaunchScope()
+{
+    if (idx >= 0) cudaEventRecord(c->prof_ev[idx + 1], st);
+}
+
 template <bool INV, class Op>
 static void launch_ntt(const fhe_ctx* c, const Op& op, cudaStream_t st)
 {
@@ -78,12 +101,14 @@ static void launch_ntt(const fhe_ctx* c, const Op& op, cudaStream_t st)
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         configured = smem;
     }
+    LaunchScope ls(c, Op::family(), st);
     fn<<<count, thr, smem, st>>>(op, c->tabs());
 }
 
 // ---------------------------------------------------------------- ops
 // in-place / out-of-place transform of rows of polynomials
 struct OpRows {
+    static const char* family() { return "ntt"; }
     const u64* src;
     u64* dst;
     int n, rows, N;
@@ -147,6 +172,7 @@ void k_add(const fhe_ctx* c, const u64* a, const u64* b, u64* out, uint32_t n_ct
 {
     size_t total = (size_t)n_ct * comps * L * c->N;
     if (!total) return;
+    LaunchScope ls(c, "elementwise", st);
     k_add_kernel<<<ew_grid(total), 256, 0, st>>>(a, b, out, total, (int)L, (int)c->logN, c->d_pc);
 }
 
@@ -174,6 +200,7 @@ void k_tensor(const fhe_ctx* c, const u64* a, const u64* b, u64* out3, uint32_t 
     const size_t per_comp = (size_t)L * c->N;
     const size_t total = (size_t)n_ct * per_comp;
     if (!total) return;
+    LaunchScope ls(c, "tensor", st);
     k_tensor_kernel<<<ew_grid(total), 256, 0, st>>>(a, b, out3, per_comp, (int)n_ct, (int)L, (int)c->logN, c->d_pc);
 }
 
@@ -201,6 +228,7 @@ void k_mul_const(const fhe_ctx* c, const u64* in, u64* out, uint32_t n_ct, uint3
 {
     size_t total = (size_t)n_ct * comps * L_out * c->N;
     if (!total) return;
+    LaunchScope ls(c, "elementwise", st);
     k_mul_const_kernel<<<ew_grid(total), 256, 0, st>>>(in, out, total, (int)comps, (int)L_in, (int)L_out, (int)c->logN,
                                                        cres, (int)cstride, c->d_pc);
 }
@@ -222,6 +250,7 @@ void k_add_const(const fhe_ctx* c, u64* ct, uint32_t n_ct, uint32_t L, const u64
 {
     size_t total = (size_t)n_ct * L * c->N;
     if (!total) return;
+    LaunchScope ls(c, "elementwise", st);
     k_add_const_kernel<<<ew_grid(total), 256, 0, st>>>(ct, total, (int)L, (int)c->logN, cres, (int)cstride, c->d_pc);
 }
 
@@ -243,6 +272,7 @@ DivC make_divc(const fhe_ctx* c, uint32_t p_index, uint32_t n_targets)
 
 // INTT of one residue row per (ct, comp) into scratch V (coefficient form)
 struct OpTakeRowInv {
+    static const char* family() { return "rescale_intt"; }
     const u64* in;
     u64* V;
     int n, L, row, N, pidx;
@@ -256,6 +286,7 @@ struct OpTakeRowInv {
 
 // out_i = (in_i - NTT([v]_{q_i})) * p^{-1} (+ addc on comp 0)
 struct OpDivFwd {
+    static const char* family() { return "rescale_ntt"; }
     const u64* in;      // [n_poly][L_in][N]
     const u64* V;       // [n_poly][N]  coefficient form mod p
     u64* out;           // [n_poly][L_out][N]
@@ -318,6 +349,7 @@ void k_rescale(const fhe_ctx* c, const u64* in, u64* out, uint32_t n_ct, uint32_
 // ---------------------------------------------------------------- relinearise
 // step 1: digits D_j = INTT(d2_j) in [0, q_j)
 struct OpDigitsInv {
+    static const char* family() { return "keyswitch_intt"; }
     const u64* d3;      // [n][3][L][N]
     u64* D;             // [n][L][N]
     int n, L, N;
@@ -336,6 +368,7 @@ struct OpDigitsInv {
 // step 2: per (ct, target t in 0..L, t = L meaning P): for every digit u,
 // NTT(D_u mod q_t) * ksk_u[k][t], accumulated over u into acc[ct][k][t]
 struct OpModUpMac {
+    static const char* family() { return "keyswitch_modup_mac"; }
     const u64* d3;
     const u64* D;
     const u64* ksk;     // [L_top][2][L_top+1][N]
@@ -376,6 +409,7 @@ struct OpModUpMac {
 
 // step 3: INTT of the P residue of both accumulators
 struct OpAccPInv {
+    static const char* family() { return "keyswitch_acc_intt"; }
     const u64* acc;
     u64* Vp;            // [n][2][N]
     int n, L, N, Ltop;
@@ -389,6 +423,7 @@ struct OpAccPInv {
 
 // step 4: ModDown + add: out_k,t = d_k,t + (acc_k,t - NTT([v]_{q_t})) * P^{-1}
 struct OpModDown {
+    static const char* family() { return "keyswitch_moddown"; }
     const u64* d3;
     const u64* acc;
     const u64* Vp;
@@ -492,6 +527,7 @@ void k_linear_mac(const fhe_ctx* c, const u64* X, uint32_t n_in, const uint32_t*
     const int N = (int)c->N;
     const int tpb = N < 256 ? N : 256;
     dim3 grid(n_out, (N + tpb - 1) / tpb, 2 * L);
+    LaunchScope ls(c, "mac", st);
     k_mac_kernel<<<grid, tpb, 0, st>>>(X, row_ptr, col, Wres, Y, (int)L, N, c->d_pc);
 }
 
@@ -501,6 +537,7 @@ enum { DOM_SECRET = 1, DOM_PK_A = 2, DOM_PK_E = 3, DOM_KSK_A = 4, DOM_KSK_E = 5,
 
 // s (ternary) in every key prime
 struct OpSecret {
+    static const char* family() { return "keygen"; }
     u64* s;
     u64 s0;
     int nprimes, N;
@@ -514,6 +551,7 @@ struct OpSecret {
 
 // pk = (-a s + e, a) over the data primes: sub 0 = a (uniform), sub 1 = e
 struct OpPublicKey {
+    static const char* family() { return "keygen"; }
     const u64* s;
     u64* pk;            // [2][Ltop][N]
     const u64* cdt;
@@ -542,6 +580,7 @@ struct OpPublicKey {
 
 // ksk_j = (-a_j s + e_j + [r == j] P s^2, a_j) over every key prime r
 struct OpRelinKey {
+    static const char* family() { return "keygen"; }
     const u64* s;
     u64* ksk;           // [Ltop][2][Ltop+1][N]
     const u64* cdt;
@@ -606,6 +645,7 @@ void k_keygen(fhe_ctx* c, cudaStream_t st)
 // ---------------------------------------------------------------- encrypt
 // per (ct, r): sub 0 = u, sub 1 = e0, sub 2 = e1
 struct OpEncrypt {
+    static const char* family() { return "encrypt"; }
     const u64* pt;      // [n][Ltop][N]
     const u64* pk;      // [2][Ltop][N]
     u64* ct;            // [n][2][Ltop][N]
@@ -649,6 +689,7 @@ void k_encrypt(const fhe_ctx* c, const u64* pt, uint32_t n_ct, uint64_t first_id
 // ---------------------------------------------------------------- decrypt
 // prologue: c0 + c1 s at residue 0 (NTT form); INTT; centred lift
 struct OpDecrypt {
+    static const char* family() { return "decrypt"; }
     const u64* ct;
     const u64* s;
     i64* m;
@@ -783,6 +824,7 @@ __global__ void __launch_bounds__(512) k_encode_kernel(const double* __restrict_
 }
 
 struct OpSignedRows {
+    static const char* family() { return "encode_ntt"; }
     const i64* m;       // [n][N]
     u64* out;           // [n][L][N]
     int n, L, N;
@@ -810,8 +852,11 @@ void k_encode(const fhe_ctx* c, const double* slots, uint32_t n_ct, uint32_t L, 
     }
     int thr = N / 8;
     thr = thr < 32 ? 32 : (thr > 512 ? 512 : thr);
+    {
+    LaunchScope ls(c, "encode_fft", st);
     k_encode_kernel<<<2 * n_ct, thr, smem, st>>>(slots, c->d_slot_of, c->d_enc_tw, c->d_enc_twist,
                                                  scale / (double)(N / 2), N, m);
+    }
     OpSignedRows op{m, pt, (int)n_ct, (int)L, N};
     launch_ntt<false>(c, op, st);
 }
@@ -867,6 +912,7 @@ void k_decode(const fhe_ctx* c, const i64* m, uint32_t n_ct, double scale, doubl
     }
     int thr = N / 4;
     thr = thr < 32 ? 32 : (thr > 512 ? 512 : thr);
+    LaunchScope ls(c, "decode_fft", st);
     k_decode_kernel<<<n_ct, thr, smem, st>>>(m, c->d_slot_of, c->d_enc_tw, c->d_enc_twist, 1.0 / scale, N, slots);
 }
 

@@ -85,6 +85,10 @@ SIGNATURES = {
     "fhe_graph_destroy": [_P],
     "fhe_graph_outputs": [_P, _P, _P, _P],
     "fhe_eval_graph": [_P, _P, _P, _U32, _P, _P, _U32, _P],
+    "fhe_profile_begin": [_P, ctypes.c_char_p, _U32],
+    "fhe_profile_end": [_P, _P, _P, _P],
+    "fhe_profile_families": [],
+    "fhe_launch_count": [_P],
     "fhe_last_error": [],
 }
 
@@ -101,7 +105,7 @@ def lib():
         for name, args in SIGNATURES.items():
             f = getattr(L, name)
             f.argtypes = args
-            f.restype = ctypes.c_char_p if name == "fhe_last_error" else ctypes.c_int
+            f.restype = ctypes.c_char_p if name in ("fhe_last_error", "fhe_profile_families") else ctypes.c_int
         _lib = L
     return _lib
 
@@ -135,6 +139,16 @@ def parameterise(cost, log_scale=40, special_mult=1.5):
     nb = ctypes.c_uint32()
     _check(lib().fhe_parameterise(cost, log_scale, special_mult, ctypes.byref(N), bits, 64, ctypes.byref(nb)))
     return N.value, [bits[i] for i in range(nb.value)]
+
+
+def launch_count():
+    out = ctypes.c_uint64()
+    _check(lib().fhe_launch_count(ctypes.byref(out)))
+    return out.value
+
+
+def profile_families():
+    return lib().fhe_profile_families().decode().split(",")
 
 
 def prime_chain(N, bits):
@@ -222,6 +236,18 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    # -- measurement -------------------------------------------------------------
+    def profile_begin(self, family, max_launches=65536):
+        _check(lib().fhe_profile_begin(self.h, family.encode(), max_launches))
+
+    def profile_end(self):
+        """-> (total device ms, launches, timed launches) of the profiled family"""
+        ms = ctypes.c_double()
+        n = ctypes.c_uint64()
+        t = ctypes.c_uint64()
+        _check(lib().fhe_profile_end(self.h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(t)))
+        return ms.value, n.value, t.value
 
     # -- allocation helpers (torch device memory) --------------------------
     def empty_ct(self, n, level, comps=2):
