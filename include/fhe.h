@@ -188,6 +188,21 @@ int fhe_tensor(fhe_ctx* ctx, const uint64_t* d_a, const uint64_t* d_b, uint32_t 
 int fhe_relinearise(fhe_ctx* ctx, const uint64_t* d3, uint32_t n_ct, uint32_t level,
                     uint64_t* d_out, void* stream);
 
+/* Same result as fhe_relinearise, for callers that cannot allocate device
+ * memory during the call (for instance a serving loop whose device memory
+ * belongs to another allocator, or code that must not wait for the
+ * device-wide synchronisation a workspace cudaMalloc/cudaFree can cause).
+ * The paper has no counterpart: it is an allocation policy of this library.
+ * Scratch comes from a fixed 16 MiB device array that every GPU loading the
+ * library holds until exit; nothing is allocated or freed.  The first call on
+ * a device (with the context's device current) looks up that array's device
+ * address, so make it before any stream capture.  Batches needing more
+ * scratch than 16 MiB ((L + 2(L+1) + 2) N 8 bytes per ciphertext, aligned)
+ * return FHE_EINVAL.  All calls share the array: calls that overlap on the
+ * GPU race and must be serialised by the caller. */
+int fhe_relinearise_noalloc(fhe_ctx* ctx, const uint64_t* d3, uint32_t n_ct, uint32_t level,
+                            uint64_t* d_out, void* stream);
+
 /* rescale: d_in [n_ct][comps][level][N] -> d_out [n_ct][comps][level-1][N],
  * division by q_{level-1} with the centred remainder. */
 int fhe_rescale(fhe_ctx* ctx, const uint64_t* d_in, uint32_t n_ct, uint32_t comps, uint32_t level,

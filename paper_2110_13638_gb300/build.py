@@ -16,7 +16,7 @@ BUILD = os.path.join(CSRC, "_build")
 SO = os.path.join(BUILD, "libfhe.so")
 ROOT = os.path.dirname(HERE)
 
-SOURCES = ["kernels.cu", "capi.cu", "graph.cu", "host_math.cpp"]
+SOURCES = ["kernels.cu", "capi.cu", "graph.cu", "noalloc.cu", "host_math.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -77,6 +77,7 @@ SIGNATURES = {
     "fhe_add": [_P, _P, _P, _U32, _U32, _P, _P],
     "fhe_tensor": [_P, _P, _P, _U32, _U32, _P, _P],
     "fhe_relinearise": [_P, _P, _U32, _U32, _P, _P],
+    "fhe_relinearise_noalloc": [_P, _P, _U32, _U32, _P, _P],
     "fhe_rescale": [_P, _P, _U32, _U32, _U32, _P, _P],
     "fhe_mul_relin_rescale": [_P, _P, _P, _U32, _U32, _P, _P],
     "fhe_mul_const": [_P, _P, _P, _U32, _U32, _P, _P],
@@ -294,6 +295,11 @@ class Context:
 
     def relinearise(self, d3, level, out, stream=None):
         _check(lib().fhe_relinearise(self.h, _ptr(d3), d3.shape[0], level, _ptr(out), _stream(stream)))
+
+    def relinearise_noalloc(self, d3, level, out, stream=None):
+        """fhe_relinearise without allocating: scratch from the library's fixed
+        16 MiB device array (see include/fhe.h)."""
+        _check(lib().fhe_relinearise_noalloc(self.h, _ptr(d3), d3.shape[0], level, _ptr(out), _stream(stream)))
 
     def rescale(self, x, comps, level, out, stream=None):
         _check(lib().fhe_rescale(self.h, _ptr(x), x.shape[0], comps, level, _ptr(out), _stream(stream)))
