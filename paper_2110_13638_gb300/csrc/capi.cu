@@ -5,6 +5,7 @@
 // whose node receptors launch the kernels of kernels.cu.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -221,6 +222,58 @@ static void free_ctx(fhe_ctx* c)
     delete c;
 }
 
+// Time every NTT schedule on a batch of forward transforms (two per SM over
+// all primes) and keep the fastest; FHE_NTT_VARIANT overrides.
+static int autotune_ntt(fhe_ctx* c)
+{
+    const char* env = std::getenv("FHE_NTT_VARIANT");
+    if (env && *env) {
+        int v = std::atoi(env);
+        if (v < 0 || v >= kNttVariants) return fail(FHE_EINVAL, "FHE_NTT_VARIANT out of range");
+        c->ntt_variant = v;
+        return FHE_OK;
+    }
+    const uint32_t rows = c->L_top + 1;
+    uint32_t groups = (304 + rows - 1) / rows;
+    const size_t bytes = (size_t)groups * rows * c->N * 8;
+    u64* buf = nullptr;
+    cudaError_t e = cudaMalloc((void**)&buf, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_check(e, "autotune buffer");
+    }
+    cudaMemset(buf, 0, bytes);
+    uint8_t pm[64];
+    for (uint32_t r = 0; r < rows; ++r) pm[r] = (uint8_t)r;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best = 1e30f;
+    for (int v = 0; v < kNttVariants; ++v) {
+        c->ntt_variant = v;
+        k_ntt_rows(c, buf, groups, rows, pm, true, nullptr);       // warm-up
+        cudaEventRecord(a, nullptr);
+        for (int it = 0; it < 3; ++it) k_ntt_rows(c, buf, groups, rows, pm, true, nullptr);
+        cudaEventRecord(b, nullptr);
+        e = cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (e != cudaSuccess) break;
+        const float us = ms * 1000.f / (3.f * groups * rows);
+        c->ntt_variant_us[v] = us;
+        if (us < best) best = us;
+    }
+    int pick = 0;
+    for (int v = 0; v < kNttVariants; ++v)
+        if (c->ntt_variant_us[v] == best) { pick = v; break; }
+    c->ntt_variant = pick;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(buf);
+    if (e != cudaSuccess) return cuda_check(e, "autotune");
+    return FHE_OK;
+}
+
 int fhe_ctx_create(uint32_t N, const uint32_t* bits, uint32_t n_bits, uint32_t log_scale, fhe_ctx** out)
 {
     if (!out || !bits) return fail(FHE_EINVAL, "null argument");
@@ -306,6 +359,11 @@ int fhe_ctx_create(uint32_t N, const uint32_t* bits, uint32_t n_bits, uint32_t l
     }
     c->key_bytes = np * sizeof(PrimeC) + 2 * twf.size() * sizeof(ulonglong2) + cdt.size() * 8 +
                    (etw.size() + etwist.size()) * sizeof(double4) + slot_of.size() * 4;
+    rc = autotune_ntt(c);
+    if (rc != FHE_OK) {
+        free_ctx(c);
+        return rc;
+    }
     *out = c;
     return FHE_OK;
 }
@@ -329,6 +387,8 @@ int fhe_ctx_query(const fhe_ctx* c, fhe_ctx_info* out)
     out->log_scale = c->log_scale;
     for (size_t i = 0; i < c->primes.size() && i < 64; ++i) out->primes[i] = c->primes[i];
     out->key_bytes = c->key_bytes;
+    out->ntt_variant = (uint32_t)c->ntt_variant;
+    for (int v = 0; v < kNttVariants && v < 4; ++v) out->ntt_variant_us[v] = c->ntt_variant_us[v];
     return FHE_OK;
 }
 

@@ -14,6 +14,8 @@ struct fhe_ctx {
     std::vector<PrimeC> pc;        // host copy of the per-prime constants
     double delta = 0.0;
     int device = 0;
+    int ntt_variant = 0;           // NTT schedule (see ntt_variant_name), autotuned
+    float ntt_variant_us[3] = {0, 0, 0};   // autotuner timings per variant (us per transform)
 
     // resident tables
     PrimeC* d_pc = nullptr;
@@ -163,5 +165,7 @@ void k_encode(const fhe_ctx* c, const double* slots, uint32_t n_ct, uint32_t L, 
 void k_decode(const fhe_ctx* c, const i64* m, uint32_t n_ct, double scale, double* slots, cudaStream_t st);
 
 uint64_t stream_key(uint64_t seed, uint64_t domain, uint64_t object);
+const char* ntt_variant_name(int v);
+constexpr int kNttVariants = 3;
 
 }  // namespace fhe

@@ -16,8 +16,6 @@
 
 namespace fhe {
 
-static constexpr int kLogR = 4;      // radix-16 register passes
-static constexpr int kMaxT = 512;    // threads per transform block (128 registers each)
 static constexpr u64 kGamma = 0x9E3779B97F4A7C15ull;
 
 // ---------------------------------------------------------------- PRNG
@@ -86,16 +84,16 @@ LaunchScope::~LaunchScope()
     if (idx >= 0) cudaEventRecord(c->prof_ev[idx + 1], st);
 }
 
-template <bool INV, class Op>
-static void launch_ntt(const fhe_ctx* c, const Op& op, cudaStream_t st)
+// NTT schedule variants (radix of the register passes, threads per block);
+// the context's autotuner picks one per ring degree.
+template <bool INV, int LOGR, int MAXT, class Op>
+static void launch_ntt_v(const fhe_ctx* c, const Op& op, int count, cudaStream_t st)
 {
-    const int count = op.count();
-    if (count <= 0) return;
     const int N = (int)c->N;
-    int thr = N / 16;
-    thr = thr < 32 ? 32 : (thr > kMaxT ? kMaxT : thr);
+    int thr = N >> LOGR;
+    thr = thr < 32 ? 32 : (thr > MAXT ? MAXT : thr);
     const size_t smem = (size_t)ntt_smem_words(N) * sizeof(u64);
-    auto fn = k_ntt_op<INV, kLogR, kMaxT, Op>;
+    auto fn = k_ntt_op<INV, LOGR, MAXT, Op>;
     static size_t configured = 0;        // per instantiation
     if (configured < smem) {
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -103,6 +101,27 @@ static void launch_ntt(const fhe_ctx* c, const Op& op, cudaStream_t st)
     }
     LaunchScope ls(c, Op::family(), st);
     fn<<<count, thr, smem, st>>>(op, c->tabs());
+}
+
+template <bool INV, class Op>
+static void launch_ntt(const fhe_ctx* c, const Op& op, cudaStream_t st)
+{
+    const int count = op.count();
+    if (count <= 0) return;
+    switch (c->ntt_variant) {
+    case 1: launch_ntt_v<INV, 3, 1024>(c, op, count, st); break;
+    case 2: launch_ntt_v<INV, 4, 1024>(c, op, count, st); break;
+    default: launch_ntt_v<INV, 4, 512>(c, op, count, st); break;
+    }
+}
+
+const char* ntt_variant_name(int v)
+{
+    switch (v) {
+    case 1: return "radix-8 passes, 1024 threads";
+    case 2: return "radix-16 passes, 1024 threads";
+    default: return "radix-16 passes, 512 threads";
+    }
 }
 
 // ---------------------------------------------------------------- ops

@@ -1,0 +1,139 @@
+"""Full-size workloads on the GPU, in the launch configuration bench.py times.
+
+- The encrypted CNN's first two blocks (conv 5x5x5 stride 2 over 784 input
+  ciphertexts, then the degree-3 sigmoid fit over 720 ciphertexts) at
+  N = 16384, L = 8: sampled outputs are recomputed one by one by the oracle
+  (each needs only its 25 input encryptions) and must be bit-exact.
+- The whole CNN and the whole yield MLP: decrypted outputs within 1e-4 of the
+  FP64 plaintext forward pass with the same polynomial activations.
+- Every NTT schedule the autotuner can pick gives bit-exact results."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import __graft_entry__
+from oracle import ckks
+from paper_2110_13638_gb300 import fhe, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+BITS9 = [60] + [40] * 7 + [60]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    c = fhe.Context(16384, BITS9, 40)
+    c.keygen(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def octx():
+    o = ckks.Context(16384, BITS9, 40)
+    o.keygen(0)
+    return o
+
+
+def encrypt_all(ctx, x, first=0):
+    n = x.shape[0]
+    pt = ctx.empty_pt(n, ctx.L_top)
+    ctx.encode(torch.tensor(x, device="cuda"), ctx.L_top, ctx.delta, pt)
+    ct = ctx.empty_ct(n, ctx.L_top)
+    ctx.encrypt(pt, first, ct)
+    return ct
+
+
+def run_graph(ctx, graph, ct):
+    G = fhe.Graph(graph)
+    n_out, L_out = G.outputs(ctx)
+    out = ctx.empty_ct(n_out, L_out)
+    meta = G.eval(ctx, [ct], out)
+    return out, meta, L_out
+
+
+def test_cnn_first_blocks_sampled_bit_exact(ctx, octx):
+    g, x = W.cfg1()
+    head = W.chain_graph(784, [g["nodes"][1], g["nodes"][2]])      # conv, sigmoid fit
+    ct = encrypt_all(ctx, x)
+    out, meta, L_out = run_graph(ctx, head, ct)
+    assert out.shape[0] == 720 and L_out == 5
+    rows = ckks.csr_rows(g["nodes"][1])
+    for k in (0, 363, 719):
+        idx, ws = rows[k]
+        xs = [octx.encrypt(octx.encode(x[int(i)]), int(i)) for i in idx]
+        y = octx.linear(xs, [(np.arange(len(idx)), ws)], [g["nodes"][1]["bias"][k]])[0]
+        y = octx.poly3(y, g["nodes"][2]["coeffs"])
+        got = out[k:k + 1].clone()
+        ctx.ct_convert(got, L_out, True, got)
+        torch.cuda.synchronize()
+        assert np.array_equal(fhe.raw_u64(got)[0], y.c), k
+        assert meta[k][1] == y.scale
+
+
+def _decrypted(ctx, out, meta, L_out):
+    n = out.shape[0]
+    m = torch.empty((n, ctx.N), dtype=torch.int64, device="cuda")
+    ctx.decrypt(out, L_out, m)
+    z = torch.empty((n, ctx.N // 2), dtype=torch.float64, device="cuda")
+    ctx.decode(m, meta[0][1], z)
+    return z.cpu().numpy()
+
+
+@pytest.mark.parametrize("builder", [W.cfg1, W.cfg2])
+def test_full_network_matches_fp64(ctx, builder):
+    g, x = builder()
+    ct = encrypt_all(ctx, x, first=5000)
+    out, meta, L_out = run_graph(ctx, g, ct)
+    assert L_out == 1
+    z = _decrypted(ctx, out, meta, L_out)
+    ref = ckks.forward_fp64(g, W.input_nodes(g), [x])
+    (node, r), = ref.items()
+    err = float(np.max(np.abs(z - r)))
+    assert err < 1e-4, (err, float(np.max(np.abs(r))))
+
+
+def test_dense_square_full_matches_fp64():
+    __graft_entry__.build()
+    c = fhe.Context(8192, [60, 40, 40, 60], 40)
+    c.keygen(0)
+    g, x = W.cfg0()
+    ct = encrypt_all(c, x)
+    out, meta, L_out = run_graph(c, g, ct)
+    z = _decrypted(c, out, meta, L_out)
+    ref = ckks.forward_fp64(g, W.input_nodes(g), [x])
+    (node, r), = ref.items()
+    assert float(np.max(np.abs(z - r))) < 1e-4
+    c.close()
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_every_ntt_schedule_bit_exact(octx, variant):
+    __graft_entry__.build()
+    os.environ["FHE_NTT_VARIANT"] = str(variant)
+    try:
+        c = fhe.Context(16384, BITS9, 40)
+    finally:
+        del os.environ["FHE_NTT_VARIANT"]
+    assert c.ntt_variant == variant
+    c.keygen(0)
+    rng = np.random.default_rng(variant)
+    L = 6
+    A = np.stack([np.stack([rng.integers(0, q, 16384, dtype=np.uint64) for q in octx.q[:L]]) for _ in range(2)])
+    B = np.stack([np.stack([rng.integers(0, q, 16384, dtype=np.uint64) for q in octx.q[:L]]) for _ in range(2)])
+    ta = torch.from_numpy(A[None].view(np.int64).copy()).cuda()
+    tb = torch.from_numpy(B[None].view(np.int64).copy()).cuda()
+    c.ct_convert(ta, L, False, ta)
+    c.ct_convert(tb, L, False, tb)
+    out = c.empty_ct(1, L - 1)
+    c.mul_relin_rescale(ta, tb, L, out)
+    c.ct_convert(out, L - 1, True, out)
+    torch.cuda.synchronize()
+    want = octx.rescale(octx.relinearise(octx.tensor(ckks.Ciphertext(A, L, 1.0), ckks.Ciphertext(B, L, 1.0)))).c
+    assert np.array_equal(fhe.raw_u64(out)[0], want)
+    c.close()
