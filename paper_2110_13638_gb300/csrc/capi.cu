@@ -398,7 +398,7 @@ int fhe_keygen(fhe_ctx* c, uint64_t seed, void* stream)
     cudaStream_t st = (cudaStream_t)stream;
     const size_t N = c->N, Lt = c->L_top;
     if (!c->d_s) {
-        size_t bs = (Lt + 1) * N * 8, bp = 2 * Lt * N * 8, bk = Lt * 2 * (Lt + 1) * N * 8;
+        size_t bs = (Lt + 1) * N * 8, bp = 2 * Lt * N * 8, bk = Lt * 2 * (Lt + 1) * N * 16;
         cudaError_t e = cudaMalloc((void**)&c->d_s, bs);
         if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_pk, bp);
         if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_ksk, bk);
@@ -450,7 +450,11 @@ int fhe_encrypt(fhe_ctx* c, const uint64_t* d_pt, uint32_t n_ct, uint64_t first_
     CHECK_KEYS(c);
     if (n_ct == 0) return FHE_OK;
     if (!d_pt || !d_ct) return fail(FHE_EINVAL, "null buffer");
-    k_encrypt(c, (const u64*)d_pt, n_ct, first_ct_id, (u64*)d_ct, (cudaStream_t)stream);
+    Arena ar;
+    const size_t need = encrypt_scratch_bytes(c, n_ct);
+    int rc = ws_reserve(c, need, &ar);
+    if (rc) return rc;
+    k_encrypt(c, (const u64*)d_pt, n_ct, first_ct_id, (u64*)d_ct, ar.take(need), (cudaStream_t)stream);
     CUDA_LAST("encrypt launch");
     return FHE_OK;
 }

@@ -31,7 +31,7 @@ struct fhe_ctx {
     uint64_t seed = 0;
     u64* d_s = nullptr;            // [L_top + 1][N]
     u64* d_pk = nullptr;           // [2][L_top][N]
-    u64* d_ksk = nullptr;          // [L_top][2][L_top + 1][N]
+    ulonglong2* d_ksk = nullptr;   // [L_top][2][L_top + 1][N] (key word, Shoup quotient)
     size_t key_bytes = 0;
 
     // call workspace (grows on demand)
@@ -70,7 +70,10 @@ struct fhe_node_const {
     void* buf = nullptr;       // one device allocation holding the arrays below
     uint32_t* row_ptr = nullptr;
     uint32_t* col = nullptr;
-    u64* W = nullptr;          // LINEAR: [nnz][L] weight residues
+    u64* W = nullptr;          // LINEAR: weight residues, tile order (see k_linear_mac_tiled)
+    uint4* tiles = nullptr;    // LINEAR: row tiles {col_off, K, n_rows, w_off}
+    uint32_t* tile_rows = nullptr;
+    uint32_t n_tiles = 0;
     u64* bias = nullptr;       // LINEAR: [n_out][L-1] bias residues
     u64* c3 = nullptr;         // POLY: constant residues (shared by all ciphertexts)
     u64* c2 = nullptr;
@@ -156,8 +159,15 @@ void k_add_const(const fhe_ctx* c, u64* ct, uint32_t n_ct, uint32_t L, const u64
 void k_linear_mac(const fhe_ctx* c, const u64* X, uint32_t n_in, const uint32_t* row_ptr, const uint32_t* col,
                   const u64* Wres, uint32_t n_out, uint32_t L, u64* Y, cudaStream_t st);
 
+// tiled gather-MAC (rows sharing a column list computed together)
+constexpr int kMacTile = 8;
+void k_linear_mac_tiled(const fhe_ctx* c, const u64* X, const uint4* tiles, uint32_t n_tiles, const uint32_t* rows,
+                        const uint32_t* col, const u64* W, uint32_t L, u64* Y, cudaStream_t st);
+
 void k_keygen(fhe_ctx* c, cudaStream_t st);
-void k_encrypt(const fhe_ctx* c, const u64* pt, uint32_t n_ct, uint64_t first_id, u64* ct, cudaStream_t st);
+size_t encrypt_scratch_bytes(const fhe_ctx* c, uint32_t n_ct);
+void k_encrypt(const fhe_ctx* c, const u64* pt, uint32_t n_ct, uint64_t first_id, u64* ct, void* scratch,
+               cudaStream_t st);
 void k_decrypt(const fhe_ctx* c, const u64* ct, uint32_t n_ct, uint32_t L, i64* m, cudaStream_t st);
 size_t encode_scratch_bytes(const fhe_ctx* c, uint32_t n_ct);
 void k_encode(const fhe_ctx* c, const double* slots, uint32_t n_ct, uint32_t L, double scale, u64* pt,

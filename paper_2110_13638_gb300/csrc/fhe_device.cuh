@@ -101,7 +101,10 @@ __device__ __forceinline__ int spad(int j) { return j + (j >> 4); }
 
 __host__ __device__ constexpr int ntt_smem_words(int N) { return N + (N >> 4); }
 
-// forward Cooley-Tukey pass over stages s0 .. s0+K-1 (distances N>>(s+1))
+// forward Cooley-Tukey pass over stages s0 .. s0+K-1 (distances N>>(s+1)).
+// A group is the 2^K elements j0 + i 2^ltb; at stage l its pairs (i, i+h),
+// h = 2^(K-1-l), with i = m 2h + t share the twiddle psi_rev[2^st + g 2^l + m],
+// so each group loads 2^K - 1 twiddles per pass.
 template <int K>
 __device__ __forceinline__ void ntt_fwd_pass(u64* sm, int logN, int s0, const ulonglong2* __restrict__ tw,
                                              u64 q, u64 q2, int tid, int nthr)
@@ -120,17 +123,19 @@ __device__ __forceinline__ void ntt_fwd_pass(u64* sm, int logN, int s0, const ul
 #pragma unroll
         for (int l = 0; l < K; ++l) {
             const int h = R >> (l + 1);
-            const int st = s0 + l;
+            const ulonglong2* twl = tw + (1 << (s0 + l)) + (g << l);
 #pragma unroll
-            for (int i = 0; i < R; ++i) {
-                if (i & h) continue;
-                const int j = j0 + (i << ltb);
-                const ulonglong2 w = __ldg(&tw[(1 << st) + (j >> (logN - st))]);
-                u64 X = x[i];
-                X = X >= q2 ? X - q2 : X;
-                const u64 T = mul_shoup_lazy(x[i + h], w.x, w.y, q);
-                x[i] = X + T;
-                x[i + h] = X + q2 - T;
+            for (int m = 0; m < (1 << l); ++m) {
+                const ulonglong2 w = __ldg(&twl[m]);
+#pragma unroll
+                for (int t = 0; t < h; ++t) {
+                    const int i = m * 2 * h + t;
+                    u64 X = x[i];
+                    X = X >= q2 ? X - q2 : X;
+                    const u64 T = mul_shoup_lazy(x[i + h], w.x, w.y, q);
+                    x[i] = X + T;
+                    x[i + h] = X + q2 - T;
+                }
             }
         }
 #pragma unroll
@@ -138,7 +143,9 @@ __device__ __forceinline__ void ntt_fwd_pass(u64* sm, int logN, int s0, const ul
     }
 }
 
-// inverse Gentleman-Sande pass over distances 2^lt0 .. 2^(lt0+K-1)
+// inverse Gentleman-Sande pass over distances 2^lt0 .. 2^(lt0+K-1); at stage l
+// (distance 2^(lt0+l), h = 2^l) the pairs i = m 2h + t share the twiddle
+// psi_inv_rev[N / 2^(lt0+l+1) + g 2^(K-l-1) + m].
 template <int K>
 __device__ __forceinline__ void ntt_inv_pass(u64* sm, int logN, int lt0, const ulonglong2* __restrict__ tw,
                                              u64 q, u64 q2, int tid, int nthr)
@@ -156,17 +163,19 @@ __device__ __forceinline__ void ntt_inv_pass(u64* sm, int logN, int lt0, const u
 #pragma unroll
         for (int l = 0; l < K; ++l) {
             const int h = 1 << l;
-            const int lt = lt0 + l;                       // distance 2^lt
+            const ulonglong2* twl = tw + (N >> (lt0 + l + 1)) + (g << (K - l - 1));
 #pragma unroll
-            for (int i = 0; i < R; ++i) {
-                if (i & h) continue;
-                const int j = j0 + (i << lt0);
-                const ulonglong2 w = __ldg(&tw[(N >> (lt + 1)) + (j >> (lt + 1))]);
-                const u64 X = x[i], Y = x[i + h];
-                u64 S = X + Y;
-                S = S >= q2 ? S - q2 : S;
-                x[i] = S;
-                x[i + h] = mul_shoup_lazy(X + q2 - Y, w.x, w.y, q);
+            for (int m = 0; m < (R >> (l + 1)); ++m) {
+                const ulonglong2 w = __ldg(&twl[m]);
+#pragma unroll
+                for (int t = 0; t < h; ++t) {
+                    const int i = m * 2 * h + t;
+                    const u64 X = x[i], Y = x[i + h];
+                    u64 S = X + Y;
+                    S = S >= q2 ? S - q2 : S;
+                    x[i] = S;
+                    x[i + h] = mul_shoup_lazy(X + q2 - Y, w.x, w.y, q);
+                }
             }
         }
 #pragma unroll
@@ -233,13 +242,19 @@ struct NttTables {
 
 // ---------------------------------------------------------------- kernel
 // Generic batched transform with a fused prologue and epilogue.  Op supplies
+//   static const char* family()             -- name for the measurement hook
 //   int  count() const                      -- number of transform units
 //   int  nsub(int p) const                  -- transforms in unit p (run in order)
 //   int  prime(int p, int u) const          -- key-prime index of transform u
 //   bool direct(int p, int u) const         -- skip the transform (store reads input itself)
 //   u64  load(int p, int u, int j, const PrimeC&) const   -- input value in [0, q)
-//   void store(int p, int u, int j, u64 v, const PrimeC&) const -- v in [0, q)
-// Grid-stride over units so one launch may cover any batch.
+//   Pre  pre(int p, int u, int j) const     -- global words the epilogue needs (issued
+//                                              for several j before any store)
+//   void store(int p, int u, int j, u64 v, const Pre&, const PrimeC&) const -- v in [0, q)
+// Grid-stride over units so one launch may cover any batch.  Prologue loads
+// and epilogue pre-loads are issued kUnroll at a time per thread.
+constexpr int kUnroll = 4;
+
 template <bool INV, int LOGR, int MAXT, class Op>
 __global__ void __launch_bounds__(MAXT, 1) k_ntt_op(Op op, NttTables T)
 {
@@ -252,17 +267,42 @@ __global__ void __launch_bounds__(MAXT, 1) k_ntt_op(Op op, NttTables T)
         for (int u = 0; u < ns; ++u) {
             const int pi = op.prime(p, u);
             const PrimeC P = T.pc[pi];
-            if (op.direct(p, u)) {
-                for (int j = tid; j < N; j += nthr) op.store(p, u, j, 0, P);
-                continue;
+            const bool dir = op.direct(p, u);
+            if (!dir) {
+                for (int j0 = tid; j0 < N; j0 += nthr * kUnroll) {
+                    u64 v[kUnroll];
+#pragma unroll
+                    for (int k = 0; k < kUnroll; ++k) {
+                        const int j = j0 + k * nthr;
+                        v[k] = j < N ? op.load(p, u, j, P) : 0;
+                    }
+#pragma unroll
+                    for (int k = 0; k < kUnroll; ++k) {
+                        const int j = j0 + k * nthr;
+                        if (j < N) sm[spad(j)] = v[k];
+                    }
+                }
+                __syncthreads();
+                if (INV) ntt_inv_smem<LOGR>(sm, logN, T.tw_inv + (size_t)pi * N, P.q, tid, nthr);
+                else ntt_fwd_smem<LOGR>(sm, logN, T.tw_fwd + (size_t)pi * N, P.q, tid, nthr);
             }
-            for (int j = tid; j < N; j += nthr) sm[spad(j)] = op.load(p, u, j, P);
-            __syncthreads();
-            if (INV) ntt_inv_smem<LOGR>(sm, logN, T.tw_inv + (size_t)pi * N, P.q, tid, nthr);
-            else ntt_fwd_smem<LOGR>(sm, logN, T.tw_fwd + (size_t)pi * N, P.q, tid, nthr);
-            for (int j = tid; j < N; j += nthr) {
-                const u64 x = sm[spad(j)];
-                op.store(p, u, j, INV ? inv_final(x, P) : fwd_final(x, P.q), P);
+            for (int j0 = tid; j0 < N; j0 += nthr * kUnroll) {
+                typename Op::Pre pr[kUnroll];
+                u64 v[kUnroll];
+#pragma unroll
+                for (int k = 0; k < kUnroll; ++k) {
+                    const int j = j0 + k * nthr;
+                    if (j < N) {
+                        pr[k] = op.pre(p, u, j);
+                        const u64 x = dir ? 0 : sm[spad(j)];
+                        v[k] = dir ? 0 : (INV ? inv_final(x, P) : fwd_final(x, P.q));
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < kUnroll; ++k) {
+                    const int j = j0 + k * nthr;
+                    if (j < N) op.store(p, u, j, v[k], pr[k], P);
+                }
             }
             __syncthreads();
         }

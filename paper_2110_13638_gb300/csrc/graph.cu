@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <vector>
 
 #include "../../include/fhe.h"
@@ -93,14 +94,44 @@ struct Exec {
             std::memcpy(host.data() + off, src, bytes);
             return off;
         };
-        size_t o_rp = 0, o_col = 0, o_W = 0, o_b = 0, o_c3 = 0, o_c2 = 0, o_c1 = 0, o_c0 = 0;
+        size_t o_rp = 0, o_tr = 0, o_col = 0, o_W = 0, o_b = 0, o_c3 = 0, o_c2 = 0, o_c1 = 0, o_c0 = 0;
         if (nd.kind == FHE_NODE_LINEAR) {
             const double qd = (double)c->primes[L - 1];
-            const size_t nnz = nd.col_idx.size();
-            std::vector<u64> W(nnz * L);
-            for (size_t e = 0; e < nnz; ++e) {
-                const int64_t w = (int64_t)std::llround(nd.weight[e] * qd);
-                for (uint32_t r = 0; r < L; ++r) W[e * L + r] = mod_signed(w, c->primes[r]);
+            // group rows with identical column lists, split groups into tiles
+            std::map<std::vector<uint32_t>, std::vector<uint32_t>> groups;
+            std::vector<std::vector<uint32_t>> order;
+            for (uint32_t o = 0; o < nd.n_out; ++o) {
+                std::vector<uint32_t> cols(nd.col_idx.begin() + nd.row_ptr[o], nd.col_idx.begin() + nd.row_ptr[o + 1]);
+                auto it = groups.find(cols);
+                if (it == groups.end()) {
+                    groups[cols] = {o};
+                    order.push_back(cols);
+                } else {
+                    it->second.push_back(o);
+                }
+            }
+            std::vector<uint4> tiles;
+            std::vector<uint32_t> trows, tcol;
+            std::vector<u64> W;
+            for (const auto& cols : order) {
+                const std::vector<uint32_t>& rs = groups[cols];
+                const uint32_t col_off = (uint32_t)tcol.size();
+                tcol.insert(tcol.end(), cols.begin(), cols.end());
+                for (size_t t0 = 0; t0 < rs.size(); t0 += kMacTile) {
+                    const uint32_t nr = (uint32_t)std::min<size_t>(kMacTile, rs.size() - t0);
+                    const uint32_t w_off = (uint32_t)(W.size() / ((size_t)L * kMacTile));  // in terms
+                    tiles.push_back(make_uint4(col_off, (uint32_t)cols.size(), nr, w_off));
+                    for (int o = 0; o < kMacTile; ++o) trows.push_back(o < (int)nr ? rs[t0 + o] : 0u);
+                    W.resize(W.size() + (size_t)cols.size() * kMacTile * L, 0);
+                    for (size_t e = 0; e < cols.size(); ++e)
+                        for (uint32_t o = 0; o < nr; ++o) {
+                            const uint32_t row = rs[t0 + o];
+                            const double wv = nd.weight[nd.row_ptr[row] + e];
+                            const int64_t w = (int64_t)std::llround(wv * qd);
+                            for (uint32_t r = 0; r < L; ++r)
+                                W[(((size_t)w_off + e) * L + r) * kMacTile + o] = mod_signed(w, c->primes[r]);
+                        }
+                }
             }
             const double s_out = (s_in * qd) / qd;
             std::vector<u64> B((size_t)nd.n_out * (L - 1));
@@ -108,8 +139,10 @@ struct Exec {
                 const int64_t b = (int64_t)std::llround(nd.bias[o] * s_out);
                 for (uint32_t r = 0; r + 1 < L; ++r) B[(size_t)o * (L - 1) + r] = mod_signed(b, c->primes[r]);
             }
-            o_rp = put(nd.row_ptr.data(), nd.row_ptr.size() * 4);
-            o_col = put(nd.col_idx.data(), std::max<size_t>(1, nd.col_idx.size()) * 4);
+            nc.n_tiles = (uint32_t)tiles.size();
+            o_rp = put(tiles.data(), std::max<size_t>(1, tiles.size()) * sizeof(uint4));
+            o_tr = put(trows.data(), std::max<size_t>(1, trows.size()) * 4);
+            o_col = put(tcol.data(), std::max<size_t>(1, tcol.size()) * 4);
             o_W = put(W.data(), std::max<size_t>(1, W.size()) * 8);
             o_b = put(B.data(), std::max<size_t>(1, B.size()) * 8);
         } else if (nd.kind == FHE_NODE_POLY) {
@@ -139,7 +172,8 @@ struct Exec {
         nc.L = L;
         nc.s_in = s_in;
         if (nd.kind == FHE_NODE_LINEAR) {
-            nc.row_ptr = (uint32_t*)(b + o_rp);
+            nc.tiles = (uint4*)(b + o_rp);
+            nc.tile_rows = (uint32_t*)(b + o_tr);
             nc.col = (uint32_t*)(b + o_col);
             nc.W = (u64*)(b + o_W);
             nc.bias = (u64*)(b + o_b);
@@ -197,7 +231,7 @@ struct Exec {
         if (!dry && ok()) {
             fhe_node_const* k = node_const(i, L, x.scale);
             if (!k) return y;
-            k_linear_mac(c, x.p, x.n, k->row_ptr, k->col, k->W, nd.n_out, L, Y, st);
+            k_linear_mac_tiled(c, x.p, k->tiles, k->n_tiles, k->tile_rows, k->col, k->W, L, Y, st);
             k_rescale(c, Y, out, nd.n_out, 2, L, k->bias, L - 1, sc, st);
         }
         y.p = out;

@@ -137,7 +137,9 @@ struct OpRows {
     __device__ int prime(int p, int) const { return pmap[p % rows]; }
     __device__ bool direct(int, int) const { return false; }
     __device__ u64 load(int p, int, int j, const PrimeC&) const { return src[(size_t)p * N + j]; }
-    __device__ void store(int p, int, int j, u64 v, const PrimeC&) const { dst[(size_t)p * N + j] = v; }
+    struct Pre {};
+    __device__ Pre pre(int, int, int) const { return {}; }
+    __device__ void store(int p, int, int j, u64 v, const Pre&, const PrimeC&) const { dst[(size_t)p * N + j] = v; }
 };
 
 void k_ntt_rows(const fhe_ctx* c, u64* d, uint32_t n_poly, uint32_t rows, const uint8_t* row_prime, bool forward,
@@ -300,7 +302,9 @@ struct OpTakeRowInv {
     __device__ int prime(int, int) const { return pidx; }
     __device__ bool direct(int, int) const { return false; }
     __device__ u64 load(int p, int, int j, const PrimeC&) const { return in[((size_t)p * L + row) * N + j]; }
-    __device__ void store(int p, int, int j, u64 v, const PrimeC&) const { V[(size_t)p * N + j] = v; }
+    struct Pre {};
+    __device__ Pre pre(int, int, int) const { return {}; }
+    __device__ void store(int p, int, int j, u64 v, const Pre&, const PrimeC&) const { V[(size_t)p * N + j] = v; }
 };
 
 // out_i = (in_i - NTT([v]_{q_i})) * p^{-1} (+ addc on comp 0)
@@ -321,13 +325,20 @@ struct OpDivFwd {
         const int poly = p / L_out, i = p % L_out;
         return centred_to(V[(size_t)poly * N + j], d.p, d.p_half, d.pmod[i], Q);
     }
-    __device__ void store(int p, int, int j, u64 v, const PrimeC& Q) const
+    struct Pre { u64 x, c; };
+    __device__ Pre pre(int p, int, int j) const
     {
         const int poly = p / L_out, i = p % L_out;
-        const u64 x = in[((size_t)poly * L_in + i) * N + j];
-        u64 r = mul_shoup(sub_mod(x, v, Q.q), d.inv[i], d.invs[i], Q.q);
-        if (addc && (poly % comps) == 0) r = add_mod(r, addc[(size_t)(poly / comps) * addc_stride + i], Q.q);
-        out[((size_t)poly * L_out + i) * N + j] = r;
+        Pre r;
+        r.x = in[((size_t)poly * L_in + i) * N + j];
+        r.c = (addc && (poly % comps) == 0) ? addc[(size_t)(poly / comps) * addc_stride + i] : 0;
+        return r;
+    }
+    __device__ void store(int p, int, int j, u64 v, const Pre& pr, const PrimeC& Q) const
+    {
+        const int poly = p / L_out, i = p % L_out;
+        const u64 r = mul_shoup(sub_mod(pr.x, v, Q.q), d.inv[i], d.invs[i], Q.q);
+        out[((size_t)poly * L_out + i) * N + j] = add_mod(r, pr.c, Q.q);
     }
 };
 
@@ -381,17 +392,20 @@ struct OpDigitsInv {
         const int ct = p / L, r = p % L;
         return d3[(((size_t)ct * 3 + 2) * L + r) * N + j];
     }
-    __device__ void store(int p, int, int j, u64 v, const PrimeC&) const { D[(size_t)p * N + j] = v; }
+    struct Pre {};
+    __device__ Pre pre(int, int, int) const { return {}; }
+    __device__ void store(int p, int, int j, u64 v, const Pre&, const PrimeC&) const { D[(size_t)p * N + j] = v; }
 };
 
 // step 2: per (ct, target t in 0..L, t = L meaning P): for every digit u,
-// NTT(D_u mod q_t) * ksk_u[k][t], accumulated over u into acc[ct][k][t]
+// NTT(D_u mod q_t) * ksk_u[k][t], accumulated over u into acc[ct][k][t].
+// Keys carry their Shoup quotients, so each key product is one Shoup product.
 struct OpModUpMac {
     static const char* family() { return "keyswitch_modup_mac"; }
     const u64* d3;
     const u64* D;
-    const u64* ksk;     // [L_top][2][L_top+1][N]
-    u64* acc;           // [n][2][L+1][N]
+    const ulonglong2* ksk;  // [L_top][2][L_top+1][N] (k, floor(k 2^64 / q))
+    u64* acc;               // [n][2][L+1][N]
     int n, L, N, Ltop;
     __host__ __device__ int count() const { return n * (L + 1); }
     __device__ int nsub(int) const { return L; }
@@ -406,23 +420,34 @@ struct OpModUpMac {
         const int ct = p / (L + 1);
         return reduce64(D[((size_t)ct * L + u) * N + j], Q);
     }
-    __device__ void store(int p, int u, int j, u64 v, const PrimeC& Q) const
+    struct Pre {
+        ulonglong2 k0, k1;
+        u64 a0, a1, dv;
+    };
+    __device__ Pre pre(int p, int u, int j) const
     {
         const int ct = p / (L + 1), t = p % (L + 1);
         const int tk = t == L ? Ltop : t;
-        if (t == u) v = d3[(((size_t)ct * 3 + 2) * L + t) * N + j];    // NTT(d2_t) is d2_t
-        const u64* k0 = ksk + (((size_t)u * 2 + 0) * (Ltop + 1) + tk) * N;
-        const u64* k1 = ksk + (((size_t)u * 2 + 1) * (Ltop + 1) + tk) * N;
-        u64* a0 = acc + (((size_t)ct * 2 + 0) * (L + 1) + t) * N;
-        u64* a1 = acc + (((size_t)ct * 2 + 1) * (L + 1) + t) * N;
-        const u64 p0 = mul_mod(v, k0[j], Q), p1 = mul_mod(v, k1[j], Q);
-        if (u == 0) {
-            a0[j] = p0;
-            a1[j] = p1;
+        Pre r;
+        r.k0 = __ldg(&ksk[(((size_t)u * 2 + 0) * (Ltop + 1) + tk) * N + j]);
+        r.k1 = __ldg(&ksk[(((size_t)u * 2 + 1) * (Ltop + 1) + tk) * N + j]);
+        if (u > 0) {
+            r.a0 = acc[(((size_t)ct * 2 + 0) * (L + 1) + t) * N + j];
+            r.a1 = acc[(((size_t)ct * 2 + 1) * (L + 1) + t) * N + j];
         } else {
-            a0[j] = add_mod(a0[j], p0, Q.q);
-            a1[j] = add_mod(a1[j], p1, Q.q);
+            r.a0 = r.a1 = 0;
         }
+        r.dv = (t == u) ? d3[(((size_t)ct * 3 + 2) * L + t) * N + j] : 0;   // NTT(d2_t) is d2_t
+        return r;
+    }
+    __device__ void store(int p, int u, int j, u64 v, const Pre& pr, const PrimeC& Q) const
+    {
+        const int ct = p / (L + 1), t = p % (L + 1);
+        if (t == u) v = pr.dv;
+        const u64 p0 = mul_shoup(v, pr.k0.x, pr.k0.y, Q.q);
+        const u64 p1 = mul_shoup(v, pr.k1.x, pr.k1.y, Q.q);
+        acc[(((size_t)ct * 2 + 0) * (L + 1) + t) * N + j] = u == 0 ? p0 : add_mod(pr.a0, p0, Q.q);
+        acc[(((size_t)ct * 2 + 1) * (L + 1) + t) * N + j] = u == 0 ? p1 : add_mod(pr.a1, p1, Q.q);
     }
 };
 
@@ -437,7 +462,9 @@ struct OpAccPInv {
     __device__ int prime(int, int) const { return Ltop; }
     __device__ bool direct(int, int) const { return false; }
     __device__ u64 load(int p, int, int j, const PrimeC&) const { return acc[((size_t)p * (L + 1) + L) * N + j]; }
-    __device__ void store(int p, int, int j, u64 v, const PrimeC&) const { Vp[(size_t)p * N + j] = v; }
+    struct Pre {};
+    __device__ Pre pre(int, int, int) const { return {}; }
+    __device__ void store(int p, int, int j, u64 v, const Pre&, const PrimeC&) const { Vp[(size_t)p * N + j] = v; }
 };
 
 // step 4: ModDown + add: out_k,t = d_k,t + (acc_k,t - NTT([v]_{q_t})) * P^{-1}
@@ -458,14 +485,22 @@ struct OpModDown {
         const int poly = p / L, t = p % L;             // poly = ct*2 + k
         return centred_to(Vp[(size_t)poly * N + j], d.p, d.p_half, d.pmod[t], Q);
     }
-    __device__ void store(int p, int, int j, u64 v, const PrimeC& Q) const
+    struct Pre { u64 a, dk; };
+    __device__ Pre pre(int p, int, int j) const
     {
         const int poly = p / L, t = p % L;
         const int ct = poly >> 1, k = poly & 1;
-        const u64 a = acc[((size_t)poly * (L + 1) + t) * N + j];
-        const u64 ks = mul_shoup(sub_mod(a, v, Q.q), d.inv[t], d.invs[t], Q.q);
-        const u64 dk = d3[(((size_t)ct * 3 + k) * L + t) * N + j];
-        out[(((size_t)ct * 2 + k) * L + t) * N + j] = add_mod(dk, ks, Q.q);
+        Pre r;
+        r.a = acc[((size_t)poly * (L + 1) + t) * N + j];
+        r.dk = d3[(((size_t)ct * 3 + k) * L + t) * N + j];
+        return r;
+    }
+    __device__ void store(int p, int, int j, u64 v, const Pre& pr, const PrimeC& Q) const
+    {
+        const int poly = p / L, t = p % L;
+        const int ct = poly >> 1, k = poly & 1;
+        const u64 ks = mul_shoup(sub_mod(pr.a, v, Q.q), d.inv[t], d.invs[t], Q.q);
+        out[(((size_t)ct * 2 + k) * L + t) * N + j] = add_mod(pr.dk, ks, Q.q);
     }
 };
 
@@ -550,6 +585,93 @@ void k_linear_mac(const fhe_ctx* c, const u64* X, uint32_t n_in, const uint32_t*
     k_mac_kernel<<<grid, tpb, 0, st>>>(X, row_ptr, col, Wres, Y, (int)L, N, c->d_pc);
 }
 
+// Tiled form: rows sharing one column list are computed together, up to
+// kMacTile per thread, so each input word is loaded once per tile.
+//   tiles[t] = {col_off, K, n_rows, w_off}; rows[t * kMacTile + o] = output row;
+//   W[((w_off + e) * L + r) * kMacTile + o] = weight residue of (row o, term e)
+// (the tile's weights of one term and residue are contiguous: 4 vector loads).
+// Terms are processed four at a time with their input loads issued together.
+__device__ __forceinline__ void mac128(u64& lo, u64& hi, u64 x, u64 w)
+{
+    const u64 pl = x * w, ph = __umul64hi(x, w);
+    lo += pl;
+    hi += ph + (lo < pl ? 1 : 0);
+}
+
+__global__ void __launch_bounds__(256) k_mac_tiled_kernel(const u64* __restrict__ X, const uint4* __restrict__ tiles,
+                                                           const uint32_t* __restrict__ rows,
+                                                           const uint32_t* __restrict__ col,
+                                                           const u64* __restrict__ W, u64* __restrict__ Y, int L, int N,
+                                                           const PrimeC* __restrict__ pc)
+{
+    const uint4 tl = tiles[blockIdx.x];
+    const int j = blockIdx.y * blockDim.x + threadIdx.x;
+    const int kr = blockIdx.z;
+    const int r = kr % L;
+    if (j >= N) return;
+    const PrimeC P = pc[r];
+    const size_t ct_stride = (size_t)2 * L * N;
+    const u64* Xj = X + (size_t)kr * N + j;
+    const uint32_t* cl = col + tl.x;
+    const ulonglong2* w2 = reinterpret_cast<const ulonglong2*>(W + ((size_t)tl.w * L + r) * kMacTile);
+    const size_t wstep = (size_t)L * kMacTile / 2;        // ulonglong2 per term
+    u64 lo[kMacTile], hi[kMacTile];
+#pragma unroll
+    for (int o = 0; o < kMacTile; ++o) lo[o] = hi[o] = 0;
+    const uint32_t K = tl.y;
+    uint32_t e = 0;
+    int cnt = 0;
+    for (; e + 4 <= K; e += 4) {
+        u64 x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = Xj[(size_t)__ldg(&cl[e + u]) * ct_stride];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const ulonglong2* we = w2 + (size_t)(e + u) * wstep;
+#pragma unroll
+            for (int o2 = 0; o2 < kMacTile / 2; ++o2) {
+                const ulonglong2 wv = __ldg(&we[o2]);
+                mac128(lo[2 * o2], hi[2 * o2], x[u], wv.x);
+                mac128(lo[2 * o2 + 1], hi[2 * o2 + 1], x[u], wv.y);
+            }
+        }
+        cnt += 4;
+        if (cnt == 32) {                // hi < 32 * 2^58: fold before it can overflow
+#pragma unroll
+            for (int o = 0; o < kMacTile; ++o) {
+                lo[o] = reduce128(hi[o], lo[o], P);
+                hi[o] = 0;
+            }
+            cnt = 0;
+        }
+    }
+    for (; e < K; ++e) {
+        const u64 x = Xj[(size_t)__ldg(&cl[e]) * ct_stride];
+        const ulonglong2* we = w2 + (size_t)e * wstep;
+#pragma unroll
+        for (int o2 = 0; o2 < kMacTile / 2; ++o2) {
+            const ulonglong2 wv = __ldg(&we[o2]);
+            mac128(lo[2 * o2], hi[2 * o2], x, wv.x);
+            mac128(lo[2 * o2 + 1], hi[2 * o2 + 1], x, wv.y);
+        }
+    }
+    const size_t off = (size_t)kr * N + j;
+#pragma unroll
+    for (int o = 0; o < kMacTile; ++o)
+        if (o < (int)tl.z) Y[(size_t)rows[blockIdx.x * kMacTile + o] * ct_stride + off] = reduce128(hi[o], lo[o], P);
+}
+
+void k_linear_mac_tiled(const fhe_ctx* c, const u64* X, const uint4* tiles, uint32_t n_tiles, const uint32_t* rows,
+                        const uint32_t* col, const u64* W, uint32_t L, u64* Y, cudaStream_t st)
+{
+    if (n_tiles == 0) return;
+    const int N = (int)c->N;
+    const int tpb = N < 256 ? N : 256;
+    dim3 grid(n_tiles, (N + tpb - 1) / tpb, 2 * L);
+    LaunchScope ls(c, "mac", st);
+    k_mac_tiled_kernel<<<grid, tpb, 0, st>>>(X, tiles, rows, col, W, Y, (int)L, N, c->d_pc);
+}
+
 // ---------------------------------------------------------------- keys
 enum { DOM_SECRET = 1, DOM_PK_A = 2, DOM_PK_E = 3, DOM_KSK_A = 4, DOM_KSK_E = 5,
        DOM_ENC_U = 6, DOM_ENC_E0 = 7, DOM_ENC_E1 = 8 };
@@ -565,7 +687,9 @@ struct OpSecret {
     __device__ int prime(int p, int) const { return p; }
     __device__ bool direct(int, int) const { return false; }
     __device__ u64 load(int, int, int j, const PrimeC& P) const { return from_signed(draw_ternary(s0, j), P); }
-    __device__ void store(int p, int, int j, u64 v, const PrimeC&) const { s[(size_t)p * N + j] = v; }
+    struct Pre {};
+    __device__ Pre pre(int, int, int) const { return {}; }
+    __device__ void store(int p, int, int j, u64 v, const Pre&, const PrimeC&) const { s[(size_t)p * N + j] = v; }
 };
 
 // pk = (-a s + e, a) over the data primes: sub 0 = a (uniform), sub 1 = e
@@ -584,24 +708,35 @@ struct OpPublicKey {
     {
         return u == 0 ? draw_uniform(sa, j, p, P) : from_signed(draw_gauss(se, j, cdt), P);
     }
-    __device__ void store(int p, int u, int j, u64 v, const PrimeC& P) const
+    struct Pre { u64 x; };
+    __device__ Pre pre(int p, int u, int j) const
+    {
+        return {u == 0 ? s[(size_t)p * N + j] : pk[(size_t)p * N + j]};
+    }
+    __device__ void store(int p, int u, int j, u64 v, const Pre& pr, const PrimeC& P) const
     {
         u64* b = pk + (size_t)p * N;
         u64* a = pk + ((size_t)Ltop + p) * N;
         if (u == 0) {
             a[j] = v;
-            b[j] = sub_mod(0, mul_mod(v, s[(size_t)p * N + j], P), P.q);
+            b[j] = sub_mod(0, mul_mod(v, pr.x, P), P.q);
         } else {
-            b[j] = add_mod(b[j], v, P.q);
+            b[j] = add_mod(pr.x, v, P.q);
         }
     }
 };
 
-// ksk_j = (-a_j s + e_j + [r == j] P s^2, a_j) over every key prime r
+// ksk_j = (-a_j s + e_j + [r == j] P s^2, a_j) over every key prime r; each
+// key word is stored with its Shoup quotient floor(k 2^64 / q)
+__device__ __forceinline__ ulonglong2 with_shoup(u64 k, u64 q)
+{
+    return make_ulonglong2(k, (u64)(((unsigned __int128)k << 64) / q));
+}
+
 struct OpRelinKey {
     static const char* family() { return "keygen"; }
     const u64* s;
-    u64* ksk;           // [Ltop][2][Ltop+1][N]
+    ulonglong2* ksk;    // [Ltop][2][Ltop+1][N]
     const u64* cdt;
     const u64* sa;      // per digit stream keys (device array [Ltop])
     const u64* se;
@@ -616,19 +751,27 @@ struct OpRelinKey {
         const int dj = p / (Ltop + 1), r = p % (Ltop + 1);
         return u == 0 ? draw_uniform(sa[dj], j, r, P) : from_signed(draw_gauss(se[dj], j, cdt), P);
     }
-    __device__ void store(int p, int u, int j, u64 v, const PrimeC& P) const
+    struct Pre { u64 sr, b; };
+    __device__ Pre pre(int p, int u, int j) const
     {
         const int dj = p / (Ltop + 1), r = p % (Ltop + 1);
-        u64* b = ksk + (((size_t)dj * 2 + 0) * (Ltop + 1) + r) * N;
-        u64* a = ksk + (((size_t)dj * 2 + 1) * (Ltop + 1) + r) * N;
-        const u64 sr = s[(size_t)r * N + j];
+        Pre x;
+        x.sr = s[(size_t)r * N + j];
+        x.b = u == 1 ? ksk[(((size_t)dj * 2 + 0) * (Ltop + 1) + r) * N + j].x : 0;
+        return x;
+    }
+    __device__ void store(int p, int u, int j, u64 v, const Pre& pr, const PrimeC& P) const
+    {
+        const int dj = p / (Ltop + 1), r = p % (Ltop + 1);
+        ulonglong2* b = ksk + (((size_t)dj * 2 + 0) * (Ltop + 1) + r) * N;
+        ulonglong2* a = ksk + (((size_t)dj * 2 + 1) * (Ltop + 1) + r) * N;
         if (u == 0) {
-            a[j] = v;
-            b[j] = sub_mod(0, mul_mod(v, sr, P), P.q);
+            a[j] = with_shoup(v, P.q);
+            b[j] = make_ulonglong2(sub_mod(0, mul_mod(v, pr.sr, P), P.q), 0);
         } else {
-            u64 x = add_mod(b[j], v, P.q);
-            if (r == dj) x = add_mod(x, mul_mod(Pmod[r], mul_mod(sr, sr, P), P), P.q);
-            b[j] = x;
+            u64 x = add_mod(pr.b, v, P.q);
+            if (r == dj) x = add_mod(x, mul_mod(Pmod[r], mul_mod(pr.sr, pr.sr, P), P), P.q);
+            b[j] = with_shoup(x, P.q);
         }
     }
 };
@@ -662,46 +805,96 @@ void k_keygen(fhe_ctx* c, cudaStream_t st)
 }
 
 // ---------------------------------------------------------------- encrypt
+// The integer samples of a ciphertext (u, e0, e1) are drawn once per
+// coefficient by k_sample_enc (int8, [n][3][N]) and then reduced into every
+// residue by the transform prologue.
+__device__ __forceinline__ i64 draw_gauss_bs(u64 s0, int j, const u64* __restrict__ cdt)
+{
+    const u64 u = sm_out(s0, (u64)j);
+    int lo = 0, hi = 38;                 // number of thresholds <= u (table increasing)
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(&cdt[mid]) <= u) lo = mid + 1;
+        else hi = mid;
+    }
+    return (i64)lo - 19;
+}
+
+__global__ void k_sample_enc_kernel(int8_t* __restrict__ S, int n, int N, u64 seed, u64 first,
+                                    const u64* __restrict__ cdt)
+{
+    const size_t total = (size_t)n * N;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int ci = (int)(i / N), j = (int)(i % N);
+        const u64 id = first + (u64)ci;
+        int8_t* o = S + (size_t)ci * 3 * N + j;
+        o[0] = (int8_t)draw_ternary(sm_out(sm_out(seed, (u64)DOM_ENC_U), id), j);
+        o[N] = (int8_t)draw_gauss_bs(sm_out(sm_out(seed, (u64)DOM_ENC_E0), id), j, cdt);
+        o[2 * (size_t)N] = (int8_t)draw_gauss_bs(sm_out(sm_out(seed, (u64)DOM_ENC_E1), id), j, cdt);
+    }
+}
+
 // per (ct, r): sub 0 = u, sub 1 = e0, sub 2 = e1
 struct OpEncrypt {
     static const char* family() { return "encrypt"; }
     const u64* pt;      // [n][Ltop][N]
     const u64* pk;      // [2][Ltop][N]
     u64* ct;            // [n][2][Ltop][N]
-    const u64* cdt;
-    u64 seed, first;
+    const int8_t* S;    // [n][3][N] samples
     int n, Ltop, N;
     __host__ __device__ int count() const { return n * Ltop; }
     __device__ int nsub(int) const { return 3; }
     __device__ int prime(int p, int) const { return p % Ltop; }
     __device__ bool direct(int, int) const { return false; }
-    __device__ u64 key(int dom, int ct_i) const { return sm_out(sm_out(seed, (u64)dom), first + (u64)ct_i); }
     __device__ u64 load(int p, int u, int j, const PrimeC& P) const
     {
         const int ci = p / Ltop;
-        if (u == 0) return from_signed(draw_ternary(key(DOM_ENC_U, ci), j), P);
-        return from_signed(draw_gauss(key(u == 1 ? DOM_ENC_E0 : DOM_ENC_E1, ci), j, cdt), P);
+        return from_signed((i64)S[((size_t)ci * 3 + u) * N + j], P);
     }
-    __device__ void store(int p, int u, int j, u64 v, const PrimeC& P) const
+    struct Pre { u64 a, b, c; };
+    __device__ Pre pre(int p, int u, int j) const
+    {
+        const int ci = p / Ltop, r = p % Ltop;
+        Pre x;
+        if (u == 0) {
+            x.a = pt[((size_t)ci * Ltop + r) * N + j];
+            x.b = pk[(size_t)r * N + j];
+            x.c = pk[((size_t)Ltop + r) * N + j];
+        } else {
+            x.a = ct[(((size_t)ci * 2 + (u == 1 ? 0 : 1)) * Ltop + r) * N + j];
+            x.b = x.c = 0;
+        }
+        return x;
+    }
+    __device__ void store(int p, int u, int j, u64 v, const Pre& pr, const PrimeC& P) const
     {
         const int ci = p / Ltop, r = p % Ltop;
         u64* c0 = ct + (((size_t)ci * 2 + 0) * Ltop + r) * N;
         u64* c1 = ct + (((size_t)ci * 2 + 1) * Ltop + r) * N;
         if (u == 0) {
-            const u64 m = pt[((size_t)ci * Ltop + r) * N + j];
-            c0[j] = add_mod(mul_mod(v, pk[(size_t)r * N + j], P), m, P.q);
-            c1[j] = mul_mod(v, pk[((size_t)Ltop + r) * N + j], P);
+            c0[j] = add_mod(mul_mod(v, pr.b, P), pr.a, P.q);
+            c1[j] = mul_mod(v, pr.c, P);
         } else if (u == 1) {
-            c0[j] = add_mod(c0[j], v, P.q);
+            c0[j] = add_mod(pr.a, v, P.q);
         } else {
-            c1[j] = add_mod(c1[j], v, P.q);
+            c1[j] = add_mod(pr.a, v, P.q);
         }
     }
 };
 
-void k_encrypt(const fhe_ctx* c, const u64* pt, uint32_t n_ct, uint64_t first_id, u64* ct, cudaStream_t st)
+size_t encrypt_scratch_bytes(const fhe_ctx* c, uint32_t n_ct) { return (size_t)n_ct * 3 * c->N; }
+
+void k_encrypt(const fhe_ctx* c, const u64* pt, uint32_t n_ct, uint64_t first_id, u64* ct, void* scratch,
+               cudaStream_t st)
 {
-    OpEncrypt op{pt, c->d_pk, ct, c->d_cdt, c->seed, first_id, (int)n_ct, (int)c->L_top, (int)c->N};
+    if (n_ct == 0) return;
+    int8_t* S = (int8_t*)scratch;
+    {
+        const size_t total = (size_t)n_ct * c->N;
+        LaunchScope ls(c, "encrypt", st);
+        k_sample_enc_kernel<<<ew_grid(total), 256, 0, st>>>(S, (int)n_ct, (int)c->N, c->seed, first_id, c->d_cdt);
+    }
+    OpEncrypt op{pt, c->d_pk, ct, S, (int)n_ct, (int)c->L_top, (int)c->N};
     launch_ntt<false>(c, op, st);
 }
 
@@ -723,7 +916,9 @@ struct OpDecrypt {
         const u64 c1 = ct[(((size_t)p * 2 + 1) * L) * N + j];
         return add_mod(c0, mul_mod(c1, s[j], P), P.q);
     }
-    __device__ void store(int p, int, int j, u64 v, const PrimeC& P) const
+    struct Pre {};
+    __device__ Pre pre(int, int, int) const { return {}; }
+    __device__ void store(int p, int, int j, u64 v, const Pre&, const PrimeC& P) const
     {
         m[(size_t)p * N + j] = v > P.half ? (i64)v - (i64)P.q : (i64)v;
     }
@@ -852,7 +1047,9 @@ struct OpSignedRows {
     __device__ int prime(int p, int) const { return p % L; }
     __device__ bool direct(int, int) const { return false; }
     __device__ u64 load(int p, int, int j, const PrimeC& P) const { return from_signed(m[(size_t)(p / L) * N + j], P); }
-    __device__ void store(int p, int, int j, u64 v, const PrimeC&) const { out[(size_t)p * N + j] = v; }
+    struct Pre {};
+    __device__ Pre pre(int, int, int) const { return {}; }
+    __device__ void store(int p, int, int j, u64 v, const Pre&, const PrimeC&) const { out[(size_t)p * N + j] = v; }
 };
 
 size_t encode_scratch_bytes(const fhe_ctx* c, uint32_t n_ct) { return (size_t)n_ct * c->N * sizeof(i64); }
