@@ -57,8 +57,8 @@ typedef struct {
     uint32_t log_scale;  /* scale = 2^log_scale */
     uint64_t primes[64]; /* q_0 .. q_{L_top-1}, then the special prime P */
     uint64_t key_bytes;  /* device bytes held for keys and tables */
-    uint32_t ntt_variant;        /* NTT schedule the autotuner picked (0..2) */
-    float ntt_variant_us[4];     /* autotuner: microseconds per transform of each schedule */
+    uint32_t ntt_variant;        /* NTT schedule the autotuner picked (0..4) */
+    float ntt_variant_us[8];     /* autotuner: microseconds per transform of each schedule */
 } fhe_ctx_info;
 
 /* Per-ciphertext metadata returned by graph evaluation. */
@@ -126,7 +126,7 @@ int fhe_gauss_table(uint64_t* out38);
 /* Build the context on the current CUDA device: primes, NTT tables and
  * encoder tables resident in HBM.  The NTT schedule (radix of the register
  * passes, threads per block) is autotuned here by timing each candidate on a
- * batch of transforms; the environment variable FHE_NTT_VARIANT=0|1|2 fixes
+ * batch of transforms; the environment variable FHE_NTT_VARIANT=0..4 fixes
  * it instead.  bits: coefficient-modulus bit sizes, the
  * last one being the special prime; log_scale: scale 2^log_scale.
  * N must be a power of two in [16, 16384]. */

@@ -219,6 +219,7 @@ static void free_ctx(fhe_ctx* c)
     cudaFree(c->d_pk);
     cudaFree(c->d_ksk);
     cudaFree(c->ws);
+    cudaFree(c->d_ntt2);
     delete c;
 }
 
@@ -229,7 +230,7 @@ static int autotune_ntt(fhe_ctx* c)
     const char* env = std::getenv("FHE_NTT_VARIANT");
     if (env && *env) {
         int v = std::atoi(env);
-        if (v < 0 || v >= kNttVariants) return fail(FHE_EINVAL, "FHE_NTT_VARIANT out of range");
+        if (v < 0 || v >= kNttVariants) return fail(FHE_EINVAL, "FHE_NTT_VARIANT out of range (0..4)");
         c->ntt_variant = v;
         return FHE_OK;
     }
@@ -353,6 +354,15 @@ int fhe_ctx_create(uint32_t N, const uint32_t* bits, uint32_t n_bits, uint32_t l
     up((void**)&c->d_enc_tw, etw.data(), etw.size() * sizeof(double4));
     up((void**)&c->d_enc_twist, etwist.data(), etwist.size() * sizeof(double4));
     up((void**)&c->d_slot_of, slot_of.data(), slot_of.size() * sizeof(uint32_t));
+    if (rc == FHE_OK) {
+        // two-pass NTT intermediate: 128 MiB (or 64 transforms for small rings)
+        c->ntt2_words = std::max<size_t>((size_t)1 << 24, (size_t)64 * N);
+        cudaError_t err = cudaMalloc((void**)&c->d_ntt2, c->ntt2_words * 8);
+        if (err != cudaSuccess) {
+            cudaGetLastError();
+            rc = cuda_check(err, "two-pass NTT scratch");
+        }
+    }
     if (rc != FHE_OK) {
         free_ctx(c);
         return rc;
@@ -388,7 +398,7 @@ int fhe_ctx_query(const fhe_ctx* c, fhe_ctx_info* out)
     for (size_t i = 0; i < c->primes.size() && i < 64; ++i) out->primes[i] = c->primes[i];
     out->key_bytes = c->key_bytes;
     out->ntt_variant = (uint32_t)c->ntt_variant;
-    for (int v = 0; v < kNttVariants && v < 4; ++v) out->ntt_variant_us[v] = c->ntt_variant_us[v];
+    for (int v = 0; v < kNttVariants && v < 8; ++v) out->ntt_variant_us[v] = c->ntt_variant_us[v];
     return FHE_OK;
 }
 

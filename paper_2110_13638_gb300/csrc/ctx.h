@@ -15,7 +15,10 @@ struct fhe_ctx {
     double delta = 0.0;
     int device = 0;
     int ntt_variant = 0;           // NTT schedule (see ntt_variant_name), autotuned
-    float ntt_variant_us[3] = {0, 0, 0};   // autotuner timings per variant (us per transform)
+    float ntt_variant_us[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // autotuner: us per transform per variant
+    mutable int force_single_pass = 0;   // set while a call must not use the two-pass scratch
+    u64* d_ntt2 = nullptr;         // two-pass intermediate (allocated with the context)
+    size_t ntt2_words = 0;
 
     // resident tables
     PrimeC* d_pc = nullptr;
@@ -176,6 +179,6 @@ void k_decode(const fhe_ctx* c, const i64* m, uint32_t n_ct, double scale, doubl
 
 uint64_t stream_key(uint64_t seed, uint64_t domain, uint64_t object);
 const char* ntt_variant_name(int v);
-constexpr int kNttVariants = 3;
+constexpr int kNttVariants = 5;
 
 }  // namespace fhe

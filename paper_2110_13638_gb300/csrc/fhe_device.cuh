@@ -308,3 +308,315 @@ __global__ void __launch_bounds__(MAXT, 1) k_ntt_op(Op op, NttTables T)
         }
     }
 }
+
+// ---------------------------------------------------------------- two-pass NTT
+// The ring degree N = N1 N2 (N1 = 2^k1 rows, N2 = 2^k2 columns, element
+// j = N2 i + c).  Forward: the first k1 stages (distances N/2 .. N2) act on
+// each column as an N1-point transform whose twiddles are the first N1 entries
+// of the psi table; the last k2 stages act on each row with the row's own
+// twiddles.  Inverse: rows first (distances 1 .. N2/2), then columns
+// (N1-point transforms on the prefix of the inverse table).  Each pass is a
+// kernel over small tiles (16 columns or 16 rows), so many blocks share an SM
+// and their load, compute and store phases overlap; the intermediate goes
+// through a scratch buffer S[unit][sub][N].
+constexpr int kTile2 = 16;      // columns (or rows) per block
+constexpr int kThr2 = 128;      // threads per block
+
+// column pass: N1-point transforms on the kTile2 columns held as sm[i * cs + cc]
+template <bool INV, int K>
+__device__ __forceinline__ void col_pass(u64* sm, int cs, int k1, int s0, const ulonglong2* __restrict__ tw, u64 q,
+                                         u64 q2, int tid, int nthr)
+{
+    constexpr int R = 1 << K;
+    const int tpc = nthr / cs;                 // threads per column
+    const int cc = tid % cs, gt = tid / cs;
+    const int ngroups = (1 << k1) >> K;
+    // forward: ltb = k1 - s0 - K (smallest distance); inverse: s0 is lt0 (smallest distance)
+    const int lsh = INV ? s0 : (k1 - s0 - K);
+    for (int gi = gt; gi < ngroups; gi += tpc) {
+        const int g = gi >> lsh;
+        const int r = gi & ((1 << lsh) - 1);
+        const int i0 = (g << (lsh + K)) + r;
+        u64 x[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) x[m] = sm[(i0 + (m << lsh)) * cs + cc];
+        if (!INV) {
+#pragma unroll
+            for (int l = 0; l < K; ++l) {
+                const int h = R >> (l + 1);
+                const ulonglong2* twl = tw + (1 << (s0 + l)) + (g << l);
+#pragma unroll
+                for (int m = 0; m < (1 << l); ++m) {
+                    const ulonglong2 w = __ldg(&twl[m]);
+#pragma unroll
+                    for (int t = 0; t < h; ++t) {
+                        const int i = m * 2 * h + t;
+                        u64 X = x[i];
+                        X = X >= q2 ? X - q2 : X;
+                        const u64 T = mul_shoup_lazy(x[i + h], w.x, w.y, q);
+                        x[i] = X + T;
+                        x[i + h] = X + q2 - T;
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int l = 0; l < K; ++l) {
+                const int h = 1 << l;
+                const ulonglong2* twl = tw + ((1 << k1) >> (s0 + l + 1)) + (g << (K - l - 1));
+#pragma unroll
+                for (int m = 0; m < (R >> (l + 1)); ++m) {
+                    const ulonglong2 w = __ldg(&twl[m]);
+#pragma unroll
+                    for (int t = 0; t < h; ++t) {
+                        const int i = m * 2 * h + t;
+                        const u64 X = x[i], Y = x[i + h];
+                        u64 S = X + Y;
+                        S = S >= q2 ? S - q2 : S;
+                        x[i] = S;
+                        x[i + h] = mul_shoup_lazy(X + q2 - Y, w.x, w.y, q);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < R; ++m) sm[(i0 + (m << lsh)) * cs + cc] = x[m];
+    }
+}
+
+// row pass: N2-point segments of the full transform on the rows held as
+// sm[ri * pitch + spad(c)], row ri being global row rbase + ri
+template <bool INV, int K>
+__device__ __forceinline__ void row_pass(u64* sm, int rs, int pitch, int k1, int k2, int s0, int rbase,
+                                         const ulonglong2* __restrict__ tw, u64 q, u64 q2, int tid, int nthr)
+{
+    constexpr int R = 1 << K;
+    const int tpr = nthr / rs;                 // threads per row
+    const int ri = tid / tpr, gt = tid % tpr;
+    const int i = rbase + ri;
+    const int N = 1 << (k1 + k2);
+    const int ngroups = (1 << k2) >> K;
+    const int lsh = INV ? s0 : (k2 - s0 - K);
+    u64* row = sm + ri * pitch;
+    for (int gi = gt; gi < ngroups; gi += tpr) {
+        const int g = gi >> lsh;
+        const int r = gi & ((1 << lsh) - 1);
+        const int c0 = (g << (lsh + K)) + r;
+        u64 x[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) x[m] = row[spad(c0 + (m << lsh))];
+        if (!INV) {
+            const int gf = (i << s0) + g;                 // group index in the full transform
+#pragma unroll
+            for (int l = 0; l < K; ++l) {
+                const int h = R >> (l + 1);
+                const ulonglong2* twl = tw + (1 << (k1 + s0 + l)) + ((size_t)gf << l);
+#pragma unroll
+                for (int m = 0; m < (1 << l); ++m) {
+                    const ulonglong2 w = __ldg(&twl[m]);
+#pragma unroll
+                    for (int t = 0; t < h; ++t) {
+                        const int ii = m * 2 * h + t;
+                        u64 X = x[ii];
+                        X = X >= q2 ? X - q2 : X;
+                        const u64 T = mul_shoup_lazy(x[ii + h], w.x, w.y, q);
+                        x[ii] = X + T;
+                        x[ii + h] = X + q2 - T;
+                    }
+                }
+            }
+        } else {
+            const int gf = (i << (k2 - s0 - K)) + g;
+#pragma unroll
+            for (int l = 0; l < K; ++l) {
+                const int h = 1 << l;
+                const ulonglong2* twl = tw + (N >> (s0 + l + 1)) + ((size_t)gf << (K - l - 1));
+#pragma unroll
+                for (int m = 0; m < (R >> (l + 1)); ++m) {
+                    const ulonglong2 w = __ldg(&twl[m]);
+#pragma unroll
+                    for (int t = 0; t < h; ++t) {
+                        const int ii = m * 2 * h + t;
+                        const u64 X = x[ii], Y = x[ii + h];
+                        u64 S = X + Y;
+                        S = S >= q2 ? S - q2 : S;
+                        x[ii] = S;
+                        x[ii + h] = mul_shoup_lazy(X + q2 - Y, w.x, w.y, q);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < R; ++m) row[spad(c0 + (m << lsh))] = x[m];
+    }
+}
+
+template <bool INV, int LOGR>
+__device__ __forceinline__ void col_passes(u64* sm, int cs, int k1, const ulonglong2* tw, u64 q, int tid, int nthr)
+{
+    const u64 q2 = 2 * q;
+    for (int s = 0; s < k1;) {
+        const int k = (k1 - s) < LOGR ? (k1 - s) : LOGR;
+        switch (k) {
+        case 4: col_pass<INV, 4>(sm, cs, k1, s, tw, q, q2, tid, nthr); break;
+        case 3: col_pass<INV, 3>(sm, cs, k1, s, tw, q, q2, tid, nthr); break;
+        case 2: col_pass<INV, 2>(sm, cs, k1, s, tw, q, q2, tid, nthr); break;
+        default: col_pass<INV, 1>(sm, cs, k1, s, tw, q, q2, tid, nthr); break;
+        }
+        __syncthreads();
+        s += k;
+    }
+}
+
+template <bool INV, int LOGR>
+__device__ __forceinline__ void row_passes(u64* sm, int rs, int pitch, int k1, int k2, int rbase, const ulonglong2* tw,
+                                           u64 q, int tid, int nthr)
+{
+    const u64 q2 = 2 * q;
+    for (int s = 0; s < k2;) {
+        const int k = (k2 - s) < LOGR ? (k2 - s) : LOGR;
+        switch (k) {
+        case 4: row_pass<INV, 4>(sm, rs, pitch, k1, k2, s, rbase, tw, q, q2, tid, nthr); break;
+        case 3: row_pass<INV, 3>(sm, rs, pitch, k1, k2, s, rbase, tw, q, q2, tid, nthr); break;
+        case 2: row_pass<INV, 2>(sm, rs, pitch, k1, k2, s, rbase, tw, q, q2, tid, nthr); break;
+        default: row_pass<INV, 1>(sm, rs, pitch, k1, k2, s, rbase, tw, q, q2, tid, nthr); break;
+        }
+        __syncthreads();
+        s += k;
+    }
+}
+
+struct Split2 {
+    int k1, k2;          // N1 = 2^k1 rows, N2 = 2^k2 columns
+    int cs, rs;          // columns / rows per block
+    int p0, nunits;      // unit range of this chunk
+};
+
+// First pass: prologue (op.load) + column passes (forward) or row passes
+// (inverse); writes the partial transform to S[(pp * ns + u) * N + j].
+// Blocks: (pp, u, tile) with tile = column slab (forward) or row slab (inverse).
+template <bool INV, int LOGR, class Op>
+__global__ void __launch_bounds__(kThr2) k_ntt2_first(Op op, NttTables T, Split2 sp, u64* __restrict__ S)
+{
+    extern __shared__ u64 sm[];
+    const int k1 = sp.k1, k2 = sp.k2, N1 = 1 << k1, N2 = 1 << k2, N = N1 * N2;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int ns = op.nsub(sp.p0);
+    const int tiles = INV ? N1 / sp.rs : N2 / sp.cs;
+    const int tile = blockIdx.x % tiles;
+    const int pu = blockIdx.x / tiles;
+    const int u = pu % ns, pp = pu / ns, p = sp.p0 + pp;
+    if (pp >= sp.nunits || op.direct(p, u)) return;
+    const int pi = op.prime(p, u);
+    const PrimeC P = T.pc[pi];
+    u64* out = S + (size_t)pu * N;
+    if (!INV) {
+        const int cs = sp.cs, cb = tile * cs, tot = N1 * cs;
+        for (int e0 = tid; e0 < tot; e0 += nthr * kUnroll) {
+            u64 v[kUnroll];
+#pragma unroll
+            for (int k = 0; k < kUnroll; ++k) {
+                const int e = e0 + k * nthr;
+                v[k] = e < tot ? op.load(p, u, (e / cs) * N2 + cb + (e % cs), P) : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < kUnroll; ++k)
+                if (e0 + k * nthr < tot) sm[e0 + k * nthr] = v[k];
+        }
+        __syncthreads();
+        col_passes<false, LOGR>(sm, cs, k1, T.tw_fwd + (size_t)pi * N, P.q, tid, nthr);
+        for (int e = tid; e < tot; e += nthr) out[(e / cs) * N2 + cb + (e % cs)] = sm[e];
+    } else {
+        const int rs = sp.rs, rb = tile * rs, pitch = ntt_smem_words(N2), tot = rs * N2;
+        for (int e0 = tid; e0 < tot; e0 += nthr * kUnroll) {
+            u64 v[kUnroll];
+#pragma unroll
+            for (int k = 0; k < kUnroll; ++k) {
+                const int e = e0 + k * nthr;
+                v[k] = e < tot ? op.load(p, u, rb * N2 + e, P) : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < kUnroll; ++k) {
+                const int e = e0 + k * nthr;
+                if (e < tot) sm[(e / N2) * pitch + spad(e % N2)] = v[k];
+            }
+        }
+        __syncthreads();
+        row_passes<true, LOGR>(sm, rs, pitch, k1, k2, rb, T.tw_inv + (size_t)pi * N, P.q, tid, nthr);
+        for (int e = tid; e < tot; e += nthr) out[rb * N2 + e] = sm[(e / N2) * pitch + spad(e % N2)];
+    }
+}
+
+// Second pass: for every sub u of the unit in order, read its partial
+// transform (unless direct), finish it (row passes forward, column passes
+// inverse) and run the epilogue (op.pre / op.store) on this block's tile.
+template <bool INV, int LOGR, class Op>
+__global__ void __launch_bounds__(kThr2) k_ntt2_second(Op op, NttTables T, Split2 sp, const u64* __restrict__ S)
+{
+    extern __shared__ u64 sm[];
+    const int k1 = sp.k1, k2 = sp.k2, N1 = 1 << k1, N2 = 1 << k2, N = N1 * N2;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int tiles = INV ? N2 / sp.cs : N1 / sp.rs;
+    const int tile = blockIdx.x % tiles;
+    const int pp = blockIdx.x / tiles;
+    if (pp >= sp.nunits) return;
+    const int p = sp.p0 + pp;
+    const int ns = op.nsub(p);
+    for (int u = 0; u < ns; ++u) {
+        const int pi = op.prime(p, u);
+        const PrimeC P = T.pc[pi];
+        const bool dir = op.direct(p, u);
+        const u64* in = S + ((size_t)pp * ns + u) * N;
+        if (!INV) {
+            const int rs = sp.rs, rb = tile * rs, pitch = ntt_smem_words(N2), tot = rs * N2;
+            if (!dir) {
+                for (int e = tid; e < tot; e += nthr) sm[(e / N2) * pitch + spad(e % N2)] = in[rb * N2 + e];
+                __syncthreads();
+                row_passes<false, LOGR>(sm, rs, pitch, k1, k2, rb, T.tw_fwd + (size_t)pi * N, P.q, tid, nthr);
+            }
+            for (int e0 = tid; e0 < tot; e0 += nthr * kUnroll) {
+                typename Op::Pre pr[kUnroll];
+                u64 v[kUnroll];
+#pragma unroll
+                for (int k = 0; k < kUnroll; ++k) {
+                    const int e = e0 + k * nthr;
+                    if (e < tot) {
+                        pr[k] = op.pre(p, u, rb * N2 + e);
+                        v[k] = dir ? 0 : fwd_final(sm[(e / N2) * pitch + spad(e % N2)], P.q);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < kUnroll; ++k) {
+                    const int e = e0 + k * nthr;
+                    if (e < tot) op.store(p, u, rb * N2 + e, v[k], pr[k], P);
+                }
+            }
+        } else {
+            const int cs = sp.cs, cb = tile * cs, tot = N1 * cs;
+            if (!dir) {
+                for (int e = tid; e < tot; e += nthr) sm[e] = in[(e / cs) * N2 + cb + (e % cs)];
+                __syncthreads();
+                col_passes<true, LOGR>(sm, cs, k1, T.tw_inv + (size_t)pi * N, P.q, tid, nthr);
+            }
+            for (int e0 = tid; e0 < tot; e0 += nthr * kUnroll) {
+                typename Op::Pre pr[kUnroll];
+                u64 v[kUnroll];
+#pragma unroll
+                for (int k = 0; k < kUnroll; ++k) {
+                    const int e = e0 + k * nthr;
+                    if (e < tot) {
+                        const int j = (e / cs) * N2 + cb + (e % cs);
+                        pr[k] = op.pre(p, u, j);
+                        v[k] = dir ? 0 : inv_final(sm[e], P);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < kUnroll; ++k) {
+                    const int e = e0 + k * nthr;
+                    if (e < tot) op.store(p, u, (e / cs) * N2 + cb + (e % cs), v[k], pr[k], P);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}

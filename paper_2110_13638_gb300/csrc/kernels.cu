@@ -103,14 +103,49 @@ static void launch_ntt_v(const fhe_ctx* c, const Op& op, int count, cudaStream_t
     fn<<<count, thr, smem, st>>>(op, c->tabs());
 }
 
+// two-pass schedule: column / row tiles, intermediate in the context's
+// scratch, units processed in chunks that fit it
+template <bool INV, int LOGR, class Op>
+static void launch_ntt_2pass(const fhe_ctx* c, const Op& op, int count, cudaStream_t st)
+{
+    Split2 sp;
+    sp.k1 = (int)c->logN / 2;
+    sp.k2 = (int)c->logN - sp.k1;
+    const int N1 = 1 << sp.k1, N2 = 1 << sp.k2, N = (int)c->N;
+    sp.cs = N2 < kTile2 ? N2 : kTile2;
+    sp.rs = N1 < kTile2 ? N1 : kTile2;
+    const int ns = op.nsub(0);
+    const size_t words = (size_t)(N1 * sp.cs > sp.rs * ntt_smem_words(N2) ? N1 * sp.cs : sp.rs * ntt_smem_words(N2));
+    const size_t smem = words * sizeof(u64);
+    int chunk = (int)(c->ntt2_words / ((size_t)ns * N));
+    if (chunk < 1) chunk = 1;
+    const int t1 = INV ? N1 / sp.rs : N2 / sp.cs;      // tiles of the first pass
+    const int t2 = INV ? N2 / sp.cs : N1 / sp.rs;      // tiles of the second pass
+    for (int p0 = 0; p0 < count; p0 += chunk) {
+        sp.p0 = p0;
+        sp.nunits = count - p0 < chunk ? count - p0 : chunk;
+        {
+            LaunchScope ls(c, Op::family(), st);
+            k_ntt2_first<INV, LOGR, Op><<<sp.nunits * ns * t1, kThr2, smem, st>>>(op, c->tabs(), sp, c->d_ntt2);
+        }
+        {
+            LaunchScope ls(c, Op::family(), st);
+            k_ntt2_second<INV, LOGR, Op><<<sp.nunits * t2, kThr2, smem, st>>>(op, c->tabs(), sp, c->d_ntt2);
+        }
+    }
+}
+
 template <bool INV, class Op>
 static void launch_ntt(const fhe_ctx* c, const Op& op, cudaStream_t st)
 {
     const int count = op.count();
     if (count <= 0) return;
-    switch (c->ntt_variant) {
+    const int v = c->force_single_pass && c->ntt_variant >= 3 ? 0 : c->ntt_variant;
+    switch (v) {
     case 1: launch_ntt_v<INV, 3, 1024>(c, op, count, st); break;
     case 2: launch_ntt_v<INV, 4, 1024>(c, op, count, st); break;
+    case 3: launch_ntt_2pass<INV, 4>(c, op, count, st); break;
+    case 4: launch_ntt_2pass<INV, 3>(c, op, count, st); break;
     default: launch_ntt_v<INV, 4, 512>(c, op, count, st); break;
     }
 }
@@ -120,6 +155,8 @@ const char* ntt_variant_name(int v)
     switch (v) {
     case 1: return "radix-8 passes, 1024 threads";
     case 2: return "radix-16 passes, 1024 threads";
+    case 3: return "two-pass column/row tiles, radix-16";
+    case 4: return "two-pass column/row tiles, radix-8";
     default: return "radix-16 passes, 512 threads";
     }
 }
@@ -133,7 +170,7 @@ struct OpRows {
     int n, rows, N;
     uint8_t pmap[64];
     __host__ __device__ int count() const { return n; }
-    __device__ int nsub(int) const { return 1; }
+    __host__ __device__ int nsub(int) const { return 1; }
     __device__ int prime(int p, int) const { return pmap[p % rows]; }
     __device__ bool direct(int, int) const { return false; }
     __device__ u64 load(int p, int, int j, const PrimeC&) const { return src[(size_t)p * N + j]; }
@@ -298,7 +335,7 @@ struct OpTakeRowInv {
     u64* V;
     int n, L, row, N, pidx;
     __host__ __device__ int count() const { return n; }
-    __device__ int nsub(int) const { return 1; }
+    __host__ __device__ int nsub(int) const { return 1; }
     __device__ int prime(int, int) const { return pidx; }
     __device__ bool direct(int, int) const { return false; }
     __device__ u64 load(int p, int, int j, const PrimeC&) const { return in[((size_t)p * L + row) * N + j]; }
@@ -317,7 +354,7 @@ struct OpDivFwd {
     int n_poly, comps, L_in, L_out, N, addc_stride;
     DivC d;
     __host__ __device__ int count() const { return n_poly * L_out; }
-    __device__ int nsub(int) const { return 1; }
+    __host__ __device__ int nsub(int) const { return 1; }
     __device__ int prime(int p, int) const { return p % L_out; }
     __device__ bool direct(int, int) const { return false; }
     __device__ u64 load(int p, int, int j, const PrimeC& Q) const
@@ -384,7 +421,7 @@ struct OpDigitsInv {
     u64* D;             // [n][L][N]
     int n, L, N;
     __host__ __device__ int count() const { return n * L; }
-    __device__ int nsub(int) const { return 1; }
+    __host__ __device__ int nsub(int) const { return 1; }
     __device__ int prime(int p, int) const { return p % L; }
     __device__ bool direct(int, int) const { return false; }
     __device__ u64 load(int p, int, int j, const PrimeC&) const
@@ -408,7 +445,7 @@ struct OpModUpMac {
     u64* acc;               // [n][2][L+1][N]
     int n, L, N, Ltop;
     __host__ __device__ int count() const { return n * (L + 1); }
-    __device__ int nsub(int) const { return L; }
+    __host__ __device__ int nsub(int) const { return L; }
     __device__ int prime(int p, int) const
     {
         const int t = p % (L + 1);
@@ -458,7 +495,7 @@ struct OpAccPInv {
     u64* Vp;            // [n][2][N]
     int n, L, N, Ltop;
     __host__ __device__ int count() const { return n * 2; }
-    __device__ int nsub(int) const { return 1; }
+    __host__ __device__ int nsub(int) const { return 1; }
     __device__ int prime(int, int) const { return Ltop; }
     __device__ bool direct(int, int) const { return false; }
     __device__ u64 load(int p, int, int j, const PrimeC&) const { return acc[((size_t)p * (L + 1) + L) * N + j]; }
@@ -477,7 +514,7 @@ struct OpModDown {
     int n, L, N;
     DivC d;
     __host__ __device__ int count() const { return n * 2 * L; }
-    __device__ int nsub(int) const { return 1; }
+    __host__ __device__ int nsub(int) const { return 1; }
     __device__ int prime(int p, int) const { return p % L; }
     __device__ bool direct(int, int) const { return false; }
     __device__ u64 load(int p, int, int j, const PrimeC& Q) const
@@ -683,7 +720,7 @@ struct OpSecret {
     u64 s0;
     int nprimes, N;
     __host__ __device__ int count() const { return nprimes; }
-    __device__ int nsub(int) const { return 1; }
+    __host__ __device__ int nsub(int) const { return 1; }
     __device__ int prime(int p, int) const { return p; }
     __device__ bool direct(int, int) const { return false; }
     __device__ u64 load(int, int, int j, const PrimeC& P) const { return from_signed(draw_ternary(s0, j), P); }
@@ -701,7 +738,7 @@ struct OpPublicKey {
     u64 sa, se;
     int Ltop, N;
     __host__ __device__ int count() const { return Ltop; }
-    __device__ int nsub(int) const { return 2; }
+    __host__ __device__ int nsub(int) const { return 2; }
     __device__ int prime(int p, int) const { return p; }
     __device__ bool direct(int, int) const { return false; }
     __device__ u64 load(int p, int u, int j, const PrimeC& P) const
@@ -743,7 +780,7 @@ struct OpRelinKey {
     u64 Pmod[33];       // P mod q_r
     int Ltop, N;
     __host__ __device__ int count() const { return Ltop * (Ltop + 1); }
-    __device__ int nsub(int) const { return 2; }
+    __host__ __device__ int nsub(int) const { return 2; }
     __device__ int prime(int p, int) const { return p % (Ltop + 1); }
     __device__ bool direct(int, int) const { return false; }
     __device__ u64 load(int p, int u, int j, const PrimeC& P) const
@@ -843,7 +880,7 @@ struct OpEncrypt {
     const int8_t* S;    // [n][3][N] samples
     int n, Ltop, N;
     __host__ __device__ int count() const { return n * Ltop; }
-    __device__ int nsub(int) const { return 3; }
+    __host__ __device__ int nsub(int) const { return 3; }
     __device__ int prime(int p, int) const { return p % Ltop; }
     __device__ bool direct(int, int) const { return false; }
     __device__ u64 load(int p, int u, int j, const PrimeC& P) const
@@ -907,7 +944,7 @@ struct OpDecrypt {
     i64* m;
     int n, L, N;
     __host__ __device__ int count() const { return n; }
-    __device__ int nsub(int) const { return 1; }
+    __host__ __device__ int nsub(int) const { return 1; }
     __device__ int prime(int, int) const { return 0; }
     __device__ bool direct(int, int) const { return false; }
     __device__ u64 load(int p, int, int j, const PrimeC& P) const
@@ -1043,7 +1080,7 @@ struct OpSignedRows {
     u64* out;           // [n][L][N]
     int n, L, N;
     __host__ __device__ int count() const { return n * L; }
-    __device__ int nsub(int) const { return 1; }
+    __host__ __device__ int nsub(int) const { return 1; }
     __device__ int prime(int p, int) const { return p % L; }
     __device__ bool direct(int, int) const { return false; }
     __device__ u64 load(int p, int, int j, const PrimeC& P) const { return from_signed(m[(size_t)(p / L) * N + j], P); }

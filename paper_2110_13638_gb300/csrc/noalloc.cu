@@ -75,7 +75,11 @@ extern "C" int fhe_relinearise_noalloc(fhe_ctx* c, const uint64_t* d3, uint32_t 
     void* scratch = nullptr;
     int rc = scratch_for_current_device(&scratch);
     if (rc) return rc;
+    // single-pass transforms only: the two-pass schedule would use the
+    // context's intermediate buffer in addition to the fixed array
+    c->force_single_pass = 1;
     k_relin(c, (const u64*)d3, (u64*)d_out, n_ct, level, scratch, (cudaStream_t)stream);
+    c->force_single_pass = 0;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(e, "relinearise_noalloc launch");
     return FHE_OK;
