@@ -341,6 +341,128 @@ def _host_desc():
     return {"nproc": os.cpu_count(), "cpu": model}
 
 
+# ---------------------------------------------------------------- batching sweep
+def run_batch(args):
+    """4096 ciphertext pairs at uneven levels (L = 1 + U{1..7}, seed 3), each
+    getting ct-mult + relinearise + rescale: all levels in one call whose
+    seven launches are captured in a CUDA graph, against the plain path that
+    calls fhe_mul_relin_rescale once per ciphertext."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    from paper_2110_13638_gb300 import fhe
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    bits = [60] + [40] * 7 + [60]
+    ctx = fhe.Context(16384, bits, 40)
+    ctx.keygen(0)
+    n_ct = args.batch_cts
+    levels = 1 + np.random.Generator(np.random.PCG64(3)).integers(1, 8, size=n_ct)
+    batches = []
+    for L in range(2, 9):
+        n = int((levels == L).sum())
+        if n == 0:
+            continue
+        def rnd():
+            t = torch.empty((n, 2, L, 16384), dtype=torch.int64, device="cuda")
+            for r in range(L):
+                t[:, :, r, :] = torch.randint(0, ctx.primes[r], (n, 2, 16384), device="cuda")
+            return t
+        batches.append((rnd(), rnd(), ctx.empty_ct(n, L - 1), L))
+    ctx.mul_relin_rescale_levels(batches)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            ctx.mul_relin_rescale_levels(batches)
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0.record()
+    for _ in range(args.steps):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    # plain path: one call per ciphertext
+    singles = [(a[k:k + 1], b[k:k + 1], o[k:k + 1], L) for (a, b, o, L) in batches for k in range(a.shape[0])]
+    for a, b, o, L in singles[:16]:
+        ctx.mul_relin_rescale(a, b, L, o)
+    torch.cuda.synchronize()
+    e0.record()
+    for a, b, o, L in singles:
+        ctx.mul_relin_rescale(a, b, L, o)
+    e1.record()
+    torch.cuda.synchronize()
+    ms1 = e0.elapsed_time(e1)
+    line = {"metric": "ct-mult+relin+rescale/s at N=16384", "value": round(n_ct / (ms / 1000.0), 1),
+            "unit": "ops/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64", "data": "synthetic (uniform residues)",
+            "config": {"workload": "%d ciphertext pairs at uneven levels 2..8 (seed 3), one call, 7 launches, "
+                                   "CUDA graph" % n_ct, "level_counts": {int(L): int((levels == L).sum())
+                                                                         for L in range(2, 9)},
+                       "ntt_schedule": ctx.ntt_variant},
+            "one_at_a_time": {"value": round(n_ct / (ms1 / 1000.0), 1), "unit": "ops/s",
+                              "ms_total": round(ms1, 2)},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
+def run_ntt_sweep(args):
+    """Forward residue-NTT throughput, N = 2^13 .. 2^16, 1 .. 30 primes of the
+    40-bit chain, the autotuned schedule against the fixed one (one block per
+    transform at N <= 16384, two-pass above)."""
+    import math
+    import os as _os
+    import torch
+    import __graft_entry__
+    from paper_2110_13638_gb300 import fhe
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    rows = []
+    for logN in range(13, 17):
+        N = 1 << logN
+        for nprime in (1, 2, 4, 8, 16, 30):
+            bits = [40] * nprime + [60]
+            res = {"N": N, "primes": nprime}
+            for mode in ("autotuned", "fixed"):
+                if mode == "fixed":
+                    _os.environ["FHE_NTT_VARIANT"] = "0" if N <= 16384 else "3"
+                try:
+                    ctx = fhe.Context(N, bits, 40)
+                finally:
+                    _os.environ.pop("FHE_NTT_VARIANT", None)
+                groups = max(1, (1 << 26) // (N * nprime))
+                t = torch.zeros((groups, nprime, N), dtype=torch.int64, device="cuda")
+                ctx.ntt(t, nprime, True)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(3):
+                    ctx.ntt(t, nprime, True)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / 3
+                polys = groups * nprime
+                res[mode] = {"schedule": ctx.ntt_variant, "residue_ntts_per_s": round(polys / ms * 1000.0),
+                             "Gbutterfly_s": round(polys * (N // 2) * logN / ms / 1e6, 1)}
+                ctx.close()
+                del t
+            rows.append(res)
+    best = max(r["autotuned"]["residue_ntts_per_s"] * r["N"] for r in rows)
+    line = {"metric": "residue NTTs/s (sweep)", "value": None, "unit": "NTT/s", "sweep": rows,
+            "note": "autotuned vs fixed schedule per (N, primes)"}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     rank, world, local = _env_rank()
     if rank != 0:
@@ -373,7 +495,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cnn", choices=["cnn", "mlp", "dense_square"])
+    ap.add_argument("--workload", default="cnn", choices=["cnn", "mlp", "dense_square", "batch", "ntt_sweep"])
+    ap.add_argument("--batch-cts", type=int, default=4096)
     ap.add_argument("--profile-family", default=DOMINANT)
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the dominant kernel (from profiles/)")
@@ -383,6 +506,10 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "ntt_sweep":
+        run_ntt_sweep(args)
     else:
         run_ours(args)
 

@@ -129,7 +129,8 @@ int fhe_gauss_table(uint64_t* out38);
  * batch of transforms; the environment variable FHE_NTT_VARIANT=0..4 fixes
  * it instead.  bits: coefficient-modulus bit sizes, the
  * last one being the special prime; log_scale: scale 2^log_scale.
- * N must be a power of two in [16, 16384]. */
+ * N must be a power of two in [16, 65536]; above 16384 only the two-pass
+ * NTT schedules exist and encode / decode / grouped calls are refused. */
 int fhe_ctx_create(uint32_t N, const uint32_t* bits, uint32_t n_bits,
                    uint32_t log_scale, fhe_ctx** out);
 int fhe_ctx_destroy(fhe_ctx* ctx);
@@ -217,6 +218,23 @@ int fhe_rescale(fhe_ctx* ctx, const uint64_t* d_in, uint32_t n_ct, uint32_t comp
  * d_out [n_ct][2][level-1][N] = rescale(relin(a (x) b)). */
 int fhe_mul_relin_rescale(fhe_ctx* ctx, const uint64_t* d_a, const uint64_t* d_b, uint32_t n_ct,
                           uint32_t level, uint64_t* d_out, void* stream);
+
+/* One batch of ciphertext pairs at one level (for fhe_mul_relin_rescale_levels). */
+typedef struct {
+    const uint64_t* d_a;     /* [n_ct][2][level][N] */
+    const uint64_t* d_b;     /* [n_ct][2][level][N] */
+    uint64_t* d_out;         /* [n_ct][2][level-1][N] */
+    uint32_t n_ct;
+    uint32_t level;          /* 2 .. L_top */
+} fhe_level_batch;
+
+/* ct-mult + relinearise + rescale for ciphertexts at uneven levels: each
+ * step (tensor, the four key-switching transforms, the two rescale
+ * transforms) is ONE launch over every batch, located by prefix sums, so the
+ * whole set costs seven launches and can be captured in a CUDA graph (after a
+ * first call has sized the workspace).  Up to 8 batches per call (more are
+ * processed 8 at a time).  Same results as fhe_mul_relin_rescale per batch. */
+int fhe_mul_relin_rescale_levels(fhe_ctx* ctx, const fhe_level_batch* batches, uint32_t n_batches, void* stream);
 
 /* multiply by integer constants: ct_k *= C_k (one signed constant per
  * ciphertext, host array) ; and add integer constants to the constant term. */

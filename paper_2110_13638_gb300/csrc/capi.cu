@@ -17,6 +17,8 @@
 
 using namespace fhe;
 
+static constexpr uint32_t kMaxLevelBatches = 8;
+
 namespace fhe {
 
 static thread_local std::string g_err;
@@ -231,6 +233,7 @@ static int autotune_ntt(fhe_ctx* c)
     if (env && *env) {
         int v = std::atoi(env);
         if (v < 0 || v >= kNttVariants) return fail(FHE_EINVAL, "FHE_NTT_VARIANT out of range (0..4)");
+        if (c->N > kMaxSinglePassN && v < 3) return fail(FHE_EINVAL, "N > 16384 needs a two-pass NTT schedule (3 or 4)");
         c->ntt_variant = v;
         return FHE_OK;
     }
@@ -251,6 +254,7 @@ static int autotune_ntt(fhe_ctx* c)
     cudaEventCreate(&b);
     float best = 1e30f;
     for (int v = 0; v < kNttVariants; ++v) {
+        if (c->N > kMaxSinglePassN && v < 3) continue;     // one block per transform needs N <= 16384
         c->ntt_variant = v;
         k_ntt_rows(c, buf, groups, rows, pm, true, nullptr);       // warm-up
         cudaEventRecord(a, nullptr);
@@ -264,9 +268,9 @@ static int autotune_ntt(fhe_ctx* c)
         c->ntt_variant_us[v] = us;
         if (us < best) best = us;
     }
-    int pick = 0;
+    int pick = c->N > kMaxSinglePassN ? 3 : 0;
     for (int v = 0; v < kNttVariants; ++v)
-        if (c->ntt_variant_us[v] == best) { pick = v; break; }
+        if (c->ntt_variant_us[v] > 0.f && c->ntt_variant_us[v] == best) { pick = v; break; }
     c->ntt_variant = pick;
     cudaEventDestroy(a);
     cudaEventDestroy(b);
@@ -279,7 +283,7 @@ int fhe_ctx_create(uint32_t N, const uint32_t* bits, uint32_t n_bits, uint32_t l
 {
     if (!out || !bits) return fail(FHE_EINVAL, "null argument");
     *out = nullptr;
-    if (N < 16 || N > 16384 || (N & (N - 1))) return fail(FHE_EUNSUPPORTED, "N must be a power of two in [16, 16384]");
+    if (N < 16 || N > 65536 || (N & (N - 1))) return fail(FHE_EUNSUPPORTED, "N must be a power of two in [16, 65536]");
     if (n_bits < 2 || n_bits > 33) return fail(FHE_EINVAL, "need 2..33 coefficient-modulus entries");
     if (log_scale < 1 || log_scale > 60) return fail(FHE_EINVAL, "log_scale out of range");
     std::vector<u64> ch;
@@ -446,6 +450,7 @@ int fhe_encode(fhe_ctx* c, const double* d_slots, uint32_t n_ct, uint32_t level,
     if (!d_slots || !d_pt) return fail(FHE_EINVAL, "null buffer");
     if (level < 1 || level > c->L_top) return fail(FHE_ELEVEL, "level out of range");
     if (!(scale > 0.0) || !std::isfinite(scale)) return fail(FHE_EINVAL, "bad scale");
+    if (c->N > kMaxSinglePassN) return fail(FHE_EUNSUPPORTED, "encode supports N <= 16384");
     Arena ar;
     int rc = ws_reserve(c, encode_scratch_bytes(c, n_ct), &ar);
     if (rc) return rc;
@@ -487,6 +492,7 @@ int fhe_decode(fhe_ctx* c, const int64_t* d_m, uint32_t n_ct, double scale, doub
     if (n_ct == 0) return FHE_OK;
     if (!d_m || !d_slots) return fail(FHE_EINVAL, "null buffer");
     if (!(scale > 0.0) || !std::isfinite(scale)) return fail(FHE_EINVAL, "bad scale");
+    if (c->N > kMaxSinglePassN) return fail(FHE_EUNSUPPORTED, "decode supports N <= 16384");
     k_decode(c, (const i64*)d_m, n_ct, scale, d_slots, (cudaStream_t)stream);
     CUDA_LAST("decode launch");
     return FHE_OK;
@@ -603,6 +609,38 @@ int fhe_mul_relin_rescale(fhe_ctx* c, const uint64_t* a, const uint64_t* b, uint
     k_relin(c, t3, t2, n_ct, level, sr, st);
     k_rescale(c, t2, (u64*)out, n_ct, 2, level, nullptr, 0, ss, st);
     CUDA_LAST("mul_relin_rescale launch");
+    return FHE_OK;
+}
+
+int fhe_mul_relin_rescale_levels(fhe_ctx* c, const fhe_level_batch* batches, uint32_t n_batches, void* stream)
+{
+    CHECK_CTX(c);
+    CHECK_KEYS(c);
+    if (n_batches == 0) return FHE_OK;
+    if (!batches) return fail(FHE_EINVAL, "null batch table");
+    if (c->N > kMaxSinglePassN) return fail(FHE_EUNSUPPORTED, "grouped steps need N <= 16384");
+    for (uint32_t k = 0; k < n_batches; ++k) {
+        const fhe_level_batch& b = batches[k];
+        if (b.level < 2 || b.level > c->L_top) return fail(FHE_ELEVEL, "batch level out of range");
+        if (b.n_ct && (!b.d_a || !b.d_b || !b.d_out)) return fail(FHE_EINVAL, "null batch buffer");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    for (uint32_t k0 = 0; k0 < n_batches; k0 += kMaxLevelBatches) {
+        LevelBatch g[kMaxLevelBatches];
+        int ng = 0;
+        for (uint32_t k = k0; k < n_batches && k < k0 + kMaxLevelBatches; ++k) {
+            if (batches[k].n_ct == 0) continue;
+            g[ng++] = LevelBatch{(const u64*)batches[k].d_a, (const u64*)batches[k].d_b, (u64*)batches[k].d_out,
+                                 batches[k].n_ct, batches[k].level};
+        }
+        if (ng == 0) continue;
+        const size_t need = level_groups_scratch_bytes(c, g, ng);
+        Arena ar;
+        int rc = ws_reserve(c, need, &ar);
+        if (rc) return rc;
+        k_mul_relin_rescale_groups(c, g, ng, ar.take(need), st);
+        CUDA_LAST("mul_relin_rescale_levels launch");
+    }
     return FHE_OK;
 }
 

@@ -167,6 +167,16 @@ constexpr int kMacTile = 8;
 void k_linear_mac_tiled(const fhe_ctx* c, const u64* X, const uint4* tiles, uint32_t n_tiles, const uint32_t* rows,
                         const uint32_t* col, const u64* W, uint32_t L, u64* Y, cudaStream_t st);
 
+// ct-mult + relinearise + rescale over batches at different levels (<= 8 batches)
+struct LevelBatch {
+    const u64* a;
+    const u64* b;
+    u64* out;
+    uint32_t n, L;
+};
+size_t level_groups_scratch_bytes(const fhe_ctx* c, const LevelBatch* g, int ng);
+void k_mul_relin_rescale_groups(const fhe_ctx* c, const LevelBatch* g, int ng, void* scratch, cudaStream_t st);
+
 void k_keygen(fhe_ctx* c, cudaStream_t st);
 size_t encrypt_scratch_bytes(const fhe_ctx* c, uint32_t n_ct);
 void k_encrypt(const fhe_ctx* c, const u64* pt, uint32_t n_ct, uint64_t first_id, u64* ct, void* scratch,
@@ -180,5 +190,6 @@ void k_decode(const fhe_ctx* c, const i64* m, uint32_t n_ct, double scale, doubl
 uint64_t stream_key(uint64_t seed, uint64_t domain, uint64_t object);
 const char* ntt_variant_name(int v);
 constexpr int kNttVariants = 5;
+constexpr uint32_t kMaxSinglePassN = 16384;   // one transform per block in shared memory
 
 }  // namespace fhe

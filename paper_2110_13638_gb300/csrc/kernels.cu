@@ -103,6 +103,66 @@ static void launch_ntt_v(const fhe_ctx* c, const Op& op, int count, cudaStream_t
     fn<<<count, thr, smem, st>>>(op, c->tabs());
 }
 
+// Several batches of one transform step, each with its own level, in ONE
+// launch: unit p is located in the group table by prefix sums.
+constexpr int kMaxGroups = 8;
+
+template <class Op>
+struct MultiOp {
+    static const char* family() { return Op::family(); }
+    typedef typename Op::Pre Pre;
+    Op ops[kMaxGroups];
+    int pre_[kMaxGroups + 1];
+    int ng;
+    __host__ __device__ int count() const { return pre_[ng]; }
+    __host__ __device__ int locate(int p, int& q) const
+    {
+        int g = 0;
+        while (g + 1 < ng && p >= pre_[g + 1]) ++g;
+        q = p - pre_[g];
+        return g;
+    }
+    __host__ __device__ int nsub(int p) const
+    {
+        int q;
+        const int g = locate(p, q);
+        return ops[g].nsub(q);
+    }
+    __device__ int prime(int p, int u) const
+    {
+        int q;
+        const int g = locate(p, q);
+        return ops[g].prime(q, u);
+    }
+    __device__ bool direct(int p, int u) const
+    {
+        int q;
+        const int g = locate(p, q);
+        return ops[g].direct(q, u);
+    }
+    __device__ u64 load(int p, int u, int j, const PrimeC& P) const
+    {
+        int q;
+        const int g = locate(p, q);
+        return ops[g].load(q, u, j, P);
+    }
+    __device__ Pre pre(int p, int u, int j) const
+    {
+        int q;
+        const int g = locate(p, q);
+        return ops[g].pre(q, u, j);
+    }
+    __device__ void store(int p, int u, int j, u64 v, const Pre& pr, const PrimeC& P) const
+    {
+        int q;
+        const int g = locate(p, q);
+        ops[g].store(q, u, j, v, pr, P);
+    }
+};
+
+template <class Op> struct uniform_subs { static constexpr bool value = true; };
+template <class Op> struct uniform_subs<MultiOp<Op>> { static constexpr bool value = false; };
+
 // two-pass schedule: column / row tiles, intermediate in the context's
 // scratch, units processed in chunks that fit it
 template <bool INV, int LOGR, class Op>
@@ -140,7 +200,10 @@ static void launch_ntt(const fhe_ctx* c, const Op& op, cudaStream_t st)
 {
     const int count = op.count();
     if (count <= 0) return;
-    const int v = c->force_single_pass && c->ntt_variant >= 3 ? 0 : c->ntt_variant;
+    // the two-pass schedule needs the same number of transforms in every unit
+    const bool single = c->force_single_pass || !uniform_subs<Op>::value;
+    // (callers refuse single-pass-only work above kMaxSinglePassN)
+    const int v = single && c->ntt_variant >= 3 ? 1 : c->ntt_variant;
     switch (v) {
     case 1: launch_ntt_v<INV, 3, 1024>(c, op, count, st); break;
     case 2: launch_ntt_v<INV, 4, 1024>(c, op, count, st); break;
@@ -574,6 +637,135 @@ void k_relin(const fhe_ctx* c, const u64* d3, u64* out2, uint32_t n_ct, uint32_t
     s4.N = (int)N;
     s4.d = make_divc(c, c->L_top, L);
     launch_ntt<false>(c, s4, st);
+}
+
+// ---------------------------------------------------------------- level groups
+// ct-mult + relinearise + rescale for batches at different levels: every step
+// is one launch over all batches (MultiOp), so a set of uneven-level
+// ciphertexts costs seven launches whatever its level mix.
+struct TensorGroups {
+    const u64* a[kMaxGroups];
+    const u64* b[kMaxGroups];
+    u64* out[kMaxGroups];
+    unsigned long long start[kMaxGroups + 1];
+    int L[kMaxGroups];
+    int ng;
+};
+
+__global__ void k_tensor_groups_kernel(TensorGroups G, int logN, const PrimeC* __restrict__ pc)
+{
+    const size_t total = G.start[G.ng];
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        int g = 0;
+        while (g + 1 < G.ng && i >= G.start[g + 1]) ++g;
+        const size_t w0 = i - G.start[g];
+        const size_t per_comp = (size_t)G.L[g] << logN;
+        const size_t ct = w0 / per_comp, w = w0 % per_comp;
+        const int r = (int)(w >> logN);
+        const PrimeC P = pc[r];
+        const u64* A = G.a[g] + ct * 2 * per_comp;
+        const u64* B = G.b[g] + ct * 2 * per_comp;
+        const u64 a0 = A[w], a1 = A[per_comp + w], b0 = B[w], b1 = B[per_comp + w];
+        u64* O = G.out[g] + ct * 3 * per_comp;
+        O[w] = mul_mod(a0, b0, P);
+        O[per_comp + w] = add_mod(mul_mod(a0, b1, P), mul_mod(a1, b0, P), P.q);
+        O[2 * per_comp + w] = mul_mod(a1, b1, P);
+    }
+}
+
+size_t level_groups_scratch_bytes(const fhe_ctx* c, const LevelBatch* g, int ng)
+{
+    const size_t N = c->N;
+    size_t s = 0;
+    for (int k = 0; k < ng; ++k) {
+        const size_t n = g[k].n, L = g[k].L;
+        s += arena_need({n * 3 * L * N * 8, n * 2 * L * N * 8, n * L * N * 8, n * 2 * (L + 1) * N * 8,
+                         n * 2 * N * 8, n * 2 * N * 8});
+    }
+    return s;
+}
+
+void k_mul_relin_rescale_groups(const fhe_ctx* c, const LevelBatch* g, int ng, void* scratch, cudaStream_t st)
+{
+    const size_t N = c->N;
+    Arena ar;
+    ar.base = (char*)scratch;
+    ar.cap = level_groups_scratch_bytes(c, g, ng);
+    TensorGroups tg;
+    MultiOp<OpDigitsInv> m1;
+    MultiOp<OpModUpMac> m2;
+    MultiOp<OpAccPInv> m3;
+    MultiOp<OpModDown> m4;
+    MultiOp<OpTakeRowInv> m5;
+    MultiOp<OpDivFwd> m6;
+    m1.ng = m2.ng = m3.ng = m4.ng = m5.ng = m6.ng = tg.ng = ng;
+    m1.pre_[0] = m2.pre_[0] = m3.pre_[0] = m4.pre_[0] = m5.pre_[0] = m6.pre_[0] = 0;
+    tg.start[0] = 0;
+    for (int k = 0; k < ng; ++k) {
+        const int n = (int)g[k].n, L = (int)g[k].L;
+        u64* t3 = (u64*)ar.take((size_t)n * 3 * L * N * 8);
+        u64* t2 = (u64*)ar.take((size_t)n * 2 * L * N * 8);
+        u64* D = (u64*)ar.take((size_t)n * L * N * 8);
+        u64* acc = (u64*)ar.take((size_t)n * 2 * (L + 1) * N * 8);
+        u64* Vp = (u64*)ar.take((size_t)n * 2 * N * 8);
+        u64* V = (u64*)ar.take((size_t)n * 2 * N * 8);
+        tg.a[k] = g[k].a;
+        tg.b[k] = g[k].b;
+        tg.out[k] = t3;
+        tg.L[k] = L;
+        tg.start[k + 1] = tg.start[k] + (unsigned long long)n * L * N;
+        m1.ops[k] = OpDigitsInv{t3, D, n, L, (int)N};
+        m2.ops[k] = OpModUpMac{t3, D, c->d_ksk, acc, n, L, (int)N, (int)c->L_top};
+        m3.ops[k] = OpAccPInv{acc, Vp, n, L, (int)N, (int)c->L_top};
+        OpModDown md;
+        md.d3 = t3;
+        md.acc = acc;
+        md.Vp = Vp;
+        md.out = t2;
+        md.n = n;
+        md.L = L;
+        md.N = (int)N;
+        md.d = make_divc(c, c->L_top, L);
+        m4.ops[k] = md;
+        OpTakeRowInv tr;
+        tr.in = t2;
+        tr.V = V;
+        tr.n = n * 2;
+        tr.L = L;
+        tr.row = L - 1;
+        tr.N = (int)N;
+        tr.pidx = L - 1;
+        m5.ops[k] = tr;
+        OpDivFwd dv;
+        dv.in = t2;
+        dv.V = V;
+        dv.out = g[k].out;
+        dv.addc = nullptr;
+        dv.addc_stride = 0;
+        dv.n_poly = n * 2;
+        dv.comps = 2;
+        dv.L_in = L;
+        dv.L_out = L - 1;
+        dv.N = (int)N;
+        dv.d = make_divc(c, L - 1, L - 1);
+        m6.ops[k] = dv;
+        m1.pre_[k + 1] = m1.pre_[k] + m1.ops[k].count();
+        m2.pre_[k + 1] = m2.pre_[k] + m2.ops[k].count();
+        m3.pre_[k + 1] = m3.pre_[k] + m3.ops[k].count();
+        m4.pre_[k + 1] = m4.pre_[k] + m4.ops[k].count();
+        m5.pre_[k + 1] = m5.pre_[k] + m5.ops[k].count();
+        m6.pre_[k + 1] = m6.pre_[k] + m6.ops[k].count();
+    }
+    {
+        LaunchScope ls(c, "tensor", st);
+        k_tensor_groups_kernel<<<ew_grid(tg.start[ng]), 256, 0, st>>>(tg, (int)c->logN, c->d_pc);
+    }
+    launch_ntt<true>(c, m1, st);
+    launch_ntt<false>(c, m2, st);
+    launch_ntt<true>(c, m3, st);
+    launch_ntt<false>(c, m4, st);
+    launch_ntt<true>(c, m5, st);
+    launch_ntt<false>(c, m6, st);
 }
 
 // ---------------------------------------------------------------- linear layers

@@ -63,6 +63,7 @@ extern "C" int fhe_relinearise_noalloc(fhe_ctx* c, const uint64_t* d3, uint32_t 
     if (level < 1 || level > c->L_top) return fail(FHE_ELEVEL, "level out of range");
     if (n_ct == 0) return FHE_OK;
     if (!d3 || !d_out) return fail(FHE_EINVAL, "null buffer");
+    if (c->N > kMaxSinglePassN) return fail(FHE_EUNSUPPORTED, "fhe_relinearise_noalloc supports N <= 16384");
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_check(e, "cudaGetDevice");

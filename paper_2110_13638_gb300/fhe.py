@@ -41,6 +41,11 @@ class CtMeta(ctypes.Structure):
     _fields_ = [("level", ctypes.c_uint32), ("scale", ctypes.c_double)]
 
 
+class LevelBatch(ctypes.Structure):
+    _fields_ = [("d_a", ctypes.c_void_p), ("d_b", ctypes.c_void_p), ("d_out", ctypes.c_void_p),
+                ("n_ct", ctypes.c_uint32), ("level", ctypes.c_uint32)]
+
+
 class NodeDesc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_uint32), ("n_out", ctypes.c_uint32),
                 ("row_ptr", ctypes.POINTER(ctypes.c_uint32)), ("col_idx", ctypes.POINTER(ctypes.c_uint32)),
@@ -81,6 +86,7 @@ SIGNATURES = {
     "fhe_relinearise_noalloc": [_P, _P, _U32, _U32, _P, _P],
     "fhe_rescale": [_P, _P, _U32, _U32, _U32, _P, _P],
     "fhe_mul_relin_rescale": [_P, _P, _P, _U32, _U32, _P, _P],
+    "fhe_mul_relin_rescale_levels": [_P, _P, _U32, _P],
     "fhe_mul_const": [_P, _P, _P, _U32, _U32, _P, _P],
     "fhe_add_const": [_P, _P, _P, _U32, _U32, _P],
     "fhe_graph_create": [_P, _P],
@@ -310,6 +316,14 @@ class Context:
     def mul_relin_rescale(self, a, b, level, out, stream=None):
         _check(lib().fhe_mul_relin_rescale(self.h, _ptr(a), _ptr(b), a.shape[0], level, _ptr(out),
                                            _stream(stream)))
+
+    def mul_relin_rescale_levels(self, batches, stream=None):
+        """batches: list of (a, b, out, level) tensors; every step is one
+        launch over all batches."""
+        arr = (LevelBatch * len(batches))()
+        for k, (a, b, out, level) in enumerate(batches):
+            arr[k] = LevelBatch(a.data_ptr(), b.data_ptr(), out.data_ptr(), a.shape[0], level)
+        _check(lib().fhe_mul_relin_rescale_levels(self.h, arr, len(batches), _stream(stream)))
 
     def mul_const(self, x, consts, level, out, stream=None):
         c = np.ascontiguousarray(consts, dtype=np.int64)

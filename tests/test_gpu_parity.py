@@ -277,3 +277,81 @@ def test_graph_cfg0_full_size_bit_exact():
     graph, x = W.cfg0()
     err = _graph_parity(g, o, graph, [x], [0])
     assert err < 1e-4
+
+
+# ---------------------------------------------------------------- uneven levels, one launch per step
+def test_mul_relin_rescale_levels_matches_per_batch_and_oracle():
+    g, o = pair(1024, BITS9)
+    rng = np.random.default_rng(42)
+    batches, ref_outs = [], []
+    keep = {}
+    for L in range(2, 9):
+        n = int(rng.integers(1, 4))
+        A = [rand_ct(o, L, rng) for _ in range(n)]
+        B = [rand_ct(o, L, rng) for _ in range(n)]
+        ta, tb = upload(g, A, L), upload(g, B, L)
+        out = g.empty_ct(n, L - 1)
+        ref = g.empty_ct(n, L - 1)
+        g.mul_relin_rescale(ta, tb, L, ref)
+        batches.append((ta, tb, out, L))
+        ref_outs.append(ref)
+        keep[L] = (A, B)
+    g.mul_relin_rescale_levels(batches)
+    torch.cuda.synchronize()
+    for (ta, tb, out, L), ref in zip(batches, ref_outs):
+        assert torch.equal(out, ref), L
+    # one level against the oracle directly
+    L = 5
+    A, B = keep[L]
+    got = download(g, batches[L - 2][2], L - 1)
+    want = o.rescale(o.relinearise(o.tensor(ckks.Ciphertext(A[0], L, 1.0), ckks.Ciphertext(B[0], L, 1.0)))).c
+    assert np.array_equal(got[0], want)
+
+
+def test_mul_relin_rescale_levels_in_cuda_graph():
+    g, o = pair(1024, BITS9)
+    rng = np.random.default_rng(43)
+    batches = []
+    for L in (3, 8, 6):
+        A = [rand_ct(o, L, rng) for _ in range(2)]
+        B = [rand_ct(o, L, rng) for _ in range(2)]
+        batches.append((upload(g, A, L), upload(g, B, L), g.empty_ct(2, L - 1), L))
+    g.mul_relin_rescale_levels(batches)          # sizes the workspace
+    torch.cuda.synchronize()
+    want = [b[2].clone() for b in batches]
+    for b in batches:
+        b[2].zero_()
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            g.mul_relin_rescale_levels(batches)
+    torch.cuda.current_stream().wait_stream(s)
+    graph.replay()
+    torch.cuda.synchronize()
+    for b, w in zip(batches, want):
+        assert torch.equal(b[2], w)
+
+
+# ---------------------------------------------------------------- rings above 16384 (two-pass NTT only)
+@pytest.mark.parametrize("N", [32768, 65536])
+def test_large_ring_transform_tensor_relin(N):
+    bits = [60, 40, 60]
+    g, o = pair(N, bits)
+    assert g.ntt_variant in (3, 4)
+    rng = np.random.default_rng(N)
+    L = 2
+    A = [rand_ct(o, L, rng)]
+    B = [rand_ct(o, L, rng)]
+    ta, tb = upload(g, A, L), upload(g, B, L)
+    assert np.array_equal(download(g, ta, L), np.stack(A))
+    t3 = g.empty_ct(1, L, comps=3)
+    g.tensor(ta, tb, L, t3)
+    want = o.tensor(ckks.Ciphertext(A[0], L, 1.0), ckks.Ciphertext(B[0], L, 1.0))
+    assert np.array_equal(download(g, t3, L)[0], want.c)
+    out = g.empty_ct(1, L)
+    g.relinearise(t3, L, out)
+    assert np.array_equal(download(g, out, L)[0], o.relinearise(want).c)
+    with pytest.raises(fhe.FheError):
+        g.encode(torch.zeros((1, N // 2), dtype=torch.float64, device="cuda"), L, g.delta, g.empty_pt(1, L))
