@@ -463,6 +463,79 @@ def run_ntt_sweep(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- serving
+def serving_setup(torch):
+    from paper_2110_13638_gb300 import fhe, serve, workloads as W
+    nets = []
+    ctxs = {}
+    for name, builder in (("dense_square", W.cfg0), ("cnn", W.cfg1), ("mlp", W.cfg2)):
+        g, x = builder()
+        gof, gcost = fhe.autohe(g)
+        N, bits = fhe.parameterise(max(gcost), 40, 1.5)
+        key = (N, tuple(bits))
+        if key not in ctxs:                      # one context (and one key set) per parameter set
+            c = fhe.Context(N, bits, 40)
+            c.keygen(0)
+            ctxs[key] = c
+        nets.append(serve.Network(name, g, x, ctxs[key]))
+    return nets, ctxs
+
+
+def poisson_requests(nets, seconds, lam=200.0, weights=(0.5, 0.3, 0.2), seed=4):
+    import numpy as np
+    from paper_2110_13638_gb300 import serve
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t, reqs = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / lam)
+        if t > seconds:
+            break
+        k = int(rng.choice(len(nets), p=list(weights)))
+        n = int(rng.integers(1, 8193))
+        off = int(rng.integers(0, 1 << 20))
+        reqs.append(serve.Request(len(reqs), nets[k], t, n, nets[k].inputs(off, n)))
+    return reqs
+
+
+def run_serve(args):
+    """Poisson arrivals (200 req/s, mix 0.5 / 0.3 / 0.2 of the dense+square
+    network, the CNN and the yield MLP, 1..8192 samples each) for
+    --serve-seconds, continuous batching under a 150 GB admission cap, against
+    serial one-request-at-a-time evaluation on the same GPU."""
+    import torch
+    import __graft_entry__
+    from paper_2110_13638_gb300 import serve
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    nets, ctxs = serving_setup(torch)
+    cap = 150e9
+    out = {"metric": "serve samples/s, p50/p99 ms", "unit": "samples/s", "n_gpus": 1,
+           "config": {"workload": "Poisson 200 req/s, mix 0.5/0.3/0.2 (dense+square N=8192 / CNN / yield MLP "
+                                  "N=16384), 1..8192 samples, %gs of arrivals, admission cap 150 GB" % args.serve_seconds,
+                      "parameter_sets": len(ctxs)}}
+    for mode in ("continuous", "serial"):
+        reqs = poisson_requests(nets, args.serve_seconds)
+        offered = sum(r.n for r in reqs) / args.serve_seconds
+        if mode == "continuous":
+            srv = serve.Server(nets, {"dense_square": 2, "cnn": 3, "mlp": 2}, cap, pack=True)
+        else:
+            srv = serve.Server(nets, {"dense_square": 1, "cnn": 1, "mlp": 1}, cap, pack=False, max_inflight=1)
+        torch.cuda.synchronize()
+        done, wall, backlog = srv.run(reqs, horizon=args.serve_seconds)
+        st = serve.latency_stats(done, wall)
+        st.update({"arrived": len(reqs), "backlog_at_horizon": backlog, "offered_samples_per_s": round(offered, 1),
+                   "slots": {k: len(v) for k, v in srv.slots.items()},
+                   "footprint_GB": round(srv.footprint / 1e9, 2)})
+        for net in nets:
+            d = [r for r in done if r.net is net]
+            st[net.name] = serve.latency_stats(d, wall) if d else {"completed": 0}
+        out[mode] = st
+        del srv
+        torch.cuda.synchronize()
+    out["value"] = out["continuous"].get("samples_per_s")
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args):
     rank, world, local = _env_rank()
     if rank != 0:
@@ -495,7 +568,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cnn", choices=["cnn", "mlp", "dense_square", "batch", "ntt_sweep"])
+    ap.add_argument("--workload", default="cnn", choices=["cnn", "mlp", "dense_square", "batch", "ntt_sweep", "serve"])
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--batch-cts", type=int, default=4096)
     ap.add_argument("--profile-family", default=DOMINANT)
     ap.add_argument("--traffic", type=float, default=None,
@@ -510,6 +584,8 @@ def main():
         run_batch(args)
     elif args.workload == "ntt_sweep":
         run_ntt_sweep(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

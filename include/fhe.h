@@ -133,6 +133,13 @@ int fhe_gauss_table(uint64_t* out38);
  * NTT schedules exist and encode / decode / grouped calls are refused. */
 int fhe_ctx_create(uint32_t N, const uint32_t* bits, uint32_t n_bits,
                    uint32_t log_scale, fhe_ctx** out);
+/* A fork shares the parent's tables and keys (resident once per parameter
+ * set) and owns only its workspace, so calls on a parent and its forks may
+ * run concurrently on different streams.  Forks of a fork fork the parent.
+ * The parent must outlive its forks; keys must be generated on the parent
+ * before forking (a fork copies the key pointers at fork time).  Serving
+ * infrastructure: the paper has no counterpart. */
+int fhe_ctx_fork(fhe_ctx* parent, fhe_ctx** out);
 int fhe_ctx_destroy(fhe_ctx* ctx);
 int fhe_ctx_query(const fhe_ctx* ctx, fhe_ctx_info* out);
 

@@ -210,6 +210,12 @@ int fhe_autohe(const fhe_graph_desc* g, uint32_t* group_of, uint32_t group_of_ca
 static void free_ctx(fhe_ctx* c)
 {
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    if (c->parent) {            // shared tables and keys belong to the parent
+        cudaFree(c->ws);
+        cudaFree(c->d_ntt2);
+        delete c;
+        return;
+    }
     cudaFree(c->d_pc);
     cudaFree(c->d_tw_fwd);
     cudaFree(c->d_tw_inv);
@@ -382,6 +388,47 @@ int fhe_ctx_create(uint32_t N, const uint32_t* bits, uint32_t n_bits, uint32_t l
     return FHE_OK;
 }
 
+int fhe_ctx_fork(fhe_ctx* parent, fhe_ctx** out)
+{
+    CHECK_CTX(parent);
+    if (!out) return fail(FHE_EINVAL, "null output");
+    *out = nullptr;
+    if (parent->parent) parent = parent->parent;
+    fhe_ctx* c = new fhe_ctx();
+    c->N = parent->N;
+    c->logN = parent->logN;
+    c->L_top = parent->L_top;
+    c->log_scale = parent->log_scale;
+    c->primes = parent->primes;
+    c->pc = parent->pc;
+    c->delta = parent->delta;
+    c->device = parent->device;
+    c->ntt_variant = parent->ntt_variant;
+    for (int v = 0; v < 8; ++v) c->ntt_variant_us[v] = parent->ntt_variant_us[v];
+    c->d_pc = parent->d_pc;
+    c->d_tw_fwd = parent->d_tw_fwd;
+    c->d_tw_inv = parent->d_tw_inv;
+    c->d_cdt = parent->d_cdt;
+    c->d_enc_tw = parent->d_enc_tw;
+    c->d_enc_twist = parent->d_enc_twist;
+    c->d_slot_of = parent->d_slot_of;
+    c->has_keys = parent->has_keys;
+    c->seed = parent->seed;
+    c->d_s = parent->d_s;
+    c->d_pk = parent->d_pk;
+    c->d_ksk = parent->d_ksk;
+    c->parent = parent;
+    c->ntt2_words = parent->ntt2_words;
+    cudaError_t e = cudaMalloc((void**)&c->d_ntt2, c->ntt2_words * 8);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return cuda_check(e, "fork scratch");
+    }
+    *out = c;
+    return FHE_OK;
+}
+
 int fhe_ctx_destroy(fhe_ctx* c)
 {
     if (!c) return FHE_OK;
@@ -409,6 +456,7 @@ int fhe_ctx_query(const fhe_ctx* c, fhe_ctx_info* out)
 int fhe_keygen(fhe_ctx* c, uint64_t seed, void* stream)
 {
     CHECK_CTX(c);
+    if (c->parent) return fail(FHE_EINVAL, "keygen on a fork: generate keys on the parent context");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t N = c->N, Lt = c->L_top;
     if (!c->d_s) {

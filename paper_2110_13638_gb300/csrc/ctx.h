@@ -37,6 +37,10 @@ struct fhe_ctx {
     ulonglong2* d_ksk = nullptr;   // [L_top][2][L_top + 1][N] (key word, Shoup quotient)
     size_t key_bytes = 0;
 
+    // a fork shares tables and keys with its parent (which must outlive it)
+    // and owns only its workspace and two-pass scratch
+    fhe_ctx* parent = nullptr;
+
     // call workspace (grows on demand)
     void* ws = nullptr;
     size_t ws_bytes = 0;

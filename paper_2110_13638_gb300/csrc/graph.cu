@@ -564,7 +564,8 @@ int fhe_eval_graph(fhe_ctx* c, const fhe_graph* gc, const uint64_t* const* d_in,
     if (!c || !gc || !d_in || !d_out) return fail(FHE_EINVAL, "null argument");
     if (!c->has_keys) return fail(FHE_ENOKEY, "fhe_keygen has not run");
     fhe_graph* g = const_cast<fhe_graph*>(gc);
-    if (g->cache_ctx != c) {
+    const fhe_ctx* root = c->parent ? c->parent : c;     // forks share the primes
+    if (g->cache_ctx != root) {
         bool any = false;
         for (auto& nc : g->cache) any |= (nc.buf != nullptr);
         if (any) cudaDeviceSynchronize();
@@ -572,7 +573,7 @@ int fhe_eval_graph(fhe_ctx* c, const fhe_graph* gc, const uint64_t* const* d_in,
             cudaFree(nc.buf);
             nc = fhe_node_const();
         }
-        g->cache_ctx = c;
+        g->cache_ctx = root;
     }
     for (uint32_t i = 0; i < n_inputs; ++i)
         if (!d_in[i]) return fail(FHE_EINVAL, "null input buffer");

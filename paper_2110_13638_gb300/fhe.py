@@ -70,6 +70,7 @@ SIGNATURES = {
     "fhe_prime_chain": [_U32, _P, _U32, _P],
     "fhe_gauss_table": [_P],
     "fhe_ctx_create": [_U32, _P, _U32, _U32, _P],
+    "fhe_ctx_fork": [_P, _P],
     "fhe_ctx_destroy": [_P],
     "fhe_ctx_query": [_P, _P],
     "fhe_keygen": [_P, _U64, _P],
@@ -220,9 +221,13 @@ def autohe(graph):
 class Context:
     """An RNS-CKKS context on the current CUDA device (tables and keys in HBM)."""
 
-    def __init__(self, N, bits, log_scale=40):
+    def __init__(self, N, bits, log_scale=40, _fork_of=None):
         h = ctypes.c_void_p()
-        _check(lib().fhe_ctx_create(N, _arr(bits, ctypes.c_uint32), len(bits), log_scale, ctypes.byref(h)))
+        if _fork_of is not None:
+            _check(lib().fhe_ctx_fork(_fork_of.h, ctypes.byref(h)))
+            self._parent = _fork_of          # keeps the parent alive
+        else:
+            _check(lib().fhe_ctx_create(N, _arr(bits, ctypes.c_uint32), len(bits), log_scale, ctypes.byref(h)))
         self.h = h
         info = CtxInfo()
         _check(lib().fhe_ctx_query(self.h, ctypes.byref(info)))
@@ -235,6 +240,10 @@ class Context:
         self.ntt_variant = int(info.ntt_variant)
         self.ntt_variant_us = [float(info.ntt_variant_us[i]) for i in range(5)]
         self.delta = float(2 ** log_scale)
+
+    def fork(self):
+        """A context sharing these tables and keys with its own workspace."""
+        return Context(self.N, None, self.log_scale, _fork_of=self)
 
     def close(self):
         if getattr(self, "h", None):
