@@ -3,8 +3,8 @@
 
 One step = one request of the encrypted CNN on 28x28x1 images with 8192
 samples in the slots (RNS-CKKS, N = 16384, coefficient modulus [60, 40 x 7, 60],
-scale 2^40, depth 7 from Alg. autoHE / parameterise): encode 784 slot vectors,
-encrypt them, evaluate the graph (conv 5x5x5 stride 2 -> degree-3 sigmoid fit ->
+scale 2^40, depth 7 from Alg. autoHE / parameterise): encode and encrypt 784
+slot vectors (one fused call), evaluate the graph (conv 5x5x5 stride 2 -> degree-3 sigmoid fit ->
 dense 720->100 -> sigmoid fit -> dense 100->10), decrypt and decode the 10
 outputs.  Keys are generated once, outside the timed region.
 
@@ -137,7 +137,6 @@ def run_ours(args):
     slots = torch.tensor(x, dtype=torch.float64, device=dev)
     host_slots = torch.tensor(x, dtype=torch.float64).pin_memory()
     host_out = torch.empty((n_out, N // 2), dtype=torch.float64).pin_memory()
-    pt = ctx.empty_pt(n_in, ctx.L_top)
     ct = ctx.empty_ct(n_in, ctx.L_top)
     out = ctx.empty_ct(n_out, L_out)
     m = torch.empty((n_out, N), dtype=torch.int64, device=dev)
@@ -145,8 +144,7 @@ def run_ours(args):
     meta = [None]
 
     def step(k, src):
-        ctx.encode(src, ctx.L_top, ctx.delta, pt)
-        ctx.encrypt(pt, 1_000_000 * rank + k * n_in, ct)
+        ctx.encode_encrypt(src, ctx.delta, 1_000_000 * rank + k * n_in, ct)
         meta[0] = G.eval(ctx, [ct], out)
         ctx.decrypt(out, L_out, m)
         ctx.decode(m, meta[0][0][1], z)

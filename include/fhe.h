@@ -57,7 +57,7 @@ typedef struct {
     uint32_t log_scale;  /* scale = 2^log_scale */
     uint64_t primes[64]; /* q_0 .. q_{L_top-1}, then the special prime P */
     uint64_t key_bytes;  /* device bytes held for keys and tables */
-    uint32_t ntt_variant;        /* NTT schedule the autotuner picked (0..4) */
+    uint32_t ntt_variant;        /* NTT schedule the autotuner picked (0..5) */
     float ntt_variant_us[8];     /* autotuner: microseconds per transform of each schedule */
 } fhe_ctx_info;
 
@@ -126,7 +126,7 @@ int fhe_gauss_table(uint64_t* out38);
 /* Build the context on the current CUDA device: primes, NTT tables and
  * encoder tables resident in HBM.  The NTT schedule (radix of the register
  * passes, threads per block) is autotuned here by timing each candidate on a
- * batch of transforms; the environment variable FHE_NTT_VARIANT=0..4 fixes
+ * batch of transforms; the environment variable FHE_NTT_VARIANT=0..5 fixes
  * it instead.  bits: coefficient-modulus bit sizes, the
  * last one being the special prime; log_scale: scale 2^log_scale.
  * N must be a power of two in [16, 65536]; above 16384 only the two-pass
@@ -164,6 +164,13 @@ int fhe_encode(fhe_ctx* ctx, const double* d_slots, uint32_t n_ct, uint32_t leve
  * first_ct_id + k.  d_pt [n_ct][L_top][N] -> d_ct [n_ct][2][L_top][N]. */
 int fhe_encrypt(fhe_ctx* ctx, const uint64_t* d_pt, uint32_t n_ct, uint64_t first_ct_id,
                 uint64_t* d_ct, void* stream);
+
+/* fhe_encode followed by fhe_encrypt in one pass: the encoded integer
+ * coefficients join the first noise polynomial before its transform
+ * (NTT(e0) + NTT(m) = NTT(e0 + m)), so no plaintext buffer or plaintext
+ * transform is needed.  Same ciphertexts as the two calls. */
+int fhe_encode_encrypt(fhe_ctx* ctx, const double* d_slots, uint32_t n_ct, double scale, uint64_t first_ct_id,
+                       uint64_t* d_ct, void* stream);
 
 /* Decrypt at `level`: m = c0 + c1 s, dropped to q_0, centred lift -> d_m
  * int64 [n_ct][N] (coefficient form). */

@@ -155,7 +155,10 @@ void k_relin(const fhe_ctx* c, const u64* d3, u64* out2, uint32_t n_ct, uint32_t
 // addc[ct * addc_stride + i]) added to comp 0 of the result
 size_t rescale_scratch_bytes(const fhe_ctx* c, uint32_t n_ct, uint32_t comps);
 void k_rescale(const fhe_ctx* c, const u64* in, u64* out, uint32_t n_ct, uint32_t comps, uint32_t L,
-               const u64* addc, uint32_t addc_stride, void* scratch, cudaStream_t st);
+               const u64* addc, uint32_t addc_stride, void* scratch, cudaStream_t st, const u64* mulc = nullptr);
+// degree-3 activation: t1 += x2 * c2 + (first L1 residues of x) * c1
+void k_poly_combine(const fhe_ctx* c, u64* t1, const u64* x2, const u64* x, uint32_t n_ct, uint32_t L1, uint32_t Lx,
+                    const u64* c2, const u64* c1, cudaStream_t st);
 // constants C (device residues cres[ct * cstride + r]) multiply every component;
 // reads residues r < L_out of an input stored with L_in residues
 void k_mul_const(const fhe_ctx* c, const u64* in, u64* out, uint32_t n_ct, uint32_t comps, uint32_t L_in,
@@ -190,10 +193,14 @@ size_t encode_scratch_bytes(const fhe_ctx* c, uint32_t n_ct);
 void k_encode(const fhe_ctx* c, const double* slots, uint32_t n_ct, uint32_t L, double scale, u64* pt,
               void* scratch, cudaStream_t st);
 void k_decode(const fhe_ctx* c, const i64* m, uint32_t n_ct, double scale, double* slots, cudaStream_t st);
+void encode_coefficients(const fhe_ctx* c, const double* slots, uint32_t n_ct, double scale, i64* m, cudaStream_t st);
+size_t encode_encrypt_scratch_bytes(const fhe_ctx* c, uint32_t n_ct);
+void k_encode_encrypt(const fhe_ctx* c, const double* slots, uint32_t n_ct, double scale, uint64_t first_id, u64* ct,
+                      void* scratch, cudaStream_t st);
 
 uint64_t stream_key(uint64_t seed, uint64_t domain, uint64_t object);
 const char* ntt_variant_name(int v);
-constexpr int kNttVariants = 5;
+constexpr int kNttVariants = 6;
 constexpr uint32_t kMaxSinglePassN = 16384;   // one transform per block in shared memory
 
 }  // namespace fhe

@@ -191,6 +191,7 @@ __device__ __forceinline__ void ntt_fwd_smem(u64* sm, int logN, const ulonglong2
     while (s < logN) {
         const int k = (logN - s) < LOGR ? (logN - s) : LOGR;
         switch (k) {
+        case 5: ntt_fwd_pass<5>(sm, logN, s, tw, q, q2, tid, nthr); break;
         case 4: ntt_fwd_pass<4>(sm, logN, s, tw, q, q2, tid, nthr); break;
         case 3: ntt_fwd_pass<3>(sm, logN, s, tw, q, q2, tid, nthr); break;
         case 2: ntt_fwd_pass<2>(sm, logN, s, tw, q, q2, tid, nthr); break;
@@ -209,6 +210,7 @@ __device__ __forceinline__ void ntt_inv_smem(u64* sm, int logN, const ulonglong2
     while (lt < logN) {
         const int k = (logN - lt) < LOGR ? (logN - lt) : LOGR;
         switch (k) {
+        case 5: ntt_inv_pass<5>(sm, logN, lt, tw, q, q2, tid, nthr); break;
         case 4: ntt_inv_pass<4>(sm, logN, lt, tw, q, q2, tid, nthr); break;
         case 3: ntt_inv_pass<3>(sm, logN, lt, tw, q, q2, tid, nthr); break;
         case 2: ntt_inv_pass<2>(sm, logN, lt, tw, q, q2, tid, nthr); break;

@@ -280,12 +280,9 @@ struct Exec {
         void* rs = take(relin_scratch_bytes(c, n, L));
         void* ss = take(rescale_scratch_bytes(c, n, 2));
         u64* x2 = (u64*)take(cts(n, 2, L - 1));
-        u64* xa = (u64*)take(cts(n, 2, L));
         u64* w = (u64*)take(cts(n, 2, L - 1));
         u64* T3b = (u64*)take(cts(n, 3, L - 1));
         u64* t1 = (u64*)take(cts(n, 2, L - 1));
-        u64* t2 = (u64*)take(cts(n, 2, L - 1));
-        u64* t3 = (u64*)take(cts(n, 2, L - 1));
         u64* out = (u64*)take(cts(n, 2, L - 2));
         if (!dry && ok()) {
             fhe_node_const* kc = node_const(i, L, x.scale);
@@ -293,14 +290,10 @@ struct Exec {
             k_tensor(c, x.p, x.p, T3, n, L, st);
             k_relin(c, T3, R, n, L, rs, st);
             k_rescale(c, R, x2, n, 2, L, nullptr, 0, ss, st);
-            k_mul_const(c, x.p, xa, n, 2, L, L, kc->c3, 0, st);
-            k_rescale(c, xa, w, n, 2, L, nullptr, 0, ss, st);
+            k_rescale(c, x.p, w, n, 2, L, nullptr, 0, ss, st, kc->c3);        // rescale(x * C3)
             k_tensor(c, x2, w, T3b, n, L - 1, st);
             k_relin(c, T3b, t1, n, L - 1, rs, st);
-            k_mul_const(c, x2, t2, n, 2, L - 1, L - 1, kc->c2, 0, st);
-            k_mul_const(c, x.p, t3, n, 2, L, L - 1, kc->c1, 0, st);
-            k_add(c, t1, t2, t1, n, 2, L - 1, st);
-            k_add(c, t1, t3, t1, n, 2, L - 1, st);
+            k_poly_combine(c, t1, x2, x.p, n, L - 1, L, kc->c2, kc->c1, st);  // + x2 C2 + drop(x) C1
             k_rescale(c, t1, out, n, 2, L - 1, kc->c0, 0, ss, st);
         }
         y.p = out;

@@ -203,12 +203,13 @@ static void launch_ntt(const fhe_ctx* c, const Op& op, cudaStream_t st)
     // the two-pass schedule needs the same number of transforms in every unit
     const bool single = c->force_single_pass || !uniform_subs<Op>::value;
     // (callers refuse single-pass-only work above kMaxSinglePassN)
-    const int v = single && c->ntt_variant >= 3 ? 1 : c->ntt_variant;
+    const int v = single && (c->ntt_variant == 3 || c->ntt_variant == 4) ? 1 : c->ntt_variant;
     switch (v) {
     case 1: launch_ntt_v<INV, 3, 1024>(c, op, count, st); break;
     case 2: launch_ntt_v<INV, 4, 1024>(c, op, count, st); break;
     case 3: launch_ntt_2pass<INV, 4>(c, op, count, st); break;
     case 4: launch_ntt_2pass<INV, 3>(c, op, count, st); break;
+    case 5: launch_ntt_v<INV, 5, 512>(c, op, count, st); break;
     default: launch_ntt_v<INV, 4, 512>(c, op, count, st); break;
     }
 }
@@ -220,6 +221,7 @@ const char* ntt_variant_name(int v)
     case 2: return "radix-16 passes, 1024 threads";
     case 3: return "two-pass column/row tiles, radix-16";
     case 4: return "two-pass column/row tiles, radix-8";
+    case 5: return "radix-32 passes, 512 threads";
     default: return "radix-16 passes, 512 threads";
     }
 }
@@ -375,6 +377,34 @@ void k_add_const(const fhe_ctx* c, u64* ct, uint32_t n_ct, uint32_t L, const u64
     k_add_const_kernel<<<ew_grid(total), 256, 0, st>>>(ct, total, (int)L, (int)c->logN, cres, (int)cstride, c->d_pc);
 }
 
+// T = t1 + x2 * c2 + x|_{L1} * c1 over L1 residues (x stored with Lx residues):
+// the sum of the three terms of the degree-3 activation in one pass
+__global__ void k_poly_combine_kernel(u64* __restrict__ t1, const u64* __restrict__ x2, const u64* __restrict__ x,
+                                      size_t total, int L1, int Lx, int logN, const u64* __restrict__ c2,
+                                      const u64* __restrict__ c1, const PrimeC* __restrict__ pc)
+{
+    const size_t Nm = ((size_t)1 << logN) - 1;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = i >> logN;            // (ct, comp, r), r < L1
+        const int r = (int)(row % L1);
+        const size_t poly = row / L1;
+        const PrimeC P = pc[r];
+        const u64 xv = x[((poly * Lx + r) << logN) + (i & Nm)];
+        u64 a = add_mod(t1[i], mul_mod(x2[i], c2[r], P), P.q);
+        t1[i] = add_mod(a, mul_mod(xv, c1[r], P), P.q);
+    }
+}
+
+void k_poly_combine(const fhe_ctx* c, u64* t1, const u64* x2, const u64* x, uint32_t n_ct, uint32_t L1, uint32_t Lx,
+                    const u64* c2, const u64* c1, cudaStream_t st)
+{
+    const size_t total = (size_t)n_ct * 2 * L1 * c->N;
+    if (!total) return;
+    LaunchScope ls(c, "elementwise", st);
+    k_poly_combine_kernel<<<ew_grid(total), 256, 0, st>>>(t1, x2, x, total, (int)L1, (int)Lx, (int)c->logN, c2, c1,
+                                                          c->d_pc);
+}
+
 // ---------------------------------------------------------------- rescale
 DivC make_divc(const fhe_ctx* c, uint32_t p_index, uint32_t n_targets)
 {
@@ -397,11 +427,16 @@ struct OpTakeRowInv {
     const u64* in;
     u64* V;
     int n, L, row, N, pidx;
+    const u64* mulc;    // optional: the input is first multiplied by this per-residue constant
     __host__ __device__ int count() const { return n; }
     __host__ __device__ int nsub(int) const { return 1; }
     __device__ int prime(int, int) const { return pidx; }
     __device__ bool direct(int, int) const { return false; }
-    __device__ u64 load(int p, int, int j, const PrimeC&) const { return in[((size_t)p * L + row) * N + j]; }
+    __device__ u64 load(int p, int, int j, const PrimeC& P) const
+    {
+        const u64 x = in[((size_t)p * L + row) * N + j];
+        return mulc ? mul_mod(x, mulc[row], P) : x;
+    }
     struct Pre {};
     __device__ Pre pre(int, int, int) const { return {}; }
     __device__ void store(int p, int, int j, u64 v, const Pre&, const PrimeC&) const { V[(size_t)p * N + j] = v; }
@@ -415,6 +450,7 @@ struct OpDivFwd {
     u64* out;           // [n_poly][L_out][N]
     const u64* addc;    // optional: residues of a constant added to comp 0, [n_ct][addc_stride]
     int n_poly, comps, L_in, L_out, N, addc_stride;
+    const u64* mulc;    // optional: the input is first multiplied by this per-residue constant
     DivC d;
     __host__ __device__ int count() const { return n_poly * L_out; }
     __host__ __device__ int nsub(int) const { return 1; }
@@ -437,7 +473,8 @@ struct OpDivFwd {
     __device__ void store(int p, int, int j, u64 v, const Pre& pr, const PrimeC& Q) const
     {
         const int poly = p / L_out, i = p % L_out;
-        const u64 r = mul_shoup(sub_mod(pr.x, v, Q.q), d.inv[i], d.invs[i], Q.q);
+        const u64 x = mulc ? mul_mod(pr.x, mulc[i], Q) : pr.x;
+        const u64 r = mul_shoup(sub_mod(x, v, Q.q), d.inv[i], d.invs[i], Q.q);
         out[((size_t)poly * L_out + i) * N + j] = add_mod(r, pr.c, Q.q);
     }
 };
@@ -448,7 +485,7 @@ size_t rescale_scratch_bytes(const fhe_ctx* c, uint32_t n_ct, uint32_t comps)
 }
 
 void k_rescale(const fhe_ctx* c, const u64* in, u64* out, uint32_t n_ct, uint32_t comps, uint32_t L, const u64* addc,
-               uint32_t addc_stride, void* scratch, cudaStream_t st)
+               uint32_t addc_stride, void* scratch, cudaStream_t st, const u64* mulc)
 {
     if (n_ct == 0) return;
     u64* V = (u64*)scratch;
@@ -460,6 +497,7 @@ void k_rescale(const fhe_ctx* c, const u64* in, u64* out, uint32_t n_ct, uint32_
     a.row = (int)L - 1;
     a.N = (int)c->N;
     a.pidx = (int)L - 1;
+    a.mulc = mulc;
     launch_ntt<true>(c, a, st);
     OpDivFwd b;
     b.in = in;
@@ -473,6 +511,7 @@ void k_rescale(const fhe_ctx* c, const u64* in, u64* out, uint32_t n_ct, uint32_
     b.L_out = (int)L - 1;
     b.N = (int)c->N;
     b.d = make_divc(c, L - 1, L - 1);
+    b.mulc = mulc;
     launch_ntt<false>(c, b, st);
 }
 
@@ -735,6 +774,7 @@ void k_mul_relin_rescale_groups(const fhe_ctx* c, const LevelBatch* g, int ng, v
         tr.row = L - 1;
         tr.N = (int)N;
         tr.pidx = L - 1;
+        tr.mulc = nullptr;
         m5.ops[k] = tr;
         OpDivFwd dv;
         dv.in = t2;
@@ -748,6 +788,7 @@ void k_mul_relin_rescale_groups(const fhe_ctx* c, const LevelBatch* g, int ng, v
         dv.L_out = L - 1;
         dv.N = (int)N;
         dv.d = make_divc(c, L - 1, L - 1);
+        dv.mulc = nullptr;
         m6.ops[k] = dv;
         m1.pre_[k + 1] = m1.pre_[k] + m1.ops[k].count();
         m2.pre_[k + 1] = m2.pre_[k] + m2.ops[k].count();
@@ -1070,6 +1111,8 @@ struct OpEncrypt {
     const u64* pk;      // [2][Ltop][N]
     u64* ct;            // [n][2][Ltop][N]
     const int8_t* S;    // [n][3][N] samples
+    const i64* M;       // optional [n][N] encoded coefficients (then pt is unused):
+                        // NTT(e0) + NTT(m) = NTT(e0 + m), so the plaintext needs no transform of its own
     int n, Ltop, N;
     __host__ __device__ int count() const { return n * Ltop; }
     __host__ __device__ int nsub(int) const { return 3; }
@@ -1078,7 +1121,9 @@ struct OpEncrypt {
     __device__ u64 load(int p, int u, int j, const PrimeC& P) const
     {
         const int ci = p / Ltop;
-        return from_signed((i64)S[((size_t)ci * 3 + u) * N + j], P);
+        i64 v = (i64)S[((size_t)ci * 3 + u) * N + j];
+        if (u == 1 && M) v += M[(size_t)ci * N + j];
+        return from_signed(v, P);
     }
     struct Pre { u64 a, b, c; };
     __device__ Pre pre(int p, int u, int j) const
@@ -1086,7 +1131,7 @@ struct OpEncrypt {
         const int ci = p / Ltop, r = p % Ltop;
         Pre x;
         if (u == 0) {
-            x.a = pt[((size_t)ci * Ltop + r) * N + j];
+            x.a = M ? 0 : pt[((size_t)ci * Ltop + r) * N + j];
             x.b = pk[(size_t)r * N + j];
             x.c = pk[((size_t)Ltop + r) * N + j];
         } else {
@@ -1123,7 +1168,31 @@ void k_encrypt(const fhe_ctx* c, const u64* pt, uint32_t n_ct, uint64_t first_id
         LaunchScope ls(c, "encrypt", st);
         k_sample_enc_kernel<<<ew_grid(total), 256, 0, st>>>(S, (int)n_ct, (int)c->N, c->seed, first_id, c->d_cdt);
     }
-    OpEncrypt op{pt, c->d_pk, ct, S, (int)n_ct, (int)c->L_top, (int)c->N};
+    OpEncrypt op{pt, c->d_pk, ct, S, nullptr, (int)n_ct, (int)c->L_top, (int)c->N};
+    launch_ntt<false>(c, op, st);
+}
+
+size_t encode_encrypt_scratch_bytes(const fhe_ctx* c, uint32_t n_ct)
+{
+    return arena_need({encode_scratch_bytes(c, n_ct), encrypt_scratch_bytes(c, n_ct)});
+}
+
+void k_encode_encrypt(const fhe_ctx* c, const double* slots, uint32_t n_ct, double scale, uint64_t first_id, u64* ct,
+                      void* scratch, cudaStream_t st)
+{
+    if (n_ct == 0) return;
+    Arena ar;
+    ar.base = (char*)scratch;
+    ar.cap = encode_encrypt_scratch_bytes(c, n_ct);
+    i64* m = (i64*)ar.take(encode_scratch_bytes(c, n_ct));
+    int8_t* S = (int8_t*)ar.take(encrypt_scratch_bytes(c, n_ct));
+    encode_coefficients(c, slots, n_ct, scale, m, st);
+    {
+        const size_t total = (size_t)n_ct * c->N;
+        LaunchScope ls(c, "encrypt", st);
+        k_sample_enc_kernel<<<ew_grid(total), 256, 0, st>>>(S, (int)n_ct, (int)c->N, c->seed, first_id, c->d_cdt);
+    }
+    OpEncrypt op{nullptr, c->d_pk, ct, S, m, (int)n_ct, (int)c->L_top, (int)c->N};
     launch_ntt<false>(c, op, st);
 }
 
@@ -1174,13 +1243,12 @@ __device__ __forceinline__ ddv fast_two_sum(double a, double b)
     double s = __dadd_rn(a, b);
     return {s, __dsub_rn(b, __dsub_rn(s, a))};
 }
+// double-double sum with one error-free transformation on the high parts
+// (relative error ~2^-100 of the operands: the encoder needs ~2^-70)
 __device__ __forceinline__ ddv dadd(ddv a, ddv b)
 {
     ddv s = two_sum(a.hi, b.hi);
-    ddv t = two_sum(a.lo, b.lo);
-    s.lo = __dadd_rn(s.lo, t.hi);
-    s = fast_two_sum(s.hi, s.lo);
-    s.lo = __dadd_rn(s.lo, t.lo);
+    s.lo = __dadd_rn(s.lo, __dadd_rn(a.lo, b.lo));
     return fast_two_sum(s.hi, s.lo);
 }
 __device__ __forceinline__ ddv dneg(ddv a) { return {-a.hi, -a.lo}; }
@@ -1283,12 +1351,9 @@ struct OpSignedRows {
 
 size_t encode_scratch_bytes(const fhe_ctx* c, uint32_t n_ct) { return (size_t)n_ct * c->N * sizeof(i64); }
 
-void k_encode(const fhe_ctx* c, const double* slots, uint32_t n_ct, uint32_t L, double scale, u64* pt, void* scratch,
-              cudaStream_t st)
+void encode_coefficients(const fhe_ctx* c, const double* slots, uint32_t n_ct, double scale, i64* m, cudaStream_t st)
 {
-    if (n_ct == 0) return;
     const int N = (int)c->N;
-    i64* m = (i64*)scratch;
     const size_t smem = (size_t)(N / 4) * sizeof(double4);
     static size_t configured = 0;
     if (configured < smem) {
@@ -1302,7 +1367,15 @@ void k_encode(const fhe_ctx* c, const double* slots, uint32_t n_ct, uint32_t L, 
     k_encode_kernel<<<2 * n_ct, thr, smem, st>>>(slots, c->d_slot_of, c->d_enc_tw, c->d_enc_twist,
                                                  scale / (double)(N / 2), N, m);
     }
-    OpSignedRows op{m, pt, (int)n_ct, (int)L, N};
+}
+
+void k_encode(const fhe_ctx* c, const double* slots, uint32_t n_ct, uint32_t L, double scale, u64* pt, void* scratch,
+              cudaStream_t st)
+{
+    if (n_ct == 0) return;
+    i64* m = (i64*)scratch;
+    encode_coefficients(c, slots, n_ct, scale, m, st);
+    OpSignedRows op{m, pt, (int)n_ct, (int)L, (int)c->N};
     launch_ntt<false>(c, op, st);
 }
 

@@ -77,6 +77,7 @@ SIGNATURES = {
     "fhe_export_secret": [_P, _P, _P],
     "fhe_encode": [_P, _P, _U32, _U32, ctypes.c_double, _P, _P],
     "fhe_encrypt": [_P, _P, _U32, _U64, _P, _P],
+    "fhe_encode_encrypt": [_P, _P, _U32, ctypes.c_double, _U64, _P, _P],
     "fhe_decrypt": [_P, _P, _U32, _U32, _P, _P],
     "fhe_decode": [_P, _P, _U32, ctypes.c_double, _P, _P],
     "fhe_ntt": [_P, _P, _U32, _U32, _I, _P],
@@ -238,7 +239,7 @@ class Context:
         self.primes = [int(info.primes[i]) for i in range(info.L_top + 1)]
         self.key_bytes = int(info.key_bytes)
         self.ntt_variant = int(info.ntt_variant)
-        self.ntt_variant_us = [float(info.ntt_variant_us[i]) for i in range(5)]
+        self.ntt_variant_us = [float(info.ntt_variant_us[i]) for i in range(6)]
         self.delta = float(2 ** log_scale)
 
     def fork(self):
@@ -289,6 +290,10 @@ class Context:
 
     def encrypt(self, pt, first_ct_id, out, stream=None):
         _check(lib().fhe_encrypt(self.h, _ptr(pt), pt.shape[0], first_ct_id, _ptr(out), _stream(stream)))
+
+    def encode_encrypt(self, slots, scale, first_ct_id, out, stream=None):
+        _check(lib().fhe_encode_encrypt(self.h, _ptr(slots), slots.shape[0], scale, first_ct_id, _ptr(out),
+                                        _stream(stream)))
 
     def decrypt(self, ct, level, out, stream=None):
         _check(lib().fhe_decrypt(self.h, _ptr(ct), ct.shape[0], level, _ptr(out), _stream(stream)))

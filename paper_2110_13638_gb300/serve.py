@@ -57,7 +57,6 @@ class Slot:
         self.slots_dev = torch.zeros((net.n_in, cap), dtype=torch.float64, device=dev)
         self.host_in = torch.zeros((net.n_in, cap), dtype=torch.float64).pin_memory()
         self.host_out = torch.zeros((n_out, cap), dtype=torch.float64).pin_memory()
-        self.pt = self.ctx.empty_pt(net.n_in, self.ctx.L_top)
         self.ct = self.ctx.empty_ct(net.n_in, self.ctx.L_top)
         self.out = self.ctx.empty_ct(n_out, L_out)
         self.m = torch.empty((n_out, N), dtype=torch.int64, device=dev)
@@ -75,8 +74,7 @@ class Slot:
         self.batch = batch
         with torch.cuda.stream(self.stream):
             self.slots_dev.copy_(self.host_in, non_blocking=True)
-            self.ctx.encode(self.slots_dev, self.ctx.L_top, self.ctx.delta, self.pt)
-            self.ctx.encrypt(self.pt, ct_base, self.ct)
+            self.ctx.encode_encrypt(self.slots_dev, self.ctx.delta, ct_base, self.ct)
             meta = self.G.eval(self.ctx, [self.ct], self.out)
             self.ctx.decrypt(self.out, self.L_out, self.m)
             self.ctx.decode(self.m, meta[0][1], self.z)

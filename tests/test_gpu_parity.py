@@ -355,3 +355,17 @@ def test_large_ring_transform_tensor_relin(N):
     assert np.array_equal(download(g, out, L)[0], o.relinearise(want).c)
     with pytest.raises(fhe.FheError):
         g.encode(torch.zeros((1, N // 2), dtype=torch.float64, device="cuda"), L, g.delta, g.empty_pt(1, L))
+
+
+@pytest.mark.parametrize("N,bits,n", [(1024, BITS5, 3), (16384, BITS9, 2)])
+def test_encode_encrypt_fused_equals_two_calls(N, bits, n):
+    g, o = pair(N, bits)
+    z = torch.tensor(np.random.default_rng(N).uniform(-2, 2, size=(n, N // 2)), device="cuda")
+    pt = g.empty_pt(n, g.L_top)
+    a = g.empty_ct(n, g.L_top)
+    b = g.empty_ct(n, g.L_top)
+    g.encode(z, g.L_top, g.delta, pt)
+    g.encrypt(pt, 333, a)
+    g.encode_encrypt(z, g.delta, 333, b)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
