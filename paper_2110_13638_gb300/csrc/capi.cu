@@ -326,6 +326,10 @@ int fhe_ctx_create(uint32_t N, const uint32_t* bits, uint32_t n_bits, uint32_t l
         P.ninvs = shoup(P.ninv, q);
         P.half = (q - 1) / 2;
         P.ub = (u64)((((u128)1 << 64) / q) * q);
+        for (int k = 0; k < 4; ++k) {
+            P.p21[k] = hpow(2, 21ull * (k + 1), q);
+            P.p21s[k] = shoup(P.p21[k], q);
+        }
         const u64 psi = primitive_root_2n(q, N);
         const u64 psi_inv = hinv(psi, q);
         for (uint32_t i = 0; i < N; ++i) {

@@ -171,6 +171,8 @@ void k_linear_mac(const fhe_ctx* c, const u64* X, uint32_t n_in, const uint32_t*
 
 // tiled gather-MAC (rows sharing a column list computed together)
 constexpr int kMacTile = 8;
+// primes below this bound store MAC weights as 21-bit limbs (wL | wH << 32)
+constexpr unsigned long long kLimbPrimeBound = 1ull << 42;
 void k_linear_mac_tiled(const fhe_ctx* c, const u64* X, const uint4* tiles, uint32_t n_tiles, const uint32_t* rows,
                         const uint32_t* col, const u64* W, uint32_t L, u64* Y, cudaStream_t st);
 

@@ -32,6 +32,8 @@ struct PrimeC {
     u64 ninvs;   // Shoup quotient of ninv
     u64 half;    // (q - 1) / 2
     u64 ub;      // floor(2^64 / q) * q (rejection bound of the uniform sampler)
+    u64 p21[4];  // 2^21, 2^42, 2^63, 2^84 mod q (limb positions of the MAC)
+    u64 p21s[4]; // their Shoup quotients
 };
 
 // ---------------------------------------------------------------- scalar ops

@@ -128,8 +128,12 @@ struct Exec {
                             const uint32_t row = rs[t0 + o];
                             const double wv = nd.weight[nd.row_ptr[row] + e];
                             const int64_t w = (int64_t)std::llround(wv * qd);
-                            for (uint32_t r = 0; r < L; ++r)
-                                W[(((size_t)w_off + e) * L + r) * kMacTile + o] = mod_signed(w, c->primes[r]);
+                            for (uint32_t r = 0; r < L; ++r) {
+                                u64 wr = mod_signed(w, c->primes[r]);
+                                if (c->primes[r] < kLimbPrimeBound)          // 21-bit limbs for the limb MAC
+                                    wr = (wr & ((1ull << 21) - 1)) | ((wr >> 21) << 32);
+                                W[(((size_t)w_off + e) * L + r) * kMacTile + o] = wr;
+                            }
                         }
                 }
             }
@@ -471,11 +475,16 @@ int fhe_graph_create(const fhe_graph_desc* d, fhe_graph** out)
                 delete g;
                 return fail(FHE_EINVAL, "row_ptr[0] must be 0");
             }
-            for (uint32_t o = 0; o < s.n_out; ++o)
+            for (uint32_t o = 0; o < s.n_out; ++o) {
                 if (n.row_ptr[o + 1] < n.row_ptr[o]) {
                     delete g;
                     return fail(FHE_EINVAL, "row_ptr must be non-decreasing");
                 }
+                if (n.row_ptr[o + 1] - n.row_ptr[o] >= (1u << 20)) {     // exact 64-bit limb sums
+                    delete g;
+                    return fail(FHE_EUNSUPPORTED, "a linear row has 2^20 or more terms");
+                }
+            }
             n.col_idx.assign(s.col_idx, s.col_idx + nnz);
             n.weight.assign(s.weight, s.weight + nnz);
             if (s.bias) n.bias.assign(s.bias, s.bias + s.n_out);

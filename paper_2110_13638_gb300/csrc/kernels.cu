@@ -868,6 +868,24 @@ __device__ __forceinline__ void mac128(u64& lo, u64& hi, u64 x, u64 w)
     hi += ph + (lo < pl ? 1 : 0);
 }
 
+// Limb form for primes below 2^42: x = xH 2^21 + xL and the stored weight
+// word holds wL | wH << 32 with w = wH 2^21 + wL (all limbs < 2^21), so every
+// limb product is < 2^42 and accumulates exactly in a 64-bit register with one
+// 32 x 32 + 64 multiply-add: sum x w = S0 + S1 2^21 + S2 2^42 with
+// S0 = sum xL wL, S1 = sum (xL wH + xH wL), S2 = sum xH wH (no carries for
+// fewer than 2^20 terms).
+constexpr u64 kLimbMask = (1ull << 21) - 1;
+
+__device__ __forceinline__ u64 limb_combine(u64 s0, u64 s1, u64 s2, const PrimeC& P)
+{
+    u64 lo = s0 + (s1 << 21);
+    u64 hi = (s1 >> 43) + (lo < s0 ? 1 : 0);
+    const u64 t = s2 << 42;
+    lo += t;
+    hi += (s2 >> 22) + (lo < t ? 1 : 0);
+    return reduce128(hi, lo, P);
+}
+
 __global__ void __launch_bounds__(256) k_mac_tiled_kernel(const u64* __restrict__ X, const uint4* __restrict__ tiles,
                                                            const uint32_t* __restrict__ rows,
                                                            const uint32_t* __restrict__ col,
@@ -885,10 +903,65 @@ __global__ void __launch_bounds__(256) k_mac_tiled_kernel(const u64* __restrict_
     const uint32_t* cl = col + tl.x;
     const ulonglong2* w2 = reinterpret_cast<const ulonglong2*>(W + ((size_t)tl.w * L + r) * kMacTile);
     const size_t wstep = (size_t)L * kMacTile / 2;        // ulonglong2 per term
+    const size_t off = (size_t)kr * N + j;
+    const uint32_t K = tl.y;
+    if (P.q < kLimbPrimeBound) {                            // block-uniform branch
+        u64 s0[kMacTile], s1[kMacTile], s2[kMacTile];
+#pragma unroll
+        for (int o = 0; o < kMacTile; ++o) s0[o] = s1[o] = s2[o] = 0;
+        uint32_t e = 0;
+        for (; e + 4 <= K; e += 4) {
+            u64 x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = Xj[(size_t)__ldg(&cl[e + u]) * ct_stride];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t xl = (uint32_t)(x[u] & kLimbMask), xh = (uint32_t)(x[u] >> 21);
+                const ulonglong2* we = w2 + (size_t)(e + u) * wstep;
+#pragma unroll
+                for (int o2 = 0; o2 < kMacTile / 2; ++o2) {
+                    const ulonglong2 wv = __ldg(&we[o2]);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const u64 wd = h ? wv.y : wv.x;
+                        const uint32_t wl = (uint32_t)wd, wh = (uint32_t)(wd >> 32);
+                        const int o = 2 * o2 + h;
+                        s0[o] += (u64)xl * wl;
+                        s1[o] += (u64)xl * wh;
+                        s1[o] += (u64)xh * wl;
+                        s2[o] += (u64)xh * wh;
+                    }
+                }
+            }
+        }
+        for (; e < K; ++e) {
+            const u64 xv = Xj[(size_t)__ldg(&cl[e]) * ct_stride];
+            const uint32_t xl = (uint32_t)(xv & kLimbMask), xh = (uint32_t)(xv >> 21);
+            const ulonglong2* we = w2 + (size_t)e * wstep;
+#pragma unroll
+            for (int o2 = 0; o2 < kMacTile / 2; ++o2) {
+                const ulonglong2 wv = __ldg(&we[o2]);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const u64 wd = h ? wv.y : wv.x;
+                    const uint32_t wl = (uint32_t)wd, wh = (uint32_t)(wd >> 32);
+                    const int o = 2 * o2 + h;
+                    s0[o] += (u64)xl * wl;
+                    s1[o] += (u64)xl * wh;
+                    s1[o] += (u64)xh * wl;
+                    s2[o] += (u64)xh * wh;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 0; o < kMacTile; ++o)
+            if (o < (int)tl.z)
+                Y[(size_t)rows[blockIdx.x * kMacTile + o] * ct_stride + off] = limb_combine(s0[o], s1[o], s2[o], P);
+        return;
+    }
     u64 lo[kMacTile], hi[kMacTile];
 #pragma unroll
     for (int o = 0; o < kMacTile; ++o) lo[o] = hi[o] = 0;
-    const uint32_t K = tl.y;
     uint32_t e = 0;
     int cnt = 0;
     for (; e + 4 <= K; e += 4) {
@@ -925,7 +998,6 @@ __global__ void __launch_bounds__(256) k_mac_tiled_kernel(const u64* __restrict_
             mac128(lo[2 * o2 + 1], hi[2 * o2 + 1], x, wv.y);
         }
     }
-    const size_t off = (size_t)kr * N + j;
 #pragma unroll
     for (int o = 0; o < kMacTile; ++o)
         if (o < (int)tl.z) Y[(size_t)rows[blockIdx.x * kMacTile + o] * ct_stride + off] = reduce128(hi[o], lo[o], P);
