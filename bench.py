@@ -235,6 +235,7 @@ def run_ours(args):
         "config": {"workload": desc, "N": N, "coeff_modulus_bits": bits, "log_scale": 40,
                    "samples_per_request": samples, "input_ciphertexts": n_in, "output_ciphertexts": n_out,
                    "parallelism": "replicas" if world > 1 else "single GPU",
+                   "ntt_schedule": "%d: %s" % (ctx.ntt_variant, fhe.NTT_SCHEDULES[ctx.ntt_variant]),
                    "l2": "inputs larger than L2 (1.6 GB of ciphertexts per step)"},
         "e2e": {"value": round(e2e, 2), "unit": UNIT, "h2d_bytes_per_step": int(slots.numel() * 8),
                 "d2h_bytes_per_step": int(z.numel() * 8)},
@@ -433,7 +434,7 @@ def run_ntt_sweep(args):
             res = {"N": N, "primes": nprime}
             for mode in ("autotuned", "fixed"):
                 if mode == "fixed":
-                    _os.environ["FHE_NTT_VARIANT"] = "0" if N <= 16384 else "3"
+                    _os.environ["FHE_NTT_VARIANT"] = "0" if N <= 16384 else "2"
                 try:
                     ctx = fhe.Context(N, bits, 40)
                 finally:

@@ -125,8 +125,9 @@ int fhe_gauss_table(uint64_t* out38);
 
 /* Build the context on the current CUDA device: primes, NTT tables and
  * encoder tables resident in HBM.  The NTT schedule (radix of the register
- * passes, threads per block) is autotuned here by timing each candidate on a
- * batch of transforms; the environment variable FHE_NTT_VARIANT=0..5 fixes
+ * passes, threads per block, one- or two-pass, fused global I/O) is autotuned
+ * here by timing each candidate on a rescale of 64 ciphertexts; the
+ * environment variable FHE_NTT_VARIANT=0..5 fixes
  * it instead.  bits: coefficient-modulus bit sizes, the
  * last one being the special prime; log_scale: scale 2^log_scale.
  * N must be a power of two in [16, 65536]; above 16384 only the two-pass

@@ -231,22 +231,28 @@ static void free_ctx(fhe_ctx* c)
     delete c;
 }
 
-// Time every NTT schedule on a batch of forward transforms (two per SM over
-// all primes) and keep the fastest; FHE_NTT_VARIANT overrides.
+// Time every NTT schedule on a representative fused step and keep the
+// fastest; FHE_NTT_VARIANT overrides.
 static int autotune_ntt(fhe_ctx* c)
 {
     const char* env = std::getenv("FHE_NTT_VARIANT");
     if (env && *env) {
         int v = std::atoi(env);
         if (v < 0 || v >= kNttVariants) return fail(FHE_EINVAL, "FHE_NTT_VARIANT out of range (0..5)");
-        if (c->N > kMaxSinglePassN && (v < 3 || v == 5)) return fail(FHE_EINVAL, "N > 16384 needs a two-pass NTT schedule (3 or 4)");
+        if (c->N > kMaxSinglePassN && !ntt_two_pass(v)) return fail(FHE_EINVAL, "N > 16384 needs a two-pass NTT schedule (2 or 3)");
         c->ntt_variant = v;
         return FHE_OK;
     }
+    // Timed workload: a rescale (inverse transform of the last residue, then
+    // forward transforms with a fused prologue and epilogue) of 64
+    // ciphertexts at the top level, i.e. both directions and the fused I/O the
+    // graph kernels use; plain forward transforms when there is nothing to
+    // rescale by.
+    const uint32_t L = c->L_top;
     const uint32_t rows = c->L_top + 1;
-    // about eight transforms per SM, over every prime
-    uint32_t groups = (1216 + rows - 1) / rows;
-    const size_t bytes = (size_t)groups * rows * c->N * 8;
+    const uint32_t nct = 64;
+    const uint32_t groups = (1216 + rows - 1) / rows;
+    const size_t bytes = L >= 2 ? (size_t)nct * 2 * (2 * L) * c->N * 8 : (size_t)groups * rows * c->N * 8;
     u64* buf = nullptr;
     cudaError_t e = cudaMalloc((void**)&buf, bytes);
     if (e != cudaSuccess) {
@@ -256,31 +262,41 @@ static int autotune_ntt(fhe_ctx* c)
     cudaMemset(buf, 0, bytes);
     uint8_t pm[64];
     for (uint32_t r = 0; r < rows; ++r) pm[r] = (uint8_t)r;
+    auto work = [&]() {
+        if (L >= 2) {
+            u64* in = buf;
+            u64* out = buf + (size_t)nct * 2 * L * c->N;
+            u64* V = out + (size_t)nct * 2 * (L - 1) * c->N;     // fits: 2L residues per ct allocated
+            k_rescale(c, in, out, nct, 2, L, nullptr, 0, V, nullptr);
+        } else {
+            k_ntt_rows(c, buf, groups, rows, pm, true, nullptr);
+        }
+    };
+    const float units = L >= 2 ? (float)(nct * 2 * L) : (float)(groups * rows);
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     float best = 1e30f;
     for (int v = 0; v < kNttVariants; ++v) {
-        if (c->N > kMaxSinglePassN && (v < 3 || v == 5)) continue;   // one block per transform needs N <= 16384
-        if (v == 5) continue;        // radix-32 spills in the fused steps: only by explicit request
+        if (c->N > kMaxSinglePassN && !ntt_two_pass(v)) continue;   // one block per transform needs N <= 16384
         c->ntt_variant = v;
-        k_ntt_rows(c, buf, groups, rows, pm, true, nullptr);       // warm-up
+        work();                                                     // warm-up
         float us_best = 1e30f;
         for (int trial = 0; trial < 3 && e == cudaSuccess; ++trial) {
             cudaEventRecord(a, nullptr);
-            for (int it = 0; it < 2; ++it) k_ntt_rows(c, buf, groups, rows, pm, true, nullptr);
+            for (int it = 0; it < 2; ++it) work();
             cudaEventRecord(b, nullptr);
             e = cudaEventSynchronize(b);
             float ms = 0.f;
             cudaEventElapsedTime(&ms, a, b);
-            const float us = ms * 1000.f / (2.f * groups * rows);
+            const float us = ms * 1000.f / (2.f * units);
             if (us < us_best) us_best = us;
         }
         if (e != cudaSuccess) break;
         c->ntt_variant_us[v] = us_best;
         if (us_best < best) best = us_best;
     }
-    int pick = c->N > kMaxSinglePassN ? 3 : 0;
+    int pick = c->N > kMaxSinglePassN ? 2 : 0;
     for (int v = 0; v < kNttVariants; ++v)
         if (c->ntt_variant_us[v] > 0.f && c->ntt_variant_us[v] == best) { pick = v; break; }
     c->ntt_variant = pick;

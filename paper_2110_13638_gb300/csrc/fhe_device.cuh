@@ -17,6 +17,7 @@
 // accesses for every pass stride).
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 typedef unsigned long long u64;
@@ -193,7 +194,6 @@ __device__ __forceinline__ void ntt_fwd_smem(u64* sm, int logN, const ulonglong2
     while (s < logN) {
         const int k = (logN - s) < LOGR ? (logN - s) : LOGR;
         switch (k) {
-        case 5: ntt_fwd_pass<5>(sm, logN, s, tw, q, q2, tid, nthr); break;
         case 4: ntt_fwd_pass<4>(sm, logN, s, tw, q, q2, tid, nthr); break;
         case 3: ntt_fwd_pass<3>(sm, logN, s, tw, q, q2, tid, nthr); break;
         case 2: ntt_fwd_pass<2>(sm, logN, s, tw, q, q2, tid, nthr); break;
@@ -212,7 +212,6 @@ __device__ __forceinline__ void ntt_inv_smem(u64* sm, int logN, const ulonglong2
     while (lt < logN) {
         const int k = (logN - lt) < LOGR ? (logN - lt) : LOGR;
         switch (k) {
-        case 5: ntt_inv_pass<5>(sm, logN, lt, tw, q, q2, tid, nthr); break;
         case 4: ntt_inv_pass<4>(sm, logN, lt, tw, q, q2, tid, nthr); break;
         case 3: ntt_inv_pass<3>(sm, logN, lt, tw, q, q2, tid, nthr); break;
         case 2: ntt_inv_pass<2>(sm, logN, lt, tw, q, q2, tid, nthr); break;
@@ -622,5 +621,140 @@ __global__ void __launch_bounds__(kThr2) k_ntt2_second(Op op, NttTables T, Split
             }
         }
         __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- fused-I/O transform
+// Same transform, but the first register pass reads its group straight from
+// the prologue (op.load: the group's 2^K global loads issued together) and
+// the last register pass hands its group straight to the epilogue
+// (op.pre / op.store), so shared memory is only used between passes.
+template <bool INV, int K, class Get, class Put>
+__device__ __forceinline__ void pass_io(int logN, int s0, const ulonglong2* __restrict__ tw, u64 q, u64 q2, int tid,
+                                        int nthr, Get& get, Put& put)
+{
+    constexpr int R = 1 << K;
+    const int N = 1 << logN;
+    const int lsh = INV ? s0 : (logN - s0 - K);
+    const int ngroups = N >> K;
+    for (int gi = tid; gi < ngroups; gi += nthr) {
+        const int g = gi >> lsh;
+        const int r = gi & ((1 << lsh) - 1);
+        const int j0 = (g << (lsh + K)) + r;
+        u64 x[R];
+        get(std::integral_constant<int, R>{}, j0, lsh, x);
+        if (!INV) {
+#pragma unroll
+            for (int l = 0; l < K; ++l) {
+                const int h = R >> (l + 1);
+                const ulonglong2* twl = tw + (1 << (s0 + l)) + (g << l);
+#pragma unroll
+                for (int m = 0; m < (1 << l); ++m) {
+                    const ulonglong2 w = __ldg(&twl[m]);
+#pragma unroll
+                    for (int t = 0; t < h; ++t) {
+                        const int i = m * 2 * h + t;
+                        u64 X = x[i];
+                        X = X >= q2 ? X - q2 : X;
+                        const u64 T = mul_shoup_lazy(x[i + h], w.x, w.y, q);
+                        x[i] = X + T;
+                        x[i + h] = X + q2 - T;
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int l = 0; l < K; ++l) {
+                const int h = 1 << l;
+                const ulonglong2* twl = tw + (N >> (s0 + l + 1)) + (g << (K - l - 1));
+#pragma unroll
+                for (int m = 0; m < (R >> (l + 1)); ++m) {
+                    const ulonglong2 w = __ldg(&twl[m]);
+#pragma unroll
+                    for (int t = 0; t < h; ++t) {
+                        const int i = m * 2 * h + t;
+                        const u64 X = x[i], Y = x[i + h];
+                        u64 S = X + Y;
+                        S = S >= q2 ? S - q2 : S;
+                        x[i] = S;
+                        x[i + h] = mul_shoup_lazy(X + q2 - Y, w.x, w.y, q);
+                    }
+                }
+            }
+        }
+        put(std::integral_constant<int, R>{}, j0, lsh, x);
+    }
+}
+
+template <bool INV, int KMAX, class Get, class Put>
+__device__ __forceinline__ void pass_io_k(int k, int logN, int s0, const ulonglong2* tw, u64 q, u64 q2, int tid, int nthr,
+                                          Get& get, Put& put)
+{
+    if constexpr (KMAX >= 1) {
+        if (k == KMAX) {
+            pass_io<INV, KMAX>(logN, s0, tw, q, q2, tid, nthr, get, put);
+            return;
+        }
+        pass_io_k<INV, KMAX - 1>(k, logN, s0, tw, q, q2, tid, nthr, get, put);
+    }
+}
+
+template <bool INV, int LOGR, int MAXT, class Op>
+__global__ void __launch_bounds__(MAXT, 1) k_ntt_io(Op op, NttTables T)
+{
+    extern __shared__ u64 sm[];
+    const int logN = T.logN;
+    const int N = 1 << logN;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int p = blockIdx.x; p < op.count(); p += gridDim.x) {
+        const int ns = op.nsub(p);
+        for (int u = 0; u < ns; ++u) {
+            const int pi = op.prime(p, u);
+            const PrimeC P = T.pc[pi];
+            if (op.direct(p, u)) {
+                for (int j = tid; j < N; j += nthr) op.store(p, u, j, 0, op.pre(p, u, j), P);
+                __syncthreads();
+                continue;
+            }
+            const u64 q = P.q, q2 = 2 * P.q;
+            const ulonglong2* tw = (INV ? T.tw_inv : T.tw_fwd) + (size_t)pi * N;
+            int s = 0;
+            bool first = true;
+            while (s < logN) {
+                const int k = (logN - s) < LOGR ? (logN - s) : LOGR;
+                const bool last = s + k >= logN;
+                auto gload = [&](auto Rc, int j0, int lsh, u64* x) {
+                    constexpr int R = decltype(Rc)::value;
+#pragma unroll
+                    for (int i = 0; i < R; ++i) x[i] = op.load(p, u, j0 + (i << lsh), P);
+                };
+                auto gsm = [&](auto Rc, int j0, int lsh, u64* x) {
+                    constexpr int R = decltype(Rc)::value;
+#pragma unroll
+                    for (int i = 0; i < R; ++i) x[i] = sm[spad(j0 + (i << lsh))];
+                };
+                auto psm = [&](auto Rc, int j0, int lsh, u64* x) {
+                    constexpr int R = decltype(Rc)::value;
+#pragma unroll
+                    for (int i = 0; i < R; ++i) sm[spad(j0 + (i << lsh))] = x[i];
+                };
+                auto pepi = [&](auto Rc, int j0, int lsh, u64* x) {
+                    constexpr int R = decltype(Rc)::value;
+#pragma unroll
+                    for (int i = 0; i < R; ++i) {
+                        const int j = j0 + (i << lsh);
+                        const typename Op::Pre pr = op.pre(p, u, j);
+                        op.store(p, u, j, INV ? inv_final(x[i], P) : fwd_final(x[i], q), pr, P);
+                    }
+                };
+                if (first && last) pass_io_k<INV, LOGR>(k, logN, s, tw, q, q2, tid, nthr, gload, pepi);
+                else if (first) pass_io_k<INV, LOGR>(k, logN, s, tw, q, q2, tid, nthr, gload, psm);
+                else if (last) pass_io_k<INV, LOGR>(k, logN, s, tw, q, q2, tid, nthr, gsm, pepi);
+                else pass_io_k<INV, LOGR>(k, logN, s, tw, q, q2, tid, nthr, gsm, psm);
+                __syncthreads();
+                first = false;
+                s += k;
+            }
+        }
     }
 }

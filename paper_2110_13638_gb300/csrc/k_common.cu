@@ -1,0 +1,230 @@
+// k_common.cu -- launch accounting, plain transforms, element-wise kernels,
+// per-level division constants.
+#include "launch.cuh"
+
+namespace fhe {
+
+static std::atomic<uint64_t> g_launches{0};
+
+uint64_t launch_count() { return g_launches.load(); }
+
+LaunchScope::LaunchScope(const fhe_ctx* ctx, const char* family, cudaStream_t s) : c(ctx), st(s)
+{
+    g_launches.fetch_add(1);
+    if (!c->prof_family.empty() && c->prof_family == family) {
+        c->prof_launches += 1;
+        if (c->prof_used + 2 <= c->prof_ev.size()) {
+            idx = (long)c->prof_used;
+            c->prof_used += 2;
+            cudaEventRecord(c->prof_ev[idx], st);
+        }
+    }
+}
+
+LaunchScope::~LaunchScope()
+{
+    if (idx >= 0) cudaEventRecord(c->prof_ev[idx + 1], st);
+}
+
+const char* ntt_variant_name(int v)
+{
+    switch (v) {
+    case 1: return "one block per transform, radix-8 passes, 1024 threads";
+    case 2: return "two-pass column/row tiles, radix-16";
+    case 3: return "two-pass column/row tiles, radix-8";
+    case 4: return "one block per transform, radix-8, loads and stores fused into the first and last pass";
+    case 5: return "one block per transform, radix-16, loads and stores fused into the first and last pass";
+    default: return "one block per transform, radix-16 passes, 512 threads";
+    }
+}
+
+// ---------------------------------------------------------------- ops
+// in-place / out-of-place transform of rows of polynomials
+struct OpRows {
+    static const char* family() { return "ntt"; }
+    const u64* src;
+    u64* dst;
+    int n, rows, N;
+    uint8_t pmap[64];
+    __host__ __device__ int count() const { return n; }
+    __host__ __device__ int nsub(int) const { return 1; }
+    __device__ int prime(int p, int) const { return pmap[p % rows]; }
+    __device__ bool direct(int, int) const { return false; }
+    __device__ u64 load(int p, int, int j, const PrimeC&) const { return src[(size_t)p * N + j]; }
+    struct Pre {};
+    __device__ Pre pre(int, int, int) const { return {}; }
+    __device__ void store(int p, int, int j, u64 v, const Pre&, const PrimeC&) const { dst[(size_t)p * N + j] = v; }
+};
+
+void k_ntt_rows(const fhe_ctx* c, u64* d, uint32_t n_poly, uint32_t rows, const uint8_t* row_prime, bool forward,
+                cudaStream_t st)
+{
+    OpRows op;
+    op.src = d;
+    op.dst = d;
+    op.n = (int)(n_poly * rows);
+    op.rows = (int)rows;
+    op.N = (int)c->N;
+    for (uint32_t r = 0; r < rows && r < 64; ++r) op.pmap[r] = row_prime[r];
+    if (forward) launch_ntt<false>(c, op, st);
+    else launch_ntt<true>(c, op, st);
+}
+
+void k_ct_to_coeff(const fhe_ctx* c, const u64* in, u64* out, uint32_t n_ct, uint32_t comps, uint32_t L, bool to_coeff,
+                   cudaStream_t st)
+{
+    OpRows op;
+    op.src = in;
+    op.dst = out;
+    op.n = (int)(n_ct * comps * L);
+    op.rows = (int)L;
+    op.N = (int)c->N;
+    for (uint32_t r = 0; r < L; ++r) op.pmap[r] = (uint8_t)r;
+    if (to_coeff) launch_ntt<true>(c, op, st);
+    else launch_ntt<false>(c, op, st);
+}
+
+// ---------------------------------------------------------------- element-wise
+// per-prime constants for element-wise kernels come from the resident table
+__global__ void k_add_kernel(const u64* __restrict__ a, const u64* __restrict__ b, u64* __restrict__ out,
+                             size_t total, int L, int logN, const PrimeC* __restrict__ pc)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)((i >> logN) % L);
+        const u64 q = pc[r].q;
+        out[i] = add_mod(a[i], b[i], q);
+    }
+}
+
+
+void k_add(const fhe_ctx* c, const u64* a, const u64* b, u64* out, uint32_t n_ct, uint32_t comps, uint32_t L,
+           cudaStream_t st)
+{
+    size_t total = (size_t)n_ct * comps * L * c->N;
+    if (!total) return;
+    LaunchScope ls(c, "elementwise", st);
+    k_add_kernel<<<ew_grid(total), 256, 0, st>>>(a, b, out, total, (int)L, (int)c->logN, c->d_pc);
+}
+
+__global__ void k_tensor_kernel(const u64* __restrict__ a, const u64* __restrict__ b, u64* __restrict__ out,
+                                size_t per_comp, int n_ct, int L, int logN, const PrimeC* __restrict__ pc)
+{
+    // per_comp = L * N; thread covers (ct, r, j)
+    const size_t total = (size_t)n_ct * per_comp;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t ct = i / per_comp, w = i % per_comp;
+        const int r = (int)(w >> logN);
+        const PrimeC P = pc[r];
+        const u64* A = a + ct * 2 * per_comp;
+        const u64* B = b + ct * 2 * per_comp;
+        const u64 a0 = A[w], a1 = A[per_comp + w], b0 = B[w], b1 = B[per_comp + w];
+        u64* O = out + ct * 3 * per_comp;
+        O[w] = mul_mod(a0, b0, P);
+        O[per_comp + w] = add_mod(mul_mod(a0, b1, P), mul_mod(a1, b0, P), P.q);
+        O[2 * per_comp + w] = mul_mod(a1, b1, P);
+    }
+}
+
+void k_tensor(const fhe_ctx* c, const u64* a, const u64* b, u64* out3, uint32_t n_ct, uint32_t L, cudaStream_t st)
+{
+    const size_t per_comp = (size_t)L * c->N;
+    const size_t total = (size_t)n_ct * per_comp;
+    if (!total) return;
+    LaunchScope ls(c, "tensor", st);
+    k_tensor_kernel<<<ew_grid(total), 256, 0, st>>>(a, b, out3, per_comp, (int)n_ct, (int)L, (int)c->logN, c->d_pc);
+}
+
+// cres[ct * cstride + r]: residues of one integer constant per ciphertext
+// (cstride = 0: one constant for all).  Reads residues r < L_out of an input
+// stored with L_in residues (L_out < L_in is a mod-drop on the fly).
+__global__ void k_mul_const_kernel(const u64* __restrict__ in, u64* __restrict__ out, size_t total, int comps, int L_in,
+                                   int L_out, int logN, const u64* __restrict__ cres, int cstride,
+                                   const PrimeC* __restrict__ pc)
+{
+    const size_t Nm = ((size_t)1 << logN) - 1;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = i >> logN;            // (ct, comp, r) with r < L_out
+        const int r = (int)(row % L_out);
+        const size_t poly = row / L_out;
+        const size_t ct = poly / comps;
+        const PrimeC P = pc[r];
+        const u64 x = in[((poly * L_in + r) << logN) + (i & Nm)];
+        out[i] = mul_mod(x, cres[ct * cstride + r], P);
+    }
+}
+
+void k_mul_const(const fhe_ctx* c, const u64* in, u64* out, uint32_t n_ct, uint32_t comps, uint32_t L_in, uint32_t L_out,
+                 const u64* cres, uint32_t cstride, cudaStream_t st)
+{
+    size_t total = (size_t)n_ct * comps * L_out * c->N;
+    if (!total) return;
+    LaunchScope ls(c, "elementwise", st);
+    k_mul_const_kernel<<<ew_grid(total), 256, 0, st>>>(in, out, total, (int)comps, (int)L_in, (int)L_out, (int)c->logN,
+                                                       cres, (int)cstride, c->d_pc);
+}
+
+// constant polynomial (C, 0, ..., 0) is C at every NTT point: add to comp 0
+__global__ void k_add_const_kernel(u64* __restrict__ ct, size_t total, int L, int logN, const u64* __restrict__ cres,
+                                   int cstride, const PrimeC* __restrict__ pc)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = i >> logN;                // (ct, r) over comp 0 only
+        const size_t n = row / L;
+        const int r = (int)(row % L);
+        const size_t idx = (n * 2 * L + r) * ((size_t)1 << logN) + (i & (((size_t)1 << logN) - 1));
+        ct[idx] = add_mod(ct[idx], cres[n * cstride + r], pc[r].q);
+    }
+}
+
+void k_add_const(const fhe_ctx* c, u64* ct, uint32_t n_ct, uint32_t L, const u64* cres, uint32_t cstride, cudaStream_t st)
+{
+    size_t total = (size_t)n_ct * L * c->N;
+    if (!total) return;
+    LaunchScope ls(c, "elementwise", st);
+    k_add_const_kernel<<<ew_grid(total), 256, 0, st>>>(ct, total, (int)L, (int)c->logN, cres, (int)cstride, c->d_pc);
+}
+
+// T = t1 + x2 * c2 + x|_{L1} * c1 over L1 residues (x stored with Lx residues):
+// the sum of the three terms of the degree-3 activation in one pass
+__global__ void k_poly_combine_kernel(u64* __restrict__ t1, const u64* __restrict__ x2, const u64* __restrict__ x,
+                                      size_t total, int L1, int Lx, int logN, const u64* __restrict__ c2,
+                                      const u64* __restrict__ c1, const PrimeC* __restrict__ pc)
+{
+    const size_t Nm = ((size_t)1 << logN) - 1;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = i >> logN;            // (ct, comp, r), r < L1
+        const int r = (int)(row % L1);
+        const size_t poly = row / L1;
+        const PrimeC P = pc[r];
+        const u64 xv = x[((poly * Lx + r) << logN) + (i & Nm)];
+        u64 a = add_mod(t1[i], mul_mod(x2[i], c2[r], P), P.q);
+        t1[i] = add_mod(a, mul_mod(xv, c1[r], P), P.q);
+    }
+}
+
+void k_poly_combine(const fhe_ctx* c, u64* t1, const u64* x2, const u64* x, uint32_t n_ct, uint32_t L1, uint32_t Lx,
+                    const u64* c2, const u64* c1, cudaStream_t st)
+{
+    const size_t total = (size_t)n_ct * 2 * L1 * c->N;
+    if (!total) return;
+    LaunchScope ls(c, "elementwise", st);
+    k_poly_combine_kernel<<<ew_grid(total), 256, 0, st>>>(t1, x2, x, total, (int)L1, (int)Lx, (int)c->logN, c2, c1,
+                                                          c->d_pc);
+}
+
+DivC make_divc(const fhe_ctx* c, uint32_t p_index, uint32_t n_targets)
+{
+    DivC d;
+    const u64 p = c->primes[p_index];
+    d.p = p;
+    d.p_half = (p - 1) / 2;
+    for (uint32_t i = 0; i < n_targets && i < 32; ++i) {
+        const u64 q = c->primes[i];
+        d.inv[i] = hinv(p % q, q);
+        d.invs[i] = shoup(d.inv[i], q);
+        d.pmod[i] = p % q;
+    }
+    return d;
+}
+
+}  // namespace fhe

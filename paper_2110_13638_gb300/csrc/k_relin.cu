@@ -1,0 +1,42 @@
+// k_relin.cu -- relinearisation: RNS key switching with per-prime digits.
+#include "ops.cuh"
+
+namespace fhe {
+
+size_t relin_scratch_bytes(const fhe_ctx* c, uint32_t n_ct, uint32_t L)
+{
+    const size_t N = c->N;
+    return arena_need({(size_t)n_ct * L * N * 8, (size_t)n_ct * 2 * (L + 1) * N * 8, (size_t)n_ct * 2 * N * 8});
+}
+
+void k_relin(const fhe_ctx* c, const u64* d3, u64* out2, uint32_t n_ct, uint32_t L, void* scratch, cudaStream_t st)
+{
+    if (n_ct == 0) return;
+    const size_t N = c->N;
+    Arena ar;
+    ar.base = (char*)scratch;
+    ar.cap = relin_scratch_bytes(c, n_ct, L);
+    u64* D = (u64*)ar.take((size_t)n_ct * L * N * 8);
+    u64* acc = (u64*)ar.take((size_t)n_ct * 2 * (L + 1) * N * 8);
+    u64* Vp = (u64*)ar.take((size_t)n_ct * 2 * N * 8);
+
+    OpDigitsInv s1{d3, D, (int)n_ct, (int)L, (int)N};
+    launch_ntt<true>(c, s1, st);
+    OpModUpMac s2{d3, D, c->d_ksk, acc, (int)n_ct, (int)L, (int)N, (int)c->L_top};
+    launch_ntt<false>(c, s2, st);
+    OpAccPInv s3{acc, Vp, (int)n_ct, (int)L, (int)N, (int)c->L_top};
+    launch_ntt<true>(c, s3, st);
+    OpModDown s4;
+    s4.d3 = d3;
+    s4.acc = acc;
+    s4.Vp = Vp;
+    s4.out = out2;
+    s4.n = (int)n_ct;
+    s4.L = (int)L;
+    s4.N = (int)N;
+    s4.d = make_divc(c, c->L_top, L);
+    launch_ntt<false>(c, s4, st);
+}
+
+
+}  // namespace fhe

@@ -1,0 +1,196 @@
+// ops.cuh -- the fused-transform ops of rescale and key switching, shared by
+// their own launchers and the multi-batch (uneven level) launcher.
+#pragma once
+#include "launch.cuh"
+
+namespace fhe {
+
+// ---------------------------------------------------------------- rescale
+
+// INTT of one residue row per (ct, comp) into scratch V (coefficient form)
+struct OpTakeRowInv {
+    static const char* family() { return "rescale_intt"; }
+    const u64* in;
+    u64* V;
+    int n, L, row, N, pidx;
+    const u64* mulc;    // optional: the input is first multiplied by this per-residue constant
+    __host__ __device__ int count() const { return n; }
+    __host__ __device__ int nsub(int) const { return 1; }
+    __device__ int prime(int, int) const { return pidx; }
+    __device__ bool direct(int, int) const { return false; }
+    __device__ u64 load(int p, int, int j, const PrimeC& P) const
+    {
+        const u64 x = in[((size_t)p * L + row) * N + j];
+        return mulc ? mul_mod(x, mulc[row], P) : x;
+    }
+    struct Pre {};
+    __device__ Pre pre(int, int, int) const { return {}; }
+    __device__ void store(int p, int, int j, u64 v, const Pre&, const PrimeC&) const { V[(size_t)p * N + j] = v; }
+};
+
+// out_i = (in_i - NTT([v]_{q_i})) * p^{-1} (+ addc on comp 0)
+struct OpDivFwd {
+    static const char* family() { return "rescale_ntt"; }
+    const u64* in;      // [n_poly][L_in][N]
+    const u64* V;       // [n_poly][N]  coefficient form mod p
+    u64* out;           // [n_poly][L_out][N]
+    const u64* addc;    // optional: residues of a constant added to comp 0, [n_ct][addc_stride]
+    int n_poly, comps, L_in, L_out, N, addc_stride;
+    const u64* mulc;    // optional: the input is first multiplied by this per-residue constant
+    DivC d;
+    __host__ __device__ int count() const { return n_poly * L_out; }
+    __host__ __device__ int nsub(int) const { return 1; }
+    __device__ int prime(int p, int) const { return p % L_out; }
+    __device__ bool direct(int, int) const { return false; }
+    __device__ u64 load(int p, int, int j, const PrimeC& Q) const
+    {
+        const int poly = p / L_out, i = p % L_out;
+        return centred_to(V[(size_t)poly * N + j], d.p, d.p_half, d.pmod[i], Q);
+    }
+    struct Pre { u64 x, c; };
+    __device__ Pre pre(int p, int, int j) const
+    {
+        const int poly = p / L_out, i = p % L_out;
+        Pre r;
+        r.x = in[((size_t)poly * L_in + i) * N + j];
+        r.c = (addc && (poly % comps) == 0) ? addc[(size_t)(poly / comps) * addc_stride + i] : 0;
+        return r;
+    }
+    __device__ void store(int p, int, int j, u64 v, const Pre& pr, const PrimeC& Q) const
+    {
+        const int poly = p / L_out, i = p % L_out;
+        const u64 x = mulc ? mul_mod(pr.x, mulc[i], Q) : pr.x;
+        const u64 r = mul_shoup(sub_mod(x, v, Q.q), d.inv[i], d.invs[i], Q.q);
+        out[((size_t)poly * L_out + i) * N + j] = add_mod(r, pr.c, Q.q);
+    }
+};
+
+// ---------------------------------------------------------------- relinearise
+// step 1: digits D_j = INTT(d2_j) in [0, q_j)
+struct OpDigitsInv {
+    static const char* family() { return "keyswitch_intt"; }
+    const u64* d3;      // [n][3][L][N]
+    u64* D;             // [n][L][N]
+    int n, L, N;
+    __host__ __device__ int count() const { return n * L; }
+    __host__ __device__ int nsub(int) const { return 1; }
+    __device__ int prime(int p, int) const { return p % L; }
+    __device__ bool direct(int, int) const { return false; }
+    __device__ u64 load(int p, int, int j, const PrimeC&) const
+    {
+        const int ct = p / L, r = p % L;
+        return d3[(((size_t)ct * 3 + 2) * L + r) * N + j];
+    }
+    struct Pre {};
+    __device__ Pre pre(int, int, int) const { return {}; }
+    __device__ void store(int p, int, int j, u64 v, const Pre&, const PrimeC&) const { D[(size_t)p * N + j] = v; }
+};
+
+// step 2: per (ct, target t in 0..L, t = L meaning P): for every digit u,
+// NTT(D_u mod q_t) * ksk_u[k][t], accumulated over u into acc[ct][k][t].
+// Keys carry their Shoup quotients, so each key product is one Shoup product.
+struct OpModUpMac {
+    static const char* family() { return "keyswitch_modup_mac"; }
+    const u64* d3;
+    const u64* D;
+    const ulonglong2* ksk;  // [L_top][2][L_top+1][N] (k, floor(k 2^64 / q))
+    u64* acc;               // [n][2][L+1][N]
+    int n, L, N, Ltop;
+    __host__ __device__ int count() const { return n * (L + 1); }
+    __host__ __device__ int nsub(int) const { return L; }
+    __device__ int prime(int p, int) const
+    {
+        const int t = p % (L + 1);
+        return t == L ? Ltop : t;
+    }
+    __device__ bool direct(int p, int u) const { return (p % (L + 1)) == u; }
+    __device__ u64 load(int p, int u, int j, const PrimeC& Q) const
+    {
+        const int ct = p / (L + 1);
+        return reduce64(D[((size_t)ct * L + u) * N + j], Q);
+    }
+    struct Pre {
+        ulonglong2 k0, k1;
+        u64 a0, a1, dv;
+    };
+    __device__ Pre pre(int p, int u, int j) const
+    {
+        const int ct = p / (L + 1), t = p % (L + 1);
+        const int tk = t == L ? Ltop : t;
+        Pre r;
+        r.k0 = __ldg(&ksk[(((size_t)u * 2 + 0) * (Ltop + 1) + tk) * N + j]);
+        r.k1 = __ldg(&ksk[(((size_t)u * 2 + 1) * (Ltop + 1) + tk) * N + j]);
+        if (u > 0) {
+            r.a0 = acc[(((size_t)ct * 2 + 0) * (L + 1) + t) * N + j];
+            r.a1 = acc[(((size_t)ct * 2 + 1) * (L + 1) + t) * N + j];
+        } else {
+            r.a0 = r.a1 = 0;
+        }
+        r.dv = (t == u) ? d3[(((size_t)ct * 3 + 2) * L + t) * N + j] : 0;   // NTT(d2_t) is d2_t
+        return r;
+    }
+    __device__ void store(int p, int u, int j, u64 v, const Pre& pr, const PrimeC& Q) const
+    {
+        const int ct = p / (L + 1), t = p % (L + 1);
+        if (t == u) v = pr.dv;
+        const u64 p0 = mul_shoup(v, pr.k0.x, pr.k0.y, Q.q);
+        const u64 p1 = mul_shoup(v, pr.k1.x, pr.k1.y, Q.q);
+        acc[(((size_t)ct * 2 + 0) * (L + 1) + t) * N + j] = u == 0 ? p0 : add_mod(pr.a0, p0, Q.q);
+        acc[(((size_t)ct * 2 + 1) * (L + 1) + t) * N + j] = u == 0 ? p1 : add_mod(pr.a1, p1, Q.q);
+    }
+};
+
+// step 3: INTT of the P residue of both accumulators
+struct OpAccPInv {
+    static const char* family() { return "keyswitch_acc_intt"; }
+    const u64* acc;
+    u64* Vp;            // [n][2][N]
+    int n, L, N, Ltop;
+    __host__ __device__ int count() const { return n * 2; }
+    __host__ __device__ int nsub(int) const { return 1; }
+    __device__ int prime(int, int) const { return Ltop; }
+    __device__ bool direct(int, int) const { return false; }
+    __device__ u64 load(int p, int, int j, const PrimeC&) const { return acc[((size_t)p * (L + 1) + L) * N + j]; }
+    struct Pre {};
+    __device__ Pre pre(int, int, int) const { return {}; }
+    __device__ void store(int p, int, int j, u64 v, const Pre&, const PrimeC&) const { Vp[(size_t)p * N + j] = v; }
+};
+
+// step 4: ModDown + add: out_k,t = d_k,t + (acc_k,t - NTT([v]_{q_t})) * P^{-1}
+struct OpModDown {
+    static const char* family() { return "keyswitch_moddown"; }
+    const u64* d3;
+    const u64* acc;
+    const u64* Vp;
+    u64* out;           // [n][2][L][N]
+    int n, L, N;
+    DivC d;
+    __host__ __device__ int count() const { return n * 2 * L; }
+    __host__ __device__ int nsub(int) const { return 1; }
+    __device__ int prime(int p, int) const { return p % L; }
+    __device__ bool direct(int, int) const { return false; }
+    __device__ u64 load(int p, int, int j, const PrimeC& Q) const
+    {
+        const int poly = p / L, t = p % L;             // poly = ct*2 + k
+        return centred_to(Vp[(size_t)poly * N + j], d.p, d.p_half, d.pmod[t], Q);
+    }
+    struct Pre { u64 a, dk; };
+    __device__ Pre pre(int p, int, int j) const
+    {
+        const int poly = p / L, t = p % L;
+        const int ct = poly >> 1, k = poly & 1;
+        Pre r;
+        r.a = acc[((size_t)poly * (L + 1) + t) * N + j];
+        r.dk = d3[(((size_t)ct * 3 + k) * L + t) * N + j];
+        return r;
+    }
+    __device__ void store(int p, int, int j, u64 v, const Pre& pr, const PrimeC& Q) const
+    {
+        const int poly = p / L, t = p % L;
+        const int ct = poly >> 1, k = poly & 1;
+        const u64 ks = mul_shoup(sub_mod(pr.a, v, Q.q), d.inv[t], d.invs[t], Q.q);
+        out[(((size_t)ct * 2 + k) * L + t) * N + j] = add_mod(pr.dk, ks, Q.q);
+    }
+};
+
+}  // namespace fhe

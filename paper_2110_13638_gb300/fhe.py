@@ -219,6 +219,17 @@ def autohe(graph):
 
 
 # ---------------------------------------------------------------- context
+# names of the NTT schedules the autotuner chooses between (index = ntt_variant)
+NTT_SCHEDULES = (
+    "radix-16 passes, 512 threads, one block per transform",
+    "radix-8 passes, 1024 threads, one block per transform",
+    "two-pass column/row tiles, radix-16",
+    "two-pass column/row tiles, radix-8",
+    "radix-8, 1024 threads, global loads/stores fused into the first/last pass",
+    "radix-16, 512 threads, global loads/stores fused into the first/last pass",
+)
+
+
 class Context:
     """An RNS-CKKS context on the current CUDA device (tables and keys in HBM)."""
 
