@@ -222,6 +222,8 @@ static void free_ctx(fhe_ctx* c)
     cudaFree(c->d_cdt);
     cudaFree(c->d_enc_tw);
     cudaFree(c->d_enc_twist);
+    cudaFree(c->d_enc_tw_q);
+    cudaFree(c->d_enc_twist_q);
     cudaFree(c->d_slot_of);
     cudaFree(c->d_s);
     cudaFree(c->d_pk);
@@ -358,13 +360,23 @@ int fhe_ctx_create(uint32_t N, const uint32_t* bits, uint32_t n_bits, uint32_t l
     std::vector<u64> cdt = gauss_cdt();
     // encoder tables: zeta^{-4k} (k < N/4), zeta^{-k} (k < N/2), slot positions
     std::vector<double4> etw(N / 4), etwist(N / 2);
+    std::vector<ulonglong2> etw_q(N / 2), etwist_q(N);
+    auto q126 = [](const dd& v) {
+        u64 lo, hi;
+        dd_to_q126(v, &lo, &hi);
+        return make_ulonglong2(lo, hi);
+    };
     for (uint32_t k = 0; k < N / 4; ++k) {
         cdd z = zeta_pow_dd(-4 * (int64_t)k, N);
         etw[k] = make_double4(z.re.hi, z.re.lo, z.im.hi, z.im.lo);
+        etw_q[2 * k] = q126(z.re);
+        etw_q[2 * k + 1] = q126(z.im);
     }
     for (uint32_t k = 0; k < N / 2; ++k) {
         cdd z = zeta_pow_dd(-(int64_t)k, N);
         etwist[k] = make_double4(z.re.hi, z.re.lo, z.im.hi, z.im.lo);
+        etwist_q[2 * k] = q126(z.re);
+        etwist_q[2 * k + 1] = q126(z.im);
     }
     std::vector<uint32_t> slot_of(N / 2);
     u64 e = 1;
@@ -389,6 +401,8 @@ int fhe_ctx_create(uint32_t N, const uint32_t* bits, uint32_t n_bits, uint32_t l
     up((void**)&c->d_cdt, cdt.data(), cdt.size() * sizeof(u64));
     up((void**)&c->d_enc_tw, etw.data(), etw.size() * sizeof(double4));
     up((void**)&c->d_enc_twist, etwist.data(), etwist.size() * sizeof(double4));
+    up((void**)&c->d_enc_tw_q, etw_q.data(), etw_q.size() * sizeof(ulonglong2));
+    up((void**)&c->d_enc_twist_q, etwist_q.data(), etwist_q.size() * sizeof(ulonglong2));
     up((void**)&c->d_slot_of, slot_of.data(), slot_of.size() * sizeof(uint32_t));
     if (rc == FHE_OK) {
         // two-pass NTT intermediate: 128 MiB (or 64 transforms for small rings)
@@ -404,7 +418,8 @@ int fhe_ctx_create(uint32_t N, const uint32_t* bits, uint32_t n_bits, uint32_t l
         return rc;
     }
     c->key_bytes = np * sizeof(PrimeC) + 2 * twf.size() * sizeof(ulonglong2) + cdt.size() * 8 +
-                   (etw.size() + etwist.size()) * sizeof(double4) + slot_of.size() * 4;
+                   (etw.size() + etwist.size()) * sizeof(double4) +
+                   (etw_q.size() + etwist_q.size()) * sizeof(ulonglong2) + slot_of.size() * 4;
     rc = autotune_ntt(c);
     if (rc != FHE_OK) {
         free_ctx(c);
@@ -437,6 +452,8 @@ int fhe_ctx_fork(fhe_ctx* parent, fhe_ctx** out)
     c->d_cdt = parent->d_cdt;
     c->d_enc_tw = parent->d_enc_tw;
     c->d_enc_twist = parent->d_enc_twist;
+    c->d_enc_tw_q = parent->d_enc_tw_q;
+    c->d_enc_twist_q = parent->d_enc_twist_q;
     c->d_slot_of = parent->d_slot_of;
     c->has_keys = parent->has_keys;
     c->seed = parent->seed;

@@ -27,6 +27,10 @@ struct fhe_ctx {
     u64* d_cdt = nullptr;          // 38 Gaussian thresholds
     double4* d_enc_tw = nullptr;   // [N/4] zeta^{-4k} as (re.hi, re.lo, im.hi, im.lo)
     double4* d_enc_twist = nullptr;// [N/2] zeta^{-k}
+    // the same roots as fixed point for the encoder: [k][0] = re, [k][1] = im,
+    // each (low word, high word | sign << 63), magnitude scaled by 2^126
+    ulonglong2* d_enc_tw_q = nullptr;    // [N/4][2]
+    ulonglong2* d_enc_twist_q = nullptr; // [N/2][2]
     uint32_t* d_slot_of = nullptr; // [N/2] FFT position l -> slot j
 
     // keys (NTT form)

@@ -231,6 +231,28 @@ cdd zeta_pow_dd(int64_t e, uint32_t N)
     return r;
 }
 
+// d 2^126 truncated toward zero, |d| <= 2
+static __int128 scaled_q126(double d)
+{
+    if (d == 0.0) return 0;
+    int e = 0;
+    const double m = std::frexp(std::fabs(d), &e);         // |d| = m 2^e, m in [0.5, 1)
+    const u64 M = (u64)std::ldexp(m, 53);                   // exact
+    const int sh = e - 53 + 126;
+    u128 v = 0;
+    if (sh >= 0) v = (u128)M << sh;
+    else if (sh > -64) v = (u128)(M >> -sh);
+    return d < 0.0 ? -(__int128)v : (__int128)v;
+}
+
+void dd_to_q126(dd v, u64* lo, u64* hi)
+{
+    const __int128 t = scaled_q126(v.hi) + scaled_q126(v.lo);
+    const u128 mag = t < 0 ? (u128)(-t) : (u128)t;
+    *lo = (u64)mag;
+    *hi = (u64)(mag >> 64) | (t < 0 ? (1ull << 63) : 0ull);
+}
+
 void parameterise(uint32_t c, uint32_t s, double p, uint32_t* N, std::vector<uint32_t>& bits)
 {
     bits.assign(c + 2, s);

@@ -36,6 +36,11 @@ struct dd { double hi, lo; };
 struct cdd { dd re, im; };
 cdd zeta_pow_dd(int64_t e, uint32_t N);
 
+// v = hi + lo (|v| <= 2) as a sign-magnitude fixed-point number with 126
+// fractional bits: magnitude = (*hi & ~2^63) 2^64 + *lo, sign = bit 63 of *hi
+// (truncated toward zero, error below 2^-126)
+void dd_to_q126(dd v, u64* lo, u64* hi);
+
 // Alg. parameterise: cost c, scale power s, special-prime multiplier p
 void parameterise(uint32_t c, uint32_t s, double p, uint32_t* N, std::vector<uint32_t>& bits);
 

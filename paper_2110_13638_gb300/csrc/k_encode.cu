@@ -1,86 +1,144 @@
-// k_encode.cu -- canonical-embedding encode (double-double) and decode (FP64).
+// k_encode.cu -- canonical-embedding encode (128-bit fixed point) and decode (FP64).
 #include "launch.cuh"
 
 namespace fhe {
 
 // ---------------------------------------------------------------- encode
-// double-double helpers (explicit _rn intrinsics: never contracted)
-struct ddv { double hi, lo; };
-__device__ __forceinline__ ddv two_sum(double a, double b)
-{
-    double s = __dadd_rn(a, b);
-    double bb = __dsub_rn(s, a);
-    double e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
-    return {s, e};
-}
-__device__ __forceinline__ ddv fast_two_sum(double a, double b)
-{
-    double s = __dadd_rn(a, b);
-    return {s, __dsub_rn(b, __dsub_rn(s, a))};
-}
-// double-double sum with one error-free transformation on the high parts
-// (relative error ~2^-100 of the operands: the encoder needs ~2^-70)
-__device__ __forceinline__ ddv dadd(ddv a, ddv b)
-{
-    ddv s = two_sum(a.hi, b.hi);
-    s.lo = __dadd_rn(s.lo, __dadd_rn(a.lo, b.lo));
-    return fast_two_sum(s.hi, s.lo);
-}
-__device__ __forceinline__ ddv dneg(ddv a) { return {-a.hi, -a.lo}; }
-__device__ __forceinline__ ddv dmul(ddv a, ddv b)
-{
-    double p = __dmul_rn(a.hi, b.hi);
-    double e = __fma_rn(a.hi, b.hi, -p);
-    e = __dadd_rn(e, __dadd_rn(__dmul_rn(a.hi, b.lo), __dmul_rn(a.lo, b.hi)));
-    return fast_two_sum(p, e);
-}
-struct cddv { ddv re, im; };
-__device__ __forceinline__ cddv cadd(cddv a, cddv b) { return {dadd(a.re, b.re), dadd(a.im, b.im)}; }
-__device__ __forceinline__ cddv csub(cddv a, cddv b) { return {dadd(a.re, dneg(b.re)), dadd(a.im, dneg(b.im))}; }
-__device__ __forceinline__ cddv cmul(cddv a, cddv b)
-{
-    return {dadd(dmul(a.re, b.re), dneg(dmul(a.im, b.im))), dadd(dmul(a.re, b.im), dmul(a.im, b.re))};
-}
-__device__ __forceinline__ cddv ld4(const double4& v) { return {{v.x, v.y}, {v.z, v.w}}; }
+// The encoder's inverse DFT runs in 128-bit fixed point on the integer pipes:
+// a value is a two's-complement integer X with value X / 2^64 (63 integer
+// bits, 64 fractional bits); a root of unity is a sign-magnitude integer with
+// 126 fractional bits.  Inputs (slot * scale / M, formed as an exact product
+// of two doubles) enter exactly to 2^-64, each product drops less than
+// 6 2^-64, so the rounded coefficients carry an absolute error below 2^-40,
+// far inside the 1e-6 band around .5 where encodings may differ.
+// Range: |slot| * scale must stay below 2^61 (intermediate sums stay below
+// 2^62); larger inputs cannot be encoded against a 60-bit first prime anyway.
+struct fx { u64 lo, hi; };
 
-// round half away from zero of a double-double to int64
-__device__ __forceinline__ i64 dd_round(ddv v)
+__device__ __forceinline__ fx fx_add(fx a, fx b)
 {
-    bool neg = v.hi < 0.0 || (v.hi == 0.0 && v.lo < 0.0);
-    if (neg) v = dneg(v);
-    double f = floor(v.hi);
-    double frac = __dadd_rn(__dsub_rn(v.hi, f), v.lo);
-    double add = floor(__dadd_rn(frac, 0.5));
-    i64 r = (i64)f + (i64)add;
+    fx r;
+    asm("add.cc.u64 %0, %2, %4;\n\taddc.u64 %1, %3, %5;" : "=l"(r.lo), "=l"(r.hi) : "l"(a.lo), "l"(a.hi), "l"(b.lo), "l"(b.hi));
+    return r;
+}
+__device__ __forceinline__ fx fx_sub(fx a, fx b)
+{
+    fx r;
+    asm("sub.cc.u64 %0, %2, %4;\n\tsubc.u64 %1, %3, %5;" : "=l"(r.lo), "=l"(r.hi) : "l"(a.lo), "l"(a.hi), "l"(b.lo), "l"(b.hi));
+    return r;
+}
+__device__ __forceinline__ fx fx_neg(fx a) { return fx_sub({0ull, 0ull}, a); }
+__device__ __forceinline__ fx fx_cneg(fx a, bool neg) { return neg ? fx_neg(a) : a; }
+__device__ __forceinline__ bool fx_isneg(fx a) { return (i64)a.hi < 0; }
+
+// exact double -> fixed point (bits below 2^-64 truncated toward zero)
+__device__ __forceinline__ fx fx_from_double(double d)
+{
+    const u64 b = (u64)__double_as_longlong(d);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (ex == 0) return {0ull, 0ull};                    // zero or below 2^-1022
+    const u64 m = (b & 0xfffffffffffffull) | (1ull << 52);
+    const int sh = ex - 1011;                             // |d| 2^64 = m 2^sh
+    fx r;
+    if (sh >= 64) r = {0ull, m << (sh - 64)};
+    else if (sh > 0) r = {m << sh, m >> (64 - sh)};
+    else if (sh > -64) r = {m >> (-sh), 0ull};
+    else r = {0ull, 0ull};
+    return fx_cneg(r, (b >> 63) != 0);
+}
+
+// x * y as fixed point, x * y = p + e exactly (two-product)
+__device__ __forceinline__ fx fx_product(double x, double y)
+{
+    const double p = __dmul_rn(x, y);
+    const double e = __fma_rn(x, y, -p);
+    return fx_add(fx_from_double(p), fx_from_double(e));
+}
+
+// (|a| |w|) / 2^126 for magnitudes a < 2^126 (value scale 2^64) and w <= 2^127
+// (scale 2^126); the a_lo w_lo partial product (below 4 units) is dropped
+__device__ __forceinline__ fx umul_q126(u64 alo, u64 ahi, u64 wlo, u64 whi)
+{
+    const u64 lo1 = ahi * whi, hi1 = __umul64hi(ahi, whi);
+    const u64 t2l = ahi * wlo, t2h = __umul64hi(ahi, wlo);
+    const u64 t3l = alo * whi, t3h = __umul64hi(alo, whi);
+    u64 ml, mh, mc;
+    asm("add.cc.u64 %0, %3, %5;\n\taddc.cc.u64 %1, %4, %6;\n\taddc.u64 %2, %7, %7;"
+        : "=l"(ml), "=l"(mh), "=l"(mc)
+        : "l"(t2l), "l"(t2h), "l"(t3l), "l"(t3h), "l"(0ull));
+    const fx top = {lo1 << 2, (hi1 << 2) | (lo1 >> 62)};
+    const fx mid = {(mh << 2) | (ml >> 62), (mc << 2) | (mh >> 62)};
+    return fx_add(top, mid);
+}
+
+struct cfx { fx re, im; };
+__device__ __forceinline__ cfx cfx_add(cfx a, cfx b) { return {fx_add(a.re, b.re), fx_add(a.im, b.im)}; }
+__device__ __forceinline__ cfx cfx_sub(cfx a, cfx b) { return {fx_sub(a.re, b.re), fx_sub(a.im, b.im)}; }
+
+// a * w for a root w = (re, im) in sign-magnitude Q126 form
+__device__ __forceinline__ cfx cfx_mul_root(cfx a, ulonglong2 wr, ulonglong2 wi)
+{
+    const bool sar = fx_isneg(a.re), sai = fx_isneg(a.im);
+    const fx ar = fx_cneg(a.re, sar), ai = fx_cneg(a.im, sai);
+    const bool sbr = (wr.y >> 63) != 0, sbi = (wi.y >> 63) != 0;
+    const u64 brh = wr.y & ~(1ull << 63), bih = wi.y & ~(1ull << 63);
+    const fx p1 = umul_q126(ar.lo, ar.hi, wr.x, brh);     // re re
+    const fx p2 = umul_q126(ai.lo, ai.hi, wi.x, bih);     // im im
+    const fx p3 = umul_q126(ar.lo, ar.hi, wi.x, bih);     // re im
+    const fx p4 = umul_q126(ai.lo, ai.hi, wr.x, brh);     // im re
+    return {fx_add(fx_cneg(p1, sar != sbr), fx_cneg(p2, sai == sbi)),
+            fx_add(fx_cneg(p3, sar != sbi), fx_cneg(p4, sai != sbr))};
+}
+
+// a (real) * w
+__device__ __forceinline__ cfx fx_mul_root(fx a, ulonglong2 wr, ulonglong2 wi)
+{
+    const bool sa = fx_isneg(a);
+    const fx aa = fx_cneg(a, sa);
+    const fx pr = umul_q126(aa.lo, aa.hi, wr.x, wr.y & ~(1ull << 63));
+    const fx pi = umul_q126(aa.lo, aa.hi, wi.x, wi.y & ~(1ull << 63));
+    return {fx_cneg(pr, sa != ((wr.y >> 63) != 0)), fx_cneg(pi, sa != ((wi.y >> 63) != 0))};
+}
+
+// round half away from zero
+__device__ __forceinline__ i64 fx_round(fx v)
+{
+    const bool neg = fx_isneg(v);
+    const fx a = fx_cneg(v, neg);
+    const i64 r = (i64)(a.hi + (a.lo >> 63));
     return neg ? -r : r;
 }
 
 // One block per (ct, half h): the N/2-point inverse DFT of the slots (placed
-// at l(j) = (5^j mod 2N - 1)/4) is split by its first decimation-in-frequency
-// stage; half h runs the N/4-point DFT of its half in shared memory.
-// Output: m_k = round(scale * Re c_k), m_{k+N/2} = round(scale * Im c_k),
-// c_k = (2/N) zeta^{-k} X_k.
+// at l(j) = (5^j mod 2N - 1)/4, pre-multiplied by scale / M) is split by its
+// first decimation-in-frequency stage; half h runs the N/4-point DFT of its
+// half in shared memory (real and imaginary parts in separate arrays).
+// Output: m_k = round(Re c_k), m_{k+N/2} = round(Im c_k), c_k = zeta^{-k} X_k.
 __global__ void __launch_bounds__(512) k_encode_kernel(const double* __restrict__ slots, const uint32_t* __restrict__ slot_of,
-                                                        const double4* __restrict__ tw, const double4* __restrict__ twist,
+                                                        const ulonglong2* __restrict__ tw, const ulonglong2* __restrict__ twist,
                                                         double scale_over_M, int N, i64* __restrict__ m)
 {
-    extern __shared__ double4 A[];       // N/4 complex dd values
+    extern __shared__ ulonglong2 S[];    // [H] real parts, then [H] imaginary parts
     const int M = N / 2, H = M / 2;
+    ulonglong2* Sr = S;
+    ulonglong2* Si = S + H;
     const int ct = blockIdx.x >> 1, h = blockIdx.x & 1;
     const double* z = slots + (size_t)ct * M;
+    auto put = [&](int i, const cfx& v) {
+        Sr[i] = make_ulonglong2(v.re.lo, v.re.hi);
+        Si[i] = make_ulonglong2(v.im.lo, v.im.hi);
+    };
+    auto get = [&](int i) {
+        const ulonglong2 r = Sr[i], q = Si[i];
+        return cfx{{r.x, r.y}, {q.x, q.y}};
+    };
     for (int l = threadIdx.x; l < H; l += blockDim.x) {
-        const double x0 = z[slot_of[l]], x1 = z[slot_of[l + H]];
-        cddv v;
-        if (h == 0) {
-            v.re = two_sum(x0, x1);
-            v.im = {0.0, 0.0};
-        } else {
-            ddv d = two_sum(x0, -x1);
-            const cddv w = ld4(tw[l]);                 // W^l, W = e^{-2 pi i / M}
-            v.re = dmul(d, w.re);
-            v.im = dmul(d, w.im);
-        }
-        A[l] = make_double4(v.re.hi, v.re.lo, v.im.hi, v.im.lo);
+        const fx a = fx_product(z[slot_of[l]], scale_over_M);
+        const fx b = fx_product(z[slot_of[l + H]], scale_over_M);
+        cfx v;
+        if (h == 0) v = {fx_add(a, b), {0ull, 0ull}};
+        else v = fx_mul_root(fx_sub(a, b), __ldg(&tw[2 * l]), __ldg(&tw[2 * l + 1]));   // W^l, W = e^{-2 pi i / M}
+        put(l, v);
     }
     __syncthreads();
     // H-point DIF, twiddle for offset o at half-size hs: W^{o * M / (2 hs)}
@@ -88,11 +146,10 @@ __global__ void __launch_bounds__(512) k_encode_kernel(const double* __restrict_
         for (int b = threadIdx.x; b < H / 2; b += blockDim.x) {
             const int blk = b / hs, o = b % hs;
             const int i0 = blk * 2 * hs + o, i1 = i0 + hs;
-            const cddv x = ld4(A[i0]), y = ld4(A[i1]);
-            const cddv s = cadd(x, y);
-            const cddv d = cmul(csub(x, y), ld4(tw[o * (M / (2 * hs))]));
-            A[i0] = make_double4(s.re.hi, s.re.lo, s.im.hi, s.im.lo);
-            A[i1] = make_double4(d.re.hi, d.re.lo, d.im.hi, d.im.lo);
+            const cfx x = get(i0), y = get(i1);
+            const int e = o * (M / (2 * hs));
+            put(i0, cfx_add(x, y));
+            put(i1, cfx_mul_root(cfx_sub(x, y), __ldg(&tw[2 * e]), __ldg(&tw[2 * e + 1])));
         }
         __syncthreads();
     }
@@ -101,11 +158,9 @@ __global__ void __launch_bounds__(512) k_encode_kernel(const double* __restrict_
     for (int p = threadIdx.x; p < H; p += blockDim.x) {
         const int kp = (int)(__brev((unsigned)p) >> (32 - lg));
         const int k = 2 * kp + h;                       // frequency index in [0, M)
-        const cddv X = ld4(A[p]);
-        cddv c = cmul(X, ld4(twist[k]));
-        const ddv s = {scale_over_M, 0.0};
-        m[(size_t)ct * N + k] = dd_round(dmul(c.re, s));
-        m[(size_t)ct * N + k + M] = dd_round(dmul(c.im, s));
+        const cfx c = cfx_mul_root(get(p), __ldg(&twist[2 * k]), __ldg(&twist[2 * k + 1]));
+        m[(size_t)ct * N + k] = fx_round(c.re);
+        m[(size_t)ct * N + k + M] = fx_round(c.im);
     }
 }
 
@@ -129,7 +184,7 @@ size_t encode_scratch_bytes(const fhe_ctx* c, uint32_t n_ct) { return (size_t)n_
 void encode_coefficients(const fhe_ctx* c, const double* slots, uint32_t n_ct, double scale, i64* m, cudaStream_t st)
 {
     const int N = (int)c->N;
-    const size_t smem = (size_t)(N / 4) * sizeof(double4);
+    const size_t smem = (size_t)(N / 4) * 2 * sizeof(ulonglong2);
     static size_t configured = 0;
     if (configured < smem) {
         cudaFuncSetAttribute(k_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -139,7 +194,7 @@ void encode_coefficients(const fhe_ctx* c, const double* slots, uint32_t n_ct, d
     thr = thr < 32 ? 32 : (thr > 512 ? 512 : thr);
     {
     LaunchScope ls(c, "encode_fft", st);
-    k_encode_kernel<<<2 * n_ct, thr, smem, st>>>(slots, c->d_slot_of, c->d_enc_tw, c->d_enc_twist,
+    k_encode_kernel<<<2 * n_ct, thr, smem, st>>>(slots, c->d_slot_of, c->d_enc_tw_q, c->d_enc_twist_q,
                                                  scale / (double)(N / 2), N, m);
     }
 }
