@@ -236,6 +236,7 @@ def run_ours(args):
                    "samples_per_request": samples, "input_ciphertexts": n_in, "output_ciphertexts": n_out,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "ntt_schedule": "%d: %s" % (ctx.ntt_variant, fhe.NTT_SCHEDULES[ctx.ntt_variant]),
+                   "ntt_schedule_keyswitch": "%d: %s" % (ctx.ntt_variant_ks, fhe.NTT_SCHEDULES[ctx.ntt_variant_ks]),
                    "l2": "inputs larger than L2 (1.6 GB of ciphertexts per step)"},
         "e2e": {"value": round(e2e, 2), "unit": UNIT, "h2d_bytes_per_step": int(slots.numel() * 8),
                 "d2h_bytes_per_step": int(z.numel() * 8)},

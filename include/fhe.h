@@ -59,6 +59,8 @@ typedef struct {
     uint64_t key_bytes;  /* device bytes held for keys and tables */
     uint32_t ntt_variant;        /* NTT schedule the autotuner picked (0..5) */
     float ntt_variant_us[8];     /* autotuner: microseconds per transform of each schedule */
+    uint32_t ntt_variant_ks;     /* schedule of the key-switching inner-product transforms */
+    float ntt_variant_ks_us[8];  /* autotuner: microseconds per digit transform of each schedule */
 } fhe_ctx_info;
 
 /* Per-ciphertext metadata returned by graph evaluation. */
@@ -126,9 +128,10 @@ int fhe_gauss_table(uint64_t* out38);
 /* Build the context on the current CUDA device: primes, NTT tables and
  * encoder tables resident in HBM.  The NTT schedule (radix of the register
  * passes, threads per block, one- or two-pass, fused global I/O) is autotuned
- * here by timing each candidate on a rescale of 64 ciphertexts; the
- * environment variable FHE_NTT_VARIANT=0..5 fixes
- * it instead.  bits: coefficient-modulus bit sizes, the
+ * here by timing each candidate on a rescale of 64 ciphertexts, and again
+ * separately for the key-switching digit transforms (whose epilogue holds the
+ * key inner product) on that step alone; the environment variable
+ * FHE_NTT_VARIANT=0..5 fixes both instead.  bits: coefficient-modulus bit sizes, the
  * last one being the special prime; log_scale: scale 2^log_scale.
  * N must be a power of two in [16, 65536]; above 16384 only the two-pass
  * NTT schedules exist and encode / decode / grouped calls are refused. */

@@ -243,6 +243,7 @@ static int autotune_ntt(fhe_ctx* c)
         if (v < 0 || v >= kNttVariants) return fail(FHE_EINVAL, "FHE_NTT_VARIANT out of range (0..5)");
         if (c->N > kMaxSinglePassN && !ntt_two_pass(v)) return fail(FHE_EINVAL, "N > 16384 needs a two-pass NTT schedule (2 or 3)");
         c->ntt_variant = v;
+        c->ntt_variant_ks = v;
         return FHE_OK;
     }
     // Timed workload: a rescale (inverse transform of the last residue, then
@@ -302,9 +303,61 @@ static int autotune_ntt(fhe_ctx* c)
     for (int v = 0; v < kNttVariants; ++v)
         if (c->ntt_variant_us[v] > 0.f && c->ntt_variant_us[v] == best) { pick = v; break; }
     c->ntt_variant = pick;
+    c->ntt_variant_ks = pick;
+    cudaFree(buf);
+    buf = nullptr;
+    // Key-switching digit transforms (key inner product in the epilogue: more
+    // registers live) get their own pick, timed on that step alone for
+    // min(L_top, 4) digits on zero data (the arithmetic is data-independent),
+    // with about 256 MiB of ciphertext data so that, as in real batches, it
+    // streams from HBM rather than sitting in L2.  Rings that fit one block
+    // per transform only take those schedules here: the two-pass ones add an
+    // HBM round trip per digit transform that a small probe would hide.
+    if (e == cudaSuccess && c->L_top >= 1) {
+        const size_t N = c->N;
+        const uint32_t Lk = c->L_top < 4 ? c->L_top : 4;
+        const size_t per_ct = (size_t)(3 * Lk + Lk + 2 * (Lk + 1)) * N;
+        const uint32_t nk = std::max<uint32_t>(1u, (uint32_t)(((size_t)1 << 25) / per_ct));
+        const size_t w_d3 = (size_t)nk * 3 * Lk * N, w_D = (size_t)nk * Lk * N, w_acc = (size_t)nk * 2 * (Lk + 1) * N;
+        const size_t w_ksk = (size_t)Lk * 2 * (Lk + 1) * N * 2;
+        e = cudaMalloc((void**)&buf, (w_d3 + w_D + w_acc + w_ksk) * 8);
+        if (e == cudaSuccess) {
+            cudaMemset(buf, 0, (w_d3 + w_D + w_acc + w_ksk) * 8);
+            const u64* d3 = buf;
+            const u64* D = buf + w_d3;
+            u64* acc = buf + w_d3 + w_D;
+            const ulonglong2* ksk = (const ulonglong2*)(buf + w_d3 + w_D + w_acc);
+            const float kunits = (float)nk * (Lk + 1) * Lk;
+            float kbest = 1e30f;
+            for (int v = 0; v < kNttVariants && e == cudaSuccess; ++v) {
+                if ((c->N > kMaxSinglePassN) != ntt_two_pass(v)) continue;
+                c->ntt_variant_ks = v;
+                k_modup_mac_step(c, d3, D, ksk, acc, nk, Lk, nullptr);       // warm-up
+                float us_best = 1e30f;
+                for (int trial = 0; trial < 3 && e == cudaSuccess; ++trial) {
+                    cudaEventRecord(a, nullptr);
+                    for (int it = 0; it < 2; ++it) k_modup_mac_step(c, d3, D, ksk, acc, nk, Lk, nullptr);
+                    cudaEventRecord(b, nullptr);
+                    e = cudaEventSynchronize(b);
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, a, b);
+                    const float us = ms * 1000.f / (2.f * kunits);
+                    if (us < us_best) us_best = us;
+                }
+                c->ntt_variant_ks_us[v] = us_best;
+                if (us_best < kbest) kbest = us_best;
+            }
+            c->ntt_variant_ks = pick;
+            for (int v = 0; v < kNttVariants; ++v)
+                if (c->ntt_variant_ks_us[v] > 0.f && c->ntt_variant_ks_us[v] == kbest) { c->ntt_variant_ks = v; break; }
+            cudaFree(buf);
+        } else {
+            cudaGetLastError();          // no room for the probe: keep the general pick
+            e = cudaSuccess;
+        }
+    }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    cudaFree(buf);
     if (e != cudaSuccess) return cuda_check(e, "autotune");
     return FHE_OK;
 }
@@ -445,7 +498,11 @@ int fhe_ctx_fork(fhe_ctx* parent, fhe_ctx** out)
     c->delta = parent->delta;
     c->device = parent->device;
     c->ntt_variant = parent->ntt_variant;
-    for (int v = 0; v < 8; ++v) c->ntt_variant_us[v] = parent->ntt_variant_us[v];
+    c->ntt_variant_ks = parent->ntt_variant_ks;
+    for (int v = 0; v < 8; ++v) {
+        c->ntt_variant_us[v] = parent->ntt_variant_us[v];
+        c->ntt_variant_ks_us[v] = parent->ntt_variant_ks_us[v];
+    }
     c->d_pc = parent->d_pc;
     c->d_tw_fwd = parent->d_tw_fwd;
     c->d_tw_inv = parent->d_tw_inv;
@@ -492,7 +549,11 @@ int fhe_ctx_query(const fhe_ctx* c, fhe_ctx_info* out)
     for (size_t i = 0; i < c->primes.size() && i < 64; ++i) out->primes[i] = c->primes[i];
     out->key_bytes = c->key_bytes;
     out->ntt_variant = (uint32_t)c->ntt_variant;
-    for (int v = 0; v < kNttVariants && v < 8; ++v) out->ntt_variant_us[v] = c->ntt_variant_us[v];
+    out->ntt_variant_ks = (uint32_t)c->ntt_variant_ks;
+    for (int v = 0; v < kNttVariants && v < 8; ++v) {
+        out->ntt_variant_us[v] = c->ntt_variant_us[v];
+        out->ntt_variant_ks_us[v] = c->ntt_variant_ks_us[v];
+    }
     return FHE_OK;
 }
 

@@ -16,6 +16,8 @@ struct fhe_ctx {
     int device = 0;
     int ntt_variant = 0;           // NTT schedule (see ntt_variant_name), autotuned
     float ntt_variant_us[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // autotuner: us per transform per variant
+    int ntt_variant_ks = 0;        // schedule of the key-switching inner-product transforms
+    float ntt_variant_ks_us[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     mutable int force_single_pass = 0;   // set while a call must not use the two-pass scratch
     u64* d_ntt2 = nullptr;         // two-pass intermediate (allocated with the context)
     size_t ntt2_words = 0;
@@ -143,6 +145,8 @@ struct DivC {           // division by one prime p into primes q_0..q_{n-1}
     u64 pmod[32];             // p mod q_i
 };
 DivC make_divc(const fhe_ctx* c, uint32_t p_index, uint32_t n_targets);
+void k_modup_mac_step(const fhe_ctx* c, const u64* d3, const u64* D, const ulonglong2* ksk, u64* acc, uint32_t n_ct,
+                      uint32_t L, cudaStream_t st);
 
 // ---- kernels (kernels.cu); all enqueue on `st` -------------------------
 void k_ntt_rows(const fhe_ctx* c, u64* d, uint32_t n_poly, uint32_t rows, const uint8_t* row_prime,

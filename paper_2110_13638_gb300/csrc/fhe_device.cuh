@@ -235,6 +235,20 @@ __device__ __forceinline__ u64 inv_final(u64 x, const PrimeC& P)
     return mul_shoup(x, P.ninv, P.ninvs, P.q);       // x in [0, 2q) times N^{-1}
 }
 
+// An Op whose store accepts forward-transform outputs in the lazy range
+// [0, 4q) declares  static constexpr bool kLazyStore = true;
+template <class Op, class = void>
+struct lazy_store : std::false_type {};
+template <class Op>
+struct lazy_store<Op, std::void_t<decltype(Op::kLazyStore)>> : std::integral_constant<bool, Op::kLazyStore> {};
+
+template <class Op>
+__device__ __forceinline__ u64 fwd_out(u64 x, u64 q)
+{
+    if constexpr (lazy_store<Op>::value) return x;
+    else return fwd_final(x, q);
+}
+
 // ---------------------------------------------------------------- tables
 struct NttTables {
     const ulonglong2* tw_fwd;   // [nprimes][N] (w, w') psi^{bitrev(i)}
@@ -251,9 +265,12 @@ struct NttTables {
 //   int  prime(int p, int u) const          -- key-prime index of transform u
 //   bool direct(int p, int u) const         -- skip the transform (store reads input itself)
 //   u64  load(int p, int u, int j, const PrimeC&) const   -- input value in [0, q)
+//                                              (forward transforms accept [0, 4q))
 //   Pre  pre(int p, int u, int j) const     -- global words the epilogue needs (issued
 //                                              for several j before any store)
 //   void store(int p, int u, int j, u64 v, const Pre&, const PrimeC&) const -- v in [0, q)
+//                                              ([0, 4q) after a forward transform if
+//                                              the Op declares kLazyStore)
 // Grid-stride over units so one launch may cover any batch.  Prologue loads
 // and epilogue pre-loads are issued kUnroll at a time per thread.
 constexpr int kUnroll = 4;
@@ -298,7 +315,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_ntt_op(Op op, NttTables T)
                     if (j < N) {
                         pr[k] = op.pre(p, u, j);
                         const u64 x = dir ? 0 : sm[spad(j)];
-                        v[k] = dir ? 0 : (INV ? inv_final(x, P) : fwd_final(x, P.q));
+                        v[k] = dir ? 0 : (INV ? inv_final(x, P) : fwd_out<Op>(x, P.q));
                     }
                 }
 #pragma unroll
@@ -585,7 +602,7 @@ __global__ void __launch_bounds__(kThr2) k_ntt2_second(Op op, NttTables T, Split
                     const int e = e0 + k * nthr;
                     if (e < tot) {
                         pr[k] = op.pre(p, u, rb * N2 + e);
-                        v[k] = dir ? 0 : fwd_final(sm[(e / N2) * pitch + spad(e % N2)], P.q);
+                        v[k] = dir ? 0 : fwd_out<Op>(sm[(e / N2) * pitch + spad(e % N2)], P.q);
                     }
                 }
 #pragma unroll
@@ -699,6 +716,8 @@ __device__ __forceinline__ void pass_io_k(int k, int logN, int s0, const ulonglo
     }
 }
 
+constexpr int kEpiBatch = 2;   // epilogue pre-loads issued together (more spills at 64 registers)
+
 template <bool INV, int LOGR, int MAXT, class Op>
 __global__ void __launch_bounds__(MAXT, 1) k_ntt_io(Op op, NttTables T)
 {
@@ -740,11 +759,16 @@ __global__ void __launch_bounds__(MAXT, 1) k_ntt_io(Op op, NttTables T)
                 };
                 auto pepi = [&](auto Rc, int j0, int lsh, u64* x) {
                     constexpr int R = decltype(Rc)::value;
+                    constexpr int B = R < kEpiBatch ? R : kEpiBatch;
 #pragma unroll
-                    for (int i = 0; i < R; ++i) {
-                        const int j = j0 + (i << lsh);
-                        const typename Op::Pre pr = op.pre(p, u, j);
-                        op.store(p, u, j, INV ? inv_final(x[i], P) : fwd_final(x[i], q), pr, P);
+                    for (int i0 = 0; i0 < R; i0 += B) {
+                        typename Op::Pre pr[B];
+#pragma unroll
+                        for (int i = 0; i < B; ++i) pr[i] = op.pre(p, u, j0 + ((i0 + i) << lsh));
+#pragma unroll
+                        for (int i = 0; i < B; ++i)
+                            op.store(p, u, j0 + ((i0 + i) << lsh),
+                                     INV ? inv_final(x[i0 + i], P) : fwd_out<Op>(x[i0 + i], q), pr[i], P);
                     }
                 };
                 if (first && last) pass_io_k<INV, LOGR>(k, logN, s, tw, q, q2, tid, nthr, gload, pepi);

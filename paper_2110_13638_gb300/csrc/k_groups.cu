@@ -79,7 +79,7 @@ void k_mul_relin_rescale_groups(const fhe_ctx* c, const LevelBatch* g, int ng, v
         tg.L[k] = L;
         tg.start[k + 1] = tg.start[k] + (unsigned long long)n * L * N;
         m1.ops[k] = OpDigitsInv{t3, D, n, L, (int)N};
-        m2.ops[k] = OpModUpMac{t3, D, c->d_ksk, acc, n, L, (int)N, (int)c->L_top};
+        m2.ops[k] = OpModUpMac{t3, D, c->d_ksk, acc, n, L, (int)N, (int)c->L_top, modup_red_mask(c, (uint32_t)L)};
         m3.ops[k] = OpAccPInv{acc, Vp, n, L, (int)N, (int)c->L_top};
         OpModDown md;
         md.d3 = t3;

@@ -22,7 +22,7 @@ void k_relin(const fhe_ctx* c, const u64* d3, u64* out2, uint32_t n_ct, uint32_t
 
     OpDigitsInv s1{d3, D, (int)n_ct, (int)L, (int)N};
     launch_ntt<true>(c, s1, st);
-    OpModUpMac s2{d3, D, c->d_ksk, acc, (int)n_ct, (int)L, (int)N, (int)c->L_top};
+    OpModUpMac s2{d3, D, c->d_ksk, acc, (int)n_ct, (int)L, (int)N, (int)c->L_top, modup_red_mask(c, L)};
     launch_ntt<false>(c, s2, st);
     OpAccPInv s3{acc, Vp, (int)n_ct, (int)L, (int)N, (int)c->L_top};
     launch_ntt<true>(c, s3, st);
@@ -38,5 +38,14 @@ void k_relin(const fhe_ctx* c, const u64* d3, u64* out2, uint32_t n_ct, uint32_t
     launch_ntt<false>(c, s4, st);
 }
 
+
+// The inner-product step alone on caller buffers (the autotuner times it):
+// L digits, keys laid out for L data primes plus one more (index L).
+void k_modup_mac_step(const fhe_ctx* c, const u64* d3, const u64* D, const ulonglong2* ksk, u64* acc, uint32_t n_ct,
+                      uint32_t L, cudaStream_t st)
+{
+    OpModUpMac op{d3, D, ksk, acc, (int)n_ct, (int)L, (int)c->N, (int)L, modup_red_mask(c, L)};
+    launch_ntt<false>(c, op, st);
+}
 
 }  // namespace fhe

@@ -99,9 +99,19 @@ static void launch_ntt_v(const fhe_ctx* c, const Op& op, int count, cudaStream_t
 // launch: unit p is located in the group table by prefix sums.
 constexpr int kMaxGroups = 8;
 
+// Ops that declare  static constexpr bool kKeySwitchMac = true  (the digit
+// transforms with the key inner product in their epilogue) run with the
+// schedule the autotuner picked for them, the rest with the general one.
+template <class Op, class = void>
+struct keyswitch_mac : std::false_type {};
+template <class Op>
+struct keyswitch_mac<Op, std::void_t<decltype(Op::kKeySwitchMac)>> : std::integral_constant<bool, Op::kKeySwitchMac> {};
+
 template <class Op>
 struct MultiOp {
     static const char* family() { return Op::family(); }
+    static constexpr bool kLazyStore = lazy_store<Op>::value;
+    static constexpr bool kKeySwitchMac = keyswitch_mac<Op>::value;
     typedef typename Op::Pre Pre;
     Op ops[kMaxGroups];
     int pre_[kMaxGroups + 1];
@@ -195,7 +205,8 @@ static void launch_ntt(const fhe_ctx* c, const Op& op, cudaStream_t st)
     // the two-pass schedule needs the same number of transforms in every unit
     // (callers refuse single-pass-only work above kMaxSinglePassN)
     const bool single = c->force_single_pass || !uniform_subs<Op>::value;
-    const int v = single && (c->ntt_variant == 2 || c->ntt_variant == 3) ? 1 : c->ntt_variant;
+    const int base = keyswitch_mac<Op>::value ? c->ntt_variant_ks : c->ntt_variant;
+    const int v = single && (base == 2 || base == 3) ? 1 : base;
     switch (v) {
     case 1: launch_ntt_v<INV, 3, 1024>(c, op, count, st); break;
     case 2: launch_ntt_2pass<INV, 4>(c, op, count, st); break;

@@ -86,16 +86,33 @@ struct OpDigitsInv {
     __device__ void store(int p, int, int j, u64 v, const Pre&, const PrimeC&) const { D[(size_t)p * N + j] = v; }
 };
 
+// digits u < L whose prime q_u exceeds 4 q_t for some target t in {q_0..q_{L-1}, P}:
+// their lift into q_t must be reduced before the forward transform, which
+// accepts inputs below 4 q_t
+inline uint32_t modup_red_mask(const fhe_ctx* c, uint32_t L)
+{
+    u64 qmin = c->primes[c->L_top];
+    for (uint32_t t = 0; t < L; ++t) qmin = c->primes[t] < qmin ? c->primes[t] : qmin;
+    uint32_t m = 0;
+    for (uint32_t u = 0; u < L; ++u)
+        if (c->primes[u] / 4 >= qmin) m |= 1u << u;
+    return m;
+}
+
 // step 2: per (ct, target t in 0..L, t = L meaning P): for every digit u,
 // NTT(D_u mod q_t) * ksk_u[k][t], accumulated over u into acc[ct][k][t].
 // Keys carry their Shoup quotients, so each key product is one Shoup product.
 struct OpModUpMac {
     static const char* family() { return "keyswitch_modup_mac"; }
+    static constexpr bool kLazyStore = true;     // the key products reduce any v < 2^64
+    static constexpr bool kKeySwitchMac = true;  // scheduled separately (heavy epilogue)
     const u64* d3;
     const u64* D;
     const ulonglong2* ksk;  // [L_top][2][L_top+1][N] (k, floor(k 2^64 / q))
     u64* acc;               // [n][2][L+1][N]
     int n, L, N, Ltop;
+    uint32_t red_mask;      // digits u whose prime exceeds 4 q_t for some target t:
+                            // only these need reducing before the forward transform
     __host__ __device__ int count() const { return n * (L + 1); }
     __host__ __device__ int nsub(int) const { return L; }
     __device__ int prime(int p, int) const
@@ -107,7 +124,8 @@ struct OpModUpMac {
     __device__ u64 load(int p, int u, int j, const PrimeC& Q) const
     {
         const int ct = p / (L + 1);
-        return reduce64(D[((size_t)ct * L + u) * N + j], Q);
+        const u64 d = D[((size_t)ct * L + u) * N + j];       // in [0, q_u)
+        return ((red_mask >> u) & 1u) ? reduce64(d, Q) : d;
     }
     struct Pre {
         ulonglong2 k0, k1;

@@ -34,7 +34,8 @@ class FheError(RuntimeError):
 class CtxInfo(ctypes.Structure):
     _fields_ = [("N", ctypes.c_uint32), ("slots", ctypes.c_uint32), ("L_top", ctypes.c_uint32),
                 ("log_scale", ctypes.c_uint32), ("primes", ctypes.c_uint64 * 64), ("key_bytes", ctypes.c_uint64),
-                ("ntt_variant", ctypes.c_uint32), ("ntt_variant_us", ctypes.c_float * 8)]
+                ("ntt_variant", ctypes.c_uint32), ("ntt_variant_us", ctypes.c_float * 8),
+                ("ntt_variant_ks", ctypes.c_uint32), ("ntt_variant_ks_us", ctypes.c_float * 8)]
 
 
 class CtMeta(ctypes.Structure):
@@ -251,6 +252,8 @@ class Context:
         self.key_bytes = int(info.key_bytes)
         self.ntt_variant = int(info.ntt_variant)
         self.ntt_variant_us = [float(info.ntt_variant_us[i]) for i in range(6)]
+        self.ntt_variant_ks = int(info.ntt_variant_ks)
+        self.ntt_variant_ks_us = [float(info.ntt_variant_ks_us[i]) for i in range(6)]
         self.delta = float(2 ** log_scale)
 
     def fork(self):
