@@ -134,7 +134,7 @@ int fhe_gauss_table(uint64_t* out38);
  * FHE_NTT_VARIANT=0..5 fixes both instead.  bits: coefficient-modulus bit sizes, the
  * last one being the special prime; log_scale: scale 2^log_scale.
  * N must be a power of two in [16, 65536]; above 16384 only the two-pass
- * NTT schedules exist and encode / decode / grouped calls are refused. */
+ * NTT schedules exist and the grouped (uneven-level) calls are refused. */
 int fhe_ctx_create(uint32_t N, const uint32_t* bits, uint32_t n_bits,
                    uint32_t log_scale, fhe_ctx** out);
 /* A fork shares the parent's tables and keys (resident once per parameter
@@ -159,7 +159,10 @@ int fhe_export_secret(fhe_ctx* ctx, uint64_t* d_out, void* stream);
 
 /* CKKS canonical-embedding encode: d_slots [n_ct][N/2] real -> plaintext
  * [n_ct][level][N] (NTT form); m_k = round(scale * sigma^{-1}(z)_k), half
- * away from zero, in double-double arithmetic. */
+ * away from zero.  The inverse DFT runs in 128-bit fixed point (64
+ * fractional bits); the unrounded coefficients are within 2^-40 of exact.
+ * Requires |slot| * scale < 2^61 (coefficients beyond that do not fit the
+ * first prime in any case); larger inputs give unspecified coefficients. */
 int fhe_encode(fhe_ctx* ctx, const double* d_slots, uint32_t n_ct, uint32_t level,
                double scale, uint64_t* d_pt, void* stream);
 

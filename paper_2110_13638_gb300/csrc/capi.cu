@@ -602,7 +602,6 @@ int fhe_encode(fhe_ctx* c, const double* d_slots, uint32_t n_ct, uint32_t level,
     if (!d_slots || !d_pt) return fail(FHE_EINVAL, "null buffer");
     if (level < 1 || level > c->L_top) return fail(FHE_ELEVEL, "level out of range");
     if (!(scale > 0.0) || !std::isfinite(scale)) return fail(FHE_EINVAL, "bad scale");
-    if (c->N > kMaxSinglePassN) return fail(FHE_EUNSUPPORTED, "encode supports N <= 16384");
     Arena ar;
     int rc = ws_reserve(c, encode_scratch_bytes(c, n_ct), &ar);
     if (rc) return rc;
@@ -634,7 +633,6 @@ int fhe_encode_encrypt(fhe_ctx* c, const double* d_slots, uint32_t n_ct, double 
     if (n_ct == 0) return FHE_OK;
     if (!d_slots || !d_ct) return fail(FHE_EINVAL, "null buffer");
     if (!(scale > 0.0) || !std::isfinite(scale)) return fail(FHE_EINVAL, "bad scale");
-    if (c->N > kMaxSinglePassN) return fail(FHE_EUNSUPPORTED, "encode supports N <= 16384");
     Arena ar;
     const size_t need = encode_encrypt_scratch_bytes(c, n_ct);
     int rc = ws_reserve(c, need, &ar);
@@ -662,7 +660,6 @@ int fhe_decode(fhe_ctx* c, const int64_t* d_m, uint32_t n_ct, double scale, doub
     if (n_ct == 0) return FHE_OK;
     if (!d_m || !d_slots) return fail(FHE_EINVAL, "null buffer");
     if (!(scale > 0.0) || !std::isfinite(scale)) return fail(FHE_EINVAL, "bad scale");
-    if (c->N > kMaxSinglePassN) return fail(FHE_EUNSUPPORTED, "decode supports N <= 16384");
     k_decode(c, (const i64*)d_m, n_ct, scale, d_slots, (cudaStream_t)stream);
     CUDA_LAST("decode launch");
     return FHE_OK;

@@ -109,36 +109,47 @@ __device__ __forceinline__ i64 fx_round(fx v)
     return neg ? -r : r;
 }
 
-// One block per (ct, half h): the N/2-point inverse DFT of the slots (placed
-// at l(j) = (5^j mod 2N - 1)/4, pre-multiplied by scale / M) is split by its
-// first decimation-in-frequency stage; half h runs the N/4-point DFT of its
-// half in shared memory (real and imaginary parts in separate arrays).
+// A ciphertext's N/2-point inverse DFT (slots placed at l(j) = (5^j mod 2N -
+// 1)/4, pre-multiplied by scale / M) is split by its first a decimation-in-
+// frequency levels into A = 2^a blocks of H = M / A <= 4096 points: block r
+// forms y_r[n] = sum_s x[n + s H] W^((n + s H) r) (W = e^{-2 pi i / M}) and runs
+// the H-point DIF of y_r in shared memory (real and imaginary parts in
+// separate arrays); its outputs are the frequencies k = A p' + r.
 // Output: m_k = round(Re c_k), m_{k+N/2} = round(Im c_k), c_k = zeta^{-k} X_k.
 __global__ void __launch_bounds__(512) k_encode_kernel(const double* __restrict__ slots, const uint32_t* __restrict__ slot_of,
                                                         const ulonglong2* __restrict__ tw, const ulonglong2* __restrict__ twist,
-                                                        double scale_over_M, int N, i64* __restrict__ m)
+                                                        double scale_over_M, int N, int logA, i64* __restrict__ m)
 {
     extern __shared__ ulonglong2 S[];    // [H] real parts, then [H] imaginary parts
-    const int M = N / 2, H = M / 2;
+    const int M = N / 2, A = 1 << logA, H = M >> logA;
     ulonglong2* Sr = S;
     ulonglong2* Si = S + H;
-    const int ct = blockIdx.x >> 1, h = blockIdx.x & 1;
+    const int ct = blockIdx.x >> logA, r = blockIdx.x & (A - 1);
     const double* z = slots + (size_t)ct * M;
     auto put = [&](int i, const cfx& v) {
         Sr[i] = make_ulonglong2(v.re.lo, v.re.hi);
         Si[i] = make_ulonglong2(v.im.lo, v.im.hi);
     };
     auto get = [&](int i) {
-        const ulonglong2 r = Sr[i], q = Si[i];
-        return cfx{{r.x, r.y}, {q.x, q.y}};
+        const ulonglong2 a = Sr[i], b = Si[i];
+        return cfx{{a.x, a.y}, {b.x, b.y}};
     };
-    for (int l = threadIdx.x; l < H; l += blockDim.x) {
-        const fx a = fx_product(z[slot_of[l]], scale_over_M);
-        const fx b = fx_product(z[slot_of[l + H]], scale_over_M);
-        cfx v;
-        if (h == 0) v = {fx_add(a, b), {0ull, 0ull}};
-        else v = fx_mul_root(fx_sub(a, b), __ldg(&tw[2 * l]), __ldg(&tw[2 * l + 1]));   // W^l, W = e^{-2 pi i / M}
-        put(l, v);
+    for (int n = threadIdx.x; n < H; n += blockDim.x) {
+        cfx y = {{0ull, 0ull}, {0ull, 0ull}};
+        for (int s = 0; s < A; ++s) {
+            const int i = n + s * H;
+            const fx x = fx_product(z[slot_of[i]], scale_over_M);
+            if (r == 0) {
+                y.re = fx_add(y.re, x);
+            } else {
+                int e = (int)(((unsigned)i * (unsigned)r) & (unsigned)(M - 1));
+                const bool neg = e >= M / 2;               // W^(M/2) = -1
+                if (neg) e -= M / 2;
+                const cfx t = fx_mul_root(x, __ldg(&tw[2 * e]), __ldg(&tw[2 * e + 1]));
+                y = neg ? cfx_sub(y, t) : cfx_add(y, t);
+            }
+        }
+        put(n, y);
     }
     __syncthreads();
     // H-point DIF, twiddle for offset o at half-size hs: W^{o * M / (2 hs)}
@@ -156,12 +167,20 @@ __global__ void __launch_bounds__(512) k_encode_kernel(const double* __restrict_
     int lg = 0;
     while ((1 << lg) < H) ++lg;
     for (int p = threadIdx.x; p < H; p += blockDim.x) {
-        const int kp = (int)(__brev((unsigned)p) >> (32 - lg));
-        const int k = 2 * kp + h;                       // frequency index in [0, M)
+        const int kp = lg ? (int)(__brev((unsigned)p) >> (32 - lg)) : 0;
+        const int k = (kp << logA) + r;                 // frequency index in [0, M)
         const cfx c = cfx_mul_root(get(p), __ldg(&twist[2 * k]), __ldg(&twist[2 * k + 1]));
         m[(size_t)ct * N + k] = fx_round(c.re);
         m[(size_t)ct * N + k + M] = fx_round(c.im);
     }
+}
+
+// blocks per ciphertext (log2) so that one block holds at most hmax points
+static int split_log(int M, int hmax)
+{
+    int a = 1;
+    while ((M >> a) > hmax) ++a;
+    return a;
 }
 
 struct OpSignedRows {
@@ -184,18 +203,20 @@ size_t encode_scratch_bytes(const fhe_ctx* c, uint32_t n_ct) { return (size_t)n_
 void encode_coefficients(const fhe_ctx* c, const double* slots, uint32_t n_ct, double scale, i64* m, cudaStream_t st)
 {
     const int N = (int)c->N;
-    const size_t smem = (size_t)(N / 4) * 2 * sizeof(ulonglong2);
+    const int logA = split_log(N / 2, 4096);
+    const int H = (N / 2) >> logA;
+    const size_t smem = (size_t)H * 2 * sizeof(ulonglong2);
     static size_t configured = 0;
     if (configured < smem) {
         cudaFuncSetAttribute(k_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         configured = smem;
     }
-    int thr = N / 8;
+    int thr = H / 2;
     thr = thr < 32 ? 32 : (thr > 512 ? 512 : thr);
     {
     LaunchScope ls(c, "encode_fft", st);
-    k_encode_kernel<<<2 * n_ct, thr, smem, st>>>(slots, c->d_slot_of, c->d_enc_tw_q, c->d_enc_twist_q,
-                                                 scale / (double)(N / 2), N, m);
+    k_encode_kernel<<<n_ct << logA, thr, smem, st>>>(slots, c->d_slot_of, c->d_enc_tw_q, c->d_enc_twist_q,
+                                                      scale / (double)(N / 2), N, logA, m);
     }
 }
 
@@ -210,25 +231,43 @@ void k_encode(const fhe_ctx* c, const double* slots, uint32_t n_ct, uint32_t L, 
 }
 
 // ---------------------------------------------------------------- decode
-// z_j = Re Z_{l(j)} / scale, Z = DFT_{N/2}(c_k zeta^k) with e^{+2 pi i / M},
-// c_k = m_k + i m_{k+N/2}; FP64, one block per ciphertext.
+// z_j = Re Z_{l(j)} / scale, Z = DFT_{N/2}(v), v_k = c_k zeta^k with
+// conj(W) = e^{+2 pi i / M}, c_k = m_k + i m_{k+N/2}; FP64.  Split like the
+// encoder: block r of A = 2^a forms y_r[n] = sum_s v[n + s H] conj(W)^((n + s H) r)
+// and runs the H-point DIF (H <= 8192); its outputs are Z_{A p' + r}.
 __global__ void __launch_bounds__(512) k_decode_kernel(const i64* __restrict__ m, const uint32_t* __restrict__ slot_of,
                                                         const double4* __restrict__ tw, const double4* __restrict__ twist,
-                                                        double inv_scale, int N, double* __restrict__ slots)
+                                                        double inv_scale, int N, int logA, double* __restrict__ slots)
 {
-    extern __shared__ double2 B[];       // N/2 complex doubles
-    const int M = N / 2;
-    const int ct = blockIdx.x;
+    extern __shared__ double2 B[];       // H complex doubles
+    const int M = N / 2, A = 1 << logA, H = M >> logA;
+    const int ct = blockIdx.x >> logA, r = blockIdx.x & (A - 1);
     const i64* mc = m + (size_t)ct * N;
-    for (int k = threadIdx.x; k < M; k += blockDim.x) {
-        const double a = (double)mc[k], b = (double)mc[k + M];
-        const double4 t = twist[k];                     // zeta^{-k}: use its conjugate
-        const double wr = t.x, wi = -t.z;
-        B[k] = make_double2(a * wr - b * wi, a * wi + b * wr);
+    for (int n = threadIdx.x; n < H; n += blockDim.x) {
+        double yr = 0.0, yi = 0.0;
+        for (int s = 0; s < A; ++s) {
+            const int k = n + s * H;
+            const double a = (double)mc[k], b = (double)mc[k + M];
+            const double4 t = twist[k];                 // zeta^{-k}: use its conjugate
+            double vr = a * t.x + b * t.z, vi = -a * t.z + b * t.x;
+            if (r != 0) {
+                int e = (int)(((unsigned)k * (unsigned)r) & (unsigned)(M - 1));
+                const bool neg = e >= M / 2;
+                if (neg) e -= M / 2;
+                const double4 w4 = tw[e];
+                const double wr = neg ? -w4.x : w4.x, wi = neg ? w4.z : -w4.z;   // conj(W^e)
+                const double ur = vr * wr - vi * wi, ui = vr * wi + vi * wr;
+                vr = ur;
+                vi = ui;
+            }
+            yr += vr;
+            yi += vi;
+        }
+        B[n] = make_double2(yr, yi);
     }
     __syncthreads();
-    for (int hs = M / 2; hs >= 1; hs >>= 1) {
-        for (int b = threadIdx.x; b < M / 2; b += blockDim.x) {
+    for (int hs = H / 2; hs >= 1; hs >>= 1) {
+        for (int b = threadIdx.x; b < H / 2; b += blockDim.x) {
             const int blk = b / hs, o = b % hs;
             const int i0 = blk * 2 * hs + o, i1 = i0 + hs;
             const double2 x = B[i0], y = B[i1];
@@ -241,10 +280,11 @@ __global__ void __launch_bounds__(512) k_decode_kernel(const i64* __restrict__ m
         __syncthreads();
     }
     int lg = 0;
-    while ((1 << lg) < M) ++lg;
-    for (int l = threadIdx.x; l < M; l += blockDim.x) {
-        const int p = (int)(__brev((unsigned)l) >> (32 - lg));
-        slots[(size_t)ct * M + slot_of[l]] = B[p].x * inv_scale;
+    while ((1 << lg) < H) ++lg;
+    for (int p = threadIdx.x; p < H; p += blockDim.x) {
+        const int tp = lg ? (int)(__brev((unsigned)p) >> (32 - lg)) : 0;
+        const int t = (tp << logA) + r;                 // DFT index in [0, M)
+        slots[(size_t)ct * M + slot_of[t]] = B[p].x * inv_scale;
     }
 }
 
@@ -252,16 +292,20 @@ void k_decode(const fhe_ctx* c, const i64* m, uint32_t n_ct, double scale, doubl
 {
     if (n_ct == 0) return;
     const int N = (int)c->N;
-    const size_t smem = (size_t)(N / 2) * sizeof(double2);
+    int logA = 0;
+    while (((N / 2) >> logA) > 8192) ++logA;
+    const int H = (N / 2) >> logA;
+    const size_t smem = (size_t)H * sizeof(double2);
     static size_t configured = 0;
     if (configured < smem) {
         cudaFuncSetAttribute(k_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         configured = smem;
     }
-    int thr = N / 4;
+    int thr = H / 2;
     thr = thr < 32 ? 32 : (thr > 512 ? 512 : thr);
     LaunchScope ls(c, "decode_fft", st);
-    k_decode_kernel<<<n_ct, thr, smem, st>>>(m, c->d_slot_of, c->d_enc_tw, c->d_enc_twist, 1.0 / scale, N, slots);
+    k_decode_kernel<<<n_ct << logA, thr, smem, st>>>(m, c->d_slot_of, c->d_enc_tw, c->d_enc_twist, 1.0 / scale, N,
+                                                      logA, slots);
 }
 
 

@@ -67,7 +67,9 @@ __device__ __forceinline__ void mac128(u64& lo, u64& hi, u64 x, u64 w)
 // limb product is < 2^42 and accumulates exactly in a 64-bit register with one
 // 32 x 32 + 64 multiply-add: sum x w = S0 + S1 2^21 + S2 2^42 with
 // S0 = sum xL wL, S1 = sum (xL wH + xH wL), S2 = sum xH wH (no carries for
-// fewer than 2^20 terms).
+// fewer than 2^20 terms).  S1 is formed Karatsuba-style as
+// sum (xL + xH)(wL + wH) - S0 - S2 (limb sums < 2^22, products < 2^44), so a
+// term costs three multiply-adds.
 constexpr u64 kLimbMask = (1ull << 21) - 1;
 
 __device__ __forceinline__ u64 limb_combine(u64 s0, u64 s1, u64 s2, const PrimeC& P)
@@ -110,7 +112,7 @@ __global__ void __launch_bounds__(256) k_mac_tiled_kernel(const u64* __restrict_
             for (int u = 0; u < 4; ++u) x[u] = Xj[(size_t)__ldg(&cl[e + u]) * ct_stride];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const uint32_t xl = (uint32_t)(x[u] & kLimbMask), xh = (uint32_t)(x[u] >> 21);
+                const uint32_t xl = (uint32_t)(x[u] & kLimbMask), xh = (uint32_t)(x[u] >> 21), xs = xl + xh;
                 const ulonglong2* we = w2 + (size_t)(e + u) * wstep;
 #pragma unroll
                 for (int o2 = 0; o2 < kMacTile / 2; ++o2) {
@@ -121,8 +123,7 @@ __global__ void __launch_bounds__(256) k_mac_tiled_kernel(const u64* __restrict_
                         const uint32_t wl = (uint32_t)wd, wh = (uint32_t)(wd >> 32);
                         const int o = 2 * o2 + h;
                         s0[o] += (u64)xl * wl;
-                        s1[o] += (u64)xl * wh;
-                        s1[o] += (u64)xh * wl;
+                        s1[o] += (u64)xs * (wl + wh);
                         s2[o] += (u64)xh * wh;
                     }
                 }
@@ -130,7 +131,7 @@ __global__ void __launch_bounds__(256) k_mac_tiled_kernel(const u64* __restrict_
         }
         for (; e < K; ++e) {
             const u64 xv = Xj[(size_t)__ldg(&cl[e]) * ct_stride];
-            const uint32_t xl = (uint32_t)(xv & kLimbMask), xh = (uint32_t)(xv >> 21);
+            const uint32_t xl = (uint32_t)(xv & kLimbMask), xh = (uint32_t)(xv >> 21), xs = xl + xh;
             const ulonglong2* we = w2 + (size_t)e * wstep;
 #pragma unroll
             for (int o2 = 0; o2 < kMacTile / 2; ++o2) {
@@ -141,8 +142,7 @@ __global__ void __launch_bounds__(256) k_mac_tiled_kernel(const u64* __restrict_
                     const uint32_t wl = (uint32_t)wd, wh = (uint32_t)(wd >> 32);
                     const int o = 2 * o2 + h;
                     s0[o] += (u64)xl * wl;
-                    s1[o] += (u64)xl * wh;
-                    s1[o] += (u64)xh * wl;
+                    s1[o] += (u64)xs * (wl + wh);
                     s2[o] += (u64)xh * wh;
                 }
             }
@@ -150,7 +150,8 @@ __global__ void __launch_bounds__(256) k_mac_tiled_kernel(const u64* __restrict_
 #pragma unroll
         for (int o = 0; o < kMacTile; ++o)
             if (o < (int)tl.z)
-                Y[(size_t)rows[blockIdx.x * kMacTile + o] * ct_stride + off] = limb_combine(s0[o], s1[o], s2[o], P);
+                Y[(size_t)rows[blockIdx.x * kMacTile + o] * ct_stride + off] =
+                    limb_combine(s0[o], s1[o] - s0[o] - s2[o], s2[o], P);
         return;
     }
     u64 lo[kMacTile], hi[kMacTile];

@@ -148,6 +148,26 @@ def mini_cnn(n_slots, seed=7, side=8, filters=2, k=3, stride=2, hidden=5, classe
     return g, x
 
 
+def deep_mlp(n_slots, seed=13, n_in=4, hidden=4, n_out=2):
+    """Multiplicative depth 8 (dense, sigmoid fit, dense, sigmoid fit, dense,
+    square), so Alg. parameterise asks for N = 32768 and [60, 40 x 8, 60]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    W0 = rng.normal(0.0, np.sqrt(2.0 / (n_in + hidden)), size=(hidden, n_in))
+    W1 = rng.normal(0.0, np.sqrt(2.0 / (2 * hidden)), size=(hidden, hidden))
+    W2 = rng.normal(0.0, np.sqrt(2.0 / (hidden + n_out)), size=(n_out, hidden))
+    sig = sigmoid_fit()
+    g = chain_graph(n_in, [
+        _linear(*dense_csr(W0), rng.normal(0.0, 0.1, size=hidden)),
+        {"kind": "poly", "coeffs": sig},
+        _linear(*dense_csr(W1), np.zeros(hidden)),
+        {"kind": "poly", "coeffs": sig},
+        _linear(*dense_csr(W2), np.zeros(n_out)),
+        {"kind": "square"},
+    ])
+    x = rng.uniform(-1.0, 1.0, size=(n_in, n_slots))
+    return g, x
+
+
 def branch_graph(n_slots, seed=11, n_in=3, n_mid=4):
     """Two inputs on paths of different depth meeting at an 'add' node (the
     x0 / x1 situation of Fig. fhe_parm_problem: x1 meets two computations,

@@ -105,7 +105,7 @@ def _encode_check(g, o, z, got_res, L):
 
 
 @pytest.mark.parametrize("N,bits,n", [(16, BITS5, 3), (1024, BITS5, 3), (8192, [60, 40, 40, 60], 2),
-                                      (16384, BITS9, 2)])
+                                      (16384, BITS9, 2), (32768, [60, 40, 60], 2), (65536, [60, 40, 60], 1)])
 def test_encode_matches_oracle(N, bits, n):
     g, o = pair(N, bits)
     rng = np.random.default_rng(7)
@@ -119,7 +119,8 @@ def test_encode_matches_oracle(N, bits, n):
 
 
 # ---------------------------------------------------------------- encrypt / decrypt / decode
-@pytest.mark.parametrize("N,bits,n", [(16, BITS5, 2), (1024, BITS5, 3), (16384, BITS9, 2)])
+@pytest.mark.parametrize("N,bits,n", [(16, BITS5, 2), (1024, BITS5, 3), (16384, BITS9, 2), (32768, [60, 40, 60], 2),
+                                      (65536, [60, 40, 60], 1)])
 def test_encrypt_decrypt_decode(N, bits, n):
     g, o = pair(N, bits)
     rng = np.random.default_rng(11)
@@ -279,6 +280,22 @@ def test_graph_cfg0_full_size_bit_exact():
     assert err < 1e-4
 
 
+def test_graph_depth8_ring32768_bit_exact():
+    """Depth 8: Alg. autoHE / parameterise choose N = 32768, [60, 40 x 8, 60];
+    every stage (encode, encrypt, layers, relinearise, rescale, decode) runs on
+    the two-pass transform."""
+    graph, _ = W.deep_mlp(n_slots=4)
+    gof, gcost = fhe.autohe(graph)
+    assert max(gcost) == 8
+    N, bits = fhe.parameterise(max(gcost), 40, 1.5)
+    assert N == 32768 and bits == [60] + [40] * 8 + [60]
+    g, o = pair(N, bits)
+    assert g.ntt_variant in (2, 3)
+    graph, x = W.deep_mlp(n_slots=N // 2)
+    err = _graph_parity(g, o, graph, [x], [0])
+    assert err < 1e-4
+
+
 # ---------------------------------------------------------------- uneven levels, one launch per step
 def test_mul_relin_rescale_levels_matches_per_batch_and_oracle():
     g, o = pair(1024, BITS9)
@@ -353,11 +370,9 @@ def test_large_ring_transform_tensor_relin(N):
     out = g.empty_ct(1, L)
     g.relinearise(t3, L, out)
     assert np.array_equal(download(g, out, L)[0], o.relinearise(want).c)
-    with pytest.raises(fhe.FheError):
-        g.encode(torch.zeros((1, N // 2), dtype=torch.float64, device="cuda"), L, g.delta, g.empty_pt(1, L))
 
 
-@pytest.mark.parametrize("N,bits,n", [(1024, BITS5, 3), (16384, BITS9, 2)])
+@pytest.mark.parametrize("N,bits,n", [(1024, BITS5, 3), (16384, BITS9, 2), (32768, [60, 40, 40, 60], 2)])
 def test_encode_encrypt_fused_equals_two_calls(N, bits, n):
     g, o = pair(N, bits)
     z = torch.tensor(np.random.default_rng(N).uniform(-2, 2, size=(n, N // 2)), device="cuda")
