@@ -115,6 +115,13 @@ int fhe_parameterise(uint32_t cost, uint32_t log_scale, double special_mult,
 int fhe_autohe(const fhe_graph_desc* g, uint32_t* group_of, uint32_t group_of_cap,
                uint32_t* group_cost, uint32_t group_cost_cap, uint32_t* n_groups);
 
+/* Alg. autoHE then Alg. parameterise on a library graph: the ring degree and
+ * coefficient-modulus bit list one parameter set needs to evaluate the whole
+ * graph (the largest cost over its parameter groups; a graph whose groups
+ * should get separate parameter sets uses fhe_autohe instead).  Host only. */
+int fhe_autoparam(const fhe_graph* g, uint32_t log_scale, double special_mult,
+                  uint32_t* N, uint32_t* bits, uint32_t bits_cap, uint32_t* n_bits);
+
 /* Prime chain for (N, bits): q > 2^b, q = 1 mod 2N, increasing per size.
  * out receives n_bits primes (last = special prime).  Host only. */
 int fhe_prime_chain(uint32_t N, const uint32_t* bits, uint32_t n_bits, uint64_t* out);
@@ -280,6 +287,35 @@ int fhe_graph_outputs(fhe_ctx* ctx, const fhe_graph* g, uint32_t* n_out_cts, uin
  * with one fhe_ct_meta each. */
 int fhe_eval_graph(fhe_ctx* ctx, const fhe_graph* g, const uint64_t* const* d_in, uint32_t n_inputs,
                    uint64_t* d_out, fhe_ct_meta* out_meta, uint32_t out_cap, void* stream);
+
+/* One encrypted-inference request of a served batch (Sec. 2.3 client/server
+ * model; the batching itself has no counterpart in the paper).  x holds the
+ * request's samples, one row per ciphertext of the graph's INPUT node
+ * ([n_in] rows of x_stride doubles, the first n_samples used); y receives the
+ * decoded outputs ([n_out] rows of y_stride doubles).  x and y may be device
+ * or host memory (host memory should be pinned for the call to stay
+ * asynchronous); the caller owns both. */
+typedef struct {
+    const double* x;
+    uint32_t n_samples;
+    uint32_t x_stride;
+    double* y;
+    uint32_t y_stride;
+} fhe_request;
+
+/* Serve a batch of requests through a graph with exactly one INPUT node:
+ * request k occupies the slot range after requests 0..k-1 (at most N/2
+ * samples in total, else FHE_EINVAL; unused slots hold 0), then, all on
+ * `stream`: the rows are gathered into the slots, encoded and encrypted at
+ * the top level with scale 2^log_scale and ct ids first_ct_id + i, the graph
+ * is evaluated, the outputs decrypted and decoded, and each request's columns
+ * copied to its y.  Buffers come from a context-owned batch area (grown on
+ * demand, separate from the workspace), so forks of one parameter set can
+ * serve concurrent batches on their own streams.  Results are those of
+ * fhe_encode_encrypt + fhe_eval_graph + fhe_decrypt + fhe_decode on the packed
+ * slots. */
+int fhe_eval_batch(fhe_ctx* ctx, const fhe_graph* g, const fhe_request* reqs, uint32_t n_reqs,
+                   uint64_t first_ct_id, void* stream);
 
 /* ---- measurement (no counterpart in the paper) ----------------------------
  * fhe_profile_begin: from now on, every launch of the kernel family `family`

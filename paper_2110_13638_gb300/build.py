@@ -17,7 +17,7 @@ SO = os.path.join(BUILD, "libfhe.so")
 ROOT = os.path.dirname(HERE)
 
 SOURCES = ["k_common.cu", "k_rescale.cu", "k_relin.cu", "k_groups.cu", "k_mac.cu", "k_keys.cu", "k_encode.cu",
-           "capi.cu", "graph.cu", "noalloc.cu", "host_math.cpp"]
+           "capi.cu", "graph.cu", "batch.cu", "noalloc.cu", "host_math.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

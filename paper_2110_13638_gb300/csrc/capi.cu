@@ -206,10 +206,38 @@ int fhe_autohe(const fhe_graph_desc* g, uint32_t* group_of, uint32_t group_of_ca
     return FHE_OK;
 }
 
+int fhe_autoparam(const fhe_graph* g, uint32_t log_scale, double special_mult, uint32_t* N, uint32_t* bits,
+                  uint32_t bits_cap, uint32_t* n_bits)
+{
+    if (!g) return fail(FHE_EINVAL, "null graph");
+    std::vector<fhe_node_desc> nodes(g->nodes.size());
+    uint32_t n_in = 0;
+    for (size_t i = 0; i < g->nodes.size(); ++i) {
+        std::memset(&nodes[i], 0, sizeof(fhe_node_desc));
+        nodes[i].kind = g->nodes[i].kind;
+        n_in += g->nodes[i].kind == FHE_NODE_INPUT;
+    }
+    fhe_graph_desc d;
+    d.n_nodes = (uint32_t)nodes.size();
+    d.nodes = nodes.data();
+    d.n_edges = (uint32_t)g->esrc.size();
+    d.edge_src = g->esrc.data();
+    d.edge_dst = g->edst.data();
+    std::vector<uint32_t> gcost(std::max<uint32_t>(1u, n_in));
+    uint32_t ng = 0;
+    int rc = fhe_autohe(&d, nullptr, 0, gcost.data(), (uint32_t)gcost.size(), &ng);
+    if (rc) return rc;
+    if (ng == 0) return fail(FHE_EINVAL, "graph without INPUT nodes");
+    uint32_t cost = 0;
+    for (uint32_t k = 0; k < ng; ++k) cost = std::max(cost, gcost[k]);
+    return fhe_parameterise(cost, log_scale, special_mult, N, bits, bits_cap, n_bits);
+}
+
 // ---------------------------------------------------------------- context
 static void free_ctx(fhe_ctx* c)
 {
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    cudaFree(c->bb);
     if (c->parent) {            // shared tables and keys belong to the parent
         cudaFree(c->ws);
         cudaFree(c->d_ntt2);

@@ -50,6 +50,8 @@ struct fhe_ctx {
     // call workspace (grows on demand)
     void* ws = nullptr;
     size_t ws_bytes = 0;
+    void* bb = nullptr;            // fhe_eval_batch's slots / ciphertext area (own per fork)
+    size_t bb_bytes = 0;
 
     // measurement hook: CUDA events around every launch of one kernel family
     mutable std::string prof_family;

@@ -54,6 +54,11 @@ class NodeDesc(ctypes.Structure):
                 ("coeffs", ctypes.c_double * 4)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("n_samples", ctypes.c_uint32), ("x_stride", ctypes.c_uint32),
+                ("y", ctypes.c_void_p), ("y_stride", ctypes.c_uint32)]
+
+
 class GraphDesc(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_uint32), ("nodes", ctypes.POINTER(NodeDesc)),
                 ("n_edges", ctypes.c_uint32), ("edge_src", ctypes.POINTER(ctypes.c_uint32)),
@@ -68,6 +73,7 @@ _I = ctypes.c_int
 SIGNATURES = {
     "fhe_parameterise": [_U32, _U32, ctypes.c_double, _P, _P, _U32, _P],
     "fhe_autohe": [_P, _P, _U32, _P, _U32, _P],
+    "fhe_autoparam": [_P, _U32, ctypes.c_double, _P, _P, _U32, _P],
     "fhe_prime_chain": [_U32, _P, _U32, _P],
     "fhe_gauss_table": [_P],
     "fhe_ctx_create": [_U32, _P, _U32, _U32, _P],
@@ -96,6 +102,7 @@ SIGNATURES = {
     "fhe_graph_destroy": [_P],
     "fhe_graph_outputs": [_P, _P, _P, _P],
     "fhe_eval_graph": [_P, _P, _P, _U32, _P, _P, _U32, _P],
+    "fhe_eval_batch": [_P, _P, _P, _U32, _U64, _P],
     "fhe_profile_begin": [_P, ctypes.c_char_p, _U32],
     "fhe_profile_end": [_P, _P, _P, _P],
     "fhe_profile_families": [],
@@ -399,6 +406,32 @@ class Graph:
         meta = (CtMeta * max(1, cap))()
         _check(lib().fhe_eval_graph(ctx.h, self.h, arr, len(inputs), _ptr(out), meta, cap, _stream(stream)))
         return [(meta[i].level, meta[i].scale) for i in range(cap)]
+
+    def autoparam(self, log_scale=40, special_mult=1.5):
+        """(N, coefficient-modulus bits) of one parameter set for the whole graph."""
+        N = ctypes.c_uint32()
+        bits = (ctypes.c_uint32 * 64)()
+        nb = ctypes.c_uint32()
+        _check(lib().fhe_autoparam(self.h, log_scale, special_mult, ctypes.byref(N), bits, 64, ctypes.byref(nb)))
+        return N.value, [bits[i] for i in range(nb.value)]
+
+    def eval_batch(self, ctx, requests, first_ct_id, stream=None):
+        """requests: list of (x, y) float64 tensors (device or pinned host),
+        x [n_in][>= n] and y [n_out][>= n] with unit column stride, or
+        (x, y, n) to use only the first n columns.  Packs them into the slots,
+        encrypts, evaluates, decrypts and decodes in one call."""
+        arr = (Request * max(1, len(requests)))()
+        for k, rq in enumerate(requests):
+            x, y = rq[0], rq[1]
+            n = rq[2] if len(rq) > 2 else x.shape[1]
+            assert x.dtype == y.dtype == torch_float64() and x.stride(1) == 1 and y.stride(1) == 1
+            arr[k] = Request(x.data_ptr(), n, x.stride(0), y.data_ptr(), y.stride(0))
+        _check(lib().fhe_eval_batch(ctx.h, self.h, arr, len(requests), first_ct_id, _stream(stream)))
+
+
+def torch_float64():
+    import torch
+    return torch.float64
 
 
 def raw_u64(t):

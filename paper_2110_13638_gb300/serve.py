@@ -11,9 +11,10 @@ device footprint stays under the admission cap.
 Scheduling: waiting requests of a network are packed into the free slot
 ranges of one batch (batch-in-slots: a request of n samples takes n
 consecutive slots of the shared ciphertexts; one that does not fit a batch
-is split across batches and completes with its last part).  A batch runs
-encode -> encrypt -> graph -> decrypt -> decode on its slot's stream; batches
-on different slots overlap on the device.  New requests are admitted as
+is split across batches and completes with its last part).  A batch is one
+native call (fhe_eval_batch: gather -> encode+encrypt -> graph -> decrypt ->
+decode -> scatter) on its slot's stream; batches on different slots overlap
+on the device.  New requests are admitted as
 slots free up, without waiting for other batches (continuous batching).
 Latency = completion time - arrival time.
 
@@ -52,34 +53,25 @@ class Slot:
         self.G = fhe.Graph(net.graph)
         n_out, L_out = self.G.outputs(self.ctx)
         self.n_out, self.L_out = n_out, L_out
-        N, cap = self.ctx.N, net.capacity
-        dev = torch.device("cuda")
-        self.slots_dev = torch.zeros((net.n_in, cap), dtype=torch.float64, device=dev)
+        cap = net.capacity
         self.host_in = torch.zeros((net.n_in, cap), dtype=torch.float64).pin_memory()
         self.host_out = torch.zeros((n_out, cap), dtype=torch.float64).pin_memory()
-        self.ct = self.ctx.empty_ct(net.n_in, self.ctx.L_top)
-        self.out = self.ctx.empty_ct(n_out, L_out)
-        self.m = torch.empty((n_out, N), dtype=torch.int64, device=dev)
-        self.z = torch.empty((n_out, N // 2), dtype=torch.float64, device=dev)
         self.event = torch.cuda.Event()
         self.batch = None
-        self.ct_id = 0
 
     def launch(self, batch, torch, ct_base):
-        """batch: list of (request, part offset in the request, slot offset, n)."""
+        """batch: list of (request, part offset in the request, slot offset, n),
+        slot offsets consecutive from 0.  One fhe_eval_batch call: each part's
+        columns go from pinned staging to the device and its outputs come back
+        to pinned staging, all on this slot's stream."""
         hin = self.host_in.numpy()
-        hin[:] = 0.0
+        reqs = []
         for req, roff, soff, n in batch:
             hin[:, soff:soff + n] = req.x[:, roff:roff + n]
+            reqs.append((self.host_in[:, soff:], self.host_out[:, soff:], n))
         self.batch = batch
-        with torch.cuda.stream(self.stream):
-            self.slots_dev.copy_(self.host_in, non_blocking=True)
-            self.ctx.encode_encrypt(self.slots_dev, self.ctx.delta, ct_base, self.ct)
-            meta = self.G.eval(self.ctx, [self.ct], self.out)
-            self.ctx.decrypt(self.out, self.L_out, self.m)
-            self.ctx.decode(self.m, meta[0][1], self.z)
-            self.host_out.copy_(self.z, non_blocking=True)
-            self.event.record(self.stream)
+        self.G.eval_batch(self.ctx, reqs, ct_base, stream=self.stream)
+        self.event.record(self.stream)
 
     def done(self):
         return self.batch is not None and self.event.query()
@@ -123,8 +115,10 @@ class Server:
         self.ct_counter = 1 << 40
 
     def _warm(self, s):
-        """one batch so the slot's workspace and graph constants exist"""
-        s.launch([], self.torch, 0)
+        """one full batch so the slot's workspace, batch area and graph
+        constants exist before it is counted against the cap"""
+        dummy = Request(-1, s.net, 0.0, s.net.capacity, np.zeros((s.net.n_in, s.net.capacity)))
+        s.launch([(dummy, 0, 0, s.net.capacity)], self.torch, 0)
         s.stream.synchronize()
         s.batch = None
 

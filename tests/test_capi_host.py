@@ -70,6 +70,28 @@ def test_autohe_branches_and_disjoint():
     assert fhe.autohe(g) == ([0, 1], [2, 7])
 
 
+@pytest.mark.parametrize("builder", [W.cfg0, W.cfg1, W.cfg2, W.deep_mlp, W.branch_graph])
+def test_autoparam_matches_oracle(builder):
+    g, _ = builder(n_slots=4)
+    _, o_cost, _ = params.autohe(g, W.input_nodes(g))
+    G = fhe.Graph(g)
+    p = params.parameterise(max(o_cost), 40, 1.5)
+    assert G.autoparam(40, 1.5) == (p["poly_modulus_degree"], p["coeff_modulus"])
+    G.close()
+
+
+def test_autoparam_takes_the_largest_group():
+    g0, _ = W.cfg0(n_slots=4)
+    g2, _ = W.cfg2(n_slots=4)
+    off = len(g0["nodes"])
+    g = {"nodes": g0["nodes"] + g2["nodes"],
+         "edges": g0["edges"] + [(a + off, b + off) for a, b in g2["edges"]]}
+    G = fhe.Graph(g)
+    p = params.parameterise(7, 40, 1.5)
+    assert G.autoparam() == (p["poly_modulus_degree"], p["coeff_modulus"])
+    G.close()
+
+
 def test_host_errors_are_reported():
     with pytest.raises(fhe.FheError) as e:
         fhe.prime_chain(1000, [60, 40])

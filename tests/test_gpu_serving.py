@@ -57,3 +57,54 @@ def test_results_alone_equal_results_in_the_mix():
         ref = ckks.forward_fp64(r.net.graph, W.input_nodes(r.net.graph), [r.x])
         (node, want), = ref.items()
         assert np.max(np.abs(r.y - want)) < 1e-4, r.rid
+
+
+def test_eval_batch_equals_the_separate_calls():
+    """fhe_eval_batch (gather, encode+encrypt, graph, decrypt, decode,
+    scatter in one call) gives exactly what the separate entry points give on
+    the packed slots; host (pinned) request buffers give the same."""
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    N = 1024
+    c = fhe.Context(N, [60] + [40] * 7 + [60], 40)
+    c.keygen(0)
+    graph, x = W.mini_cnn(n_slots=N // 2)
+    G = fhe.Graph(graph)
+    n_out, L_out = G.outputs(c)
+    sizes, offs = [100, 7, 300], [0, 100, 107]
+    xs = [torch.tensor(x[:, o:o + n], device="cuda") for n, o in zip(sizes, offs)]
+    ys = [torch.full((n_out, n), -7.0, dtype=torch.float64, device="cuda") for n in sizes]
+    G.eval_batch(c, list(zip(xs, ys)), 500)
+    # the same steps one call at a time
+    slots = torch.zeros((x.shape[0], N // 2), dtype=torch.float64, device="cuda")
+    slots[:, :407] = torch.tensor(x[:, :407], device="cuda")
+    ct = c.empty_ct(x.shape[0], c.L_top)
+    c.encode_encrypt(slots, c.delta, 500, ct)
+    out = c.empty_ct(n_out, L_out)
+    meta = G.eval(c, [ct], out)
+    m = torch.empty((n_out, N), dtype=torch.int64, device="cuda")
+    c.decrypt(out, L_out, m)
+    z = torch.empty((n_out, N // 2), dtype=torch.float64, device="cuda")
+    c.decode(m, meta[0][1], z)
+    torch.cuda.synchronize()
+    for y, n, o in zip(ys, sizes, offs):
+        assert torch.equal(y, z[:, o:o + n])
+    ref = ckks.forward_fp64(graph, W.input_nodes(graph), [x[:, :407]])
+    (node, want), = ref.items()
+    got = torch.cat(ys, dim=1).cpu().numpy()
+    assert np.max(np.abs(got - want)) < 1e-4
+    # pinned host buffers, wider strides (only the first n columns used)
+    hx = [torch.zeros((x.shape[0], n + 5), dtype=torch.float64).pin_memory() for n in sizes]
+    hy = [torch.zeros((n_out, n + 3), dtype=torch.float64).pin_memory() for n in sizes]
+    for h, n, o in zip(hx, sizes, offs):
+        h[:, :n] = torch.tensor(x[:, o:o + n])
+    G.eval_batch(c, [(a, b, n) for a, b, n in zip(hx, hy, sizes)], 500)
+    torch.cuda.synchronize()
+    for h, y, n in zip(hy, ys, sizes):
+        assert torch.equal(h[:, :n], y.cpu())
+    # more samples than slots
+    big = torch.zeros((x.shape[0], N // 2 + 1), dtype=torch.float64, device="cuda")
+    with pytest.raises(fhe.FheError):
+        G.eval_batch(c, [(big, torch.zeros((n_out, N // 2 + 1), dtype=torch.float64, device="cuda"))], 0)
+    G.close()
+    c.close()
