@@ -310,6 +310,45 @@ class Context:
         """x^2 = rescale(relinearise(x (x) x)), one level."""
         return self.rescale(self.relinearise(self.tensor(x, x)))
 
+    def affine(self, x, a):
+        """a0 + a1 x in one level, like a one-term linear block:
+            y = rescale(x * llround(a1 * q)) + llround(a0 * scale(y)),  q = q_{L-1}"""
+        L = x.level
+        assert L >= 2, "an affine activation needs one level"
+        q = float(self.q[L - 1])
+        y = self.rescale(self.mul_const(x, llround(float(a[1]) * q), q))
+        return self.add_const(y, llround(float(a[0]) * y.scale))
+
+    def poly2(self, x, a):
+        """a0 + a1 x + a2 x^2 in two levels (Eq. relu_approximate has this
+        form); the degree-3 schedule without its cubic term:
+            x2 = rescale(relin(x (x) x))                     scale s2 = s*s/q
+            T  = x2 * llround(a2 * s_2) + drop(x) * llround(a1 * q'),  s_2 = s*q'/s2
+            y  = rescale(T) + llround(a0 * scale(y))"""
+        L = x.level
+        assert L >= 3, "a degree-2 activation needs two levels"
+        q = float(self.q[L - 1])
+        qp = float(self.q[L - 2])
+        s = x.scale
+        s2 = (s * s) / q
+        x2 = self.rescale(self.relinearise(self.tensor(x, x)))
+        sg2 = (s * qp) / s2
+        t2 = self.mul_const(x2, llround(float(a[2]) * sg2), sg2)
+        t3 = self.mul_const(self.mod_drop(x, L - 1), llround(float(a[1]) * qp), qp)
+        y = self.rescale(self.add(t2, t3))
+        return self.add_const(y, llround(float(a[0]) * y.scale))
+
+    def poly(self, x, a):
+        """Polynomial activation of degree len(a) - 1 (1, 2 or 3)."""
+        d = len(a) - 1
+        if d == 1:
+            return self.affine(x, a)
+        if d == 2:
+            return self.poly2(x, a)
+        if d == 3:
+            return self.poly3(x, a)
+        raise ValueError("polynomial degree %d (1..3 supported)" % d)
+
     def poly3(self, x, a):
         """a0 + a1 x + a2 x^2 + a3 x^3 in two levels (Eq. sigmoid_approximate
         has this form).  With q = q_{L-1}, q' = q_{L-2} and s the scale of x:
@@ -421,7 +460,10 @@ def eval_graph(ctx, graph, inputs, signals):
         if k == "linear":
             return ctx.linear(s, csr_rows(node), node["bias"])
         if k == "poly":
-            return [ctx.poly3(x, node["coeffs"]) for x in s]
+            return [ctx.poly(x, node["coeffs"]) for x in s]
+        if k == "relu":
+            a = relu_coeffs(node["q"])
+            return [ctx.poly(x, a) for x in s]
         if k == "square":
             return [ctx.square(x) for x in s]
         if k == "add":
@@ -429,6 +471,13 @@ def eval_graph(ctx, graph, inputs, signals):
         raise ValueError(k)
 
     return fire(graph, inputs, signals, apply_fn, lambda sigs: _stack_cts(ctx, sigs, None))
+
+
+def relu_coeffs(q):
+    """Eq. relu_approximate: R(x) ~ 4/(3 pi q) x^2 + x/2 + q/(3 pi) on [-q, q]
+    (q: the approximation range), as [a0, a1, a2] in FP64."""
+    q = float(q)
+    return [q / (3 * math.pi), 0.5, 4 / (3 * math.pi * q)]
 
 
 def csr_rows(node):
@@ -460,9 +509,14 @@ def forward_fp64(graph, inputs, signals):
                     out[o] += float(w) * s[i]
                 out[o] += float(node["bias"][o])
             return out
-        if k == "poly":
-            a = node["coeffs"]
-            return a[0] + a[1] * s + a[2] * s * s + a[3] * s * s * s
+        if k in ("poly", "relu"):
+            a = node["coeffs"] if k == "poly" else relu_coeffs(node["q"])
+            out = np.zeros_like(s) + a[0]
+            p = np.ones_like(s)
+            for ak in a[1:]:
+                p = p * s
+                out = out + ak * p
+            return out
         if k == "square":
             return s * s
         raise ValueError(k)

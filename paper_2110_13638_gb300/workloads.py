@@ -148,6 +148,25 @@ def mini_cnn(n_slots, seed=7, side=8, filters=2, k=3, stride=2, hidden=5, classe
     return g, x
 
 
+def cnn_relu(n_slots=8192, relu_q=4.0, **kw):
+    """The CNN with the paper's ReLU approximation (Eq. relu_approximate,
+    range q) as the activation after the convolution (Sec. 3.2 pairs the
+    cross-correlation with ReLU) and the sigmoid fit after the dense layer."""
+    g, x = cfg1(n_slots=n_slots, **kw)
+    g["nodes"][2] = {"kind": "relu", "q": float(relu_q)}
+    return g, x
+
+
+def mini_cnn_relu(n_slots, seed=17, relu_q=3.0):
+    """Small network with the three polynomial degrees: conv -> ReLU
+    approximation (degree 2) -> dense -> linear sigmoid 0.5 + 0.197 x
+    (degree 1, the linear part of Eq. sigmoid_approximate) -> dense."""
+    g, x = mini_cnn(n_slots, seed=seed)
+    g["nodes"][2] = {"kind": "relu", "q": float(relu_q)}
+    g["nodes"][4] = {"kind": "poly", "coeffs": [0.5, 0.197]}
+    return g, x
+
+
 def deep_mlp(n_slots, seed=13, n_in=4, hidden=4, n_out=2):
     """Multiplicative depth 8 (dense, sigmoid fit, dense, sigmoid fit, dense,
     square), so Alg. parameterise asks for N = 32768 and [60, 40 x 8, 60]."""

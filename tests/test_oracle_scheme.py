@@ -233,6 +233,56 @@ def test_square_and_poly3_blocks(ctx64):
     assert np.max(np.abs(ctx.decode(ctx.decrypt(y), y.scale) - ref)) < 1e-6
 
 
+def test_affine_and_poly2_blocks(ctx64):
+    ctx = ctx64
+    N = ctx.N
+    z = np.random.default_rng(9).uniform(-3, 3, N // 2)
+    ct = ctx.encrypt(ctx.encode(z), 6)
+    y1 = ctx.poly(ct, [0.5, 0.197])
+    assert y1.level == ctx.L_top - 1 and y1.scale == ctx.delta
+    assert np.max(np.abs(ctx.decode(ctx.decrypt(y1), y1.scale) - (0.5 + 0.197 * z))) < 1e-6
+    a = [0.3, 0.5, 0.11]
+    y2 = ctx.poly(ct, a)
+    assert y2.level == ctx.L_top - 2
+    assert abs(y2.scale / ctx.delta - 1) < 1e-9
+    ref = a[0] + a[1] * z + a[2] * z * z
+    assert np.max(np.abs(ctx.decode(ctx.decrypt(y2), y2.scale) - ref)) < 1e-6
+    with pytest.raises(ValueError):
+        ctx.poly(ct, [1.0, 2.0, 3.0, 4.0, 5.0])
+
+
+@pytest.mark.parametrize("q", [1.0, 3.0, 4.0, 10.0])
+def test_relu_approximation_is_the_degree2_chebyshev_truncation(q):
+    """Eq. relu_approximate equals the first three terms of the Chebyshev
+    series of max(0, x) on [-q, q] (Gauss-Chebyshev quadrature), in the power
+    basis; at x = +-q it is off max(0, x) by 5q/(3 pi) - q/2 (about 0.031 q)."""
+    n = 200000
+    t = np.cos(np.pi * (np.arange(n) + 0.5) / n)
+    f = np.maximum(0.0, q * t)
+    c = [(2.0 / n) * np.sum(f * np.cos(k * np.arccos(t))) for k in range(3)]
+    # c0/2 + c1 T1(x/q) + c2 T2(x/q), T2(u) = 2u^2 - 1
+    a0 = c[0] / 2 - c[2]
+    a1 = c[1] / q
+    a2 = 2 * c[2] / (q * q)
+    got = ckks.relu_coeffs(q)
+    assert np.allclose(got, [a0, a1, a2], rtol=1e-6, atol=1e-9)
+    r = lambda x: got[0] + got[1] * x + got[2] * x * x
+    assert abs(r(0.0) - q / (3 * np.pi)) < 1e-12
+    assert abs(r(q) - q) < q * 0.05 and abs(r(-q)) < q * 0.05
+
+
+def test_node_costs_of_activations():
+    from oracle import params
+    assert params.node_cost({"kind": "poly", "coeffs": [0.5, 0.197]}) == 1
+    assert params.node_cost({"kind": "poly", "coeffs": [0.1, 0.2, 0.3]}) == 2
+    assert params.node_cost({"kind": "poly", "coeffs": [0.1, 0.2, 0.3, 0.4]}) == 2
+    assert params.node_cost({"kind": "relu", "q": 3.0}) == 2
+    g, _ = W.mini_cnn_relu(8)
+    assert ckks.graph_depth(g, W.input_nodes(g)) == 6
+    g, _ = W.cnn_relu(8)
+    assert ckks.graph_depth(g, W.input_nodes(g)) == 7
+
+
 def test_sigmoid_fit_reproduces_printed_coefficients():
     got = W.sigmoid_fit()
     want = golden_io.sigmoid_coeffs()
@@ -253,6 +303,19 @@ def test_graph_eval_mini_cnn_matches_fp64():
     ref = ckks.forward_fp64(g, W.input_nodes(g), [x])
     (o, ys), = out.items()
     assert len(ys) == ref[o].shape[0] == 3
+    for y, r in zip(ys, ref[o]):
+        assert y.level == 1
+        assert np.max(np.abs(ctx.decode(ctx.decrypt(y), y.scale) - r)) < 1e-4
+
+
+def test_graph_eval_relu_and_affine_match_fp64():
+    g, x = W.mini_cnn_relu(n_slots=32)
+    ctx = ckks.Context(64, [60] + [40] * 6 + [60])
+    ctx.keygen(0)
+    cts = [ctx.encrypt(ctx.encode(v), i) for i, v in enumerate(x)]
+    out = ckks.eval_graph(ctx, g, W.input_nodes(g), [cts])
+    ref = ckks.forward_fp64(g, W.input_nodes(g), [x])
+    (o, ys), = out.items()
     for y, r in zip(ys, ref[o]):
         assert y.level == 1
         assert np.max(np.abs(ctx.decode(ctx.decrypt(y), y.scale) - r)) < 1e-4
