@@ -20,7 +20,7 @@ def node_cost(node):
     if k in ("linear", "square"):
         return 1
     if k == "poly":
-        return 1 if len(node["coeffs"]) == 2 else 2      # affine: one rescale
+        return 1 if len(node.get("coeffs", (0, 0, 0, 0))) == 2 else 2   # affine: one rescale
     if k == "relu":
         return 2                                         # degree 2 (Eq. relu_approximate)
     return 0
