@@ -34,6 +34,15 @@ def _env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+DATA = {
+    "cnn": "synthetic (seeded U[0,1] 28x28 images, He-normal weights; Fashion-MNIST not available)",
+    "cnn_relu": "synthetic (seeded U[0,1] 28x28 images, He-normal weights; Fashion-MNIST not available)",
+    "mlp": "synthetic (seeded lognormal lags + Gaussian weather, Xavier weights; strawberry data not available)",
+    "dense_square": "synthetic (seeded U[-1,1] inputs, N(0,0.5) weights)",
+    "deep": "synthetic (seeded U[-1,1] inputs, Glorot weights)",
+}
+
+
 def workload(name):
     from paper_2110_13638_gb300 import workloads as W
     if name == "cnn":
@@ -45,6 +54,13 @@ def workload(name):
     if name == "dense_square":
         g, x = W.cfg0()
         return g, x, "dense 8 -> 4 then x^2"
+    if name == "cnn_relu":
+        g, x = W.cnn_relu()
+        return g, x, ("encrypted CNN 28x28x1, conv5x5x5/2 -> ReLU approx (Eq. relu_approximate, q=4) -> 720x100 "
+                      "-> sigmoid3 -> 100x10")
+    if name == "deep":
+        g, x = W.deep_mlp(n_slots=16384, n_in=64, hidden=64, n_out=8)
+        return g, x, "depth-8 MLP 64 -> 64 -> sigmoid3 -> 64 -> sigmoid3 -> 8 -> x^2 (N=32768, [60,40x8,60])"
     raise SystemExit("unknown workload " + name)
 
 
@@ -231,13 +247,13 @@ def run_ours(args):
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dev_ms / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-        "data": "synthetic (seeded U[0,1] 28x28 images, He-normal weights; Fashion-MNIST not available)",
+        "data": DATA.get(args.workload, "synthetic"),
         "config": {"workload": desc, "N": N, "coeff_modulus_bits": bits, "log_scale": 40,
                    "samples_per_request": samples, "input_ciphertexts": n_in, "output_ciphertexts": n_out,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "ntt_schedule": "%d: %s" % (ctx.ntt_variant, fhe.NTT_SCHEDULES[ctx.ntt_variant]),
                    "ntt_schedule_keyswitch": "%d: %s" % (ctx.ntt_variant_ks, fhe.NTT_SCHEDULES[ctx.ntt_variant_ks]),
-                   "l2": "inputs larger than L2 (1.6 GB of ciphertexts per step)"},
+                   "l2": "inputs larger than L2 (%.2f GB of input ciphertexts per step)" % (n_in * 2 * ctx.L_top * N * 8 / 1e9)},
         "e2e": {"value": round(e2e, 2), "unit": UNIT, "h2d_bytes_per_step": int(slots.numel() * 8),
                 "d2h_bytes_per_step": int(z.numel() * 8)},
         "gpu_launches": int(launches),
@@ -302,13 +318,14 @@ def oracle_sample(name):
             parts.append("linear(%d terms, L=%d) %.3fs x %d" % (len(idx), L, t, node["n_out"]))
             n_prev = node["n_out"]
             L -= 1
-        elif kind == "poly":
+        elif kind in ("poly", "relu"):
+            a = node["coeffs"] if kind == "poly" else ckks.relu_coeffs(node["q"])
             t0 = time.perf_counter()
-            o.poly3(rand_ct(L, o.delta), node["coeffs"])
+            o.poly(rand_ct(L, o.delta), a)
             t = time.perf_counter() - t0
             total += t * n_prev
-            parts.append("poly3(L=%d) %.3fs x %d" % (L, t, n_prev))
-            L -= 2
+            parts.append("poly%d(L=%d) %.3fs x %d" % (len(a) - 1, L, t, n_prev))
+            L -= 1 if len(a) == 2 else 2
         elif kind == "square":
             t0 = time.perf_counter()
             o.square(rand_ct(L, o.delta))
@@ -568,7 +585,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cnn", choices=["cnn", "mlp", "dense_square", "batch", "ntt_sweep", "serve"])
+    ap.add_argument("--workload", default="cnn", choices=["cnn", "mlp", "dense_square", "cnn_relu", "deep", "batch", "ntt_sweep", "serve"])
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--batch-cts", type=int, default=4096)
     ap.add_argument("--profile-family", default=DOMINANT)

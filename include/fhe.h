@@ -77,10 +77,13 @@ typedef struct {
 enum {
     FHE_NODE_INPUT = 0,  /* source: encrypted input signal (type of concern) */
     FHE_NODE_LINEAR = 1, /* y_o = sum_e w_e x_{col_e} + b_o (dense or conv), cost 1 */
-    FHE_NODE_POLY = 2,   /* a0 + a1 x + a2 x^2 + a3 x^3 per ciphertext, cost 2 */
+    FHE_NODE_POLY = 2,   /* a0 + a1 x (+ a2 x^2 (+ a3 x^3)) per ciphertext, degree 1..3;
+                            cost 1 for degree 1, else 2 */
     FHE_NODE_SQUARE = 3, /* x^2 per ciphertext, cost 1 */
     FHE_NODE_ADD = 4,    /* element-wise sum of the in-edge lists, cost 0 */
-    FHE_NODE_OUTPUT = 5  /* sink: result handed to the client (type of concern) */
+    FHE_NODE_OUTPUT = 5, /* sink: result handed to the client (type of concern) */
+    FHE_NODE_RELU = 6    /* Eq. relu_approximate with range q = coeffs[0]:
+                            4/(3 pi q) x^2 + x/2 + q/(3 pi), a degree-2 POLY, cost 2 */
 };
 
 typedef struct {
@@ -90,7 +93,8 @@ typedef struct {
     const uint32_t* col_idx;  /* LINEAR: CSR column = index into the stacked input */
     const double* weight;     /* LINEAR: CSR values (FP64) */
     const double* bias;       /* LINEAR: n_out biases (FP64), may be NULL = 0 */
-    double coeffs[4];         /* POLY: a0..a3 */
+    double coeffs[4];         /* POLY: a0..a_degree; RELU: coeffs[0] = range q > 0 */
+    uint32_t degree;          /* POLY: 1, 2 or 3 (0 means 3) */
 } fhe_node_desc;
 
 typedef struct {

@@ -124,12 +124,13 @@ int fhe_gauss_table(uint64_t* out38)
 // Alg. autoHE_discover: largest accumulated cost from source s at every node;
 // a node of the concern type (input / output) reached from another source
 // restarts discovery as its own source with cost 0.
-static uint32_t node_cost(uint32_t kind)
+static uint32_t node_cost(const fhe_node_desc& nd)
 {
-    switch (kind) {
+    switch (nd.kind) {
     case FHE_NODE_LINEAR: return 1;
     case FHE_NODE_SQUARE: return 1;
-    case FHE_NODE_POLY: return 2;
+    case FHE_NODE_POLY: return nd.degree == 1 ? 1 : 2;    // affine: one rescale
+    case FHE_NODE_RELU: return 2;
     default: return 0;
     }
 }
@@ -153,7 +154,7 @@ struct Discover {
         if (is_concern(g->nodes[n].kind) && s != n) {
             run(n, n, 0);
         } else {
-            for (uint32_t i : succ[n]) run(i, s, c + node_cost(g->nodes[i].kind));
+            for (uint32_t i : succ[n]) run(i, s, c + node_cost(g->nodes[i]));
         }
         --depth;
     }
@@ -215,6 +216,7 @@ int fhe_autoparam(const fhe_graph* g, uint32_t log_scale, double special_mult, u
     for (size_t i = 0; i < g->nodes.size(); ++i) {
         std::memset(&nodes[i], 0, sizeof(fhe_node_desc));
         nodes[i].kind = g->nodes[i].kind;
+        nodes[i].degree = g->nodes[i].degree;
         n_in += g->nodes[i].kind == FHE_NODE_INPUT;
     }
     fhe_graph_desc d;

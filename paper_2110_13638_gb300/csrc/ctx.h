@@ -76,6 +76,7 @@ struct fhe_graph_node {
     std::vector<uint32_t> row_ptr, col_idx;
     std::vector<double> weight, bias;
     double coeffs[4] = {0, 0, 0, 0};
+    uint32_t degree = 3;       // POLY / RELU (RELU: coefficients of Eq. relu_approximate, degree 2)
 };
 
 // device constants of one node at its planned level (built on first use)
@@ -166,9 +167,10 @@ void k_relin(const fhe_ctx* c, const u64* d3, u64* out2, uint32_t n_ct, uint32_t
 size_t rescale_scratch_bytes(const fhe_ctx* c, uint32_t n_ct, uint32_t comps);
 void k_rescale(const fhe_ctx* c, const u64* in, u64* out, uint32_t n_ct, uint32_t comps, uint32_t L,
                const u64* addc, uint32_t addc_stride, void* scratch, cudaStream_t st, const u64* mulc = nullptr);
-// degree-3 activation: t1 += x2 * c2 + (first L1 residues of x) * c1
+// polynomial activation: t1 (+)= x2 * c2 + (first L1 residues of x) * c1
+// (accumulate: add to t1; else overwrite it)
 void k_poly_combine(const fhe_ctx* c, u64* t1, const u64* x2, const u64* x, uint32_t n_ct, uint32_t L1, uint32_t Lx,
-                    const u64* c2, const u64* c1, cudaStream_t st);
+                    const u64* c2, const u64* c1, cudaStream_t st, bool accumulate = true);
 // constants C (device residues cres[ct * cstride + r]) multiply every component;
 // reads residues r < L_out of an input stored with L_in residues
 void k_mul_const(const fhe_ctx* c, const u64* in, u64* out, uint32_t n_ct, uint32_t comps, uint32_t L_in,

@@ -8,10 +8,14 @@
 // sequence of batched kernel launches on the caller's stream:
 //   LINEAR  y_o = rescale(sum_e llround(w_e q_{L-1}) x_{col_e}) + llround(b_o s_y)
 //   SQUARE  rescale(relin(x (x) x))
-//   POLY    x2 = rescale(relin(x (x) x));  w = rescale(x * llround(a3 s3));
+//   POLY    degree 3: x2 = rescale(relin(x (x) x));  w = rescale(x * llround(a3 s3));
 //           T = relin(x2 (x) w) + x2 * llround(a2 s_2) + drop(x) * llround(a1 q');
 //           y = rescale(T) + llround(a0 s_y)
 //           (s3 = q' q / s2, s_2 = s q' / s2, s2 = s s / q; q = q_{L-1}, q' = q_{L-2})
+//           degree 2: the same without w and the relin(x2 (x) w) term
+//           degree 1: y = rescale(x * llround(a1 q)) + llround(a0 s_y)
+//   RELU    Eq. relu_approximate with range q: the degree-2 POLY with
+//           a0 = q / (3 pi), a1 = 1/2, a2 = 4 / (3 pi q)
 // Nominal scales are FP64 values updated in exactly this order.
 // A dry run with the same allocation sequence sizes the workspace first.
 #include <algorithm>
@@ -149,19 +153,19 @@ struct Exec {
             o_col = put(tcol.data(), std::max<size_t>(1, tcol.size()) * 4);
             o_W = put(W.data(), std::max<size_t>(1, W.size()) * 8);
             o_b = put(B.data(), std::max<size_t>(1, B.size()) * 8);
-        } else if (nd.kind == FHE_NODE_POLY) {
+        } else if (nd.kind == FHE_NODE_POLY || nd.kind == FHE_NODE_RELU) {
             PolyK k = poly_constants(nd, L, s_in);
-            std::vector<u64> r3(L), r2(L - 1), r1(L - 1), r0(L - 2);
-            for (uint32_t r = 0; r < L; ++r) r3[r] = mod_signed(k.C3, c->primes[r]);
-            for (uint32_t r = 0; r + 1 < L; ++r) {
+            std::vector<u64> r3(L), r2(L), r1(L), r0(L);          // residues of C3..C0 at every prime of level L
+            for (uint32_t r = 0; r < L; ++r) {
+                r3[r] = mod_signed(k.C3, c->primes[r]);
                 r2[r] = mod_signed(k.C2, c->primes[r]);
                 r1[r] = mod_signed(k.C1, c->primes[r]);
+                r0[r] = mod_signed(k.C0, c->primes[r]);
             }
-            for (uint32_t r = 0; r + 2 < L; ++r) r0[r] = mod_signed(k.C0, c->primes[r]);
             o_c3 = put(r3.data(), r3.size() * 8);
             o_c2 = put(r2.data(), r2.size() * 8);
             o_c1 = put(r1.data(), r1.size() * 8);
-            o_c0 = put(r0.data(), std::max<size_t>(1, r0.size()) * 8);
+            o_c0 = put(r0.data(), r0.size() * 8);
         } else {
             return nullptr;
         }
@@ -192,13 +196,19 @@ struct Exec {
 
     // ------------------------------------------------ scale schedule of POLY
     struct PolyK {
-        int64_t C3, C2, C1, C0;
-        double s_x2, s_w, s_t1, s_t2, s_t3, s_y;
+        int64_t C3 = 0, C2 = 0, C1 = 0, C0 = 0;
+        double s_x2 = 0, s_w = 0, s_t1 = 0, s_t2 = 0, s_t3 = 0, s_y = 0;
     };
     PolyK poly_constants(const fhe_graph_node& nd, uint32_t L, double s) const
     {
         PolyK k;
         const double q = (double)c->primes[L - 1];
+        if (nd.degree == 1) {
+            k.C1 = (int64_t)std::llround(nd.coeffs[1] * q);
+            k.s_y = (s * q) / q;
+            k.C0 = (int64_t)std::llround(nd.coeffs[0] * k.s_y);
+            return k;
+        }
         const double qp = (double)c->primes[L - 2];
         const double s2 = (s * s) / q;
         k.s_x2 = (s * s) / q;
@@ -211,7 +221,7 @@ struct Exec {
         k.s_t2 = k.s_x2 * sg2;
         k.C1 = (int64_t)std::llround(nd.coeffs[1] * qp);
         k.s_t3 = s * qp;
-        k.s_y = k.s_t1 / qp;
+        k.s_y = (nd.degree == 3 ? k.s_t1 : k.s_t2) / qp;
         k.C0 = (int64_t)std::llround(nd.coeffs[0] * k.s_y);
         return k;
     }
@@ -273,12 +283,15 @@ struct Exec {
     {
         Sig y;
         const uint32_t L = x.L, n = x.n;
-        if (L < 3) { err(FHE_ELEVEL, "a degree-3 activation needs three primes"); return y; }
+        const uint32_t deg = g->nodes[i].degree;
+        if (deg == 1) return affine(i, x);
+        if (L < 3) { err(FHE_ELEVEL, "a degree-2 or -3 activation needs three primes"); return y; }
         const PolyK k = poly_constants(g->nodes[i], L, x.scale);
-        if (!scale_match(k.s_t1, k.s_t2) || !scale_match(k.s_t1, k.s_t3)) {
+        if ((deg == 3 && !scale_match(k.s_t1, k.s_t2)) || !scale_match(k.s_t2, k.s_t3)) {
             err(FHE_ESCALE, "polynomial terms disagree in scale");
             return y;
         }
+        if (deg == 2) return poly2(i, x, k);
         u64* T3 = (u64*)take(cts(n, 3, L));
         u64* R = (u64*)take(cts(n, 2, L));
         void* rs = take(relin_scratch_bytes(c, n, L));
@@ -299,6 +312,57 @@ struct Exec {
             k_relin(c, T3b, t1, n, L - 1, rs, st);
             k_poly_combine(c, t1, x2, x.p, n, L - 1, L, kc->c2, kc->c1, st);  // + x2 C2 + drop(x) C1
             k_rescale(c, t1, out, n, 2, L - 1, kc->c0, 0, ss, st);
+        }
+        y.p = out;
+        y.n = n;
+        y.L = L - 2;
+        y.scale = k.s_y;
+        y.set = true;
+        return y;
+    }
+
+    // degree 1: y = rescale(x * C1) + C0, one fused rescale
+    Sig affine(uint32_t i, const Sig& x)
+    {
+        Sig y;
+        const uint32_t L = x.L, n = x.n;
+        if (L < 2) { err(FHE_ELEVEL, "an affine activation needs two primes"); return y; }
+        const PolyK k = poly_constants(g->nodes[i], L, x.scale);
+        void* ss = take(rescale_scratch_bytes(c, n, 2));
+        u64* out = (u64*)take(cts(n, 2, L - 1));
+        if (!dry && ok()) {
+            fhe_node_const* kc = node_const(i, L, x.scale);
+            if (!kc) return y;
+            k_rescale(c, x.p, out, n, 2, L, kc->c0, 0, ss, st, kc->c1);
+        }
+        y.p = out;
+        y.n = n;
+        y.L = L - 1;
+        y.scale = k.s_y;
+        y.set = true;
+        return y;
+    }
+
+    // degree 2: x2 = rescale(relin(x (x) x)); y = rescale(x2 C2 + drop(x) C1) + C0
+    Sig poly2(uint32_t i, const Sig& x, const PolyK& k)
+    {
+        Sig y;
+        const uint32_t L = x.L, n = x.n;
+        u64* T3 = (u64*)take(cts(n, 3, L));
+        u64* R = (u64*)take(cts(n, 2, L));
+        void* rs = take(relin_scratch_bytes(c, n, L));
+        void* ss = take(rescale_scratch_bytes(c, n, 2));
+        u64* x2 = (u64*)take(cts(n, 2, L - 1));
+        u64* t = (u64*)take(cts(n, 2, L - 1));
+        u64* out = (u64*)take(cts(n, 2, L - 2));
+        if (!dry && ok()) {
+            fhe_node_const* kc = node_const(i, L, x.scale);
+            if (!kc) return y;
+            k_tensor(c, x.p, x.p, T3, n, L, st);
+            k_relin(c, T3, R, n, L, rs, st);
+            k_rescale(c, R, x2, n, 2, L, nullptr, 0, ss, st);
+            k_poly_combine(c, t, x2, x.p, n, L - 1, L, kc->c2, kc->c1, st, false);   // x2 C2 + drop(x) C1
+            k_rescale(c, t, out, n, 2, L - 1, kc->c0, 0, ss, st);
         }
         y.p = out;
         y.n = n;
@@ -392,7 +456,8 @@ struct Exec {
         case FHE_NODE_ADD: return s;
         case FHE_NODE_LINEAR: return linear(n, s);
         case FHE_NODE_SQUARE: return square(s);
-        case FHE_NODE_POLY: return poly(n, s);
+        case FHE_NODE_POLY:
+        case FHE_NODE_RELU: return poly(n, s);
         default: err(FHE_EINVAL, "unknown node kind"); return Sig();
         }
     }
@@ -460,7 +525,7 @@ int fhe_graph_create(const fhe_graph_desc* d, fhe_graph** out)
         fhe_graph_node n;
         n.kind = s.kind;
         n.n_out = s.n_out;
-        if (s.kind > FHE_NODE_OUTPUT) {
+        if (s.kind > FHE_NODE_RELU) {
             delete g;
             return fail(FHE_EINVAL, "unknown node kind");
         }
@@ -496,6 +561,26 @@ int fhe_graph_create(const fhe_graph_desc* d, fhe_graph** out)
                 }
         }
         for (int k = 0; k < 4; ++k) n.coeffs[k] = s.coeffs[k];
+        if (s.kind == FHE_NODE_POLY) {
+            n.degree = s.degree == 0 ? 3 : s.degree;
+            if (n.degree > 3) {
+                delete g;
+                return fail(FHE_EUNSUPPORTED, "polynomial degree above 3");
+            }
+            for (uint32_t k = n.degree + 1; k < 4; ++k) n.coeffs[k] = 0.0;
+        } else if (s.kind == FHE_NODE_RELU) {
+            // Eq. relu_approximate with range q, as a degree-2 polynomial
+            const double q = s.coeffs[0];
+            if (!(q > 0.0) || !std::isfinite(q)) {
+                delete g;
+                return fail(FHE_EINVAL, "ReLU approximation range q must be positive");
+            }
+            n.degree = 2;
+            n.coeffs[0] = q / (3 * M_PI);
+            n.coeffs[1] = 0.5;
+            n.coeffs[2] = 4 / (3 * M_PI * q);
+            n.coeffs[3] = 0.0;
+        }
         g->nodes.push_back(n);
     }
     for (uint32_t e = 0; e < d->n_edges; ++e) {

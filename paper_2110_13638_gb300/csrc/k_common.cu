@@ -188,7 +188,7 @@ void k_add_const(const fhe_ctx* c, u64* ct, uint32_t n_ct, uint32_t L, const u64
 // the sum of the three terms of the degree-3 activation in one pass
 __global__ void k_poly_combine_kernel(u64* __restrict__ t1, const u64* __restrict__ x2, const u64* __restrict__ x,
                                       size_t total, int L1, int Lx, int logN, const u64* __restrict__ c2,
-                                      const u64* __restrict__ c1, const PrimeC* __restrict__ pc)
+                                      const u64* __restrict__ c1, const PrimeC* __restrict__ pc, bool accumulate)
 {
     const size_t Nm = ((size_t)1 << logN) - 1;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
@@ -197,19 +197,20 @@ __global__ void k_poly_combine_kernel(u64* __restrict__ t1, const u64* __restric
         const size_t poly = row / L1;
         const PrimeC P = pc[r];
         const u64 xv = x[((poly * Lx + r) << logN) + (i & Nm)];
-        u64 a = add_mod(t1[i], mul_mod(x2[i], c2[r], P), P.q);
+        u64 a = mul_mod(x2[i], c2[r], P);
+        if (accumulate) a = add_mod(t1[i], a, P.q);
         t1[i] = add_mod(a, mul_mod(xv, c1[r], P), P.q);
     }
 }
 
 void k_poly_combine(const fhe_ctx* c, u64* t1, const u64* x2, const u64* x, uint32_t n_ct, uint32_t L1, uint32_t Lx,
-                    const u64* c2, const u64* c1, cudaStream_t st)
+                    const u64* c2, const u64* c1, cudaStream_t st, bool accumulate)
 {
     const size_t total = (size_t)n_ct * 2 * L1 * c->N;
     if (!total) return;
     LaunchScope ls(c, "elementwise", st);
     k_poly_combine_kernel<<<ew_grid(total), 256, 0, st>>>(t1, x2, x, total, (int)L1, (int)Lx, (int)c->logN, c2, c1,
-                                                          c->d_pc);
+                                                          c->d_pc, accumulate);
 }
 
 DivC make_divc(const fhe_ctx* c, uint32_t p_index, uint32_t n_targets)

@@ -17,9 +17,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 SO_PATH = os.path.join(_HERE, "csrc", "_build", "libfhe.so")
 
-FHE_NODE_INPUT, FHE_NODE_LINEAR, FHE_NODE_POLY, FHE_NODE_SQUARE, FHE_NODE_ADD, FHE_NODE_OUTPUT = range(6)
+(FHE_NODE_INPUT, FHE_NODE_LINEAR, FHE_NODE_POLY, FHE_NODE_SQUARE, FHE_NODE_ADD, FHE_NODE_OUTPUT,
+ FHE_NODE_RELU) = range(7)
 _KINDS = {"input": FHE_NODE_INPUT, "linear": FHE_NODE_LINEAR, "poly": FHE_NODE_POLY,
-          "square": FHE_NODE_SQUARE, "add": FHE_NODE_ADD, "output": FHE_NODE_OUTPUT}
+          "square": FHE_NODE_SQUARE, "add": FHE_NODE_ADD, "output": FHE_NODE_OUTPUT, "relu": FHE_NODE_RELU}
 
 ERRORS = {-1: "FHE_EINVAL", -2: "FHE_ENOMEM", -3: "FHE_ELEVEL", -4: "FHE_ESCALE", -5: "FHE_ECUDA",
           -6: "FHE_ETIMEOUT", -7: "FHE_EUNSUPPORTED", -8: "FHE_ENOKEY"}
@@ -51,7 +52,7 @@ class NodeDesc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_uint32), ("n_out", ctypes.c_uint32),
                 ("row_ptr", ctypes.POINTER(ctypes.c_uint32)), ("col_idx", ctypes.POINTER(ctypes.c_uint32)),
                 ("weight", ctypes.POINTER(ctypes.c_double)), ("bias", ctypes.POINTER(ctypes.c_double)),
-                ("coeffs", ctypes.c_double * 4)]
+                ("coeffs", ctypes.c_double * 4), ("degree", ctypes.c_uint32)]
 
 
 class Request(ctypes.Structure):
@@ -205,8 +206,14 @@ class _GraphArrays:
             elif n["kind"] == "input":
                 d.n_out = int(n.get("n", 0))
             if n["kind"] == "poly":
-                for k in range(4):
-                    d.coeffs[k] = float(n["coeffs"][k])
+                a = [float(v) for v in n["coeffs"]]
+                if not 2 <= len(a) <= 4:
+                    raise ValueError("polynomial nodes take 2 to 4 coefficients (degree 1..3)")
+                d.degree = len(a) - 1
+                for k in range(len(a)):
+                    d.coeffs[k] = a[k]
+            elif n["kind"] == "relu":
+                d.coeffs[0] = float(n["q"])
         src = np.array([e[0] for e in graph["edges"]], dtype=np.uint32)
         dst = np.array([e[1] for e in graph["edges"]], dtype=np.uint32)
         self.keep += [src, dst]

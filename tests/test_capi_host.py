@@ -50,7 +50,7 @@ def test_gaussian_table_matches_oracle():
     assert fhe.gauss_table() == params.gauss_cdt()
 
 
-@pytest.mark.parametrize("builder", [W.cfg0, W.cfg1, W.cfg2])
+@pytest.mark.parametrize("builder", [W.cfg0, W.cfg1, W.cfg2, W.cnn_relu, W.mini_cnn_relu, W.deep_mlp])
 def test_autohe_matches_oracle(builder):
     g, _ = builder(n_slots=4)
     gof, gcost = fhe.autohe(g)
@@ -70,7 +70,8 @@ def test_autohe_branches_and_disjoint():
     assert fhe.autohe(g) == ([0, 1], [2, 7])
 
 
-@pytest.mark.parametrize("builder", [W.cfg0, W.cfg1, W.cfg2, W.deep_mlp, W.branch_graph])
+@pytest.mark.parametrize("builder", [W.cfg0, W.cfg1, W.cfg2, W.deep_mlp, W.branch_graph, W.cnn_relu,
+                                     W.mini_cnn_relu])
 def test_autoparam_matches_oracle(builder):
     g, _ = builder(n_slots=4)
     _, o_cost, _ = params.autohe(g, W.input_nodes(g))

@@ -85,7 +85,7 @@ def _decrypted(ctx, out, meta, L_out):
     return z.cpu().numpy()
 
 
-@pytest.mark.parametrize("builder", [W.cfg1, W.cfg2])
+@pytest.mark.parametrize("builder", [W.cfg1, W.cfg2, W.cnn_relu])
 def test_full_network_matches_fp64(ctx, builder):
     g, x = builder()
     ct = encrypt_all(ctx, x, first=5000)

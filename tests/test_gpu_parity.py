@@ -280,6 +280,15 @@ def test_graph_cfg0_full_size_bit_exact():
     assert err < 1e-4
 
 
+def test_graph_relu_and_affine_bit_exact():
+    """Eq. relu_approximate (degree 2) after the convolution and the linear
+    sigmoid 0.5 + 0.197 x (degree 1) after the dense layer."""
+    graph, x = W.mini_cnn_relu(n_slots=512)
+    g, o = pair(1024, [60] + [40] * 6 + [60])
+    err = _graph_parity(g, o, graph, [x], [0])
+    assert err < 1e-4
+
+
 def test_graph_depth8_ring32768_bit_exact():
     """Depth 8: Alg. autoHE / parameterise choose N = 32768, [60, 40 x 8, 60];
     every stage (encode, encrypt, layers, relinearise, rescale, decode) runs on
