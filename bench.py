@@ -113,10 +113,10 @@ class ClockSampler:
 
 def modup_mac_mul32(ctx, plan):
     """Algorithmic 32-bit multiplies of the key-switching ModUp + key inner
-    product kernel over one request (see the design notes): per ciphertext at
-    level L, L*L forward transforms of (N/2) log2 N Shoup butterflies (10
-    multiplies each) and 2 L (L+1) N key products (mul_mod: 4 for the 128-bit
-    product + 14 for the 128-bit reduction)."""
+    product kernel over one request: per ciphertext at level L, L*L forward
+    transforms of (N/2) log2 N Shoup butterflies and 2 L (L+1) N Shoup key
+    products, 10 multiplies each (a 64x64 high product = 4, two 64-bit low
+    products = 3 + 3)."""
     import math
     N = ctx.N
     lg = int(math.log2(N))
@@ -124,7 +124,7 @@ def modup_mac_mul32(ctx, plan):
     for n_ct, L in plan:
         bfly = L * L * (N // 2) * lg
         prods = 2 * L * (L + 1) * N
-        tot += n_ct * (bfly * 10 + prods * 18)
+        tot += n_ct * (bfly + prods) * 10
     return tot
 
 

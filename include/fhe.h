@@ -142,7 +142,8 @@ int fhe_gauss_table(uint64_t* out38);
  * here by timing each candidate on a rescale of 64 ciphertexts, and again
  * separately for the key-switching digit transforms (whose epilogue holds the
  * key inner product) on that step alone; the environment variable
- * FHE_NTT_VARIANT=0..5 fixes both instead.  bits: coefficient-modulus bit sizes, the
+ * FHE_NTT_VARIANT=0..5 fixes both instead (and FHE_NTT_VARIANT_KS, when set
+ * with it, the key-switching one).  bits: coefficient-modulus bit sizes, the
  * last one being the special prime; log_scale: scale 2^log_scale.
  * N must be a power of two in [16, 65536]; above 16384 only the two-pass
  * NTT schedules exist and the grouped (uneven-level) calls are refused. */

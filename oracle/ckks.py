@@ -473,6 +473,66 @@ def eval_graph(ctx, graph, inputs, signals):
     return fire(graph, inputs, signals, apply_fn, lambda sigs: _stack_cts(ctx, sigs, None))
 
 
+def refresh_ct_id(node, k):
+    """Object id of the k-th ciphertext re-encrypted at rotation node `node`."""
+    return (1 << 40) + (node << 20) + k
+
+
+def eval_graph_grouped(ctxs, graph, signals):
+    """Encrypted evaluation of a graph with rotation (client refresh) nodes.
+    Alg. autoHE over the input and rotation nodes gives the parameter groups;
+    ctxs maps group id -> Context (its parameter set, keys generated).
+    signals: per input node (node order), its list of ciphertexts encrypted
+    under its group's context.  Every node computes in the context of the
+    group it belongs to; a rotation node hands its ciphertexts to the client,
+    which decrypts and decodes them under the upstream group's keys and
+    encodes and encrypts them under the rotation's own group
+    (ct id refresh_ct_id(node, k)).  Returns {output node: [Ciphertext]}."""
+    from .params import autohe, ingress_nodes
+    ing = ingress_nodes(graph)
+    group_of, _, sources = autohe(graph, ing)
+
+    def group_above(n):
+        gs = {group_of[k] for k in sources.get(n, {})}
+        assert len(gs) == 1, "node %d is reached from several parameter groups" % n
+        return gs.pop()
+
+    def apply_fn(n, node, s):
+        if isinstance(s, dict):
+            edges = s["edges"]
+            if node["kind"] == "add":
+                ctx = ctxs[group_above(n)]
+                out = edges[0]
+                for sig in edges[1:]:
+                    out = [ctx.add(a, b) for a, b in zip(out, sig)]
+                return out
+            s = [ct for sig in edges for ct in sig]
+        k = node["kind"]
+        if k in ("input", "output"):
+            return s
+        if k == "rotate":
+            up, down = ctxs[group_above(n)], ctxs[group_of[n]]
+            out = []
+            for i, ct in enumerate(s):
+                z = up.decode(up.decrypt(ct), ct.scale)
+                out.append(down.encrypt(down.encode(z), refresh_ct_id(n, i)))
+            return out
+        ctx = ctxs[group_above(n)]
+        if k == "linear":
+            return ctx.linear(s, csr_rows(node), node["bias"])
+        if k == "poly":
+            return [ctx.poly(x, node["coeffs"]) for x in s]
+        if k == "relu":
+            return [ctx.poly(x, relu_coeffs(node["q"])) for x in s]
+        if k == "square":
+            return [ctx.square(x) for x in s]
+        raise ValueError(k)
+
+    some = next(iter(ctxs.values()))
+    inputs = [i for i in ing if graph["nodes"][i]["kind"] == "input"]
+    return fire(graph, inputs, signals, apply_fn, lambda sigs: _stack_cts(some, sigs, None))
+
+
 def relu_coeffs(q):
     """Eq. relu_approximate: R(x) ~ 4/(3 pi q) x^2 + x/2 + q/(3 pi) on [-q, q]
     (q: the approximation range), as [a0, a1, a2] in FP64."""
@@ -499,7 +559,7 @@ def forward_fp64(graph, inputs, signals):
                 return out
             s = np.concatenate(edges, axis=0)
         k = node["kind"]
-        if k in ("input", "output"):
+        if k in ("input", "output", "rotate"):
             return s
         if k == "linear":
             rows = csr_rows(node)

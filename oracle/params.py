@@ -12,7 +12,13 @@ from decimal import Decimal, getcontext
 # Node costs (Sec. 3.1 "FHE parameterisation": the edge A->B carries the
 # computational depth of B).  Encrypt/decrypt nodes are the "type of concern".
 # ---------------------------------------------------------------------------
-CONCERN_KINDS = ("input", "output")
+CONCERN_KINDS = ("input", "output", "rotate")
+
+
+def ingress_nodes(graph):
+    """Sources of parameter groups: encrypted inputs and rotations (client
+    refresh points), in node order."""
+    return [i for i, n in enumerate(graph["nodes"]) if n["kind"] in ("input", "rotate")]
 
 
 def node_cost(node):

@@ -264,16 +264,21 @@ static void free_ctx(fhe_ctx* c)
 }
 
 // Time every NTT schedule on a representative fused step and keep the
-// fastest; FHE_NTT_VARIANT overrides.
+// fastest; FHE_NTT_VARIANT fixes both picks, FHE_NTT_VARIANT_KS (with it)
+// the key-switching one separately.
 static int autotune_ntt(fhe_ctx* c)
 {
     const char* env = std::getenv("FHE_NTT_VARIANT");
     if (env && *env) {
-        int v = std::atoi(env);
-        if (v < 0 || v >= kNttVariants) return fail(FHE_EINVAL, "FHE_NTT_VARIANT out of range (0..5)");
-        if (c->N > kMaxSinglePassN && !ntt_two_pass(v)) return fail(FHE_EINVAL, "N > 16384 needs a two-pass NTT schedule (2 or 3)");
+        const char* env_ks = std::getenv("FHE_NTT_VARIANT_KS");
+        const int v = std::atoi(env), vk = (env_ks && *env_ks) ? std::atoi(env_ks) : v;
+        for (int x : {v, vk}) {
+            if (x < 0 || x >= kNttVariants) return fail(FHE_EINVAL, "FHE_NTT_VARIANT(_KS) out of range (0..5)");
+            if (c->N > kMaxSinglePassN && !ntt_two_pass(x))
+                return fail(FHE_EINVAL, "N > 16384 needs a two-pass NTT schedule (2 or 3)");
+        }
         c->ntt_variant = v;
-        c->ntt_variant_ks = v;
+        c->ntt_variant_ks = vk;
         return FHE_OK;
     }
     // Timed workload: a rescale (inverse transform of the last residue, then

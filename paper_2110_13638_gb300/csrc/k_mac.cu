@@ -82,7 +82,7 @@ __device__ __forceinline__ u64 limb_combine(u64 s0, u64 s1, u64 s2, const PrimeC
     return reduce128(hi, lo, P);
 }
 
-__global__ void __launch_bounds__(256) k_mac_tiled_kernel(const u64* __restrict__ X, const uint4* __restrict__ tiles,
+__global__ void __launch_bounds__(256, 2) k_mac_tiled_kernel(const u64* __restrict__ X, const uint4* __restrict__ tiles,
                                                            const uint32_t* __restrict__ rows,
                                                            const uint32_t* __restrict__ col,
                                                            const u64* __restrict__ W, u64* __restrict__ Y, int L, int N,
@@ -106,10 +106,21 @@ __global__ void __launch_bounds__(256) k_mac_tiled_kernel(const u64* __restrict_
 #pragma unroll
         for (int o = 0; o < kMacTile; ++o) s0[o] = s1[o] = s2[o] = 0;
         uint32_t e = 0;
+        // terms four at a time; the next four inputs are loaded before the
+        // current four are multiplied (their latency hides behind the MACs)
+        u64 xn[4];
+        if (K >= 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) xn[u] = Xj[(size_t)__ldg(&cl[u]) * ct_stride];
+        }
         for (; e + 4 <= K; e += 4) {
             u64 x[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) x[u] = Xj[(size_t)__ldg(&cl[e + u]) * ct_stride];
+            for (int u = 0; u < 4; ++u) x[u] = xn[u];
+            if (e + 8 <= K) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) xn[u] = Xj[(size_t)__ldg(&cl[e + 4 + u]) * ct_stride];
+            }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const uint32_t xl = (uint32_t)(x[u] & kLimbMask), xh = (uint32_t)(x[u] >> 21), xs = xl + xh;

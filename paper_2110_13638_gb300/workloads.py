@@ -167,6 +167,27 @@ def mini_cnn_relu(n_slots, seed=17, relu_q=3.0):
     return g, x
 
 
+def with_rotation(g, after):
+    """The chain graph g with a rotation (client refresh) node inserted after
+    node `after`: the ciphertexts go back to the client, are decrypted and
+    re-encrypted, and the rest of the network is a new parameter group."""
+    nodes = g["nodes"][:after + 1] + [{"kind": "rotate"}] + g["nodes"][after + 1:]
+    edges = [(i, i + 1) for i in range(len(nodes) - 1)]
+    return {"nodes": nodes, "edges": edges}
+
+
+def cnn_rotate(n_slots=8192, **kw):
+    """The CNN with one rotation after the first sigmoid fit: groups of cost
+    3 (conv, sigmoid) and 4 (dense, sigmoid, dense) instead of one of cost 7."""
+    g, x = cfg1(n_slots=n_slots, **kw)
+    return with_rotation(g, 2), x
+
+
+def mini_cnn_rotate(n_slots, seed=7):
+    g, x = mini_cnn(n_slots, seed=seed)
+    return with_rotation(g, 2), x
+
+
 def deep_mlp(n_slots, seed=13, n_in=4, hidden=4, n_out=2):
     """Multiplicative depth 8 (dense, sigmoid fit, dense, sigmoid fit, dense,
     square), so Alg. parameterise asks for N = 32768 and [60, 40 x 8, 60]."""

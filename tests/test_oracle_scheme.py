@@ -321,6 +321,33 @@ def test_graph_eval_relu_and_affine_match_fp64():
         assert np.max(np.abs(ctx.decode(ctx.decrypt(y), y.scale) - r)) < 1e-4
 
 
+def test_grouped_eval_with_rotation_matches_fp64():
+    """A rotation (client refresh) splits the CNN into parameter groups of
+    cost 3 and 4; each group evaluates under its own keys and the refreshed
+    ciphertexts restart at the second group's top level."""
+    from oracle import params
+    g, x = W.mini_cnn_rotate(n_slots=32)
+    ing = params.ingress_nodes(g)
+    assert [g["nodes"][i]["kind"] for i in ing] == ["input", "rotate"]
+    group_of, cost, _ = params.autohe(g, ing)
+    assert cost == [3, 4] and group_of[ing[0]] == 0 and group_of[ing[1]] == 1
+    ctxs = {}
+    for grp, c in enumerate(cost):
+        bits = params.parameterise(c)["coeff_modulus"]
+        ctxs[grp] = ckks.Context(64, bits)
+        ctxs[grp].keygen(grp)
+    cts = [ctxs[0].encrypt(ctxs[0].encode(v), i) for i, v in enumerate(x)]
+    out = ckks.eval_graph_grouped(ctxs, g, [cts])
+    ref = ckks.forward_fp64(g, W.input_nodes(g), [x])
+    (o, ys), = out.items()
+    for y, r in zip(ys, ref[o]):
+        assert y.level == 1
+        assert np.max(np.abs(ctxs[1].decode(ctxs[1].decrypt(y), y.scale) - r)) < 1e-4
+    # the same network without the rotation needs one group of cost 7
+    g1, _ = W.mini_cnn(n_slots=32)
+    assert params.autohe(g1, W.input_nodes(g1))[1] == [7]
+
+
 def test_graph_eval_branches_level_match():
     g, xs = W.branch_graph(n_slots=32)
     ins = W.input_nodes(g)
