@@ -82,8 +82,13 @@ enum {
     FHE_NODE_SQUARE = 3, /* x^2 per ciphertext, cost 1 */
     FHE_NODE_ADD = 4,    /* element-wise sum of the in-edge lists, cost 0 */
     FHE_NODE_OUTPUT = 5, /* sink: result handed to the client (type of concern) */
-    FHE_NODE_RELU = 6    /* Eq. relu_approximate with range q = coeffs[0]:
+    FHE_NODE_RELU = 6,   /* Eq. relu_approximate with range q = coeffs[0]:
                             4/(3 pi q) x^2 + x/2 + q/(3 pi), a degree-2 POLY, cost 2 */
+    FHE_NODE_ROTATE = 7  /* rotation (client refresh, Sec. 3.1): a concern node where the
+                            ciphertexts go back to the client to be decrypted and
+                            re-encrypted; it ends one parameter group and starts
+                            another.  fhe_eval_graph refuses graphs that contain it:
+                            each group is evaluated on its own context. */
 };
 
 typedef struct {
@@ -113,9 +118,11 @@ typedef struct {
 int fhe_parameterise(uint32_t cost, uint32_t log_scale, double special_mult,
                      uint32_t* N, uint32_t* bits, uint32_t bits_cap, uint32_t* n_bits);
 
-/* Alg. autoHE / autoHE_discover over a graph: parameter groups of the input
- * nodes and each group's largest cost.  group_of[i] receives the group of the
- * i-th INPUT node (in node order); group_cost[g] the cost of group g.  Host only. */
+/* Alg. autoHE / autoHE_discover over a graph: parameter groups of the
+ * ingress nodes (INPUT and ROTATE, the sources of ciphertexts under fresh
+ * keys) and each group's largest cost.  group_of[i] receives the group of the
+ * i-th ingress node (in node order); group_cost[g] the cost of group g.
+ * Host only. */
 int fhe_autohe(const fhe_graph_desc* g, uint32_t* group_of, uint32_t group_of_cap,
                uint32_t* group_cost, uint32_t group_cost_cap, uint32_t* n_groups);
 

@@ -135,7 +135,10 @@ static uint32_t node_cost(const fhe_node_desc& nd)
     }
 }
 
-static bool is_concern(uint32_t kind) { return kind == FHE_NODE_INPUT || kind == FHE_NODE_OUTPUT; }
+static bool is_concern(uint32_t kind)
+{
+    return kind == FHE_NODE_INPUT || kind == FHE_NODE_OUTPUT || kind == FHE_NODE_ROTATE;
+}
 
 struct Discover {
     const fhe_graph_desc* g;
@@ -174,9 +177,9 @@ int fhe_autohe(const fhe_graph_desc* g, uint32_t* group_of, uint32_t group_of_ca
         auto& v = D.succ[a];
         if (std::find(v.begin(), v.end(), b) == v.end()) v.push_back(b);
     }
-    std::vector<uint32_t> inputs;
+    std::vector<uint32_t> inputs;          // ingress nodes: INPUT and ROTATE
     for (uint32_t i = 0; i < g->n_nodes; ++i)
-        if (g->nodes[i].kind == FHE_NODE_INPUT) inputs.push_back(i);
+        if (g->nodes[i].kind == FHE_NODE_INPUT || g->nodes[i].kind == FHE_NODE_ROTATE) inputs.push_back(i);
     for (uint32_t i : inputs) D.run(i, i, 0);
     if (D.overflow) return fail(FHE_EINVAL, "graph traversal too deep (cycle without a concern node?)");
     std::map<uint32_t, uint32_t> gof;
@@ -217,7 +220,7 @@ int fhe_autoparam(const fhe_graph* g, uint32_t log_scale, double special_mult, u
         std::memset(&nodes[i], 0, sizeof(fhe_node_desc));
         nodes[i].kind = g->nodes[i].kind;
         nodes[i].degree = g->nodes[i].degree;
-        n_in += g->nodes[i].kind == FHE_NODE_INPUT;
+        n_in += g->nodes[i].kind == FHE_NODE_INPUT || g->nodes[i].kind == FHE_NODE_ROTATE;
     }
     fhe_graph_desc d;
     d.n_nodes = (uint32_t)nodes.size();

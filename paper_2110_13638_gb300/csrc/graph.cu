@@ -458,6 +458,10 @@ struct Exec {
         case FHE_NODE_SQUARE: return square(s);
         case FHE_NODE_POLY:
         case FHE_NODE_RELU: return poly(n, s);
+        case FHE_NODE_ROTATE:
+            err(FHE_EUNSUPPORTED, "a rotation node hands its ciphertexts to the client: evaluate each parameter group "
+                                  "on its own context");
+            return Sig();
         default: err(FHE_EINVAL, "unknown node kind"); return Sig();
         }
     }
@@ -525,7 +529,7 @@ int fhe_graph_create(const fhe_graph_desc* d, fhe_graph** out)
         fhe_graph_node n;
         n.kind = s.kind;
         n.n_out = s.n_out;
-        if (s.kind > FHE_NODE_RELU) {
+        if (s.kind > FHE_NODE_ROTATE) {
             delete g;
             return fail(FHE_EINVAL, "unknown node kind");
         }

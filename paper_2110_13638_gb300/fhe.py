@@ -18,9 +18,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 SO_PATH = os.path.join(_HERE, "csrc", "_build", "libfhe.so")
 
 (FHE_NODE_INPUT, FHE_NODE_LINEAR, FHE_NODE_POLY, FHE_NODE_SQUARE, FHE_NODE_ADD, FHE_NODE_OUTPUT,
- FHE_NODE_RELU) = range(7)
+ FHE_NODE_RELU, FHE_NODE_ROTATE) = range(8)
 _KINDS = {"input": FHE_NODE_INPUT, "linear": FHE_NODE_LINEAR, "poly": FHE_NODE_POLY,
-          "square": FHE_NODE_SQUARE, "add": FHE_NODE_ADD, "output": FHE_NODE_OUTPUT, "relu": FHE_NODE_RELU}
+          "square": FHE_NODE_SQUARE, "add": FHE_NODE_ADD, "output": FHE_NODE_OUTPUT, "relu": FHE_NODE_RELU,
+          "rotate": FHE_NODE_ROTATE}
 
 ERRORS = {-1: "FHE_EINVAL", -2: "FHE_ENOMEM", -3: "FHE_ELEVEL", -4: "FHE_ESCALE", -5: "FHE_ECUDA",
           -6: "FHE_ETIMEOUT", -7: "FHE_EUNSUPPORTED", -8: "FHE_ENOKEY"}
@@ -223,9 +224,10 @@ class _GraphArrays:
 
 
 def autohe(graph):
-    """(group of each input node in node order, cost of each group)."""
+    """(group of each ingress node -- INPUT and ROTATE -- in node order, cost of
+    each group)."""
     ga = _GraphArrays(graph)
-    n_in = sum(1 for n in graph["nodes"] if n["kind"] == "input")
+    n_in = sum(1 for n in graph["nodes"] if n["kind"] in ("input", "rotate"))
     gof = (ctypes.c_uint32 * max(1, n_in))()
     gcost = (ctypes.c_uint32 * max(1, n_in))()
     ng = ctypes.c_uint32()

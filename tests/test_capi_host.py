@@ -59,6 +59,17 @@ def test_autohe_matches_oracle(builder):
     assert gof == [o_gof[i] for i in W.input_nodes(g)]
 
 
+def test_autohe_groups_rotation_nodes():
+    from oracle import params as P
+    g, _ = W.mini_cnn_rotate(4)
+    gof, gcost = fhe.autohe(g)
+    o_gof, o_cost, _ = P.autohe(g, P.ingress_nodes(g))
+    assert gcost == o_cost == [3, 4]
+    assert gof == [o_gof[i] for i in P.ingress_nodes(g)]
+    g, _ = W.cnn_rotate(4)
+    assert fhe.autohe(g)[1] == [3, 4]
+
+
 def test_autohe_branches_and_disjoint():
     g, _ = W.branch_graph(4)
     assert fhe.autohe(g) == ([0, 0], [3])

@@ -305,6 +305,52 @@ def test_graph_depth8_ring32768_bit_exact():
     assert err < 1e-4
 
 
+def test_grouped_rotation_bit_exact_per_group():
+    """A rotation (client refresh) after the first sigmoid: groups of cost 3
+    and 4, each on its own context.  Group 0's ciphertexts at the rotation and
+    group 1's outputs (from the device's refreshed inputs) are bit-exact
+    against the oracle; the decoded outputs are within 1e-4 of FP64."""
+    from oracle import params
+    from paper_2110_13638_gb300 import groups
+    graph, x = W.mini_cnn_rotate(n_slots=512)
+    N = 1024
+    cost = params.autohe(graph, params.ingress_nodes(graph))[1]
+    assert cost == [3, 4]
+    pairs = [pair(N, params.parameterise(c)["coeff_modulus"], seed=gi) for gi, c in enumerate(cost)]
+    net = groups.GroupedNetwork(graph, contexts={gi: p[0] for gi, p in enumerate(pairs)})
+    assert net.order == [0, 1]
+    res = net.evaluate([torch.tensor(x, device="cuda")], first_ct_id=0)
+    torch.cuda.synchronize()
+    rot, out_node = 3, 7
+    assert graph["nodes"][rot]["kind"] == "rotate" and graph["nodes"][out_node]["kind"] == "output"
+    # group 0: input -> conv -> sigmoid -> (rotation)
+    g0, o0 = pairs[0]
+    cts = [o0.encrypt(o0.encode(x[i]), i) for i in range(x.shape[0])]
+    seg0 = W.chain_graph(x.shape[0], graph["nodes"][1:3])
+    want0 = ckks.eval_graph(o0, seg0, [0], [cts])
+    (_, y0), = want0.items()
+    dev0, L0, sc0 = net.last_sinks[rot]
+    got0 = download(g0, dev0.contiguous(), L0)
+    for k, y in enumerate(y0):
+        assert y.level == L0 and sc0[k] == y.scale
+        assert np.array_equal(got0[k], y.c), k
+    # group 1 from the device's refreshed ciphertexts: dense -> sigmoid -> dense
+    g1, o1 = pairs[1]
+    ref_in = net.last_ingress[rot]
+    fresh = download(g1, ref_in, g1.L_top)
+    cts1 = [ckks.Ciphertext(fresh[k], g1.L_top, o1.delta) for k in range(fresh.shape[0])]
+    seg1 = W.chain_graph(fresh.shape[0], graph["nodes"][4:7])
+    want1 = ckks.eval_graph(o1, seg1, [0], [cts1])
+    (_, y1), = want1.items()
+    dev1, L1, sc1 = net.last_sinks[out_node]
+    got1 = download(g1, dev1.contiguous(), L1)
+    for k, y in enumerate(y1):
+        assert np.array_equal(got1[k], y.c), k
+    ref = ckks.forward_fp64(graph, W.input_nodes(graph), [x])
+    assert float(np.max(np.abs(res[out_node].cpu().numpy() - ref[out_node]))) < 1e-4
+    net.close()
+
+
 # ---------------------------------------------------------------- uneven levels, one launch per step
 def test_mul_relin_rescale_levels_matches_per_batch_and_oracle():
     g, o = pair(1024, BITS9)
