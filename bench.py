@@ -28,6 +28,11 @@ DOMINANT = "keyswitch_modup_mac"
 # GB300 figures used by the ALU roofline (recipe: 152 SMs, 2070 MHz max SM clock;
 # 64 INT32 multiply lanes per SM = 4 SMSPs x 16)
 SMS, SM_MHZ_MAX, MUL32_LANES = 152, 2070.0, 64
+# DRAM bytes (read + write) of the key-switching ModUp + key-product kernel
+# per (ciphertext, target prime, digit) unit, from one ncu capture of that
+# kernel (schedule 5) on 64 ciphertexts at L = 7: 232.7 MB read + 118.1 MB
+# written over 64 * 8 * 7 units.  Scaled by units to the bench's launches.
+KS_DRAM_BYTES_PER_UNIT = (232.722944e6 + 118.0544e6) / (64 * 8 * 7)
 
 
 def _env_rank():
@@ -58,6 +63,10 @@ def workload(name):
         g, x = W.cnn_relu()
         return g, x, ("encrypted CNN 28x28x1, conv5x5x5/2 -> ReLU approx (Eq. relu_approximate, q=4) -> 720x100 "
                       "-> sigmoid3 -> 100x10")
+    if name == "cnn_rotate":
+        g, x = W.cnn_rotate()
+        return g, x, ("encrypted CNN with a rotation (client refresh) after the first sigmoid: groups "
+                      "conv5x5x5/2 -> sigmoid3 | 720x100 -> sigmoid3 -> 100x10")
     if name == "deep":
         g, x = W.deep_mlp(n_slots=16384, n_in=64, hidden=64, n_out=8)
         return g, x, "depth-8 MLP 64 -> 64 -> sigmoid3 -> 64 -> sigmoid3 -> 8 -> x^2 (N=32768, [60,40x8,60])"
@@ -221,10 +230,14 @@ def run_ours(args):
     for node in g["nodes"]:
         if node["kind"] == "linear":
             L -= 1
-        elif node["kind"] == "poly":
+        elif node["kind"] in ("poly", "relu"):
+            deg = len(node["coeffs"]) - 1 if node["kind"] == "poly" else 2
             n = n_out_prev
-            plan += [(n, L), (n, L - 1)]
-            L -= 2
+            if deg == 3:
+                plan += [(n, L), (n, L - 1)]
+            elif deg == 2:
+                plan += [(n, L)]
+            L -= 1 if deg == 1 else 2
         elif node["kind"] == "square":
             plan += [(n_out_prev, L)]
             L -= 1
@@ -238,8 +251,12 @@ def run_ours(args):
         per_launch_ms = prof_ms / prof_timed
         achieved = work / (prof_ms / 1000.0) / 1e12
         peak = SMS * MUL32_LANES * SM_MHZ_MAX * 1e6 / 1e12
+        units = sum(n * (Lr + 1) * Lr for n, Lr in plan)       # (ciphertext, target, digit) transforms
+        traffic = args.traffic
+        if traffic is None and plan:
+            traffic = round(KS_DRAM_BYTES_PER_UNIT * units / len(plan))
         roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
-                "unit": "T int32-mul/s", "frac": round(achieved / peak, 4), "traffic": args.traffic,
+                "unit": "T int32-mul/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                 "kernel": DOMINANT, "launches": prof_n, "avg_launch_ms": round(per_launch_ms, 4),
                 "share_of_step": round(prof_ms / dev_ms, 4),
                 "peak_source": "derived: 152 SMs x 64 INT32 multiply lanes x 2070 MHz"}
@@ -514,8 +531,70 @@ def poisson_requests(nets, seconds, lam=200.0, weights=(0.5, 0.3, 0.2), seed=4):
     return reqs
 
 
+def run_grouped(args):
+    """A network with rotation nodes: one context per parameter group
+    (Alg. autoHE + parameterise per group), each group on the device, the
+    client refresh (decrypt, decode, encode, encrypt) between groups on the
+    device too.  Step = one request through every group."""
+    import torch
+    import __graft_entry__
+    from paper_2110_13638_gb300 import fhe, groups
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    g, x, desc = workload(args.workload)
+    net = groups.GroupedNetwork(g)
+    dev = torch.device("cuda", 0)
+    slots = torch.tensor(x, dtype=torch.float64, device=dev)
+    host_slots = torch.tensor(x, dtype=torch.float64).pin_memory()
+    outs = [i for i, n in enumerate(g["nodes"]) if n["kind"] == "output"]
+    res = None
+    for k in range(args.warmup):
+        res = net.evaluate([slots], first_ct_id=k << 24)
+    torch.cuda.synchronize()
+    host_out = {o: torch.empty(tuple(res[o].shape), dtype=torch.float64).pin_memory() for o in outs}
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = fhe.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for k in range(args.steps):
+        net.evaluate([slots], first_ct_id=(args.warmup + k) << 24)
+    e1.record()
+    torch.cuda.synchronize()
+    dev_ms = e0.elapsed_time(e1)
+    launches = fhe.launch_count() - launches0
+    clk = clocks.stop()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record()
+    for k in range(args.steps):
+        slots.copy_(host_slots, non_blocking=True)
+        r = net.evaluate([slots], first_ct_id=(10 * args.steps + k) << 24)
+        for o in outs:
+            host_out[o].copy_(r[o], non_blocking=True)
+    e3.record()
+    torch.cuda.synchronize()
+    e2e_ms = e2.elapsed_time(e3)
+    samples = x.shape[1] * args.steps
+    line = {
+        "metric": METRIC, "value": round(samples / (dev_ms / 1000.0), 2), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dev_ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": DATA.get(args.workload, "synthetic"),
+        "config": {"workload": desc, "groups": [
+            {"cost": c, "N": net.ctx[i].N, "L_top": net.ctx[i].L_top} for i, c in enumerate(net.group_cost)],
+            "samples_per_request": int(x.shape[1])},
+        "e2e": {"value": round(samples / (e2e_ms / 1000.0), 2), "unit": UNIT,
+                "h2d_bytes_per_step": int(slots.numel() * 8),
+                "d2h_bytes_per_step": int(sum(res[o].numel() for o in outs) * 8)},
+        "gpu_launches": int(launches), "clocks": clk, "roofline": None,
+    }
+    print(json.dumps(line), flush=True)
+    net.close()
+
+
 def run_serve(args):
-    """Poisson arrivals (200 req/s, mix 0.5 / 0.3 / 0.2 of the dense+square
+    """Poisson arrivals (--serve-rate, 200 req/s by default; mix 0.5 / 0.3 / 0.2 of the dense+square
     network, the CNN and the yield MLP, 1..8192 samples each) for
     --serve-seconds, continuous batching under a 150 GB admission cap, against
     serial one-request-at-a-time evaluation on the same GPU."""
@@ -527,11 +606,12 @@ def run_serve(args):
     nets, ctxs = serving_setup(torch)
     cap = 150e9
     out = {"metric": "serve samples/s, p50/p99 ms", "unit": "samples/s", "n_gpus": 1,
-           "config": {"workload": "Poisson 200 req/s, mix 0.5/0.3/0.2 (dense+square N=8192 / CNN / yield MLP "
-                                  "N=16384), 1..8192 samples, %gs of arrivals, admission cap 150 GB" % args.serve_seconds,
+           "config": {"workload": "Poisson %g req/s, mix 0.5/0.3/0.2 (dense+square N=8192 / CNN / yield MLP "
+                                  "N=16384), 1..8192 samples, %gs of arrivals, admission cap 150 GB"
+                                  % (args.serve_rate, args.serve_seconds),
                       "parameter_sets": len(ctxs)}}
     for mode in ("continuous", "serial"):
-        reqs = poisson_requests(nets, args.serve_seconds)
+        reqs = poisson_requests(nets, args.serve_seconds, lam=args.serve_rate)
         offered = sum(r.n for r in reqs) / args.serve_seconds
         if mode == "continuous":
             srv = serve.Server(nets, {"dense_square": 2, "cnn": 3, "mlp": 2}, cap, pack=True)
@@ -585,8 +665,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cnn", choices=["cnn", "mlp", "dense_square", "cnn_relu", "deep", "batch", "ntt_sweep", "serve"])
+    ap.add_argument("--workload", default="cnn", choices=["cnn", "mlp", "dense_square", "cnn_relu", "deep", "cnn_rotate",
+                                                          "batch", "ntt_sweep", "serve"])
     ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--batch-cts", type=int, default=4096)
     ap.add_argument("--profile-family", default=DOMINANT)
     ap.add_argument("--traffic", type=float, default=None,
@@ -603,6 +685,8 @@ def main():
         run_ntt_sweep(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "cnn_rotate":
+        run_grouped(args)
     else:
         run_ours(args)
 
