@@ -28,6 +28,7 @@ from .params import (prime_chain, primitive_2n_root, gauss_cdt, GAUSS_KMAX,
 # sampling domains of the counter-based generator
 DOM_SECRET, DOM_PK_A, DOM_PK_E, DOM_KSK_A, DOM_KSK_E = 1, 2, 3, 4, 5
 DOM_ENC_U, DOM_ENC_E0, DOM_ENC_E1 = 6, 7, 8
+DOM_GAL_A, DOM_GAL_E = 9, 10          # Galois (rotation) keys: object id = (k << 8) | digit
 
 
 def llround(x):
@@ -128,6 +129,69 @@ class Context:
                 self.ksk[j, 0, r] = b
                 self.ksk[j, 1, r] = a
 
+    # -- rotations (Galois automorphisms) ----------------------------------
+    def galois_element(self, r):
+        """k = 5^r mod 2N: X -> X^k moves slot j + r to slot j (rotation left
+        by r); 5 has order N/2 modulo 2N, so r is taken modulo N/2."""
+        return pow(5, r % (self.N // 2), 2 * self.N)
+
+    def automorphism(self, a, k, primes):
+        """a(X) -> a(X^k) mod X^N + 1 for residue rows a [len(primes)][N] in
+        coefficient form: coefficient i moves to i k mod 2N, negated when that
+        exponent is N or more."""
+        N = self.N
+        i = np.arange(N, dtype=np.int64)
+        pos = (i * k) % (2 * N)
+        dst = pos % N
+        neg = pos >= N
+        out = np.zeros_like(a)
+        for r, p in enumerate(primes):
+            v = a[r]
+            out[r, dst] = np.where(neg, (np.uint64(p) - v) % np.uint64(p), v)
+        return out
+
+    def galois_keygen(self, k):
+        """Key switching key from s(X^k) to s, in the relinearisation key's
+        form with s(X^k) in place of s^2:
+            gk_j = (-a_j s + e_j + [r == j] P s(X^k),  a_j)  over q_0..q_{L-1}, P"""
+        N, Lt = self.N, self.L_top
+        if not hasattr(self, "gk"):
+            self.gk = {}
+        if k in self.gk:
+            return self.gk[k]
+        sk = self.automorphism(np.stack([to_residue(self.s_int, p) for p in self.key_primes]), k, self.key_primes)
+        gk = np.zeros((Lt, 2, Lt + 1, N), dtype=np.uint64)
+        for j in range(Lt):
+            s_a = core.stream(self.seed, DOM_GAL_A, (k << 8) | j)
+            e_j = self._gauss(core.stream(self.seed, DOM_GAL_E, (k << 8) | j))
+            for r in range(Lt + 1):
+                p = self.key_primes[r]
+                a = core.sample_uniform(s_a, r, p, N)
+                b = (to_residue(e_j, p) + (np.uint64(p) - self.mul(a, self.s[r], r)) % np.uint64(p)) % np.uint64(p)
+                if r == j:
+                    b = (b + core.vec_mul_scalar(sk[r], self.P % p, p)) % np.uint64(p)
+                gk[j, 0, r] = b
+                gk[j, 1, r] = a
+        self.gk[k] = gk
+        return gk
+
+    def rotate(self, ct, r):
+        """Slots rotated left by r: (c0(X^k), c1(X^k)) with k = 5^r, then
+        c1(X^k) switched from s(X^k) to s with the Galois key:
+            out = (c0(X^k) + ks_0, ks_1),  ks = keyswitch(c1(X^k), gk_k)"""
+        k = self.galois_element(r)
+        L = ct.level
+        prim = self.q[:L]
+        c0 = self.automorphism(ct.c[0], k, prim)
+        c1 = self.automorphism(ct.c[1], k, prim)
+        ks = self.mod_down(self.keyswitch_accumulate(c1, L, self.galois_keygen(k)), L)
+        c = np.empty((2, L, self.N), dtype=np.uint64)
+        for t in range(L):
+            q = np.uint64(self.q[t])
+            c[0, t] = (c0[t] + ks[0, t]) % q
+            c[1, t] = ks[1, t]
+        return Ciphertext(c, L, ct.scale)
+
     # -- encode / encrypt / decrypt / decode -------------------------------
     def encode(self, z, scale=None, want_frac=False):
         """Canonical-embedding encode of N/2 real slots; integer coefficients."""
@@ -219,12 +283,14 @@ class Context:
             d[2, r] = self.mul(a.c[1, r], b.c[1, r], r)
         return Ciphertext(d, L, a.scale * b.scale)
 
-    def keyswitch_accumulate(self, d2, L):
+    def keyswitch_accumulate(self, d2, L, key=None):
         """Inner product of the per-prime digits with the key: digit j is
         residue j of d2 ([L][N], coefficient form) lifted to [0, q_j) and
         reduced into every prime of q_0..q_{L-1}, P;
-        acc_k = sum_j digit_j * ksk_j[k]  over those L+1 primes."""
+        acc_k = sum_j digit_j * ksk_j[k]  over those L+1 primes
+        (key: the relinearisation key unless another is given)."""
         N, Lt = self.N, self.L_top
+        ksk = self.ksk if key is None else key
         targets = list(range(L)) + [Lt]          # key residue indices
         acc = np.zeros((2, L + 1, N), dtype=np.uint64)
         for j in range(L):
@@ -233,7 +299,7 @@ class Context:
                 p = self.key_primes[kr]
                 Dt = D % np.uint64(p)
                 for k in range(2):
-                    prod = self.mul(Dt, self.ksk[j, k, kr], kr)
+                    prod = self.mul(Dt, ksk[j, k, kr], kr)
                     acc[k, ti] = (acc[k, ti] + prod) % np.uint64(p)
         return acc
 

@@ -283,6 +283,71 @@ def test_node_costs_of_activations():
     assert ckks.graph_depth(g, W.input_nodes(g)) == 7
 
 
+# ---------------------------------------------------------------- rotations
+def _eval_at(coeffs, x, q):
+    acc = 0
+    for c in reversed([int(v) for v in coeffs]):
+        acc = (acc * x + c) % q
+    return acc
+
+
+def test_automorphism_is_substitution_at_the_roots(ctx16):
+    """(a o X^k)(psi^e) = a(psi^(e k)) at every odd power e (the roots of
+    X^N + 1), by Horner evaluation with Python integers."""
+    ctx = ctx16
+    N, q = ctx.N, ctx.q[0]
+    psi = ctx.psi[0]
+    rng = np.random.default_rng(21)
+    a = rng.integers(0, q, N, dtype=np.uint64)
+    for k in (5, 25, 2 * N - 1, ctx.galois_element(3)):
+        b = ctx.automorphism(a[None], k, [q])[0]
+        for e in (1, 3, 7, 2 * N - 1):
+            x = pow(psi, e, q)
+            assert _eval_at(b, x, q) == _eval_at(a, pow(psi, e * k, q), q), (k, e)
+
+
+def test_galois_elements_cycle_with_order_half_n():
+    ctx = ckks.Context(64, BITS4)
+    ks = [ctx.galois_element(r) for r in range(32)]
+    assert len(set(ks)) == 32 and all(k % 2 == 1 for k in ks)
+    assert ctx.galois_element(32) == 1 and ctx.galois_element(-1) == ks[31]
+
+
+def test_rotation_rolls_the_slots(ctx64):
+    ctx = ctx64
+    N = ctx.N
+    z = np.random.default_rng(22).uniform(-1, 1, N // 2)
+    ct = ctx.encrypt(ctx.encode(z), 9)
+    for r in (1, 3, -2, 17):
+        y = ctx.rotate(ct, r)
+        assert y.level == ct.level and y.scale == ct.scale
+        got = ctx.decode(ctx.decrypt(y), y.scale)
+        assert np.max(np.abs(got - np.roll(z, -r))) < 1e-6, r
+    # rotations compose: rot(rot(x, 2), 3) = rot(x, 5)
+    y = ctx.rotate(ctx.rotate(ct, 2), 3)
+    assert np.max(np.abs(ctx.decode(ctx.decrypt(y), y.scale) - np.roll(z, -5))) < 1e-6
+
+
+def test_galois_key_switches_from_the_rotated_secret(ctx16):
+    """The key-switched component decrypts to c1(X^k) s(X^k) up to small noise:
+    ks_0 + ks_1 s - c1(X^k) s(X^k) is small modulo Q_L."""
+    ctx = ctx16
+    L = ctx.L_top
+    rng = np.random.default_rng(23)
+    c1 = np.stack([rng.integers(0, q, ctx.N, dtype=np.uint64) for q in ctx.q[:L]])
+    k = ctx.galois_element(1)
+    ks = ctx.mod_down(ctx.keyswitch_accumulate(c1, L, ctx.galois_keygen(k)), L)
+    sk = [int(v) for v in ctx.automorphism(np.array([[int(x) % ctx.q[0] for x in ctx.s_int]], dtype=np.uint64), k,
+                                                    [ctx.q[0]])[0]]
+    # reduce everything mod q_0 and compare phases there
+    q = ctx.q[0]
+    s = [int(x) % q for x in ctx.s_int]
+    lhs = [(int(a) + int(b)) % q for a, b in zip(ks[0, 0], _schoolbook_z([int(v) for v in ks[1, 0]], s))]
+    rhs = [x % q for x in _schoolbook_z([int(v) for v in c1[0]], sk)]
+    diff = [((a - b + q // 2) % q) - q // 2 for a, b in zip(lhs, rhs)]
+    assert max(abs(d) for d in diff) < 2 ** 20
+
+
 def test_sigmoid_fit_reproduces_printed_coefficients():
     got = W.sigmoid_fit()
     want = golden_io.sigmoid_coeffs()
