@@ -208,6 +208,24 @@ int fhe_decrypt(fhe_ctx* ctx, const uint64_t* d_ct, uint32_t n_ct, uint32_t leve
 int fhe_decode(fhe_ctx* ctx, const int64_t* d_m, uint32_t n_ct, double scale,
                double* d_slots, void* stream);
 
+/* ---- rotations (slot rotation by a Galois automorphism) ------------------
+ * Needed by slot-packed layouts (the paper's kernel masquerading, Sec. 3.2,
+ * rotates ciphertexts to line pixels up with kernel positions).  Rotation
+ * by r moves slot j + r to slot j (left), via X -> X^k, k = 5^r mod 2N, and a
+ * key switch from s(X^k) back to s with a rotation key. */
+
+/* Generate (once per parameter set, on the parent context) the rotation keys
+ * for the given slot steps; each is resident like the relinearisation key
+ * (L_top x 2 x (L_top + 1) x N x 16 bytes).  Keys already present are kept.
+ * Sampling: domains 9 (uniform) and 10 (noise), object (k << 8) | digit.
+ * Synchronises `stream`. */
+int fhe_galois_keygen(fhe_ctx* ctx, const int32_t* steps, uint32_t n_steps, void* stream);
+
+/* d_out [n_ct][2][level][N] = rotation of d_ct by `step` slots (NTT form).
+ * FHE_ENOKEY if the rotation key of that step has not been generated. */
+int fhe_rotate(fhe_ctx* ctx, const uint64_t* d_ct, uint32_t n_ct, uint32_t level, int32_t step, uint64_t* d_out,
+               void* stream);
+
 /* ---- layout conversion (parity export / import) ------------------------- */
 
 /* n_poly residue polynomials [n_poly][rows][N]: rows-th row r belongs to

@@ -261,6 +261,7 @@ static void free_ctx(fhe_ctx* c)
     cudaFree(c->d_s);
     cudaFree(c->d_pk);
     cudaFree(c->d_ksk);
+    for (auto& kv : c->galois) cudaFree(kv.second);
     cudaFree(c->ws);
     cudaFree(c->d_ntt2);
     delete c;
@@ -771,6 +772,70 @@ int fhe_relinearise(fhe_ctx* c, const uint64_t* d3, uint32_t n_ct, uint32_t leve
     if (rc) return rc;
     k_relin(c, (const u64*)d3, (u64*)out, n_ct, level, ar.take(need), (cudaStream_t)stream);
     CUDA_LAST("relinearise launch");
+    return FHE_OK;
+}
+
+static u64 galois_element(const fhe_ctx* c, int32_t step)
+{
+    const int64_t half = c->N / 2;
+    int64_t r = step % half;
+    if (r < 0) r += half;
+    u64 k = 1;
+    for (int64_t i = 0; i < r; ++i) k = (k * 5) % (2ull * c->N);
+    return k;
+}
+
+int fhe_galois_keygen(fhe_ctx* c, const int32_t* steps, uint32_t n_steps, void* stream)
+{
+    CHECK_CTX(c);
+    CHECK_KEYS(c);
+    if (c->parent) return fail(FHE_EINVAL, "generate rotation keys on the parent context");
+    if (n_steps && !steps) return fail(FHE_EINVAL, "null steps");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)c->L_top * 2 * (c->L_top + 1) * c->N * sizeof(ulonglong2);
+    for (uint32_t i = 0; i < n_steps; ++i) {
+        const u64 k = galois_element(c, steps[i]);
+        if (k == 1 || c->galois.count(k)) continue;         // identity, or already there
+        ulonglong2* key = nullptr;
+        cudaError_t e = cudaMalloc((void**)&key, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return cuda_check(e, "rotation key allocation");
+        }
+        k_galois_keygen(c, k, key, st);
+        c->galois[k] = key;
+        c->key_bytes += bytes;
+    }
+    CUDA_LAST("rotation keygen launch");
+    return cuda_check(cudaStreamSynchronize(st), "rotation keygen");
+}
+
+int fhe_rotate(fhe_ctx* c, const uint64_t* d_ct, uint32_t n_ct, uint32_t level, int32_t step, uint64_t* d_out,
+               void* stream)
+{
+    CHECK_CTX(c);
+    CHECK_KEYS(c);
+    CHECK_LEVEL(c, level, 1);
+    if (n_ct == 0) return FHE_OK;
+    if (!d_ct || !d_out) return fail(FHE_EINVAL, "null buffer");
+    const u64 k = galois_element(c, step);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t w = (size_t)n_ct * 2 * level * c->N * 8;
+    if (k == 1) {
+        if (d_out == d_ct) return FHE_OK;
+        return cuda_check(cudaMemcpyAsync(d_out, d_ct, w, cudaMemcpyDeviceToDevice, st), "rotate copy");
+    }
+    const fhe_ctx* root = c->parent ? c->parent : c;
+    auto it = root->galois.find(k);
+    if (it == root->galois.end()) return fail(FHE_ENOKEY, "no rotation key for this step (fhe_galois_keygen)");
+    Arena ar;
+    const size_t d3b = (size_t)n_ct * 3 * level * c->N * 8, rs = relin_scratch_bytes(c, n_ct, level);
+    int rc = ws_reserve(c, arena_need({d3b, rs}), &ar);
+    if (rc) return rc;
+    u64* d3 = (u64*)ar.take(d3b);
+    k_automorph(c, (const u64*)d_ct, d3, n_ct, level, k, st);
+    k_relin(c, d3, (u64*)d_out, n_ct, level, ar.take(rs), st, it->second);
+    CUDA_LAST("rotate launch");
     return FHE_OK;
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 #include <cstdint>
 #include <string>
+#include <map>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -41,6 +42,7 @@ struct fhe_ctx {
     u64* d_s = nullptr;            // [L_top + 1][N]
     u64* d_pk = nullptr;           // [2][L_top][N]
     ulonglong2* d_ksk = nullptr;   // [L_top][2][L_top + 1][N] (key word, Shoup quotient)
+    std::map<u64, ulonglong2*> galois;   // Galois element k -> rotation key (same layout); forks use the parent's
     size_t key_bytes = 0;
 
     // a fork shares tables and keys with its parent (which must outlive it)
@@ -161,7 +163,13 @@ void k_add(const fhe_ctx* c, const u64* a, const u64* b, u64* out, uint32_t n_ct
 void k_tensor(const fhe_ctx* c, const u64* a, const u64* b, u64* out3, uint32_t n_ct, uint32_t L, cudaStream_t st);
 // scratch: relin_scratch_bytes(n_ct, L)
 size_t relin_scratch_bytes(const fhe_ctx* c, uint32_t n_ct, uint32_t L);
-void k_relin(const fhe_ctx* c, const u64* d3, u64* out2, uint32_t n_ct, uint32_t L, void* scratch, cudaStream_t st);
+// key: the relinearisation key unless another key of the same layout is given
+void k_relin(const fhe_ctx* c, const u64* d3, u64* out2, uint32_t n_ct, uint32_t L, void* scratch, cudaStream_t st,
+             const ulonglong2* key = nullptr);
+// rotation key for Galois element k into `key` ([L_top][2][L_top + 1][N])
+void k_galois_keygen(fhe_ctx* c, u64 k, ulonglong2* key, cudaStream_t st);
+// d3 = (c0(X^k), 0, c1(X^k)) of ciphertexts [n][2][L][N] in NTT form
+void k_automorph(const fhe_ctx* c, const u64* ct, u64* d3, uint32_t n_ct, uint32_t L, u64 k, cudaStream_t st);
 // scratch: rescale_scratch_bytes; addc: optional constants (device residues,
 // addc[ct * addc_stride + i]) added to comp 0 of the result
 size_t rescale_scratch_bytes(const fhe_ctx* c, uint32_t n_ct, uint32_t comps);

@@ -62,6 +62,16 @@ __device__ __forceinline__ ulonglong2 with_shoup(u64 k, u64 q)
     return make_ulonglong2(k, (u64)(((unsigned __int128)k << 64) / q));
 }
 
+// A rotation key (galois = k, the Galois element) has s(X^k) in place of s^2.
+// In NTT form s(X^k) is a permutation of s: index j holds the evaluation at
+// psi^(2 brv(j) + 1), and s(X^k) there is s at psi^((2 brv(j) + 1) k).
+__device__ __forceinline__ int galois_index(int j, u64 k, int logN)
+{
+    const unsigned b = __brev((unsigned)j) >> (32 - logN);
+    const u64 e = ((2ull * b + 1ull) * k) & ((2ull << logN) - 1ull);
+    return (int)(__brev((unsigned)((e - 1) >> 1)) >> (32 - logN));
+}
+
 struct OpRelinKey {
     static const char* family() { return "keygen"; }
     const u64* s;
@@ -71,6 +81,8 @@ struct OpRelinKey {
     const u64* se;
     u64 Pmod[33];       // P mod q_r
     int Ltop, N;
+    u64 galois = 0;     // 0: relinearisation key (s^2); else rotation key for this k
+    int logN = 0;
     __host__ __device__ int count() const { return Ltop * (Ltop + 1); }
     __host__ __device__ int nsub(int) const { return 2; }
     __device__ int prime(int p, int) const { return p % (Ltop + 1); }
@@ -80,13 +92,14 @@ struct OpRelinKey {
         const int dj = p / (Ltop + 1), r = p % (Ltop + 1);
         return u == 0 ? draw_uniform(sa[dj], j, r, P) : from_signed(draw_gauss(se[dj], j, cdt), P);
     }
-    struct Pre { u64 sr, b; };
+    struct Pre { u64 sr, b, sk; };
     __device__ Pre pre(int p, int u, int j) const
     {
         const int dj = p / (Ltop + 1), r = p % (Ltop + 1);
         Pre x;
         x.sr = s[(size_t)r * N + j];
         x.b = u == 1 ? ksk[(((size_t)dj * 2 + 0) * (Ltop + 1) + r) * N + j].x : 0;
+        x.sk = (galois && u == 1 && r == dj) ? s[(size_t)r * N + galois_index(j, galois, logN)] : 0;
         return x;
     }
     __device__ void store(int p, int u, int j, u64 v, const Pre& pr, const PrimeC& P) const
@@ -99,7 +112,7 @@ struct OpRelinKey {
             b[j] = make_ulonglong2(sub_mod(0, mul_mod(v, pr.sr, P), P.q), 0);
         } else {
             u64 x = add_mod(pr.b, v, P.q);
-            if (r == dj) x = add_mod(x, mul_mod(Pmod[r], mul_mod(pr.sr, pr.sr, P), P), P.q);
+            if (r == dj) x = add_mod(x, mul_mod(Pmod[r], galois ? pr.sk : mul_mod(pr.sr, pr.sr, P), P), P.q);
             b[j] = with_shoup(x, P.q);
         }
     }
@@ -131,6 +144,61 @@ void k_keygen(fhe_ctx* c, cudaStream_t st)
     ok.N = N;
     launch_ntt<false>(c, ok, st);
     cudaFreeAsync(dkeys, st);
+}
+
+void k_galois_keygen(fhe_ctx* c, u64 k, ulonglong2* key, cudaStream_t st)
+{
+    const int N = (int)c->N, Lt = (int)c->L_top;
+    std::vector<u64> h(2 * Lt);
+    for (int j = 0; j < Lt; ++j) {
+        h[j] = stream_key(c->seed, DOM_GAL_A, (k << 8) | (u64)j);
+        h[Lt + j] = stream_key(c->seed, DOM_GAL_E, (k << 8) | (u64)j);
+    }
+    u64* dkeys = nullptr;
+    cudaMallocAsync((void**)&dkeys, h.size() * 8, st);
+    cudaMemcpyAsync(dkeys, h.data(), h.size() * 8, cudaMemcpyHostToDevice, st);
+    OpRelinKey ok;
+    ok.s = c->d_s;
+    ok.ksk = key;
+    ok.cdt = c->d_cdt;
+    ok.sa = dkeys;
+    ok.se = dkeys + Lt;
+    for (int r = 0; r <= Lt && r < 33; ++r) ok.Pmod[r] = c->primes[Lt] % c->primes[r];
+    ok.Ltop = Lt;
+    ok.N = N;
+    ok.galois = k;
+    ok.logN = (int)c->logN;
+    launch_ntt<false>(c, ok, st);
+    cudaFreeAsync(dkeys, st);
+}
+
+// (c0(X^k), 0, c1(X^k)): NTT-form automorphism is the index permutation above
+__global__ void k_automorph_kernel(const u64* __restrict__ ct, u64* __restrict__ d3, size_t total, int L, int logN,
+                                   u64 k)
+{
+    const size_t Nm = ((size_t)1 << logN) - 1;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = i >> logN;           // (ct, comp of d3, r)
+        const int r = (int)(row % L);
+        const size_t rest = row / L;
+        const int comp = (int)(rest % 3);
+        const size_t n = rest / 3;
+        const int j = (int)(i & Nm);
+        u64 v = 0;
+        if (comp != 1) {
+            const int src_comp = comp == 0 ? 0 : 1;
+            v = ct[(((n * 2 + src_comp) * L + r) << logN) + galois_index(j, k, logN)];
+        }
+        d3[i] = v;
+    }
+}
+
+void k_automorph(const fhe_ctx* c, const u64* ct, u64* d3, uint32_t n_ct, uint32_t L, u64 k, cudaStream_t st)
+{
+    const size_t total = (size_t)n_ct * 3 * L * c->N;
+    if (!total) return;
+    LaunchScope ls(c, "elementwise", st);
+    k_automorph_kernel<<<ew_grid(total), 256, 0, st>>>(ct, d3, total, (int)L, (int)c->logN, k);
 }
 
 // ---------------------------------------------------------------- encrypt

@@ -9,7 +9,8 @@ size_t relin_scratch_bytes(const fhe_ctx* c, uint32_t n_ct, uint32_t L)
     return arena_need({(size_t)n_ct * L * N * 8, (size_t)n_ct * 2 * (L + 1) * N * 8, (size_t)n_ct * 2 * N * 8});
 }
 
-void k_relin(const fhe_ctx* c, const u64* d3, u64* out2, uint32_t n_ct, uint32_t L, void* scratch, cudaStream_t st)
+void k_relin(const fhe_ctx* c, const u64* d3, u64* out2, uint32_t n_ct, uint32_t L, void* scratch, cudaStream_t st,
+             const ulonglong2* key)
 {
     if (n_ct == 0) return;
     const size_t N = c->N;
@@ -22,7 +23,7 @@ void k_relin(const fhe_ctx* c, const u64* d3, u64* out2, uint32_t n_ct, uint32_t
 
     OpDigitsInv s1{d3, D, (int)n_ct, (int)L, (int)N};
     launch_ntt<true>(c, s1, st);
-    OpModUpMac s2{d3, D, c->d_ksk, acc, (int)n_ct, (int)L, (int)N, (int)c->L_top, modup_red_mask(c, L)};
+    OpModUpMac s2{d3, D, key ? key : c->d_ksk, acc, (int)n_ct, (int)L, (int)N, (int)c->L_top, modup_red_mask(c, L)};
     launch_ntt<false>(c, s2, st);
     OpAccPInv s3{acc, Vp, (int)n_ct, (int)L, (int)N, (int)c->L_top};
     launch_ntt<true>(c, s3, st);

@@ -12,7 +12,7 @@
 namespace fhe {
 
 enum { DOM_SECRET = 1, DOM_PK_A = 2, DOM_PK_E = 3, DOM_KSK_A = 4, DOM_KSK_E = 5,
-       DOM_ENC_U = 6, DOM_ENC_E0 = 7, DOM_ENC_E1 = 8 };
+       DOM_ENC_U = 6, DOM_ENC_E0 = 7, DOM_ENC_E1 = 8, DOM_GAL_A = 9, DOM_GAL_E = 10 };
 
 static constexpr u64 kGamma = 0x9E3779B97F4A7C15ull;
 

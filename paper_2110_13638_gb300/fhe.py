@@ -105,6 +105,8 @@ SIGNATURES = {
     "fhe_graph_outputs": [_P, _P, _P, _P],
     "fhe_eval_graph": [_P, _P, _P, _U32, _P, _P, _U32, _P],
     "fhe_eval_batch": [_P, _P, _P, _U32, _U64, _P],
+    "fhe_galois_keygen": [_P, _P, _U32, _P],
+    "fhe_rotate": [_P, _P, _U32, _U32, ctypes.c_int32, _P, _P],
     "fhe_profile_begin": [_P, ctypes.c_char_p, _U32],
     "fhe_profile_end": [_P, _P, _P, _P],
     "fhe_profile_families": [],
@@ -345,6 +347,14 @@ class Context:
 
     def tensor(self, a, b, level, out, stream=None):
         _check(lib().fhe_tensor(self.h, _ptr(a), _ptr(b), a.shape[0], level, _ptr(out), _stream(stream)))
+
+    def galois_keygen(self, steps, stream=None):
+        """Rotation keys for the given slot steps (parent context)."""
+        arr = _arr([int(v) for v in steps], ctypes.c_int32)
+        _check(lib().fhe_galois_keygen(self.h, arr, len(steps), _stream(stream)))
+
+    def rotate(self, ct, level, step, out, stream=None):
+        _check(lib().fhe_rotate(self.h, _ptr(ct), ct.shape[0], level, int(step), _ptr(out), _stream(stream)))
 
     def relinearise(self, d3, level, out, stream=None):
         _check(lib().fhe_relinearise(self.h, _ptr(d3), d3.shape[0], level, _ptr(out), _stream(stream)))

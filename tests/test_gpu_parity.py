@@ -280,6 +280,38 @@ def test_graph_cfg0_full_size_bit_exact():
     assert err < 1e-4
 
 
+@pytest.mark.parametrize("N,bits,L,steps", [(1024, BITS9, 8, [1, 3, -2, 100]), (1024, BITS9, 3, [5]),
+                                             (16384, BITS9, 8, [1, 28])])
+def test_rotation_bit_exact(N, bits, L, steps):
+    """Galois automorphism in NTT form (index permutation) + key switch with
+    the rotation key: bit-exact against the oracle's coefficient-form
+    substitution and its rotation keys."""
+    g, o = pair(N, bits)
+    g.galois_keygen(steps)
+    rng = np.random.default_rng(N + L)
+    A = rand_ct(o, L, rng)
+    ta = upload(g, [A], L)
+    for r in steps:
+        out = g.empty_ct(1, L)
+        g.rotate(ta, L, r, out)
+        want = o.rotate(ckks.Ciphertext(A, L, 1.0), r).c
+        assert np.array_equal(download(g, out, L)[0], want), r
+    # an encrypted vector decrypts rolled
+    z = rng.uniform(-1, 1, size=(1, N // 2))
+    ct = g.empty_ct(1, g.L_top)
+    g.encode_encrypt(torch.tensor(z, device="cuda"), g.delta, 4242, ct)
+    g.galois_keygen([7])
+    rot = g.empty_ct(1, g.L_top)
+    g.rotate(ct, g.L_top, 7, rot)
+    m = torch.empty((1, N), dtype=torch.int64, device="cuda")
+    g.decrypt(rot, g.L_top, m)
+    zs = torch.empty((1, N // 2), dtype=torch.float64, device="cuda")
+    g.decode(m, g.delta, zs)
+    assert float(np.max(np.abs(zs.cpu().numpy()[0] - np.roll(z[0], -7)))) < 1e-6
+    with pytest.raises(fhe.FheError):
+        g.rotate(ct, g.L_top, 11, rot)          # no key for this step
+
+
 def test_graph_relu_and_affine_bit_exact():
     """Eq. relu_approximate (degree 2) after the convolution and the linear
     sigmoid 0.5 + 0.197 x (degree 1) after the dense layer."""
