@@ -192,6 +192,66 @@ class Context:
             c[1, t] = ks[1, t]
         return Ciphertext(c, L, ct.scale)
 
+    # -- plaintext vectors (slot-wise products) ----------------------------
+    def mul_plain(self, ct, m, sigma):
+        """Slot-wise product with a plaintext vector: every component times
+        the encoded plaintext m (int64 coefficients, scale sigma), a ring
+        product in each prime."""
+        c = np.empty_like(ct.c)
+        for r in range(ct.level):
+            mr = to_residue(m, self.q[r])
+            for k in range(ct.c.shape[0]):
+                c[k, r] = self.mul(ct.c[k, r], mr, r)
+        return Ciphertext(c, ct.level, ct.scale * sigma)
+
+    def add_plain(self, ct, m):
+        """Slot-wise sum with a plaintext vector (encoded at the ciphertext's scale)."""
+        c = ct.c.copy()
+        for r in range(ct.level):
+            q = np.uint64(self.q[r])
+            c[0, r] = (c[0, r] + to_residue(m, self.q[r])) % q
+        return Ciphertext(c, ct.level, ct.scale)
+
+    def conv_packed(self, xs, node):
+        """Kernel masquerading (Sec. 3.2) with the sum done by rotations: the
+        images packed in a ciphertext (image b's pixel (i, j) at slot
+        b S + i W + j) are convolved with every filter at once.  For each kernel
+        position (dr, dc) the ciphertext is rotated by dr W + dc so that the
+        pixel under that kernel position sits at its output slot; the merged
+        mask-and-kernel vector (weight K[f, dr, dc] at the valid output slots
+        b S + s r W + s c, zero elsewhere) multiplies it slot-wise; the k^2
+        products are summed, rescaled, and the bias vector is added:
+            y_f = rescale(sum_p rot(x, off_p) * encode(M_fp, q_{L-1})) + encode(b_f V, s_y)
+        Outputs are filter-major: y[f * n + i] for input ciphertext i."""
+        F, k = node["filters"], node["k"]
+        M = self.N // 2
+        L, s = xs[0].level, xs[0].scale
+        q = float(self.q[L - 1])
+        valid = packed_valid_slots(node, M)
+        offs = [dr * node["W"] + dc for dr in range(k) for dc in range(k)]
+        W_ = np.asarray(node["weight"], dtype=np.float64).reshape(F, k * k)
+        masks = []
+        for f in range(F):
+            row = []
+            for p in range(k * k):
+                v = np.zeros(M)
+                v[valid] = W_[f, p]
+                row.append(self.encode(v, q))
+            masks.append(row)
+        out = [[None] * len(xs) for _ in range(F)]
+        for i, x in enumerate(xs):
+            rots = [x if o == 0 else self.rotate(x, o) for o in offs]
+            for f in range(F):
+                acc = None
+                for p in range(k * k):
+                    t = self.mul_plain(rots[p], masks[f][p], q)
+                    acc = t if acc is None else self.add(acc, t)
+                y = self.rescale(acc)
+                bv = np.zeros(M)
+                bv[valid] = float(node["bias"][f])
+                out[f][i] = self.add_plain(y, self.encode(bv, y.scale))
+        return [ct for row in out for ct in row]
+
     # -- encode / encrypt / decrypt / decode -------------------------------
     def encode(self, z, scale=None, want_frac=False):
         """Canonical-embedding encode of N/2 real slots; integer coefficients."""
@@ -525,6 +585,8 @@ def eval_graph(ctx, graph, inputs, signals):
             return s
         if k == "linear":
             return ctx.linear(s, csr_rows(node), node["bias"])
+        if k == "conv_packed":
+            return ctx.conv_packed(s, node)
         if k == "poly":
             return [ctx.poly(x, node["coeffs"]) for x in s]
         if k == "relu":
@@ -537,6 +599,34 @@ def eval_graph(ctx, graph, inputs, signals):
         raise ValueError(k)
 
     return fire(graph, inputs, signals, apply_fn, lambda sigs: _stack_cts(ctx, sigs, None))
+
+
+def packed_valid_slots(node, M):
+    """Output slots b S + s r W + s c of a packed convolution (b < images,
+    r, c < output side), in image, row, column order."""
+    S, W, st, k = node["slot_stride"], node["W"], node["stride"], node["k"]
+    OH = (node["H"] - k) // st + 1
+    OW = (W - k) // st + 1
+    idx = [b * S + st * r * W + st * c for b in range(node["images"]) for r in range(OH) for c in range(OW)]
+    assert max(idx) < M
+    return np.array(idx, dtype=np.int64)
+
+
+def relayout_packed(z, node, n_in):
+    """Client side of a refresh after a packed convolution: decoded filter
+    ciphertexts z [F * n_in][slots] (filter-major) -> one row per feature
+    f * OH * OW + r * OW + c, one column per image i * images + b."""
+    F = node["filters"]
+    M = z.shape[1]
+    valid = packed_valid_slots(node, M)
+    per_img = len(valid) // node["images"]
+    out = np.zeros((F * per_img, M))
+    for f in range(F):
+        for i in range(n_in):
+            v = z[f * n_in + i][valid].reshape(node["images"], per_img)
+            for b in range(node["images"]):
+                out[f * per_img:(f + 1) * per_img, i * node["images"] + b] = v[b]
+    return out
 
 
 def refresh_ct_id(node, k):
@@ -578,12 +668,17 @@ def eval_graph_grouped(ctxs, graph, signals):
             return s
         if k == "rotate":
             up, down = ctxs[group_above(n)], ctxs[group_of[n]]
-            out = []
-            for i, ct in enumerate(s):
-                z = up.decode(up.decrypt(ct), ct.scale)
-                out.append(down.encrypt(down.encode(z), refresh_ct_id(n, i)))
-            return out
+            z = np.stack([up.decode(up.decrypt(ct), ct.scale) for ct in s])
+            if "relayout" in node:                    # client re-packs the slots
+                geo = node["relayout"]
+                z = relayout_packed(z, geo, len(s) // geo["filters"])
+            Md = down.N // 2
+            if z.shape[1] < Md:
+                z = np.pad(z, ((0, 0), (0, Md - z.shape[1])))
+            return [down.encrypt(down.encode(z[i]), refresh_ct_id(n, i)) for i in range(z.shape[0])]
         ctx = ctxs[group_above(n)]
+        if k == "conv_packed":
+            return ctx.conv_packed(s, node)
         if k == "linear":
             return ctx.linear(s, csr_rows(node), node["bias"])
         if k == "poly":
@@ -625,8 +720,25 @@ def forward_fp64(graph, inputs, signals):
                 return out
             s = np.concatenate(edges, axis=0)
         k = node["kind"]
-        if k in ("input", "output", "rotate"):
+        if k in ("input", "output"):
             return s
+        if k == "rotate":
+            return relayout_packed(s, node["relayout"], s.shape[0] // node["relayout"]["filters"]) \
+                if "relayout" in node else s
+        if k == "conv_packed":
+            F, kk = node["filters"], node["k"]
+            valid = packed_valid_slots(node, s.shape[1])
+            W_ = np.asarray(node["weight"], dtype=np.float64).reshape(F, kk * kk)
+            offs = [dr * node["W"] + dc for dr in range(kk) for dc in range(kk)]
+            out = np.zeros((F * s.shape[0], s.shape[1]))
+            for f in range(F):
+                for i in range(s.shape[0]):
+                    acc = np.zeros(s.shape[1])
+                    for p, o in enumerate(offs):
+                        acc[valid] += W_[f, p] * np.roll(s[i], -o)[valid]
+                    acc[valid] += float(node["bias"][f])
+                    out[f * s.shape[0] + i] = acc
+            return out
         if k == "linear":
             rows = csr_rows(node)
             out = np.zeros((len(rows), s.shape[1]))

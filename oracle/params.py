@@ -23,7 +23,7 @@ def ingress_nodes(graph):
 
 def node_cost(node):
     k = node["kind"]
-    if k in ("linear", "square"):
+    if k in ("linear", "square", "conv_packed"):
         return 1
     if k == "poly":
         return 1 if len(node.get("coeffs", (0, 0, 0, 0))) == 2 else 2   # affine: one rescale

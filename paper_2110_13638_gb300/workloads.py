@@ -188,6 +188,40 @@ def mini_cnn_rotate(n_slots, seed=7):
     return with_rotation(g, 2), x
 
 
+def cnn_masquerade(n_ct, slots, seed=7, side=8, filters=2, k=3, stride=2, hidden=5, classes=3):
+    """Kernel masquerading (Sec. 3.2): images packed side by side in each
+    ciphertext (slot stride side^2), the convolution evaluated on the packed
+    ciphertexts (rotations line every pixel up with its output slot, the
+    merged mask-and-kernel vectors multiply slot-wise), a sigmoid fit on the
+    packed result, then a rotation (client refresh) where the client re-packs
+    the conv outputs one feature per ciphertext, images in slots, for the
+    dense layers.  Parameter groups of cost 3 and 4."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    S = side * side
+    images = slots // S
+    K = rng.normal(0.0, np.sqrt(2.0 / (k * k)), size=(filters, k, k))
+    OH = (side - k) // stride + 1
+    n_feat = filters * OH * OH
+    W1 = rng.normal(0.0, np.sqrt(2.0 / n_feat), size=(hidden, n_feat))
+    W2 = rng.normal(0.0, np.sqrt(2.0 / hidden), size=(classes, hidden))
+    b0 = rng.normal(0.0, 0.1, size=filters)
+    geo = {"H": side, "W": side, "k": k, "stride": stride, "filters": filters, "images": images, "slot_stride": S}
+    conv = dict(geo, kind="conv_packed", weight=K, bias=b0)
+    sig = sigmoid_fit()
+    nodes = [{"kind": "input", "n": n_ct}, conv, {"kind": "poly", "coeffs": sig},
+             {"kind": "rotate", "relayout": geo},
+             _linear(*dense_csr(W1), rng.normal(0.0, 0.1, size=hidden)),
+             {"kind": "poly", "coeffs": sig},
+             _linear(*dense_csr(W2), np.zeros(classes)), {"kind": "output"}]
+    edges = [(i, i + 1) for i in range(len(nodes) - 1)]
+    imgs = rng.uniform(0.0, 1.0, size=(n_ct * images, S))
+    x = np.zeros((n_ct, slots))
+    for i in range(n_ct):
+        for b in range(images):
+            x[i, b * S:(b + 1) * S] = imgs[i * images + b]
+    return {"nodes": nodes, "edges": edges}, x
+
+
 def deep_mlp(n_slots, seed=13, n_in=4, hidden=4, n_out=2):
     """Multiplicative depth 8 (dense, sigmoid fit, dense, sigmoid fit, dense,
     square), so Alg. parameterise asks for N = 32768 and [60, 40 x 8, 60]."""

@@ -348,6 +348,70 @@ def test_galois_key_switches_from_the_rotated_secret(ctx16):
     assert max(abs(d) for d in diff) < 2 ** 20
 
 
+# ---------------------------------------------------------------- kernel masquerading
+def _direct_conv(x, node, images, slots_per_img):
+    """features [F * OH * OW][n_ct * images] by plain loops over unpacked images"""
+    F, k, st, H, Wd = node["filters"], node["k"], node["stride"], node["H"], node["W"]
+    OH, OW = (H - k) // st + 1, (Wd - k) // st + 1
+    K = np.asarray(node["weight"])
+    cols = []
+    for i in range(x.shape[0]):
+        for b in range(images):
+            img = x[i, b * slots_per_img:b * slots_per_img + H * Wd].reshape(H, Wd)
+            col = np.zeros(F * OH * OW)
+            for f in range(F):
+                for r in range(OH):
+                    for c in range(OW):
+                        v = sum(K[f, dr, dc] * img[st * r + dr, st * c + dc] for dr in range(k) for dc in range(k))
+                        col[f * OH * OW + r * OW + c] = v + node["bias"][f]
+            cols.append(col)
+    return np.stack(cols, axis=1)
+
+
+def test_packed_conv_and_relayout_equal_the_direct_convolution():
+    g, x = W.cnn_masquerade(3, 32, side=4, k=2, stride=2)
+    conv = g["nodes"][1]
+    sub = {"nodes": [g["nodes"][0], conv, dict(g["nodes"][3]), {"kind": "output"}],
+           "edges": [(0, 1), (1, 2), (2, 3)]}
+    got = ckks.forward_fp64(sub, [0], [x])[3]
+    want = _direct_conv(x, conv, conv["images"], conv["slot_stride"])
+    assert np.allclose(got[:, :want.shape[1]], want, atol=1e-12)
+    assert np.all(got[:, want.shape[1]:] == 0)
+
+
+def test_conv_packed_decrypts_to_the_convolution(ctx64):
+    ctx = ctx64
+    g, x = W.cnn_masquerade(2, ctx.N // 2, side=4, k=3, stride=1)
+    conv = g["nodes"][1]
+    cts = [ctx.encrypt(ctx.encode(v), 300 + i) for i, v in enumerate(x)]
+    ys = ctx.conv_packed(cts, conv)
+    assert len(ys) == conv["filters"] * 2 and ys[0].level == ctx.L_top - 1
+    z = np.stack([ctx.decode(ctx.decrypt(y), y.scale) for y in ys])
+    feats = ckks.relayout_packed(z, conv, 2)
+    want = _direct_conv(x, conv, conv["images"], conv["slot_stride"])
+    assert np.max(np.abs(feats[:, :want.shape[1]] - want)) < 1e-6
+    invalid = np.ones(ctx.N // 2, dtype=bool)
+    invalid[ckks.packed_valid_slots(conv, ctx.N // 2)] = False
+    assert np.max(np.abs(z[:, invalid])) < 1e-6      # the masks zero every other slot
+
+
+def test_grouped_masquerade_cnn_matches_fp64():
+    from oracle import params
+    g, x = W.cnn_masquerade(2, 32, side=4, k=2, stride=2)
+    cost = params.autohe(g, params.ingress_nodes(g))[1]
+    assert cost == [3, 4]
+    ctxs = {}
+    for grp, c in enumerate(cost):
+        ctxs[grp] = ckks.Context(64, params.parameterise(c)["coeff_modulus"])
+        ctxs[grp].keygen(grp)
+    cts = [ctxs[0].encrypt(ctxs[0].encode(v), i) for i, v in enumerate(x)]
+    out = ckks.eval_graph_grouped(ctxs, g, [cts])
+    ref = ckks.forward_fp64(g, W.input_nodes(g), [x])
+    (o, ys), = out.items()
+    for y, r in zip(ys, ref[o]):
+        assert np.max(np.abs(ctxs[1].decode(ctxs[1].decrypt(y), y.scale) - r)) < 1e-4
+
+
 def test_sigmoid_fit_reproduces_printed_coefficients():
     got = W.sigmoid_fit()
     want = golden_io.sigmoid_coeffs()
