@@ -84,11 +84,21 @@ enum {
     FHE_NODE_OUTPUT = 5, /* sink: result handed to the client (type of concern) */
     FHE_NODE_RELU = 6,   /* Eq. relu_approximate with range q = coeffs[0]:
                             4/(3 pi q) x^2 + x/2 + q/(3 pi), a degree-2 POLY, cost 2 */
-    FHE_NODE_ROTATE = 7  /* rotation (client refresh, Sec. 3.1): a concern node where the
+    FHE_NODE_ROTATE = 7, /* rotation (client refresh, Sec. 3.1): a concern node where the
                             ciphertexts go back to the client to be decrypted and
                             re-encrypted; it ends one parameter group and starts
                             another.  fhe_eval_graph refuses graphs that contain it:
                             each group is evaluated on its own context. */
+    FHE_NODE_CONV_PACKED = 8 /* kernel masquerading (Sec. 3.2) on images packed in slots
+                            (image b's pixel (i, j) at slot b S + i W + j): per kernel
+                            position the input is rotated by dr W + dc and multiplied
+                            slot-wise by the merged mask-and-kernel vector (weight at
+                            the valid output slots b S + s r W + s c, zero elsewhere);
+                            the k^2 products are summed, rescaled and the bias vector
+                            added.  n_out = filters F, weight = [F][k][k], bias = [F],
+                            conv = {H, W, k, stride, images per ciphertext, S}; outputs
+                            filter-major (F x inputs); needs the rotation keys of the
+                            k^2 offsets (generated on first use); cost 1 */
 };
 
 typedef struct {
@@ -100,6 +110,7 @@ typedef struct {
     const double* bias;       /* LINEAR: n_out biases (FP64), may be NULL = 0 */
     double coeffs[4];         /* POLY: a0..a_degree; RELU: coeffs[0] = range q > 0 */
     uint32_t degree;          /* POLY: 1, 2 or 3 (0 means 3) */
+    uint32_t conv[6];         /* CONV_PACKED: H, W, k, stride, images, slot stride S */
 } fhe_node_desc;
 
 typedef struct {
@@ -225,6 +236,12 @@ int fhe_galois_keygen(fhe_ctx* ctx, const int32_t* steps, uint32_t n_steps, void
  * FHE_ENOKEY if the rotation key of that step has not been generated. */
 int fhe_rotate(fhe_ctx* ctx, const uint64_t* d_ct, uint32_t n_ct, uint32_t level, int32_t step, uint64_t* d_out,
                void* stream);
+
+/* dst[r][c] = src_flat[index[r * cols + c]] (0 where the index is negative),
+ * doubles, device memory: the client-side re-packing of decoded slots between
+ * parameter groups (e.g. packed conv outputs -> one feature per ciphertext). */
+int fhe_gather_slots(const double* d_src, const int64_t* d_index, uint32_t rows, uint32_t cols, double* d_dst,
+                     void* stream);
 
 /* ---- layout conversion (parity export / import) ------------------------- */
 

@@ -86,6 +86,39 @@ static u64 mod_signed(int64_t v, u64 q)
         if (_e != cudaSuccess) return cuda_check(_e, what);                  \
     } while (0)
 
+// ---------------------------------------------------------------- rotation keys
+namespace fhe {
+u64 galois_element_of(const fhe_ctx* c, int64_t step)
+{
+    const int64_t half = c->N / 2;
+    int64_t r = step % half;
+    if (r < 0) r += half;
+    u64 k = 1;
+    for (int64_t i = 0; i < r; ++i) k = (k * 5) % (2ull * c->N);
+    return k;
+}
+
+// generate the missing rotation keys of `steps` on the parent context (async on st)
+int galois_keys_for(fhe_ctx* root, const std::vector<int64_t>& steps, cudaStream_t st)
+{
+    const size_t bytes = (size_t)root->L_top * 2 * (root->L_top + 1) * root->N * sizeof(ulonglong2);
+    for (int64_t step : steps) {
+        const u64 k = galois_element_of(root, step);
+        if (k == 1 || root->galois.count(k)) continue;       // identity, or already there
+        ulonglong2* key = nullptr;
+        cudaError_t e = cudaMalloc((void**)&key, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return cuda_check(e, "rotation key allocation");
+        }
+        k_galois_keygen(root, k, key, st);
+        root->galois[k] = key;
+        root->key_bytes += bytes;
+    }
+    return FHE_OK;
+}
+}  // namespace fhe
+
 extern "C" {
 
 const char* fhe_last_error(void) { return g_err.c_str(); }
@@ -131,6 +164,7 @@ static uint32_t node_cost(const fhe_node_desc& nd)
     case FHE_NODE_SQUARE: return 1;
     case FHE_NODE_POLY: return nd.degree == 1 ? 1 : 2;    // affine: one rescale
     case FHE_NODE_RELU: return 2;
+    case FHE_NODE_CONV_PACKED: return 1;
     default: return 0;
     }
 }
@@ -237,6 +271,7 @@ int fhe_autoparam(const fhe_graph* g, uint32_t log_scale, double special_mult, u
     for (uint32_t k = 0; k < ng; ++k) cost = std::max(cost, gcost[k]);
     return fhe_parameterise(cost, log_scale, special_mult, N, bits, bits_cap, n_bits);
 }
+
 
 // ---------------------------------------------------------------- context
 static void free_ctx(fhe_ctx* c)
@@ -775,16 +810,6 @@ int fhe_relinearise(fhe_ctx* c, const uint64_t* d3, uint32_t n_ct, uint32_t leve
     return FHE_OK;
 }
 
-static u64 galois_element(const fhe_ctx* c, int32_t step)
-{
-    const int64_t half = c->N / 2;
-    int64_t r = step % half;
-    if (r < 0) r += half;
-    u64 k = 1;
-    for (int64_t i = 0; i < r; ++i) k = (k * 5) % (2ull * c->N);
-    return k;
-}
-
 int fhe_galois_keygen(fhe_ctx* c, const int32_t* steps, uint32_t n_steps, void* stream)
 {
     CHECK_CTX(c);
@@ -792,22 +817,21 @@ int fhe_galois_keygen(fhe_ctx* c, const int32_t* steps, uint32_t n_steps, void* 
     if (c->parent) return fail(FHE_EINVAL, "generate rotation keys on the parent context");
     if (n_steps && !steps) return fail(FHE_EINVAL, "null steps");
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t bytes = (size_t)c->L_top * 2 * (c->L_top + 1) * c->N * sizeof(ulonglong2);
-    for (uint32_t i = 0; i < n_steps; ++i) {
-        const u64 k = galois_element(c, steps[i]);
-        if (k == 1 || c->galois.count(k)) continue;         // identity, or already there
-        ulonglong2* key = nullptr;
-        cudaError_t e = cudaMalloc((void**)&key, bytes);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return cuda_check(e, "rotation key allocation");
-        }
-        k_galois_keygen(c, k, key, st);
-        c->galois[k] = key;
-        c->key_bytes += bytes;
-    }
+    std::vector<int64_t> v(steps, steps + n_steps);
+    int rc = galois_keys_for(c, v, st);
+    if (rc) return rc;
     CUDA_LAST("rotation keygen launch");
     return cuda_check(cudaStreamSynchronize(st), "rotation keygen");
+}
+
+int fhe_gather_slots(const double* d_src, const int64_t* d_index, uint32_t rows, uint32_t cols, double* d_dst,
+                     void* stream)
+{
+    if ((size_t)rows * cols == 0) return FHE_OK;
+    if (!d_src || !d_index || !d_dst) return fail(FHE_EINVAL, "null buffer");
+    k_gather_slots(d_src, d_index, (size_t)rows * cols, d_dst, (cudaStream_t)stream);
+    CUDA_LAST("gather launch");
+    return FHE_OK;
 }
 
 int fhe_rotate(fhe_ctx* c, const uint64_t* d_ct, uint32_t n_ct, uint32_t level, int32_t step, uint64_t* d_out,
@@ -818,7 +842,7 @@ int fhe_rotate(fhe_ctx* c, const uint64_t* d_ct, uint32_t n_ct, uint32_t level, 
     CHECK_LEVEL(c, level, 1);
     if (n_ct == 0) return FHE_OK;
     if (!d_ct || !d_out) return fail(FHE_EINVAL, "null buffer");
-    const u64 k = galois_element(c, step);
+    const u64 k = galois_element_of(c, step);
     cudaStream_t st = (cudaStream_t)stream;
     const size_t w = (size_t)n_ct * 2 * level * c->N * 8;
     if (k == 1) {

@@ -79,6 +79,7 @@ struct fhe_graph_node {
     std::vector<double> weight, bias;
     double coeffs[4] = {0, 0, 0, 0};
     uint32_t degree = 3;       // POLY / RELU (RELU: coefficients of Eq. relu_approximate, degree 2)
+    uint32_t conv[6] = {0, 0, 0, 0, 0, 0};   // CONV_PACKED: H, W, k, stride, images, slot stride
 };
 
 // device constants of one node at its planned level (built on first use)
@@ -97,6 +98,8 @@ struct fhe_node_const {
     u64* c2 = nullptr;
     u64* c1 = nullptr;
     u64* c0 = nullptr;
+    u64* pt = nullptr;         // CONV_PACKED: mask-and-kernel plaintexts [F][k^2][L][N] (NTT form)
+    u64* bias_pt = nullptr;    // CONV_PACKED: bias plaintexts [F][L-1][N]
 };
 
 struct fhe_graph {
@@ -170,6 +173,15 @@ void k_relin(const fhe_ctx* c, const u64* d3, u64* out2, uint32_t n_ct, uint32_t
 void k_galois_keygen(fhe_ctx* c, u64 k, ulonglong2* key, cudaStream_t st);
 // d3 = (c0(X^k), 0, c1(X^k)) of ciphertexts [n][2][L][N] in NTT form
 void k_automorph(const fhe_ctx* c, const u64* ct, u64* d3, uint32_t n_ct, uint32_t L, u64 k, cudaStream_t st);
+// Galois element of a slot rotation by `step`; rotation keys of the given steps
+u64 galois_element_of(const fhe_ctx* c, int64_t step);
+int galois_keys_for(fhe_ctx* root, const std::vector<int64_t>& steps, cudaStream_t st);
+// packed convolution: Y[f * n + i] (+)= X[i] * PT[f][p] slot-wise (NTT form, both components)
+void k_plain_mac(const fhe_ctx* c, u64* Y, const u64* X, const u64* PT, uint32_t F, uint32_t n, uint32_t L,
+                 uint32_t p, uint32_t k2, bool accumulate, cudaStream_t st);
+// comp 0 of out[f * n + i] += BIAS[f] (level L1)
+void k_add_plain(const fhe_ctx* c, u64* out, const u64* bias, uint32_t F, uint32_t n, uint32_t L1, cudaStream_t st);
+void k_gather_slots(const double* src, const int64_t* index, size_t total, double* dst, cudaStream_t st);
 // scratch: rescale_scratch_bytes; addc: optional constants (device residues,
 // addc[ct * addc_stride + i]) added to comp 0 of the result
 size_t rescale_scratch_bytes(const fhe_ctx* c, uint32_t n_ct, uint32_t comps);

@@ -91,6 +91,7 @@ struct Exec {
             nc = fhe_node_const();
         }
         const fhe_graph_node& nd = g->nodes[i];
+        if (nd.kind == FHE_NODE_CONV_PACKED) return conv_const(i, L, s_in);
         std::vector<char> host;
         auto put = [&](const void* src, size_t bytes) {
             size_t off = host.size();
@@ -192,6 +193,106 @@ struct Exec {
             nc.c0 = (u64*)(b + o_c0);
         }
         return &nc;
+    }
+
+    // ------------------------------------------------ packed convolution
+    // output slots b S + s r W + s c of every image b, row r, column c
+    std::vector<uint32_t> conv_valid(const fhe_graph_node& nd) const
+    {
+        const uint32_t H = nd.conv[0], W = nd.conv[1], k = nd.conv[2], st_ = nd.conv[3], imgs = nd.conv[4],
+                       S = nd.conv[5];
+        const uint32_t OH = (H - k) / st_ + 1, OW = (W - k) / st_ + 1;
+        std::vector<uint32_t> v;
+        for (uint32_t b = 0; b < imgs; ++b)
+            for (uint32_t r = 0; r < OH; ++r)
+                for (uint32_t cc = 0; cc < OW; ++cc) v.push_back(b * S + st_ * r * W + st_ * cc);
+        return v;
+    }
+
+    // mask-and-kernel plaintexts (scale q_{L-1}, level L) and bias plaintexts
+    // (scale of the output, level L-1), encoded on the device once per level
+    fhe_node_const* conv_const(uint32_t i, uint32_t L, double s_in)
+    {
+        fhe_node_const& nc = g->cache[i];
+        const fhe_graph_node& nd = g->nodes[i];
+        const size_t N = c->N, M = N / 2;
+        const uint32_t F = nd.n_out, k2 = nd.conv[2] * nd.conv[2];
+        const std::vector<uint32_t> valid = conv_valid(nd);
+        for (uint32_t v : valid)
+            if (v >= M) { err(FHE_EINVAL, "packed images exceed the ciphertext's slots"); return nullptr; }
+        const double qd = (double)c->primes[L - 1];
+        const double s_out = (s_in * qd) / qd;
+        std::vector<double> V((size_t)(F * k2 + F) * M, 0.0);
+        for (uint32_t f = 0; f < F; ++f) {
+            for (uint32_t p = 0; p < k2; ++p)
+                for (uint32_t v : valid) V[((size_t)f * k2 + p) * M + v] = nd.weight[(size_t)f * k2 + p];
+            for (uint32_t v : valid) V[((size_t)F * k2 + f) * M + v] = nd.bias[f];
+        }
+        const size_t b_pt = al((size_t)F * k2 * L * N * 8), b_bias = al((size_t)F * (L - 1) * N * 8);
+        const size_t b_v = al(V.size() * 8), b_s = al(encode_scratch_bytes(c, F * k2));
+        char* tmp = nullptr;
+        cudaError_t e = cudaMalloc(&nc.buf, b_pt + b_bias);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&tmp, b_v + b_s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, V.data(), V.size() * 8, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(tmp);
+            rc = cuda_check(e, "packed convolution constants");
+            return nullptr;
+        }
+        nc.pt = (u64*)nc.buf;
+        nc.bias_pt = (u64*)((char*)nc.buf + b_pt);
+        k_encode(c, (const double*)tmp, F * k2, L, qd, nc.pt, tmp + b_v, st);
+        k_encode(c, (const double*)tmp + (size_t)F * k2 * M, F, L - 1, s_out, nc.bias_pt, tmp + b_v, st);
+        e = cudaStreamSynchronize(st);
+        cudaFree(tmp);
+        if (e != cudaSuccess) { rc = cuda_check(e, "packed convolution constants"); return nullptr; }
+        nc.L = L;
+        nc.s_in = s_in;
+        return &nc;
+    }
+
+    Sig conv_packed(uint32_t i, const Sig& x)
+    {
+        Sig y;
+        const fhe_graph_node& nd = g->nodes[i];
+        const uint32_t L = x.L, n = x.n, F = nd.n_out, k = nd.conv[2], W = nd.conv[1];
+        if (L < 2) { err(FHE_ELEVEL, "packed convolution needs two primes"); return y; }
+        u64* R = (u64*)take(cts(n, 2, L));
+        u64* d3 = (u64*)take(cts(n, 3, L));
+        void* rs = take(relin_scratch_bytes(c, n, L));
+        u64* Y = (u64*)take(cts(F * n, 2, L));
+        void* ss = take(rescale_scratch_bytes(c, F * n, 2));
+        u64* out = (u64*)take(cts(F * n, 2, L - 1));
+        if (!dry && ok()) {
+            fhe_ctx* root = c->parent ? c->parent : c;
+            std::vector<int64_t> offs;
+            for (uint32_t dr = 0; dr < k; ++dr)
+                for (uint32_t dc = 0; dc < k; ++dc) offs.push_back((int64_t)(dr * W + dc));
+            rc = galois_keys_for(root, offs, st);
+            if (!ok()) return y;
+            fhe_node_const* kc = node_const(i, L, x.scale);
+            if (!kc) return y;
+            for (uint32_t p = 0; p < k * k; ++p) {
+                const u64* src = x.p;
+                if (offs[p] != 0) {
+                    const u64 gk = galois_element_of(c, offs[p]);
+                    k_automorph(c, x.p, d3, n, L, gk, st);
+                    k_relin(c, d3, R, n, L, rs, st, root->galois[gk]);
+                    src = R;
+                }
+                k_plain_mac(c, Y, src, kc->pt, F, n, L, p, k * k, p > 0, st);
+            }
+            k_rescale(c, Y, out, F * n, 2, L, nullptr, 0, ss, st);
+            k_add_plain(c, out, kc->bias_pt, F, n, L - 1, st);
+        }
+        const double qd = (double)c->primes[L - 1];
+        y.p = out;
+        y.n = F * n;
+        y.L = L - 1;
+        y.scale = (x.scale * qd) / qd;
+        y.set = true;
+        return y;
     }
 
     // ------------------------------------------------ scale schedule of POLY
@@ -458,6 +559,7 @@ struct Exec {
         case FHE_NODE_SQUARE: return square(s);
         case FHE_NODE_POLY:
         case FHE_NODE_RELU: return poly(n, s);
+        case FHE_NODE_CONV_PACKED: return conv_packed(n, s);
         case FHE_NODE_ROTATE:
             err(FHE_EUNSUPPORTED, "a rotation node hands its ciphertexts to the client: evaluate each parameter group "
                                   "on its own context");
@@ -529,7 +631,7 @@ int fhe_graph_create(const fhe_graph_desc* d, fhe_graph** out)
         fhe_graph_node n;
         n.kind = s.kind;
         n.n_out = s.n_out;
-        if (s.kind > FHE_NODE_ROTATE) {
+        if (s.kind > FHE_NODE_CONV_PACKED) {
             delete g;
             return fail(FHE_EINVAL, "unknown node kind");
         }
@@ -565,6 +667,18 @@ int fhe_graph_create(const fhe_graph_desc* d, fhe_graph** out)
                 }
         }
         for (int k = 0; k < 4; ++k) n.coeffs[k] = s.coeffs[k];
+        if (s.kind == FHE_NODE_CONV_PACKED) {
+            for (int k = 0; k < 6; ++k) n.conv[k] = s.conv[k];
+            const uint32_t H = n.conv[0], W = n.conv[1], k = n.conv[2], st_ = n.conv[3], imgs = n.conv[4],
+                           S = n.conv[5];
+            if (!s.n_out || !s.weight || !k || !st_ || !imgs || k > H || k > W || S < H * W) {
+                delete g;
+                return fail(FHE_EINVAL, "packed convolution: bad geometry or missing weights");
+            }
+            n.weight.assign(s.weight, s.weight + (size_t)s.n_out * k * k);
+            if (s.bias) n.bias.assign(s.bias, s.bias + s.n_out);
+            else n.bias.assign(s.n_out, 0.0);
+        }
         if (s.kind == FHE_NODE_POLY) {
             n.degree = s.degree == 0 ? 3 : s.degree;
             if (n.degree > 3) {

@@ -11,7 +11,7 @@ uint64_t launch_count() { return g_launches.load(); }
 LaunchScope::LaunchScope(const fhe_ctx* ctx, const char* family, cudaStream_t s) : c(ctx), st(s)
 {
     g_launches.fetch_add(1);
-    if (!c->prof_family.empty() && c->prof_family == family) {
+    if (c && !c->prof_family.empty() && c->prof_family == family) {
         c->prof_launches += 1;
         if (c->prof_used + 2 <= c->prof_ev.size()) {
             idx = (long)c->prof_used;
@@ -226,6 +226,77 @@ DivC make_divc(const fhe_ctx* c, uint32_t p_index, uint32_t n_targets)
         d.pmod[i] = p % q;
     }
     return d;
+}
+
+// ---------------------------------------------------------------- packed convolution
+__global__ void k_plain_mac_kernel(u64* __restrict__ Y, const u64* __restrict__ X, const u64* __restrict__ PT,
+                                   size_t total, int F, int n, int L, int p, int k2, int logN,
+                                   const PrimeC* __restrict__ pc, bool accumulate)
+{
+    const size_t Nm = ((size_t)1 << logN) - 1;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = i >> logN;            // ((f * n + ct) * 2 + comp) * L + r
+        const int r = (int)(row % L);
+        const size_t fc = row / L;               // (f * n + ct) * 2 + comp
+        const int comp = (int)(fc & 1);
+        const size_t fi = fc >> 1;
+        const int ct = (int)(fi % n), f = (int)(fi / n);
+        const int j = (int)(i & Nm);
+        const PrimeC P = pc[r];
+        const u64 x = X[((((size_t)ct * 2 + comp) * L + r) << logN) + j];
+        const u64 w = PT[((((size_t)f * k2 + p) * L + r) << logN) + j];
+        u64 v = mul_mod(x, w, P);
+        if (accumulate) v = add_mod(Y[i], v, P.q);
+        Y[i] = v;
+    }
+}
+
+void k_plain_mac(const fhe_ctx* c, u64* Y, const u64* X, const u64* PT, uint32_t F, uint32_t n, uint32_t L,
+                 uint32_t p, uint32_t k2, bool accumulate, cudaStream_t st)
+{
+    const size_t total = (size_t)F * n * 2 * L * c->N;
+    if (!total) return;
+    LaunchScope ls(c, "elementwise", st);
+    k_plain_mac_kernel<<<ew_grid(total), 256, 0, st>>>(Y, X, PT, total, (int)F, (int)n, (int)L, (int)p, (int)k2,
+                                                       (int)c->logN, c->d_pc, accumulate);
+}
+
+__global__ void k_add_plain_kernel(u64* __restrict__ out, const u64* __restrict__ bias, size_t total, int n, int L1,
+                                   int logN, const PrimeC* __restrict__ pc)
+{
+    const size_t Nm = ((size_t)1 << logN) - 1;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = i >> logN;            // (f * n + ct) * L1 + r, component 0 only
+        const int r = (int)(row % L1);
+        const size_t fi = row / L1;
+        const int f = (int)(fi / n);
+        const size_t o = (((fi * 2) * L1 + r) << logN) + (i & Nm);
+        out[o] = add_mod(out[o], bias[(((size_t)f * L1 + r) << logN) + (i & Nm)], pc[r].q);
+    }
+}
+
+void k_add_plain(const fhe_ctx* c, u64* out, const u64* bias, uint32_t F, uint32_t n, uint32_t L1, cudaStream_t st)
+{
+    const size_t total = (size_t)F * n * L1 * c->N;
+    if (!total) return;
+    LaunchScope ls(c, "elementwise", st);
+    k_add_plain_kernel<<<ew_grid(total), 256, 0, st>>>(out, bias, total, (int)n, (int)L1, (int)c->logN, c->d_pc);
+}
+
+__global__ void k_gather_slots_kernel(const double* __restrict__ src, const int64_t* __restrict__ index, size_t total,
+                                      double* __restrict__ dst)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int64_t k = index[i];
+        dst[i] = k >= 0 ? src[k] : 0.0;
+    }
+}
+
+void k_gather_slots(const double* src, const int64_t* index, size_t total, double* dst, cudaStream_t st)
+{
+    if (!total) return;
+    LaunchScope ls(nullptr, "gather", st);
+    k_gather_slots_kernel<<<ew_grid(total), 256, 0, st>>>(src, index, total, dst);
 }
 
 }  // namespace fhe

@@ -18,10 +18,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 SO_PATH = os.path.join(_HERE, "csrc", "_build", "libfhe.so")
 
 (FHE_NODE_INPUT, FHE_NODE_LINEAR, FHE_NODE_POLY, FHE_NODE_SQUARE, FHE_NODE_ADD, FHE_NODE_OUTPUT,
- FHE_NODE_RELU, FHE_NODE_ROTATE) = range(8)
+ FHE_NODE_RELU, FHE_NODE_ROTATE, FHE_NODE_CONV_PACKED) = range(9)
 _KINDS = {"input": FHE_NODE_INPUT, "linear": FHE_NODE_LINEAR, "poly": FHE_NODE_POLY,
           "square": FHE_NODE_SQUARE, "add": FHE_NODE_ADD, "output": FHE_NODE_OUTPUT, "relu": FHE_NODE_RELU,
-          "rotate": FHE_NODE_ROTATE}
+          "rotate": FHE_NODE_ROTATE, "conv_packed": FHE_NODE_CONV_PACKED}
 
 ERRORS = {-1: "FHE_EINVAL", -2: "FHE_ENOMEM", -3: "FHE_ELEVEL", -4: "FHE_ESCALE", -5: "FHE_ECUDA",
           -6: "FHE_ETIMEOUT", -7: "FHE_EUNSUPPORTED", -8: "FHE_ENOKEY"}
@@ -53,7 +53,7 @@ class NodeDesc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_uint32), ("n_out", ctypes.c_uint32),
                 ("row_ptr", ctypes.POINTER(ctypes.c_uint32)), ("col_idx", ctypes.POINTER(ctypes.c_uint32)),
                 ("weight", ctypes.POINTER(ctypes.c_double)), ("bias", ctypes.POINTER(ctypes.c_double)),
-                ("coeffs", ctypes.c_double * 4), ("degree", ctypes.c_uint32)]
+                ("coeffs", ctypes.c_double * 4), ("degree", ctypes.c_uint32), ("conv", ctypes.c_uint32 * 6)]
 
 
 class Request(ctypes.Structure):
@@ -106,6 +106,7 @@ SIGNATURES = {
     "fhe_eval_graph": [_P, _P, _P, _U32, _P, _P, _U32, _P],
     "fhe_eval_batch": [_P, _P, _P, _U32, _U64, _P],
     "fhe_galois_keygen": [_P, _P, _U32, _P],
+    "fhe_gather_slots": [_P, _P, _U32, _U32, _P, _P],
     "fhe_rotate": [_P, _P, _U32, _U32, ctypes.c_int32, _P, _P],
     "fhe_profile_begin": [_P, ctypes.c_char_p, _U32],
     "fhe_profile_end": [_P, _P, _P, _P],
@@ -185,6 +186,12 @@ def gauss_table():
     return [int(v) for v in out]
 
 
+def gather_slots(src, index, rows, cols, dst, stream=None):
+    """dst[r][c] = src.flatten()[index[r * cols + c]] (0 where index < 0);
+    float64 device tensors, int64 device index."""
+    _check(lib().fhe_gather_slots(_ptr(src), _ptr(index), rows, cols, _ptr(dst), _stream(stream)))
+
+
 class _GraphArrays:
     """Keeps the C arrays of a graph description alive while it is used."""
 
@@ -208,6 +215,15 @@ class _GraphArrays:
                 d.bias = b.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
             elif n["kind"] == "input":
                 d.n_out = int(n.get("n", 0))
+            elif n["kind"] == "conv_packed":
+                w = np.ascontiguousarray(np.asarray(n["weight"], dtype=np.float64).reshape(-1))
+                b = np.ascontiguousarray(n["bias"], dtype=np.float64)
+                self.keep += [w, b]
+                d.n_out = int(n["filters"])
+                d.weight = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+                d.bias = b.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+                for k, key in enumerate(("H", "W", "k", "stride", "images", "slot_stride")):
+                    d.conv[k] = int(n[key])
             if n["kind"] == "poly":
                 a = [float(v) for v in n["coeffs"]]
                 if not 2 <= len(a) <= 4:

@@ -26,6 +26,30 @@ def refresh_ct_id(node, k):
     return REFRESH_BASE + (node << 20) + k
 
 
+def _out_side(geo, side):
+    return (geo[side] - geo["k"]) // geo["stride"] + 1
+
+
+def _relayout_index(geo, n_in, m_up, m_down):
+    """Gather table of the client's re-packing after a packed convolution:
+    decoded filter ciphertexts [F * n_in][m_up] (filter-major) -> one row per
+    feature f * OH * OW + r * OW + c, image i * images + b in column
+    (m_down columns, -1 = zero)."""
+    F, imgs, S, W, st = geo["filters"], geo["images"], geo["slot_stride"], geo["W"], geo["stride"]
+    OH, OW = _out_side(geo, "H"), _out_side(geo, "W")
+    if n_in * imgs > m_down:
+        raise ValueError("%d images do not fit %d slots after the refresh" % (n_in * imgs, m_down))
+    idx = np.full((F * OH * OW, m_down), -1, dtype=np.int64)
+    for f in range(F):
+        for r in range(OH):
+            for c in range(OW):
+                row = f * OH * OW + r * OW + c
+                for i in range(n_in):
+                    for b in range(imgs):
+                        idx[row, i * imgs + b] = (f * n_in + i) * m_up + b * S + st * r * W + st * c
+    return idx
+
+
 def _succ(graph, n):
     return [b for a, b in graph["edges"] if a == n]
 
@@ -48,6 +72,11 @@ def _counts(graph):
                 c = len(nodes[n]["row_ptr"]) - 1
             elif k == "add":
                 c = cnt[ins[0]]
+            elif k == "conv_packed":
+                c = int(nodes[n]["filters"]) * sum(cnt[a] for a in ins)
+            elif k == "rotate" and "relayout" in nodes[n]:
+                g = nodes[n]["relayout"]
+                c = g["filters"] * _out_side(g, "H") * _out_side(g, "W")
             else:
                 c = sum(cnt[a] for a in ins)
             cnt[n] = c
@@ -72,6 +101,9 @@ class GroupedNetwork:
         self.group_of = dict(zip(self.ingress, gof))
         self.group_cost = gcost
         self.counts = _counts(graph)
+        # ciphertexts arriving at each node (its in-edges stacked); a sink's
+        # arrivals are what its group hands over
+        self.arrivals = {n: sum(self.counts[a] for a, b in graph["edges"] if b == n) for n in range(len(nodes))}
         if contexts is None:
             contexts = {}
             for g, c in enumerate(gcost):
@@ -117,6 +149,7 @@ class GroupedNetwork:
             if not moved:
                 raise ValueError("rotation groups depend on each other cyclically")
         self.sub = {g: self._subgraph(g) for g in range(len(gcost))}
+        self._relayout = {}          # rotation node -> device gather table
         self.G = {g: fhe.Graph(self.sub[g][0]) for g in range(len(gcost))}
         self.last_ingress = {}
         self.last_sinks = {}
@@ -179,10 +212,21 @@ class GroupedNetwork:
                 a = b
             off = 0
             for s in self.sinks[g]:
-                k = self.counts[s]
+                k = self.arrivals[s]
                 self.last_sinks[s] = (out[off:off + k], L_out, [mm[1] for mm in meta[off:off + k]])
                 if nodes[s]["kind"] == "rotate":
-                    slots_of[s] = z[off:off + k]     # client refresh: re-encrypted by the next group
+                    zs = z[off:off + k]              # client refresh: re-encrypted by the next group
+                    if "relayout" in nodes[s]:       # client re-packs the decoded slots
+                        geo = nodes[s]["relayout"]
+                        down = self.ctx[self.group_of[s]]
+                        rows = self.counts[s]
+                        if s not in self._relayout:
+                            idx = _relayout_index(geo, k // geo["filters"], zs.shape[1], down.N // 2)
+                            self._relayout[s] = torch.tensor(idx, device=zs.device)
+                        dst = torch.empty((rows, down.N // 2), dtype=torch.float64, device=zs.device)
+                        fhe.gather_slots(zs.contiguous(), self._relayout[s], rows, down.N // 2, dst, stream)
+                        zs = dst
+                    slots_of[s] = zs
                 else:
                     results[s] = z[off:off + k]
                 off += k

@@ -312,6 +312,50 @@ def test_rotation_bit_exact(N, bits, L, steps):
         g.rotate(ct, g.L_top, 11, rot)          # no key for this step
 
 
+def test_masquerade_cnn_bit_exact_per_group():
+    """Kernel masquerading on packed 8x8 images (8 per ciphertext at
+    N = 1024): group 0 (packed conv through rotations + sigmoid) bit-exact
+    against the oracle; the client re-packs the conv outputs one feature per
+    ciphertext; group 1 (dense, sigmoid, dense) bit-exact from the device's
+    refreshed ciphertexts; decoded outputs within 1e-4 of FP64."""
+    from oracle import params
+    from paper_2110_13638_gb300 import groups
+    N = 1024
+    graph, x = W.cnn_masquerade(4, N // 2)
+    cost = params.autohe(graph, params.ingress_nodes(graph))[1]
+    assert cost == [3, 4]
+    pairs = [pair(N, params.parameterise(c)["coeff_modulus"], seed=gi) for gi, c in enumerate(cost)]
+    net = groups.GroupedNetwork(graph, contexts={gi: p[0] for gi, p in enumerate(pairs)})
+    res = net.evaluate([torch.tensor(x, device="cuda")], first_ct_id=0)
+    torch.cuda.synchronize()
+    rot, out_node = 3, 7
+    g0, o0 = pairs[0]
+    cts = [o0.encrypt(o0.encode(x[i]), i) for i in range(x.shape[0])]
+    seg0 = {"nodes": [{"kind": "input", "n": x.shape[0]}, graph["nodes"][1], graph["nodes"][2], {"kind": "output"}],
+            "edges": [(0, 1), (1, 2), (2, 3)]}
+    (_, y0), = ckks.eval_graph(o0, seg0, [0], [cts]).items()
+    dev0, L0, sc0 = net.last_sinks[rot]
+    got0 = download(g0, dev0.contiguous(), L0)
+    assert len(y0) == got0.shape[0] == 8
+    for k, y in enumerate(y0):
+        assert y.level == L0 and sc0[k] == y.scale
+        assert np.array_equal(got0[k], y.c), k
+    g1, o1 = pairs[1]
+    fresh = download(g1, net.last_ingress[rot], g1.L_top)
+    cts1 = [ckks.Ciphertext(fresh[k], g1.L_top, o1.delta) for k in range(fresh.shape[0])]
+    seg1 = W.chain_graph(fresh.shape[0], graph["nodes"][4:7])
+    (_, y1), = ckks.eval_graph(o1, seg1, [0], [cts1]).items()
+    dev1, L1, _ = net.last_sinks[out_node]
+    got1 = download(g1, dev1.contiguous(), L1)
+    for k, y in enumerate(y1):
+        assert np.array_equal(got1[k], y.c), k
+    ref = ckks.forward_fp64(graph, W.input_nodes(graph), [x])
+    n_img = x.shape[0] * graph["nodes"][1]["images"]
+    err = float(np.max(np.abs(res[out_node].cpu().numpy()[:, :n_img] - ref[out_node][:, :n_img])))
+    assert err < 1e-4
+    net.close()
+
+
 def test_graph_relu_and_affine_bit_exact():
     """Eq. relu_approximate (degree 2) after the convolution and the linear
     sigmoid 0.5 + 0.197 x (degree 1) after the dense layer."""
