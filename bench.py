@@ -39,6 +39,21 @@ def _env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def replica_times(times_ms, dist, device):
+    """Replicas only: every rank times its own requests; the job's time is
+    the slowest rank's (all-reduce MAX over the process group, if any)."""
+    import torch
+    t = torch.tensor(list(times_ms), dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def job_rate(units_per_rank, world, ms):
+    """Whole-job throughput: the units all ranks processed / the job time."""
+    return units_per_rank * world / (ms / 1000.0)
+
+
 DATA = {
     "cnn": "synthetic (seeded U[0,1] 28x28 images, He-normal weights; Fashion-MNIST not available)",
     "cnn_relu": "synthetic (seeded U[0,1] 28x28 images, He-normal weights; Fashion-MNIST not available)",
@@ -218,13 +233,10 @@ def run_ours(args):
     barrier()
     e2e_ms = e2.elapsed_time(e3)
 
-    t = torch.tensor([dev_ms, e2e_ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    dev_ms, e2e_ms = float(t[0]), float(t[1])
+    dev_ms, e2e_ms = replica_times([dev_ms, e2e_ms], dist, dev)
     total_samples = samples * args.steps * world
-    value = total_samples / (dev_ms / 1000.0)
-    e2e = total_samples / (e2e_ms / 1000.0)
+    value = job_rate(samples * args.steps, world, dev_ms)
+    e2e = job_rate(samples * args.steps, world, e2e_ms)
 
     if rank != 0:
         if dist:
