@@ -202,7 +202,7 @@ void k_linear_mac(const fhe_ctx* c, const u64* X, uint32_t n_in, const uint32_t*
                   const u64* Wres, uint32_t n_out, uint32_t L, u64* Y, cudaStream_t st);
 
 // tiled gather-MAC (rows sharing a column list computed together)
-constexpr int kMacTile = 8;
+constexpr int kMacTile = 6;
 // primes below this bound store MAC weights as 21-bit limbs (wL | wH << 32)
 constexpr unsigned long long kLimbPrimeBound = 1ull << 42;
 void k_linear_mac_tiled(const fhe_ctx* c, const u64* X, const uint4* tiles, uint32_t n_tiles, const uint32_t* rows,

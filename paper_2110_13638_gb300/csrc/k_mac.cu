@@ -53,7 +53,7 @@ void k_linear_mac(const fhe_ctx* c, const u64* X, uint32_t n_in, const uint32_t*
 // kMacTile per thread, so each input word is loaded once per tile.
 //   tiles[t] = {col_off, K, n_rows, w_off}; rows[t * kMacTile + o] = output row;
 //   W[((w_off + e) * L + r) * kMacTile + o] = weight residue of (row o, term e)
-// (the tile's weights of one term and residue are contiguous: 4 vector loads).
+// (the tile's weights of one term and residue are contiguous: kMacTile / 2 vector loads).
 // Terms are processed four at a time with their input loads issued together.
 __device__ __forceinline__ void mac128(u64& lo, u64& hi, u64 x, u64 w)
 {
