@@ -30,9 +30,10 @@ DOMINANT = "keyswitch_modup_mac"
 SMS, SM_MHZ_MAX, MUL32_LANES = 152, 2070.0, 64
 # DRAM bytes (read + write) of the key-switching ModUp + key-product kernel
 # per (ciphertext, target prime, digit) unit, from one ncu capture of that
-# kernel (schedule 5) on 64 ciphertexts at L = 7: 232.7 MB read + 118.1 MB
-# written over 64 * 8 * 7 units.  Scaled by units to the bench's launches.
-KS_DRAM_BYTES_PER_UNIT = (232.722944e6 + 118.0544e6) / (64 * 8 * 7)
+# kernel (schedule 5) on 64 ciphertexts at L = 7 (--workload relin):
+# 231.2 MB read + 117.1 MB written over 64 * 8 * 7 units.  Scaled by units
+# to the bench's launches.
+KS_DRAM_BYTES_PER_UNIT = (231.158272e6 + 117.12896e6) / (64 * 8 * 7)
 
 
 def _env_rank():
@@ -394,6 +395,42 @@ def _host_desc():
 
 
 # ---------------------------------------------------------------- batching sweep
+def run_relin(args):
+    """Relinearisations of --batch-cts random tensor products at --level,
+    N = 16384, [60, 40 x 7, 60]: the key-switching step alone (also the small
+    case the ncu captures of the key-switching kernels use)."""
+    import torch
+    import __graft_entry__
+    from paper_2110_13638_gb300 import fhe
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    ctx = fhe.Context(16384, [60] + [40] * 7 + [60], 40)
+    ctx.keygen(0)
+    n, L = args.batch_cts, args.level
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1)
+    d3 = torch.empty((n, 3, L, 16384), dtype=torch.int64, device="cuda")
+    for r in range(L):
+        d3[:, :, r, :] = torch.randint(0, ctx.primes[r], (n, 3, 16384), device="cuda", generator=gen)
+    out = ctx.empty_ct(n, L)
+    for _ in range(args.warmup):
+        ctx.relinearise(d3, L, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        ctx.relinearise(d3, L, out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    print(json.dumps({"metric": "relinearisations/s at N=16384", "value": round(n * args.steps / (ms / 1000.0), 1),
+                      "unit": "ops/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True, "dtype": "u64",
+                      "data": "synthetic (uniform residues, seed 1)",
+                      "config": {"workload": "relinearise %d tensor products at L=%d" % (n, L),
+                                 "ntt_schedule_keyswitch": ctx.ntt_variant_ks}}), flush=True)
+
+
 def run_batch(args):
     """4096 ciphertext pairs at uneven levels (L = 1 + U{1..7}, seed 3), each
     getting ct-mult + relinearise + rescale: all levels in one call whose
@@ -686,10 +723,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cnn", choices=["cnn", "mlp", "dense_square", "cnn_relu", "deep", "cnn_rotate",
-                                                          "cnn_masquerade", "batch", "ntt_sweep", "serve"])
+                                                          "cnn_masquerade", "batch", "relin", "ntt_sweep", "serve"])
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--batch-cts", type=int, default=4096)
+    ap.add_argument("--level", type=int, default=7, help="level of --workload relin")
     ap.add_argument("--profile-family", default=DOMINANT)
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the dominant kernel (from profiles/)")
@@ -701,6 +739,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "relin":
+        run_relin(args)
     elif args.workload == "ntt_sweep":
         run_ntt_sweep(args)
     elif args.workload == "serve":
