@@ -295,6 +295,7 @@ static void free_ctx(fhe_ctx* c)
     cudaFree(c->d_slot_of);
     cudaFree(c->d_s);
     cudaFree(c->d_pk);
+    cudaFree(c->d_pks);
     cudaFree(c->d_ksk);
     for (auto& kv : c->galois) cudaFree(kv.second);
     cudaFree(c->ws);
@@ -590,6 +591,7 @@ int fhe_ctx_fork(fhe_ctx* parent, fhe_ctx** out)
     c->seed = parent->seed;
     c->d_s = parent->d_s;
     c->d_pk = parent->d_pk;
+    c->d_pks = parent->d_pks;
     c->d_ksk = parent->d_ksk;
     c->parent = parent;
     c->ntt2_words = parent->ntt2_words;
@@ -641,12 +643,13 @@ int fhe_keygen(fhe_ctx* c, uint64_t seed, void* stream)
         size_t bs = (Lt + 1) * N * 8, bp = 2 * Lt * N * 8, bk = Lt * 2 * (Lt + 1) * N * 16;
         cudaError_t e = cudaMalloc((void**)&c->d_s, bs);
         if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_pk, bp);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_pks, bp);
         if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_ksk, bk);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return cuda_check(e, "key allocation");
         }
-        c->key_bytes += bs + bp + bk;
+        c->key_bytes += bs + 2 * bp + bk;
     }
     c->seed = seed;
     k_keygen(c, st);

@@ -41,6 +41,7 @@ struct fhe_ctx {
     uint64_t seed = 0;
     u64* d_s = nullptr;            // [L_top + 1][N]
     u64* d_pk = nullptr;           // [2][L_top][N]
+    u64* d_pks = nullptr;          // [2][L_top][N] Shoup quotients floor(pk 2^64 / q) of d_pk
     ulonglong2* d_ksk = nullptr;   // [L_top][2][L_top + 1][N] (key word, Shoup quotient)
     std::map<u64, ulonglong2*> galois;   // Galois element k -> rotation key (same layout); forks use the parent's
     size_t key_bytes = 0;

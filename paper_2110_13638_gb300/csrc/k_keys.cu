@@ -118,6 +118,17 @@ struct OpRelinKey {
     }
 };
 
+// Shoup quotients of the public key, so encryption multiplies by it with one
+// Shoup product per word
+__global__ void k_pk_shoup_kernel(const u64* __restrict__ pk, u64* __restrict__ pks, size_t total, int Lt, int logN,
+                                  const PrimeC* __restrict__ pc)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)((i >> logN) % Lt);
+        pks[i] = with_shoup(pk[i], pc[r].q).y;
+    }
+}
+
 void k_keygen(fhe_ctx* c, cudaStream_t st)
 {
     const int N = (int)c->N, Lt = (int)c->L_top;
@@ -125,6 +136,11 @@ void k_keygen(fhe_ctx* c, cudaStream_t st)
     launch_ntt<false>(c, os, st);
     OpPublicKey op{c->d_s, c->d_pk, c->d_cdt, stream_key(c->seed, DOM_PK_A, 0), stream_key(c->seed, DOM_PK_E, 0), Lt, N};
     launch_ntt<false>(c, op, st);
+    {
+        const size_t total = (size_t)2 * Lt * N;
+        LaunchScope ls(c, "keygen", st);
+        k_pk_shoup_kernel<<<ew_grid(total), 256, 0, st>>>(c->d_pk, c->d_pks, total, Lt, (int)c->logN, c->d_pc);
+    }
     std::vector<u64> h(2 * Lt);
     for (int j = 0; j < Lt; ++j) {
         h[j] = stream_key(c->seed, DOM_KSK_A, (u64)j);
@@ -236,6 +252,7 @@ struct OpEncrypt {
     static const char* family() { return "encrypt"; }
     const u64* pt;      // [n][Ltop][N]
     const u64* pk;      // [2][Ltop][N]
+    const u64* pks;     // their Shoup quotients
     u64* ct;            // [n][2][Ltop][N]
     const int8_t* S;    // [n][3][N] samples
     const i64* M;       // optional [n][N] encoded coefficients (then pt is unused):
@@ -252,7 +269,7 @@ struct OpEncrypt {
         if (u == 1 && M) v += M[(size_t)ci * N + j];
         return from_signed(v, P);
     }
-    struct Pre { u64 a, b, c; };
+    struct Pre { u64 a, b, bs, c, cs; };
     __device__ Pre pre(int p, int u, int j) const
     {
         const int ci = p / Ltop, r = p % Ltop;
@@ -260,10 +277,12 @@ struct OpEncrypt {
         if (u == 0) {
             x.a = M ? 0 : pt[((size_t)ci * Ltop + r) * N + j];
             x.b = pk[(size_t)r * N + j];
+            x.bs = pks[(size_t)r * N + j];
             x.c = pk[((size_t)Ltop + r) * N + j];
+            x.cs = pks[((size_t)Ltop + r) * N + j];
         } else {
             x.a = ct[(((size_t)ci * 2 + (u == 1 ? 0 : 1)) * Ltop + r) * N + j];
-            x.b = x.c = 0;
+            x.b = x.bs = x.c = x.cs = 0;
         }
         return x;
     }
@@ -273,8 +292,8 @@ struct OpEncrypt {
         u64* c0 = ct + (((size_t)ci * 2 + 0) * Ltop + r) * N;
         u64* c1 = ct + (((size_t)ci * 2 + 1) * Ltop + r) * N;
         if (u == 0) {
-            c0[j] = add_mod(mul_mod(v, pr.b, P), pr.a, P.q);
-            c1[j] = mul_mod(v, pr.c, P);
+            c0[j] = add_mod(mul_shoup(v, pr.b, pr.bs, P.q), pr.a, P.q);
+            c1[j] = mul_shoup(v, pr.c, pr.cs, P.q);
         } else if (u == 1) {
             c0[j] = add_mod(pr.a, v, P.q);
         } else {
@@ -295,7 +314,7 @@ void k_encrypt(const fhe_ctx* c, const u64* pt, uint32_t n_ct, uint64_t first_id
         LaunchScope ls(c, "encrypt", st);
         k_sample_enc_kernel<<<ew_grid(total), 256, 0, st>>>(S, (int)n_ct, (int)c->N, c->seed, first_id, c->d_cdt);
     }
-    OpEncrypt op{pt, c->d_pk, ct, S, nullptr, (int)n_ct, (int)c->L_top, (int)c->N};
+    OpEncrypt op{pt, c->d_pk, c->d_pks, ct, S, nullptr, (int)n_ct, (int)c->L_top, (int)c->N};
     launch_ntt<false>(c, op, st);
 }
 
@@ -319,7 +338,7 @@ void k_encode_encrypt(const fhe_ctx* c, const double* slots, uint32_t n_ct, doub
         LaunchScope ls(c, "encrypt", st);
         k_sample_enc_kernel<<<ew_grid(total), 256, 0, st>>>(S, (int)n_ct, (int)c->N, c->seed, first_id, c->d_cdt);
     }
-    OpEncrypt op{nullptr, c->d_pk, ct, S, m, (int)n_ct, (int)c->L_top, (int)c->N};
+    OpEncrypt op{nullptr, c->d_pk, c->d_pks, ct, S, m, (int)n_ct, (int)c->L_top, (int)c->N};
     launch_ntt<false>(c, op, st);
 }
 
