@@ -77,8 +77,10 @@ typedef struct {
 enum {
     FHE_NODE_INPUT = 0,  /* source: encrypted input signal (type of concern) */
     FHE_NODE_LINEAR = 1, /* y_o = sum_e w_e x_{col_e} + b_o (dense or conv), cost 1 */
-    FHE_NODE_POLY = 2,   /* a0 + a1 x (+ a2 x^2 (+ a3 x^3)) per ciphertext, degree 1..3;
-                            cost 1 for degree 1, else 2 */
+    FHE_NODE_POLY = 2,   /* sum_i a_i x^i per ciphertext, degree 1..31: degree 1 cost 1,
+                            2 and 3 cost 2 (dedicated schedules), 4..31 cost
+                            ceil(log2 degree) + 1 (powers by products, one combining
+                            rescale) */
     FHE_NODE_SQUARE = 3, /* x^2 per ciphertext, cost 1 */
     FHE_NODE_ADD = 4,    /* element-wise sum of the in-edge lists, cost 0 */
     FHE_NODE_OUTPUT = 5, /* sink: result handed to the client (type of concern) */
@@ -109,8 +111,9 @@ typedef struct {
     const double* weight;     /* LINEAR: CSR values (FP64) */
     const double* bias;       /* LINEAR: n_out biases (FP64), may be NULL = 0 */
     double coeffs[4];         /* POLY: a0..a_degree; RELU: coeffs[0] = range q > 0 */
-    uint32_t degree;          /* POLY: 1, 2 or 3 (0 means 3) */
+    uint32_t degree;          /* POLY: 1..31 (0 means 3) */
     uint32_t conv[6];         /* CONV_PACKED: H, W, k, stride, images, slot stride S */
+    const double* coeffs_hi;  /* POLY of degree > 3: a_0 .. a_degree */
 } fhe_node_desc;
 
 typedef struct {

@@ -29,6 +29,7 @@ from .params import (prime_chain, primitive_2n_root, gauss_cdt, GAUSS_KMAX,
 DOM_SECRET, DOM_PK_A, DOM_PK_E, DOM_KSK_A, DOM_KSK_E = 1, 2, 3, 4, 5
 DOM_ENC_U, DOM_ENC_E0, DOM_ENC_E1 = 6, 7, 8
 DOM_GAL_A, DOM_GAL_E = 9, 10          # Galois (rotation) keys: object id = (k << 8) | digit
+MAX_POLY_DEGREE = 31
 
 
 def llround(x):
@@ -465,7 +466,7 @@ class Context:
         return self.add_const(y, llround(float(a[0]) * y.scale))
 
     def poly(self, x, a):
-        """Polynomial activation of degree len(a) - 1 (1, 2 or 3)."""
+        """Polynomial activation of degree len(a) - 1 (1 .. 31)."""
         d = len(a) - 1
         if d == 1:
             return self.affine(x, a)
@@ -473,7 +474,45 @@ class Context:
             return self.poly2(x, a)
         if d == 3:
             return self.poly3(x, a)
-        raise ValueError("polynomial degree %d (1..3 supported)" % d)
+        if 4 <= d <= MAX_POLY_DEGREE:
+            return self.poly_powers(x, a)
+        raise ValueError("polynomial degree %d (1..%d supported)" % (d, MAX_POLY_DEGREE))
+
+    def poly_powers(self, x, a):
+        """Degree d >= 4 in ceil(log2 d) + 1 levels.  Powers: x^(2^j) by
+        squaring, any other x^i = x^(2^j) x^(i - 2^j) (2^j the largest power of
+        two below i), each product relinearised and rescaled, the operand at
+        the higher level first mod-dropped to the other's level.  With l* the
+        lowest level among the powers and S = s q_{l*-1} (s the scale of x):
+            T = sum_{i >= 1, a_i != 0} drop(x^i, l*) * llround(a_i * S / s_i)
+            y = rescale(T) + llround(a0 * scale(y))
+        (s_i the scale of x^i; the terms are added in increasing i)."""
+        d = len(a) - 1
+        pw = {1: x}
+        for i in range(2, d + 1):
+            j = 1 << (i.bit_length() - 1)
+            if j == i:
+                j = i // 2
+            A, B = pw[j], pw[i - j]
+            lv = min(A.level, B.level)
+            assert lv >= 2, "not enough levels for degree %d" % d
+            A = A if A.level == lv else self.mod_drop(A, lv)
+            B = B if B.level == lv else self.mod_drop(B, lv)
+            pw[i] = self.rescale(self.relinearise(self.tensor(A, B)))
+        lstar = min(p.level for p in pw.values())
+        assert lstar >= 2, "not enough levels for degree %d" % d
+        S = x.scale * float(self.q[lstar - 1])
+        T = None
+        for i in range(1, d + 1):
+            if float(a[i]) == 0.0:
+                continue
+            p = pw[i] if pw[i].level == lstar else self.mod_drop(pw[i], lstar)
+            sig = S / p.scale
+            t = self.mul_const(p, llround(float(a[i]) * sig), sig)
+            T = t if T is None else self.add(T, t)
+        assert T is not None, "polynomial without non-constant terms"
+        y = self.rescale(T)
+        return self.add_const(y, llround(float(a[0]) * y.scale))
 
     def poly3(self, x, a):
         """a0 + a1 x + a2 x^2 + a3 x^3 in two levels (Eq. sigmoid_approximate

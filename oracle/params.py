@@ -26,7 +26,12 @@ def node_cost(node):
     if k in ("linear", "square", "conv_packed"):
         return 1
     if k == "poly":
-        return 1 if len(node.get("coeffs", (0, 0, 0, 0))) == 2 else 2   # affine: one rescale
+        d = len(node.get("coeffs", (0, 0, 0, 0))) - 1
+        if d == 1:
+            return 1                                       # affine: one rescale
+        if d <= 3:
+            return 2
+        return (d - 1).bit_length() + 1                    # ceil(log2 d) powers + the combining rescale
     if k == "relu":
         return 2                                         # degree 2 (Eq. relu_approximate)
     return 0

@@ -162,7 +162,13 @@ static uint32_t node_cost(const fhe_node_desc& nd)
     switch (nd.kind) {
     case FHE_NODE_LINEAR: return 1;
     case FHE_NODE_SQUARE: return 1;
-    case FHE_NODE_POLY: return nd.degree == 1 ? 1 : 2;    // affine: one rescale
+    case FHE_NODE_POLY: {
+        const uint32_t d = nd.degree == 0 ? 3 : nd.degree;
+        if (d <= 3) return d == 1 ? 1 : 2;                  // affine: one rescale
+        uint32_t lg = 0;
+        while ((1u << lg) < d) ++lg;
+        return lg + 1;                                      // powers, then the combining rescale
+    }
     case FHE_NODE_RELU: return 2;
     case FHE_NODE_CONV_PACKED: return 1;
     default: return 0;

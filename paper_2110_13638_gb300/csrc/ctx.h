@@ -81,6 +81,7 @@ struct fhe_graph_node {
     double coeffs[4] = {0, 0, 0, 0};
     uint32_t degree = 3;       // POLY / RELU (RELU: coefficients of Eq. relu_approximate, degree 2)
     uint32_t conv[6] = {0, 0, 0, 0, 0, 0};   // CONV_PACKED: H, W, k, stride, images, slot stride
+    std::vector<double> poly;  // POLY of degree > 3: a_0 .. a_degree
 };
 
 // device constants of one node at its planned level (built on first use)
@@ -99,6 +100,7 @@ struct fhe_node_const {
     u64* c2 = nullptr;
     u64* c1 = nullptr;
     u64* c0 = nullptr;
+    u64* cpow = nullptr;       // POLY degree > 3: residues of C_1..C_d at l* primes, then C_0 ([d + 1][l*])
     u64* pt = nullptr;         // CONV_PACKED: mask-and-kernel plaintexts [F][k^2][L][N] (NTT form)
     u64* bias_pt = nullptr;    // CONV_PACKED: bias plaintexts [F][L-1][N]
 };

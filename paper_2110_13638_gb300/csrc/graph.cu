@@ -32,6 +32,20 @@ using namespace fhe;
 
 namespace {
 
+constexpr uint32_t kMaxPolyDegree = 31;
+
+// Degree > 3: plan of the powers x^i (levels and nominal scales, FP64 in the
+// order the receptor computes them) and the combining constants.
+struct PowPlan {
+    std::vector<uint32_t> j;        // x^i = x^j x^(i - j)
+    std::vector<uint32_t> lev;      // level of x^i (lev[1] = L)
+    std::vector<double> sc;         // nominal scale of x^i
+    uint32_t lstar = 0;             // lowest level among the powers
+    std::vector<int64_t> C;         // C[i] = llround(a_i S / s_i) (0 where a_i = 0), C[0] = llround(a_0 s_y)
+    double s_T = 0.0, s_y = 0.0;    // scale of the sum (first term's) and of the result
+    bool scales_agree = true;
+};
+
 struct Sig {
     u64* p = nullptr;
     uint32_t n = 0, L = 0;
@@ -154,6 +168,14 @@ struct Exec {
             o_col = put(tcol.data(), std::max<size_t>(1, tcol.size()) * 4);
             o_W = put(W.data(), std::max<size_t>(1, W.size()) * 8);
             o_b = put(B.data(), std::max<size_t>(1, B.size()) * 8);
+        } else if (nd.kind == FHE_NODE_POLY && nd.degree > 3) {
+            const PowPlan P = pow_plan(nd, L, s_in);
+            const uint32_t ls = P.lstar;
+            std::vector<u64> cr((size_t)(nd.degree + 1) * ls, 0);
+            for (uint32_t k = 1; k <= nd.degree; ++k)
+                for (uint32_t r = 0; r < ls; ++r) cr[(size_t)(k - 1) * ls + r] = mod_signed(P.C[k], c->primes[r]);
+            for (uint32_t r = 0; r + 1 < ls; ++r) cr[(size_t)nd.degree * ls + r] = mod_signed(P.C[0], c->primes[r]);
+            o_c0 = put(cr.data(), cr.size() * 8);
         } else if (nd.kind == FHE_NODE_POLY || nd.kind == FHE_NODE_RELU) {
             PolyK k = poly_constants(nd, L, s_in);
             std::vector<u64> r3(L), r2(L), r1(L), r0(L);          // residues of C3..C0 at every prime of level L
@@ -186,6 +208,8 @@ struct Exec {
             nc.col = (uint32_t*)(b + o_col);
             nc.W = (u64*)(b + o_W);
             nc.bias = (u64*)(b + o_b);
+        } else if (nd.kind == FHE_NODE_POLY && nd.degree > 3) {
+            nc.cpow = (u64*)(b + o_c0);
         } else {
             nc.c3 = (u64*)(b + o_c3);
             nc.c2 = (u64*)(b + o_c2);
@@ -295,6 +319,103 @@ struct Exec {
         return y;
     }
 
+    // ------------------------------------------------ polynomials of degree > 3
+    PowPlan pow_plan(const fhe_graph_node& nd, uint32_t L, double s) const
+    {
+        const uint32_t d = nd.degree;
+        PowPlan p;
+        p.j.assign(d + 1, 0);
+        p.lev.assign(d + 1, 0);
+        p.sc.assign(d + 1, 0.0);
+        p.C.assign(d + 1, 0);
+        p.lev[1] = L;
+        p.sc[1] = s;
+        p.lstar = L;
+        for (uint32_t i = 2; i <= d; ++i) {
+            uint32_t j = 1;
+            while ((j << 1) <= i) j <<= 1;
+            if (j == i) j = i / 2;
+            const uint32_t lv = std::min(p.lev[j], p.lev[i - j]);
+            if (lv < 2) return p;                         // lstar stays > 0: caller reports
+            p.j[i] = j;
+            p.lev[i] = lv - 1;
+            p.sc[i] = (p.sc[j] * p.sc[i - j]) / (double)c->primes[lv - 1];
+            p.lstar = std::min(p.lstar, p.lev[i]);
+        }
+        if (p.lstar < 2) return p;
+        const double S = s * (double)c->primes[p.lstar - 1];
+        bool first = true;
+        for (uint32_t i = 1; i <= d; ++i) {
+            if (nd.poly[i] == 0.0) continue;
+            const double sig = S / p.sc[i];
+            p.C[i] = (int64_t)std::llround(nd.poly[i] * sig);
+            const double st_i = p.sc[i] * sig;
+            if (first) p.s_T = st_i;
+            else p.scales_agree &= scale_match(p.s_T, st_i);
+            first = false;
+        }
+        p.s_y = p.s_T / (double)c->primes[p.lstar - 1];
+        p.C[0] = (int64_t)std::llround(nd.poly[0] * p.s_y);
+        return p;
+    }
+
+    Sig poly_powers(uint32_t i, const Sig& x)
+    {
+        Sig y;
+        const fhe_graph_node& nd = g->nodes[i];
+        const uint32_t d = nd.degree, n = x.n;
+        const PowPlan P = pow_plan(nd, x.L, x.scale);
+        for (uint32_t k = 2; k <= d; ++k)
+            if (P.lev[k] == 0) { err(FHE_ELEVEL, "not enough primes for this polynomial degree"); return y; }
+        if (P.lstar < 2) { err(FHE_ELEVEL, "not enough primes for this polynomial degree"); return y; }
+        if (!P.scales_agree) { err(FHE_ESCALE, "polynomial terms disagree in scale"); return y; }
+        std::vector<Sig> pw(d + 1);
+        pw[1] = x;
+        for (uint32_t k = 2; k <= d; ++k) {
+            const uint32_t j = P.j[k], lv = P.lev[k] + 1;
+            const Sig A = drop_to(pw[j], lv), B = (j == k - j) ? A : drop_to(pw[k - j], lv);
+            u64* T3 = (u64*)take(cts(n, 3, lv));
+            u64* R = (u64*)take(cts(n, 2, lv));
+            void* rs = take(relin_scratch_bytes(c, n, lv));
+            void* ss = take(rescale_scratch_bytes(c, n, 2));
+            u64* out = (u64*)take(cts(n, 2, lv - 1));
+            if (!dry && ok()) {
+                k_tensor(c, A.p, B.p, T3, n, lv, st);
+                k_relin(c, T3, R, n, lv, rs, st);
+                k_rescale(c, R, out, n, 2, lv, nullptr, 0, ss, st);
+            }
+            pw[k].p = out;
+            pw[k].n = n;
+            pw[k].L = lv - 1;
+            pw[k].scale = P.sc[k];
+            pw[k].set = true;
+        }
+        const uint32_t ls = P.lstar;
+        u64* acc = (u64*)take(cts(n, 2, ls));
+        u64* tmp = (u64*)take(cts(n, 2, ls));
+        void* ss = take(rescale_scratch_bytes(c, n, 2));
+        u64* out = (u64*)take(cts(n, 2, ls - 1));
+        if (!dry && ok()) {
+            fhe_node_const* kc = node_const(i, x.L, x.scale);
+            if (!kc) return y;
+            bool first = true;
+            for (uint32_t k = 1; k <= d; ++k) {
+                if (nd.poly[k] == 0.0) continue;
+                const u64* Ck = kc->cpow + (size_t)(k - 1) * ls;
+                k_mul_const(c, pw[k].p, first ? acc : tmp, n, 2, pw[k].L, ls, Ck, 0, st);
+                if (!first) k_add(c, acc, tmp, acc, n, 2, ls, st);
+                first = false;
+            }
+            k_rescale(c, acc, out, n, 2, ls, kc->cpow + (size_t)d * ls, 0, ss, st);
+        }
+        y.p = out;
+        y.n = n;
+        y.L = ls - 1;
+        y.scale = P.s_y;
+        y.set = true;
+        return y;
+    }
+
     // ------------------------------------------------ scale schedule of POLY
     struct PolyK {
         int64_t C3 = 0, C2 = 0, C1 = 0, C0 = 0;
@@ -386,6 +507,7 @@ struct Exec {
         const uint32_t L = x.L, n = x.n;
         const uint32_t deg = g->nodes[i].degree;
         if (deg == 1) return affine(i, x);
+        if (deg > 3) return poly_powers(i, x);
         if (L < 3) { err(FHE_ELEVEL, "a degree-2 or -3 activation needs three primes"); return y; }
         const PolyK k = poly_constants(g->nodes[i], L, x.scale);
         if ((deg == 3 && !scale_match(k.s_t1, k.s_t2)) || !scale_match(k.s_t2, k.s_t3)) {
@@ -681,9 +803,22 @@ int fhe_graph_create(const fhe_graph_desc* d, fhe_graph** out)
         }
         if (s.kind == FHE_NODE_POLY) {
             n.degree = s.degree == 0 ? 3 : s.degree;
-            if (n.degree > 3) {
+            if (n.degree > kMaxPolyDegree) {
                 delete g;
-                return fail(FHE_EUNSUPPORTED, "polynomial degree above 3");
+                return fail(FHE_EUNSUPPORTED, "polynomial degree above 31");
+            }
+            if (n.degree > 3) {
+                if (!s.coeffs_hi) {
+                    delete g;
+                    return fail(FHE_EINVAL, "a polynomial of degree above 3 needs coeffs_hi");
+                }
+                n.poly.assign(s.coeffs_hi, s.coeffs_hi + n.degree + 1);
+                bool any = false;
+                for (uint32_t k = 1; k <= n.degree; ++k) any |= n.poly[k] != 0.0;
+                if (!any) {
+                    delete g;
+                    return fail(FHE_EINVAL, "polynomial without non-constant terms");
+                }
             }
             for (uint32_t k = n.degree + 1; k < 4; ++k) n.coeffs[k] = 0.0;
         } else if (s.kind == FHE_NODE_RELU) {

@@ -53,7 +53,8 @@ class NodeDesc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_uint32), ("n_out", ctypes.c_uint32),
                 ("row_ptr", ctypes.POINTER(ctypes.c_uint32)), ("col_idx", ctypes.POINTER(ctypes.c_uint32)),
                 ("weight", ctypes.POINTER(ctypes.c_double)), ("bias", ctypes.POINTER(ctypes.c_double)),
-                ("coeffs", ctypes.c_double * 4), ("degree", ctypes.c_uint32), ("conv", ctypes.c_uint32 * 6)]
+                ("coeffs", ctypes.c_double * 4), ("degree", ctypes.c_uint32), ("conv", ctypes.c_uint32 * 6),
+                ("coeffs_hi", ctypes.POINTER(ctypes.c_double))]
 
 
 class Request(ctypes.Structure):
@@ -226,11 +227,15 @@ class _GraphArrays:
                     d.conv[k] = int(n[key])
             if n["kind"] == "poly":
                 a = [float(v) for v in n["coeffs"]]
-                if not 2 <= len(a) <= 4:
-                    raise ValueError("polynomial nodes take 2 to 4 coefficients (degree 1..3)")
+                if not 2 <= len(a) <= 32:
+                    raise ValueError("polynomial nodes take 2 to 32 coefficients (degree 1..31)")
                 d.degree = len(a) - 1
-                for k in range(len(a)):
+                for k in range(min(4, len(a))):
                     d.coeffs[k] = a[k]
+                if len(a) > 4:
+                    hi = np.ascontiguousarray(a, dtype=np.float64)
+                    self.keep.append(hi)
+                    d.coeffs_hi = hi.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
             elif n["kind"] == "relu":
                 d.coeffs[0] = float(n["q"])
         src = np.array([e[0] for e in graph["edges"]], dtype=np.uint32)

@@ -222,6 +222,21 @@ def cnn_masquerade(n_ct, slots, seed=7, side=8, filters=2, k=3, stride=2, hidden
     return {"nodes": nodes, "edges": edges}, x
 
 
+def poly_chain(n_slots, seed=19, n_in=3, degrees=(5, 4)):
+    """dense -> polynomial of degree 5 -> dense -> polynomial of degree 4: the
+    generic-degree activation (Chebyshev-like random coefficients)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    blocks = []
+    for d in degrees:
+        Wm = rng.normal(0.0, np.sqrt(1.0 / n_in), size=(n_in, n_in))
+        blocks.append(_linear(*dense_csr(Wm), rng.normal(0.0, 0.1, size=n_in)))
+        a = list(rng.normal(0.0, 0.3, size=d + 1) / (1.0 + np.arange(d + 1)))
+        blocks.append({"kind": "poly", "coeffs": a})
+    g = chain_graph(n_in, blocks)
+    x = rng.uniform(-1.0, 1.0, size=(n_in, n_slots))
+    return g, x
+
+
 def deep_mlp(n_slots, seed=13, n_in=4, hidden=4, n_out=2):
     """Multiplicative depth 8 (dense, sigmoid fit, dense, sigmoid fit, dense,
     square), so Alg. parameterise asks for N = 32768 and [60, 40 x 8, 60]."""

@@ -50,7 +50,7 @@ def test_gaussian_table_matches_oracle():
     assert fhe.gauss_table() == params.gauss_cdt()
 
 
-@pytest.mark.parametrize("builder", [W.cfg0, W.cfg1, W.cfg2, W.cnn_relu, W.mini_cnn_relu, W.deep_mlp])
+@pytest.mark.parametrize("builder", [W.cfg0, W.cfg1, W.cfg2, W.cnn_relu, W.mini_cnn_relu, W.deep_mlp, W.poly_chain])
 def test_autohe_matches_oracle(builder):
     g, _ = builder(n_slots=4)
     gof, gcost = fhe.autohe(g)

@@ -356,6 +356,17 @@ def test_masquerade_cnn_bit_exact_per_group():
     net.close()
 
 
+def test_graph_generic_degree_polynomials_bit_exact():
+    """Polynomials of degree 5 and 4 (powers by products, one combining
+    rescale) inside a graph: bit-exact against the oracle."""
+    graph, x = W.poly_chain(n_slots=512)
+    gof, gcost = fhe.autohe(graph)
+    assert gcost == [1 + 4 + 1 + 3]
+    g, o = pair(1024, [60] + [40] * 9 + [60])
+    err = _graph_parity(g, o, graph, [x], [0])
+    assert err < 1e-4
+
+
 def test_graph_relu_and_affine_bit_exact():
     """Eq. relu_approximate (degree 2) after the convolution and the linear
     sigmoid 0.5 + 0.197 x (degree 1) after the dense layer."""

@@ -248,7 +248,27 @@ def test_affine_and_poly2_blocks(ctx64):
     ref = a[0] + a[1] * z + a[2] * z * z
     assert np.max(np.abs(ctx.decode(ctx.decrypt(y2), y2.scale) - ref)) < 1e-6
     with pytest.raises(ValueError):
-        ctx.poly(ct, [1.0, 2.0, 3.0, 4.0, 5.0])
+        ctx.poly(ct, [0.1] * 33)                 # degree 32: above the supported 31
+
+
+@pytest.mark.parametrize("d", [4, 5, 7, 8])
+def test_higher_degree_polynomial_block(d):
+    """Degree >= 4 by products of powers and one combining rescale: decrypts
+    to the plaintext polynomial, uses ceil(log2 d) + 1 levels, keeps the
+    scale, and its node cost says the same."""
+    from oracle import params
+    depth = (d - 1).bit_length() + 1
+    ctx = ckks.Context(64, [60] + [40] * (depth + 1) + [60])
+    ctx.keygen(1)
+    z = np.random.default_rng(d).uniform(-1.2, 1.2, ctx.N // 2)
+    ct = ctx.encrypt(ctx.encode(z), 11)
+    a = list(np.random.default_rng(100 + d).normal(0.0, 0.3, d + 1))
+    a[2] = 0.0                                 # a zero coefficient is skipped
+    y = ctx.poly(ct, a)
+    assert ctx.L_top - y.level == depth == params.node_cost({"kind": "poly", "coeffs": a})
+    assert abs(y.scale / ctx.delta - 1) < 1e-9
+    ref = sum(a[i] * z ** i for i in range(d + 1))
+    assert np.max(np.abs(ctx.decode(ctx.decrypt(y), y.scale) - ref)) < 1e-6
 
 
 @pytest.mark.parametrize("q", [1.0, 3.0, 4.0, 10.0])
