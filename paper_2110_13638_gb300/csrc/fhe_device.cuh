@@ -716,7 +716,11 @@ __device__ __forceinline__ void pass_io_k(int k, int logN, int s0, const ulonglo
     }
 }
 
-constexpr int kEpiBatch = 2;   // epilogue pre-loads issued together (more spills at 64 registers)
+// epilogue pre-loads issued together: two at 64 registers per thread (more
+// spill), up to eight with the 128 registers of the 512-thread schedules
+// (measured on the key-switching step: 8 and 16 beat 4 and 2)
+constexpr int kEpiBatch = 2;
+constexpr int kEpiBatchWide = 8;
 
 template <bool INV, int LOGR, int MAXT, class Op>
 __global__ void __launch_bounds__(MAXT, 1) k_ntt_io(Op op, NttTables T)
@@ -759,7 +763,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_ntt_io(Op op, NttTables T)
                 };
                 auto pepi = [&](auto Rc, int j0, int lsh, u64* x) {
                     constexpr int R = decltype(Rc)::value;
-                    constexpr int B = R < kEpiBatch ? R : kEpiBatch;
+                    constexpr int EB = MAXT <= 512 ? kEpiBatchWide : kEpiBatch;
+                    constexpr int B = R < EB ? R : EB;
 #pragma unroll
                     for (int i0 = 0; i0 < R; i0 += B) {
                         typename Op::Pre pr[B];
