@@ -15,7 +15,14 @@
  *   - `stream` is a cudaStream_t (NULL = legacy default stream); device work is
  *     enqueued on it and the call returns without waiting unless stated;
  *   - one context must not be used from two streams or threads at once (its
- *     workspace is shared by the calls made on it).
+ *     workspace is shared by the calls made on it); forks of one parameter
+ *     set (fhe_ctx_fork) may run concurrently.  Keys (fhe_keygen,
+ *     fhe_galois_keygen) are generated on the parent before its forks use
+ *     them; the packed convolution generates its missing rotation keys on
+ *     first use, so run one batch of a graph that has it before forking;
+ *   - growing a workspace or batch area (the first call at a larger size)
+ *     synchronises the device before freeing the old buffer; size them with
+ *     one call before stream capture or latency-critical use.
  *
  * Data layout:
  *   residue polynomial  : N u64 words, every word < its prime

@@ -169,6 +169,10 @@ void k_add(const fhe_ctx* c, const u64* a, const u64* b, u64* out, uint32_t n_ct
 void k_tensor(const fhe_ctx* c, const u64* a, const u64* b, u64* out3, uint32_t n_ct, uint32_t L, cudaStream_t st);
 // scratch: relin_scratch_bytes(n_ct, L)
 size_t relin_scratch_bytes(const fhe_ctx* c, uint32_t n_ct, uint32_t L);
+// Raise a kernel's dynamic shared-memory limit to `bytes` on the current
+// device (once per kernel, device and size; thread-safe).
+void ensure_smem(const void* kernel, size_t bytes);
+
 // key: the relinearisation key unless another key of the same layout is given
 void k_relin(const fhe_ctx* c, const u64* d3, u64* out2, uint32_t n_ct, uint32_t L, void* scratch, cudaStream_t st,
              const ulonglong2* key = nullptr);

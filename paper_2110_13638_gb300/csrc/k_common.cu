@@ -1,5 +1,8 @@
 // k_common.cu -- launch accounting, plain transforms, element-wise kernels,
 // per-level division constants.
+#include <map>
+#include <mutex>
+
 #include "launch.cuh"
 
 namespace fhe {
@@ -24,6 +27,20 @@ LaunchScope::LaunchScope(const fhe_ctx* ctx, const char* family, cudaStream_t s)
 LaunchScope::~LaunchScope()
 {
     if (idx >= 0) cudaEventRecord(c->prof_ev[idx + 1], st);
+}
+
+void ensure_smem(const void* kernel, size_t bytes)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, size_t> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& have = done[{kernel, dev}];
+    if (have < bytes) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        have = bytes;
+    }
 }
 
 const char* ntt_variant_name(int v)

@@ -206,11 +206,7 @@ void encode_coefficients(const fhe_ctx* c, const double* slots, uint32_t n_ct, d
     const int logA = split_log(N / 2, 4096);
     const int H = (N / 2) >> logA;
     const size_t smem = (size_t)H * 2 * sizeof(ulonglong2);
-    static size_t configured = 0;
-    if (configured < smem) {
-        cudaFuncSetAttribute(k_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        configured = smem;
-    }
+    ensure_smem((const void*)k_encode_kernel, smem);
     int thr = H / 2;
     thr = thr < 32 ? 32 : (thr > 512 ? 512 : thr);
     {
@@ -296,11 +292,7 @@ void k_decode(const fhe_ctx* c, const i64* m, uint32_t n_ct, double scale, doubl
     while (((N / 2) >> logA) > 8192) ++logA;
     const int H = (N / 2) >> logA;
     const size_t smem = (size_t)H * sizeof(double2);
-    static size_t configured = 0;
-    if (configured < smem) {
-        cudaFuncSetAttribute(k_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        configured = smem;
-    }
+    ensure_smem((const void*)k_decode_kernel, smem);
     int thr = H / 2;
     thr = thr < 32 ? 32 : (thr > 512 ? 512 : thr);
     LaunchScope ls(c, "decode_fft", st);

@@ -75,21 +75,14 @@ static void launch_ntt_v(const fhe_ctx* c, const Op& op, int count, cudaStream_t
     int thr = N >> LOGR;
     thr = thr < 32 ? 32 : (thr > MAXT ? MAXT : thr);
     const size_t smem = (size_t)ntt_smem_words(N) * sizeof(u64);
-    static size_t configured = 0;        // per instantiation
     if constexpr (IO) {
         auto fn = k_ntt_io<INV, LOGR, MAXT, Op>;
-        if (configured < smem) {
-            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            configured = smem;
-        }
+        ensure_smem((const void*)fn, smem);
         LaunchScope ls(c, Op::family(), st);
         fn<<<count, thr, smem, st>>>(op, c->tabs());
     } else {
         auto fn = k_ntt_op<INV, LOGR, MAXT, Op>;
-        if (configured < smem) {
-            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            configured = smem;
-        }
+        ensure_smem((const void*)fn, smem);
         LaunchScope ls(c, Op::family(), st);
         fn<<<count, thr, smem, st>>>(op, c->tabs());
     }
