@@ -107,7 +107,7 @@ __global__ void k_add_kernel(const u64* __restrict__ a, const u64* __restrict__ 
                              size_t total, int L, int logN, const PrimeC* __restrict__ pc)
 {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const int r = (int)((i >> logN) % L);
+        const uint32_t r = (uint32_t)(i >> logN) % (uint32_t)L;      // row index math in 32 bits
         const u64 q = pc[r].q;
         out[i] = add_mod(a[i], b[i], q);
     }
@@ -123,32 +123,45 @@ void k_add(const fhe_ctx* c, const u64* a, const u64* b, u64* out, uint32_t n_ct
     k_add_kernel<<<ew_grid(total), 256, 0, st>>>(a, b, out, total, (int)L, (int)c->logN, c->d_pc);
 }
 
+// thread covers (ct, r, j); a squaring (a == b) needs three products
+template <bool SQUARE>
 __global__ void k_tensor_kernel(const u64* __restrict__ a, const u64* __restrict__ b, u64* __restrict__ out,
-                                size_t per_comp, int n_ct, int L, int logN, const PrimeC* __restrict__ pc)
+                                size_t total, int L, int logN, const PrimeC* __restrict__ pc)
 {
-    // per_comp = L * N; thread covers (ct, r, j)
-    const size_t total = (size_t)n_ct * per_comp;
+    const size_t per_comp = (size_t)L << logN;
+    const size_t Nm = ((size_t)1 << logN) - 1;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t ct = i / per_comp, w = i % per_comp;
-        const int r = (int)(w >> logN);
+        const uint32_t row = (uint32_t)(i >> logN);          // ct * L + r, 32-bit index math
+        const uint32_t ct = row / (uint32_t)L, r = row - ct * (uint32_t)L;
+        const size_t w = ((size_t)r << logN) + (i & Nm);
         const PrimeC P = pc[r];
-        const u64* A = a + ct * 2 * per_comp;
-        const u64* B = b + ct * 2 * per_comp;
-        const u64 a0 = A[w], a1 = A[per_comp + w], b0 = B[w], b1 = B[per_comp + w];
-        u64* O = out + ct * 3 * per_comp;
-        O[w] = mul_mod(a0, b0, P);
-        O[per_comp + w] = add_mod(mul_mod(a0, b1, P), mul_mod(a1, b0, P), P.q);
-        O[2 * per_comp + w] = mul_mod(a1, b1, P);
+        const u64* A = a + (size_t)ct * 2 * per_comp;
+        u64* O = out + (size_t)ct * 3 * per_comp;
+        const u64 a0 = A[w], a1 = A[per_comp + w];
+        if constexpr (SQUARE) {
+            const u64 m = mul_mod(a0, a1, P);
+            O[w] = mul_mod(a0, a0, P);
+            O[per_comp + w] = add_mod(m, m, P.q);
+            O[2 * per_comp + w] = mul_mod(a1, a1, P);
+        } else {
+            const u64* B = b + (size_t)ct * 2 * per_comp;
+            const u64 b0 = B[w], b1 = B[per_comp + w];
+            O[w] = mul_mod(a0, b0, P);
+            O[per_comp + w] = add_mod(mul_mod(a0, b1, P), mul_mod(a1, b0, P), P.q);
+            O[2 * per_comp + w] = mul_mod(a1, b1, P);
+        }
     }
 }
 
 void k_tensor(const fhe_ctx* c, const u64* a, const u64* b, u64* out3, uint32_t n_ct, uint32_t L, cudaStream_t st)
 {
-    const size_t per_comp = (size_t)L * c->N;
-    const size_t total = (size_t)n_ct * per_comp;
+    const size_t total = (size_t)n_ct * L * c->N;
     if (!total) return;
     LaunchScope ls(c, "tensor", st);
-    k_tensor_kernel<<<ew_grid(total), 256, 0, st>>>(a, b, out3, per_comp, (int)n_ct, (int)L, (int)c->logN, c->d_pc);
+    if (a == b)
+        k_tensor_kernel<true><<<ew_grid(total), 256, 0, st>>>(a, b, out3, total, (int)L, (int)c->logN, c->d_pc);
+    else
+        k_tensor_kernel<false><<<ew_grid(total), 256, 0, st>>>(a, b, out3, total, (int)L, (int)c->logN, c->d_pc);
 }
 
 // cres[ct * cstride + r]: residues of one integer constant per ciphertext
@@ -160,13 +173,12 @@ __global__ void k_mul_const_kernel(const u64* __restrict__ in, u64* __restrict__
 {
     const size_t Nm = ((size_t)1 << logN) - 1;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t row = i >> logN;            // (ct, comp, r) with r < L_out
-        const int r = (int)(row % L_out);
-        const size_t poly = row / L_out;
-        const size_t ct = poly / comps;
+        const uint32_t row = (uint32_t)(i >> logN);          // (ct, comp, r) with r < L_out
+        const uint32_t poly = row / (uint32_t)L_out, r = row - poly * (uint32_t)L_out;
+        const uint32_t ct = poly / (uint32_t)comps;
         const PrimeC P = pc[r];
-        const u64 x = in[((poly * L_in + r) << logN) + (i & Nm)];
-        out[i] = mul_mod(x, cres[ct * cstride + r], P);
+        const u64 x = in[(((size_t)poly * L_in + r) << logN) + (i & Nm)];
+        out[i] = mul_mod(x, cres[(size_t)ct * cstride + r], P);
     }
 }
 
@@ -185,11 +197,10 @@ __global__ void k_add_const_kernel(u64* __restrict__ ct, size_t total, int L, in
                                    int cstride, const PrimeC* __restrict__ pc)
 {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t row = i >> logN;                // (ct, r) over comp 0 only
-        const size_t n = row / L;
-        const int r = (int)(row % L);
-        const size_t idx = (n * 2 * L + r) * ((size_t)1 << logN) + (i & (((size_t)1 << logN) - 1));
-        ct[idx] = add_mod(ct[idx], cres[n * cstride + r], pc[r].q);
+        const uint32_t row = (uint32_t)(i >> logN);          // (ct, r) over comp 0 only
+        const uint32_t n = row / (uint32_t)L, r = row - n * (uint32_t)L;
+        const size_t idx = (((size_t)n * 2 * L + r) << logN) + (i & (((size_t)1 << logN) - 1));
+        ct[idx] = add_mod(ct[idx], cres[(size_t)n * cstride + r], pc[r].q);
     }
 }
 
@@ -209,11 +220,10 @@ __global__ void k_poly_combine_kernel(u64* __restrict__ t1, const u64* __restric
 {
     const size_t Nm = ((size_t)1 << logN) - 1;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t row = i >> logN;            // (ct, comp, r), r < L1
-        const int r = (int)(row % L1);
-        const size_t poly = row / L1;
+        const uint32_t row = (uint32_t)(i >> logN);          // (ct, comp, r), r < L1
+        const uint32_t poly = row / (uint32_t)L1, r = row - poly * (uint32_t)L1;
         const PrimeC P = pc[r];
-        const u64 xv = x[((poly * Lx + r) << logN) + (i & Nm)];
+        const u64 xv = x[(((size_t)poly * Lx + r) << logN) + (i & Nm)];
         u64 a = mul_mod(x2[i], c2[r], P);
         if (accumulate) a = add_mod(t1[i], a, P.q);
         t1[i] = add_mod(a, mul_mod(xv, c1[r], P), P.q);
@@ -252,12 +262,11 @@ __global__ void k_plain_mac_kernel(u64* __restrict__ Y, const u64* __restrict__ 
 {
     const size_t Nm = ((size_t)1 << logN) - 1;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t row = i >> logN;            // ((f * n + ct) * 2 + comp) * L + r
-        const int r = (int)(row % L);
-        const size_t fc = row / L;               // (f * n + ct) * 2 + comp
+        const uint32_t row = (uint32_t)(i >> logN);          // ((f * n + ct) * 2 + comp) * L + r
+        const uint32_t fc = row / (uint32_t)L, r = row - fc * (uint32_t)L;
         const int comp = (int)(fc & 1);
-        const size_t fi = fc >> 1;
-        const int ct = (int)(fi % n), f = (int)(fi / n);
+        const uint32_t fi = fc >> 1;
+        const int f = (int)(fi / (uint32_t)n), ct = (int)(fi - (uint32_t)f * (uint32_t)n);
         const int j = (int)(i & Nm);
         const PrimeC P = pc[r];
         const u64 x = X[((((size_t)ct * 2 + comp) * L + r) << logN) + j];
@@ -283,11 +292,10 @@ __global__ void k_add_plain_kernel(u64* __restrict__ out, const u64* __restrict_
 {
     const size_t Nm = ((size_t)1 << logN) - 1;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t row = i >> logN;            // (f * n + ct) * L1 + r, component 0 only
-        const int r = (int)(row % L1);
-        const size_t fi = row / L1;
-        const int f = (int)(fi / n);
-        const size_t o = (((fi * 2) * L1 + r) << logN) + (i & Nm);
+        const uint32_t row = (uint32_t)(i >> logN);          // (f * n + ct) * L1 + r, component 0 only
+        const uint32_t fi = row / (uint32_t)L1, r = row - fi * (uint32_t)L1;
+        const int f = (int)(fi / (uint32_t)n);
+        const size_t o = ((((size_t)fi * 2) * L1 + r) << logN) + (i & Nm);
         out[o] = add_mod(out[o], bias[(((size_t)f * L1 + r) << logN) + (i & Nm)], pc[r].q);
     }
 }

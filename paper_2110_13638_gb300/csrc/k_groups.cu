@@ -24,8 +24,9 @@ __global__ void k_tensor_groups_kernel(TensorGroups G, int logN, const PrimeC* _
         while (g + 1 < G.ng && i >= G.start[g + 1]) ++g;
         const size_t w0 = i - G.start[g];
         const size_t per_comp = (size_t)G.L[g] << logN;
-        const size_t ct = w0 / per_comp, w = w0 % per_comp;
-        const int r = (int)(w >> logN);
+        const uint32_t row = (uint32_t)(w0 >> logN);         // ct * L + r, 32-bit index math
+        const uint32_t ct = row / (uint32_t)G.L[g], r = row - ct * (uint32_t)G.L[g];
+        const size_t w = ((size_t)r << logN) + (w0 & (((size_t)1 << logN) - 1));
         const PrimeC P = pc[r];
         const u64* A = G.a[g] + ct * 2 * per_comp;
         const u64* B = G.b[g] + ct * 2 * per_comp;

@@ -194,16 +194,15 @@ __global__ void k_automorph_kernel(const u64* __restrict__ ct, u64* __restrict__
 {
     const size_t Nm = ((size_t)1 << logN) - 1;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t row = i >> logN;           // (ct, comp of d3, r)
-        const int r = (int)(row % L);
-        const size_t rest = row / L;
-        const int comp = (int)(rest % 3);
-        const size_t n = rest / 3;
+        const uint32_t row = (uint32_t)(i >> logN);         // (ct, comp of d3, r), 32-bit index math
+        const uint32_t rest = row / (uint32_t)L, r = row - rest * (uint32_t)L;
+        const uint32_t n = rest / 3u;
+        const int comp = (int)(rest - n * 3u);
         const int j = (int)(i & Nm);
         u64 v = 0;
         if (comp != 1) {
             const int src_comp = comp == 0 ? 0 : 1;
-            v = ct[(((n * 2 + src_comp) * L + r) << logN) + galois_index(j, k, logN)];
+            v = ct[((((size_t)n * 2 + src_comp) * L + r) << logN) + galois_index(j, k, logN)];
         }
         d3[i] = v;
     }
