@@ -691,11 +691,18 @@ def run_serve(args):
 
 
 def run_reference(args):
+    """The oracle as it stands on the host cores (single thread), each step a
+    bounded sample of one request (one unit of every stage, extrapolated),
+    on the same metric and configuration as the GPU arm; rank 0 only."""
     rank, world, local = _env_rank()
     if rank != 0:
         return
+    if args.workload not in ("cnn", "mlp", "dense_square", "cnn_relu", "deep"):
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the graph workloads "
+                                                              "(cnn, mlp, dense_square, cnn_relu, deep)"}))
+        return
     for _ in range(args.warmup):
-        pass           # the oracle has no warm state worth priming beyond one sample
+        oracle_sample(args.workload)
     vals = []
     last = None
     t0 = time.perf_counter()
@@ -705,10 +712,17 @@ def run_reference(args):
     wall = time.perf_counter() - t0
     value = statistics.median(vals)
     g, x, desc = workload(args.workload)
+    from oracle.params import autohe, parameterise
+    from paper_2110_13638_gb300 import workloads as W
+    p = parameterise(max(autohe(g, W.input_nodes(g))[1]))
+    outs = sum(len(n["row_ptr"]) - 1 for n in g["nodes"][-2:-1] if n["kind"] == "linear") or None
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(x.shape[1] / value * 1000.0, 1), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": desc}, "impl": "reference",
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": DATA.get(args.workload, "synthetic"),
+            "config": {"workload": desc, "N": p["poly_modulus_degree"], "coeff_modulus_bits": p["coeff_modulus"],
+                       "log_scale": 40, "samples_per_request": int(x.shape[1]), "input_ciphertexts": int(x.shape[0]),
+                       "output_ciphertexts": outs, "parallelism": "host, one thread"},
+            "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": last["sample"], "host": last["host"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
