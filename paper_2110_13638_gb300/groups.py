@@ -191,7 +191,13 @@ class GroupedNetwork:
                     if nodes[i]["kind"] == "input" or z.shape[1] > ctx.N // 2:
                         raise ValueError("node %d carries %d slots; its group's ring holds %d"
                                          % (i, z.shape[1], ctx.N // 2))
-                    z = torch.nn.functional.pad(z, (0, ctx.N // 2 - z.shape[1]))   # smaller ring upstream
+                    # smaller ring upstream: the client widens each row with zeros
+                    m_up, m_dn = z.shape[1], ctx.N // 2
+                    idx = np.full((z.shape[0], m_dn), -1, dtype=np.int64)
+                    idx[:, :m_up] = np.arange(z.shape[0] * m_up, dtype=np.int64).reshape(z.shape[0], m_up)
+                    wide = torch.empty((z.shape[0], m_dn), dtype=torch.float64, device=z.device)
+                    fhe.gather_slots(z.contiguous(), torch.tensor(idx, device=z.device), z.shape[0], m_dn, wide, stream)
+                    z = wide
                 first = first_ct_id + (i << 20) if nodes[i]["kind"] == "input" else refresh_ct_id(i, 0)
                 ct = ctx.empty_ct(z.shape[0], ctx.L_top)
                 ctx.encode_encrypt(z, ctx.delta, first, ct, stream)
