@@ -176,6 +176,21 @@ def with_rotation(g, after):
     return {"nodes": nodes, "edges": edges}
 
 
+def two_rings(n_slots=4096, seed=23, n_in=4, hidden=4, n_out=2):
+    """dense -> square | rotation | dense -> sigmoid fit -> dense: groups of
+    cost 2 (N = 8192) and 4 (N = 16384); the refresh widens the slots."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    W0 = rng.normal(0.0, 0.5, size=(hidden, n_in))
+    W1 = rng.normal(0.0, 0.5, size=(hidden, hidden))
+    W2 = rng.normal(0.0, 0.5, size=(n_out, hidden))
+    g = chain_graph(n_in, [_linear(*dense_csr(W0), np.zeros(hidden)), {"kind": "square"},
+                           _linear(*dense_csr(W1), rng.normal(0.0, 0.1, size=hidden)),
+                           {"kind": "poly", "coeffs": sigmoid_fit()},
+                           _linear(*dense_csr(W2), np.zeros(n_out))])
+    x = rng.uniform(-1.0, 1.0, size=(n_in, n_slots))
+    return with_rotation(g, 2), x
+
+
 def cnn_rotate(n_slots=8192, **kw):
     """The CNN with one rotation after the first sigmoid fit: groups of cost
     3 (conv, sigmoid) and 4 (dense, sigmoid, dense) instead of one of cost 7."""

@@ -312,6 +312,35 @@ def test_rotation_bit_exact(N, bits, L, steps):
         g.rotate(ct, g.L_top, 11, rot)          # no key for this step
 
 
+def test_grouped_rotation_between_rings():
+    """Groups of cost 2 and 4 get N = 8192 and N = 16384 from Alg.
+    parameterise; the refresh widens the decoded slots to the larger ring.
+    Group 1 bit-exact from the device's refreshed ciphertexts; decoded
+    outputs within 1e-4 of FP64 on the samples that entered."""
+    from paper_2110_13638_gb300 import groups
+    graph, x = W.two_rings(n_slots=4096)
+    net = groups.GroupedNetwork(graph, seed=0)
+    assert [net.ctx[i].N for i in range(2)] == [8192, 16384]
+    res = net.evaluate([torch.tensor(x, device="cuda")], first_ct_id=0)
+    torch.cuda.synchronize()
+    rot = [i for i, n in enumerate(graph["nodes"]) if n["kind"] == "rotate"][0]
+    out_node = len(graph["nodes"]) - 1
+    g1 = net.ctx[1]
+    o1 = ckks.Context(16384, fhe.parameterise(4, 40, 1.5)[1], 40)
+    o1.keygen(1)                                   # group g keys from seed + g
+    fresh = download(g1, net.last_ingress[rot], g1.L_top)
+    cts1 = [ckks.Ciphertext(fresh[k], g1.L_top, o1.delta) for k in range(fresh.shape[0])]
+    seg1 = W.chain_graph(fresh.shape[0], graph["nodes"][rot + 1:out_node])
+    (_, y1), = ckks.eval_graph(o1, seg1, [0], [cts1]).items()
+    dev1, L1, _ = net.last_sinks[out_node]
+    got1 = download(g1, dev1.contiguous(), L1)
+    for k, y in enumerate(y1):
+        assert np.array_equal(got1[k], y.c), k
+    ref = ckks.forward_fp64(graph, W.input_nodes(graph), [x])
+    assert float(np.max(np.abs(res[out_node].cpu().numpy()[:, :4096] - ref[out_node]))) < 1e-4
+    net.close()
+
+
 def test_masquerade_cnn_bit_exact_per_group():
     """Kernel masquerading on packed 8x8 images (8 per ciphertext at
     N = 1024): group 0 (packed conv through rotations + sigmoid) bit-exact
