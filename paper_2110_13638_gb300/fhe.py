@@ -460,18 +460,15 @@ class Graph:
         x [n_in][>= n] and y [n_out][>= n] with unit column stride, or
         (x, y, n) to use only the first n columns.  Packs them into the slots,
         encrypts, evaluates, decrypts and decodes in one call."""
+        import torch
         arr = (Request * max(1, len(requests)))()
         for k, rq in enumerate(requests):
             x, y = rq[0], rq[1]
             n = rq[2] if len(rq) > 2 else x.shape[1]
-            assert x.dtype == y.dtype == torch_float64() and x.stride(1) == 1 and y.stride(1) == 1
+            if x.dtype != torch.float64 or y.dtype != torch.float64 or x.stride(1) != 1 or y.stride(1) != 1:
+                raise ValueError("requests take float64 tensors with unit column stride")
             arr[k] = Request(x.data_ptr(), n, x.stride(0), y.data_ptr(), y.stride(0))
         _check(lib().fhe_eval_batch(ctx.h, self.h, arr, len(requests), first_ct_id, _stream(stream)))
-
-
-def torch_float64():
-    import torch
-    return torch.float64
 
 
 def raw_u64(t):
