@@ -385,6 +385,33 @@ def test_masquerade_cnn_bit_exact_per_group():
     net.close()
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("N", [256, 4096])
+def test_every_schedule_at_small_rings(N, variant):
+    """Rings whose last register pass is a full radix-16 pass (log2 N a
+    multiple of 4) or shorter: every schedule gives the oracle's
+    mul + relinearise + rescale and key-switching results."""
+    import os
+    bits = [60, 40, 40, 40, 60]
+    os.environ["FHE_NTT_VARIANT"] = str(variant)
+    try:
+        g = fhe.Context(N, bits, 40)
+    finally:
+        del os.environ["FHE_NTT_VARIANT"]
+    g.keygen(0)
+    o = ckks.Context(N, bits, 40)
+    o.keygen(0)
+    rng = np.random.default_rng(N + variant)
+    L = 4
+    A, B = rand_ct(o, L, rng), rand_ct(o, L, rng)
+    ta, tb = upload(g, [A], L), upload(g, [B], L)
+    out = g.empty_ct(1, L - 1)
+    g.mul_relin_rescale(ta, tb, L, out)
+    want = o.rescale(o.relinearise(o.tensor(ckks.Ciphertext(A, L, 1.0), ckks.Ciphertext(B, L, 1.0)))).c
+    assert np.array_equal(download(g, out, L - 1)[0], want)
+    g.close()
+
+
 def test_graph_generic_degree_polynomials_bit_exact():
     """Polynomials of degree 5 and 4 (powers by products, one combining
     rescale) inside a graph: bit-exact against the oracle."""
