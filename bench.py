@@ -690,10 +690,15 @@ def run_serve(args):
     print(json.dumps(out), flush=True)
 
 
+def _oracle_worker(name):
+    return oracle_sample(name)
+
+
 def run_reference(args):
-    """The oracle as it stands on the host cores (single thread), each step a
-    bounded sample of one request (one unit of every stage, extrapolated),
-    on the same metric and configuration as the GPU arm; rank 0 only."""
+    """The oracle as it stands on every host core: each step runs one bounded
+    sample of the request (one unit of every stage, extrapolated) in each of
+    os.cpu_count() spawned processes at once; the step's rate is the sum of
+    their rates.  Same metric and configuration as the GPU arm; rank 0 only."""
     rank, world, local = _env_rank()
     if rank != 0:
         return
@@ -701,31 +706,35 @@ def run_reference(args):
         print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the graph workloads "
                                                               "(cnn, mlp, dense_square, cnn_relu, deep)"}))
         return
-    for _ in range(args.warmup):
-        oracle_sample(args.workload)
-    vals = []
-    last = None
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        last = oracle_sample(args.workload)
-        vals.append(last["value"])
-    wall = time.perf_counter() - t0
+    import multiprocessing as mp
+    procs = max(1, os.cpu_count() or 1)
+    vals, last = [], None
+    with mp.get_context("spawn").Pool(procs) as pool:
+        for _ in range(args.warmup):
+            pool.map(_oracle_worker, [args.workload] * procs)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            res = pool.map(_oracle_worker, [args.workload] * procs)
+            vals.append(sum(r["value"] for r in res))
+            last = res[0]
+        wall = time.perf_counter() - t0
     value = statistics.median(vals)
     g, x, desc = workload(args.workload)
     from oracle.params import autohe, parameterise
     from paper_2110_13638_gb300 import workloads as W
     p = parameterise(max(autohe(g, W.input_nodes(g))[1]))
     outs = sum(len(n["row_ptr"]) - 1 for n in g["nodes"][-2:-1] if n["kind"] == "linear") or None
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(x.shape[1] / value * 1000.0, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": DATA.get(args.workload, "synthetic"),
             "config": {"workload": desc, "N": p["poly_modulus_degree"], "coeff_modulus_bits": p["coeff_modulus"],
                        "log_scale": 40, "samples_per_request": int(x.shape[1]), "input_ciphertexts": int(x.shape[0]),
-                       "output_ciphertexts": outs, "parallelism": "host, one thread"},
+                       "output_ciphertexts": outs, "parallelism": "host, %d processes" % procs},
             "impl": "reference",
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": last["sample"], "host": last["host"]},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": procs, "kind": "oracle",
+                             "sample": "%d concurrent processes, each: %s" % (procs, last["sample"]),
+                             "host": last["host"]},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": round(wall, 1)}
     print(json.dumps(line), flush=True)
 
