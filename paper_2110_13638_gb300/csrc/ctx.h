@@ -205,9 +205,6 @@ void k_mul_const(const fhe_ctx* c, const u64* in, u64* out, uint32_t n_ct, uint3
 void k_add_const(const fhe_ctx* c, u64* ct, uint32_t n_ct, uint32_t L, const u64* cres, uint32_t cstride,
                  cudaStream_t st);
 // gather-MAC: Y[o][k][r] = sum_e W[e][r] X[col[e]][k][r] over CSR row o (all at level L)
-void k_linear_mac(const fhe_ctx* c, const u64* X, uint32_t n_in, const uint32_t* row_ptr, const uint32_t* col,
-                  const u64* Wres, uint32_t n_out, uint32_t L, u64* Y, cudaStream_t st);
-
 // tiled gather-MAC (rows sharing a column list computed together)
 constexpr int kMacTile = 6;
 // primes below this bound store MAC weights as 21-bit limbs (wL | wH << 32)

@@ -270,7 +270,8 @@ struct NttTables {
 //                                              for several j before any store)
 //   void store(int p, int u, int j, u64 v, const Pre&, const PrimeC&) const -- v in [0, q)
 //                                              ([0, 4q) after a forward transform if
-//                                              the Op declares kLazyStore)
+//                                              the Op declares kLazyStore; below 36 q
+//                                              in the fused-I/O kernel's unreduced form)
 // Grid-stride over units so one launch may cover any batch.  Prologue loads
 // and epilogue pre-loads are issued kUnroll at a time per thread.
 constexpr int kUnroll = 4;
@@ -646,9 +647,31 @@ __global__ void __launch_bounds__(kThr2) k_ntt2_second(Op op, NttTables T, Split
 // the prologue (op.load: the group's 2^K global loads issued together) and
 // the last register pass hands its group straight to the epilogue
 // (op.pre / op.store), so shared memory is only used between passes.
-template <bool INV, int K, class Get, class Put>
+//
+// Butterflies come in two forms.  RED: Harvey's, values brought back below
+// 2q before each butterfly (forward: X; inverse: the sum).  Unreduced, for
+// small primes: the Shoup product stays in [0, 2q) for any 64-bit
+// multiplicand, so nothing else needs reducing while the values fit 64 bits.
+//  - forward (q < kFwdNoRedBound): X is used as it is and both outputs grow
+//    by at most 2q per stage, so inputs in [0, 4q) end below
+//    (4 + 2 logN) q <= 36 q < 2^64 for logN <= 16; the epilogue reduces once;
+//  - inverse (q < kInvNoRedBound): the sum X + Y is kept as it is, so after
+//    global stage s every value is below 2^s 2q; the difference is taken as
+//    X + 2^s 2q - Y >= 0.  After logN <= 16 stages values are below
+//    2^17 q < 2^64 and the final product by N^{-1} (a Shoup product, valid
+//    for any 64-bit input) reduces them.
+constexpr u64 kFwdNoRedBound = 1ull << 58;
+constexpr u64 kInvNoRedBound = 1ull << 46;
+
+//
+// fetch(R, j0, lsh) runs before a group's values are read: the epilogue uses
+// it to issue the first batch of its global loads, whose latency then hides
+// behind the group's loads and butterflies; put(R, j0, lsh, x, fetched).
+struct NoFetch {};
+
+template <bool INV, int K, bool RED, class Get, class Put, class Fetch>
 __device__ __forceinline__ void pass_io(int logN, int s0, const ulonglong2* __restrict__ tw, u64 q, u64 q2, int tid,
-                                        int nthr, Get& get, Put& put)
+                                        int nthr, Get& get, Put& put, Fetch& fetch)
 {
     constexpr int R = 1 << K;
     const int N = 1 << logN;
@@ -658,6 +681,7 @@ __device__ __forceinline__ void pass_io(int logN, int s0, const ulonglong2* __re
         const int g = gi >> lsh;
         const int r = gi & ((1 << lsh) - 1);
         const int j0 = (g << (lsh + K)) + r;
+        auto fetched = fetch(std::integral_constant<int, R>{}, j0, lsh);
         u64 x[R];
         get(std::integral_constant<int, R>{}, j0, lsh, x);
         if (!INV) {
@@ -672,7 +696,7 @@ __device__ __forceinline__ void pass_io(int logN, int s0, const ulonglong2* __re
                     for (int t = 0; t < h; ++t) {
                         const int i = m * 2 * h + t;
                         u64 X = x[i];
-                        X = X >= q2 ? X - q2 : X;
+                        if (RED) X = X >= q2 ? X - q2 : X;
                         const u64 T = mul_shoup_lazy(x[i + h], w.x, w.y, q);
                         x[i] = X + T;
                         x[i + h] = X + q2 - T;
@@ -684,6 +708,7 @@ __device__ __forceinline__ void pass_io(int logN, int s0, const ulonglong2* __re
             for (int l = 0; l < K; ++l) {
                 const int h = 1 << l;
                 const ulonglong2* twl = tw + (N >> (s0 + l + 1)) + (g << (K - l - 1));
+                const u64 c = RED ? q2 : (q2 << (s0 + l));       // bound of Y at this stage
 #pragma unroll
                 for (int m = 0; m < (R >> (l + 1)); ++m) {
                     const ulonglong2 w = __ldg(&twl[m]);
@@ -692,28 +717,42 @@ __device__ __forceinline__ void pass_io(int logN, int s0, const ulonglong2* __re
                         const int i = m * 2 * h + t;
                         const u64 X = x[i], Y = x[i + h];
                         u64 S = X + Y;
-                        S = S >= q2 ? S - q2 : S;
+                        if (RED) S = S >= q2 ? S - q2 : S;
                         x[i] = S;
-                        x[i + h] = mul_shoup_lazy(X + q2 - Y, w.x, w.y, q);
+                        x[i + h] = mul_shoup_lazy(X + c - Y, w.x, w.y, q);
                     }
                 }
             }
         }
-        put(std::integral_constant<int, R>{}, j0, lsh, x);
+        put(std::integral_constant<int, R>{}, j0, lsh, x, fetched);
     }
 }
 
-template <bool INV, int KMAX, class Get, class Put>
+template <bool INV, int KMAX, bool RED, class Get, class Put, class Fetch>
 __device__ __forceinline__ void pass_io_k(int k, int logN, int s0, const ulonglong2* tw, u64 q, u64 q2, int tid, int nthr,
-                                          Get& get, Put& put)
+                                          Get& get, Put& put, Fetch& fetch)
 {
     if constexpr (KMAX >= 1) {
         if (k == KMAX) {
-            pass_io<INV, KMAX>(logN, s0, tw, q, q2, tid, nthr, get, put);
+            pass_io<INV, KMAX, RED>(logN, s0, tw, q, q2, tid, nthr, get, put, fetch);
             return;
         }
-        pass_io_k<INV, KMAX - 1>(k, logN, s0, tw, q, q2, tid, nthr, get, put);
+        pass_io_k<INV, KMAX - 1, RED>(k, logN, s0, tw, q, q2, tid, nthr, get, put, fetch);
     }
+}
+
+template <class Pre, int B>
+struct PreBatch {
+    Pre v[B];
+};
+
+// forward outputs of the unreduced form, below 36 q: a lazy-store Op takes
+// them as they are, any other Op gets them reduced into [0, q)
+template <class Op>
+__device__ __forceinline__ u64 fwd_out_wide(u64 x, const PrimeC& P)
+{
+    if constexpr (lazy_store<Op>::value) return x;
+    else return reduce64(x, P);
 }
 
 // epilogue pre-loads issued together: two at 64 registers per thread (more
@@ -721,6 +760,10 @@ __device__ __forceinline__ void pass_io_k(int k, int logN, int s0, const ulonglo
 // (measured on the key-switching step: 8 and 16 beat 4 and 2)
 constexpr int kEpiBatch = 2;
 constexpr int kEpiBatchWide = 8;
+// epilogue loads issued before the last pass's butterflies: four with the
+// 128 registers of the 512-thread schedules, none at 64 (they would spill)
+template <int MAXT>
+constexpr int kEpiPrefetch = MAXT <= 512 ? 4 : 0;
 
 template <bool INV, int LOGR, int MAXT, class Op>
 __global__ void __launch_bounds__(MAXT, 1) k_ntt_io(Op op, NttTables T)
@@ -740,10 +783,14 @@ __global__ void __launch_bounds__(MAXT, 1) k_ntt_io(Op op, NttTables T)
                 continue;
             }
             const u64 q = P.q, q2 = 2 * P.q;
+            const bool wide = q < (INV ? kInvNoRedBound : kFwdNoRedBound);    // block-uniform
             const ulonglong2* tw = (INV ? T.tw_inv : T.tw_fwd) + (size_t)pi * N;
             int s = 0;
             bool first = true;
             while (s < logN) {
+                // the remainder pass comes last: a small-radix last pass keeps the
+                // epilogue's registers free (the remainder first measured 37% slower
+                // on the key-switching step)
                 const int k = (logN - s) < LOGR ? (logN - s) : LOGR;
                 const bool last = s + k >= logN;
                 auto gload = [&](auto Rc, int j0, int lsh, u64* x) {
@@ -756,30 +803,64 @@ __global__ void __launch_bounds__(MAXT, 1) k_ntt_io(Op op, NttTables T)
 #pragma unroll
                     for (int i = 0; i < R; ++i) x[i] = sm[spad(j0 + (i << lsh))];
                 };
-                auto psm = [&](auto Rc, int j0, int lsh, u64* x) {
+                auto psm = [&](auto Rc, int j0, int lsh, u64* x, NoFetch) {
                     constexpr int R = decltype(Rc)::value;
 #pragma unroll
                     for (int i = 0; i < R; ++i) sm[spad(j0 + (i << lsh))] = x[i];
                 };
-                auto pepi = [&](auto Rc, int j0, int lsh, u64* x) {
+                constexpr int EB = MAXT <= 512 ? kEpiBatchWide : kEpiBatch;
+                auto nofetch = [&](auto, int, int) { return NoFetch{}; };
+                // the first PF elements' loads are issued before the
+                // butterflies, the rest in batches of EB after them
+                auto efetch = [&](auto Rc, int j0, int lsh) {
                     constexpr int R = decltype(Rc)::value;
-                    constexpr int EB = MAXT <= 512 ? kEpiBatchWide : kEpiBatch;
-                    constexpr int B = R < EB ? R : EB;
+                    constexpr int PF = R < kEpiPrefetch<MAXT> ? R : kEpiPrefetch<MAXT>;
+                    if constexpr (PF == 0) {
+                        return NoFetch{};
+                    } else {
+                        PreBatch<typename Op::Pre, PF> f;
 #pragma unroll
-                    for (int i0 = 0; i0 < R; i0 += B) {
-                        typename Op::Pre pr[B];
-#pragma unroll
-                        for (int i = 0; i < B; ++i) pr[i] = op.pre(p, u, j0 + ((i0 + i) << lsh));
-#pragma unroll
-                        for (int i = 0; i < B; ++i)
-                            op.store(p, u, j0 + ((i0 + i) << lsh),
-                                     INV ? inv_final(x[i0 + i], P) : fwd_out<Op>(x[i0 + i], q), pr[i], P);
+                        for (int i = 0; i < PF; ++i) f.v[i] = op.pre(p, u, j0 + (i << lsh));
+                        return f;
                     }
                 };
-                if (first && last) pass_io_k<INV, LOGR>(k, logN, s, tw, q, q2, tid, nthr, gload, pepi);
-                else if (first) pass_io_k<INV, LOGR>(k, logN, s, tw, q, q2, tid, nthr, gload, psm);
-                else if (last) pass_io_k<INV, LOGR>(k, logN, s, tw, q, q2, tid, nthr, gsm, pepi);
-                else pass_io_k<INV, LOGR>(k, logN, s, tw, q, q2, tid, nthr, gsm, psm);
+                auto pepi = [&](auto Rc, int j0, int lsh, u64* x, const auto& f) {
+                    constexpr int R = decltype(Rc)::value;
+                    constexpr int PF = R < kEpiPrefetch<MAXT> ? R : kEpiPrefetch<MAXT>;
+                    constexpr int B = R < EB ? R : EB;
+                    auto out = [&](int i, const typename Op::Pre& pr) {
+                        op.store(p, u, j0 + (i << lsh),
+                                 INV    ? inv_final(x[i], P)
+                                 : wide ? fwd_out_wide<Op>(x[i], P)
+                                        : fwd_out<Op>(x[i], q),
+                                 pr, P);
+                    };
+                    if constexpr (PF > 0) {
+#pragma unroll
+                        for (int i = 0; i < PF; ++i) out(i, f.v[i]);
+                    }
+#pragma unroll
+                    for (int i0 = PF; i0 < R; i0 += B) {
+                        typename Op::Pre pr[B];
+#pragma unroll
+                        for (int i = 0; i < B; ++i)
+                            if (i0 + i < R) pr[i] = op.pre(p, u, j0 + ((i0 + i) << lsh));
+#pragma unroll
+                        for (int i = 0; i < B; ++i)
+                            if (i0 + i < R) out(i0 + i, pr[i]);
+                    }
+                };
+                auto run = [&](auto redc, auto& get, auto& put, auto& fetch) {
+                    pass_io_k<INV, LOGR, decltype(redc)::value>(k, logN, s, tw, q, q2, tid, nthr, get, put, fetch);
+                };
+                auto run_rw = [&](auto& get, auto& put, auto& fetch) {
+                    if (wide) run(std::false_type{}, get, put, fetch);
+                    else run(std::true_type{}, get, put, fetch);
+                };
+                if (first && last) run_rw(gload, pepi, efetch);
+                else if (first) run_rw(gload, psm, nofetch);
+                else if (last) run_rw(gsm, pepi, efetch);
+                else run_rw(gsm, psm, nofetch);
                 __syncthreads();
                 first = false;
                 s += k;

@@ -3,52 +3,6 @@
 
 namespace fhe {
 
-// ---------------------------------------------------------------- linear layers
-// Y[o][k][r][j] = sum_{e in row o} W[e][r] * X[col[e]][k][r][j]  (mod q_r)
-// grid: x = output o (fastest, so outputs sharing inputs run together and
-// reuse the input slice from L2), y = coefficient block, z = k * L + r.
-__global__ void __launch_bounds__(256) k_mac_kernel(const u64* __restrict__ X, const uint32_t* __restrict__ row_ptr,
-                                                     const uint32_t* __restrict__ col, const u64* __restrict__ W,
-                                                     u64* __restrict__ Y, int L, int N, const PrimeC* __restrict__ pc)
-{
-    const int o = blockIdx.x;
-    const int j = blockIdx.y * blockDim.x + threadIdx.x;
-    const int kr = blockIdx.z;
-    const int r = kr % L;
-    if (j >= N) return;
-    const PrimeC P = pc[r];
-    const size_t ct_stride = (size_t)2 * L * N;
-    const size_t off = (size_t)kr * N + j;
-    const uint32_t e0 = row_ptr[o], e1 = row_ptr[o + 1];
-    u64 lo = 0, hi = 0;
-    int cnt = 0;
-    for (uint32_t e = e0; e < e1; ++e) {
-        const u64 x = X[(size_t)col[e] * ct_stride + off];
-        const u64 w = W[(size_t)e * L + r];
-        const u64 pl = x * w, ph = __umul64hi(x, w);
-        lo += pl;
-        hi += ph + (lo < pl ? 1 : 0);
-        if (++cnt == 32) {              // hi < 32 * 2^58: fold before it can overflow
-            lo = reduce128(hi, lo, P);
-            hi = 0;
-            cnt = 0;
-        }
-    }
-    Y[(size_t)o * ct_stride + off] = reduce128(hi, lo, P);
-}
-
-void k_linear_mac(const fhe_ctx* c, const u64* X, uint32_t n_in, const uint32_t* row_ptr, const uint32_t* col,
-                  const u64* Wres, uint32_t n_out, uint32_t L, u64* Y, cudaStream_t st)
-{
-    (void)n_in;
-    if (n_out == 0) return;
-    const int N = (int)c->N;
-    const int tpb = N < 256 ? N : 256;
-    dim3 grid(n_out, (N + tpb - 1) / tpb, 2 * L);
-    LaunchScope ls(c, "mac", st);
-    k_mac_kernel<<<grid, tpb, 0, st>>>(X, row_ptr, col, Wres, Y, (int)L, N, c->d_pc);
-}
-
 // Tiled form: rows sharing one column list are computed together, up to
 // kMacTile per thread, so each input word is loaded once per tile.
 //   tiles[t] = {col_off, K, n_rows, w_off}; rows[t * kMacTile + o] = output row;

@@ -129,7 +129,7 @@ struct OpModUpMac {
     }
     struct Pre {
         ulonglong2 k0, k1;
-        u64 a0, a1, dv;
+        u64 a0, a1;
     };
     __device__ Pre pre(int p, int u, int j) const
     {
@@ -144,13 +144,12 @@ struct OpModUpMac {
         } else {
             r.a0 = r.a1 = 0;
         }
-        r.dv = (t == u) ? d3[(((size_t)ct * 3 + 2) * L + t) * N + j] : 0;   // NTT(d2_t) is d2_t
         return r;
     }
     __device__ void store(int p, int u, int j, u64 v, const Pre& pr, const PrimeC& Q) const
     {
         const int ct = p / (L + 1), t = p % (L + 1);
-        if (t == u) v = pr.dv;
+        if (t == u) v = d3[(((size_t)ct * 3 + 2) * L + t) * N + j];   // direct: NTT(d2_t) is d2_t
         const u64 p0 = mul_shoup(v, pr.k0.x, pr.k0.y, Q.q);
         const u64 p1 = mul_shoup(v, pr.k1.x, pr.k1.y, Q.q);
         acc[(((size_t)ct * 2 + 0) * (L + 1) + t) * N + j] = u == 0 ? p0 : add_mod(pr.a0, p0, Q.q);
