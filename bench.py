@@ -31,9 +31,9 @@ SMS, SM_MHZ_MAX, MUL32_LANES = 152, 2070.0, 64
 # DRAM bytes (read + write) of the key-switching ModUp + key-product kernel
 # per (ciphertext, target prime, digit) unit, from one ncu capture of that
 # kernel (schedule 5) on 64 ciphertexts at L = 7 (--workload relin):
-# 231.2 MB read + 117.1 MB written over 64 * 8 * 7 units.  Scaled by units
+# 226.9 MB read + 111.3 MB written over 64 * 8 * 7 units.  Scaled by units
 # to the bench's launches.
-KS_DRAM_BYTES_PER_UNIT = (231.158272e6 + 117.12896e6) / (64 * 8 * 7)
+KS_DRAM_BYTES_PER_UNIT = (226.922496e6 + 111.259904e6) / (64 * 8 * 7)
 
 
 def _env_rank():
