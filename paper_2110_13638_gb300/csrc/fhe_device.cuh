@@ -242,6 +242,14 @@ struct lazy_store : std::false_type {};
 template <class Op>
 struct lazy_store<Op, std::void_t<decltype(Op::kLazyStore)>> : std::integral_constant<bool, Op::kLazyStore> {};
 
+// An Op that runs once per context (key generation) declares
+//   static constexpr bool kColdPath = true;
+// and gets only the reduced butterflies of the fused-I/O kernel (half the code).
+template <class Op, class = void>
+struct cold_path : std::false_type {};
+template <class Op>
+struct cold_path<Op, std::void_t<decltype(Op::kColdPath)>> : std::integral_constant<bool, Op::kColdPath> {};
+
 template <class Op>
 __device__ __forceinline__ u64 fwd_out(u64 x, u64 q)
 {
@@ -783,7 +791,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_ntt_io(Op op, NttTables T)
                 continue;
             }
             const u64 q = P.q, q2 = 2 * P.q;
-            const bool wide = q < (INV ? kInvNoRedBound : kFwdNoRedBound);    // block-uniform
+            const bool wide = !cold_path<Op>::value && q < (INV ? kInvNoRedBound : kFwdNoRedBound);  // block-uniform
             const ulonglong2* tw = (INV ? T.tw_inv : T.tw_fwd) + (size_t)pi * N;
             int s = 0;
             bool first = true;
@@ -854,8 +862,12 @@ __global__ void __launch_bounds__(MAXT, 1) k_ntt_io(Op op, NttTables T)
                     pass_io_k<INV, LOGR, decltype(redc)::value>(k, logN, s, tw, q, q2, tid, nthr, get, put, fetch);
                 };
                 auto run_rw = [&](auto& get, auto& put, auto& fetch) {
-                    if (wide) run(std::false_type{}, get, put, fetch);
-                    else run(std::true_type{}, get, put, fetch);
+                    if constexpr (cold_path<Op>::value) {
+                        run(std::true_type{}, get, put, fetch);
+                    } else {
+                        if (wide) run(std::false_type{}, get, put, fetch);
+                        else run(std::true_type{}, get, put, fetch);
+                    }
                 };
                 if (first && last) run_rw(gload, pepi, efetch);
                 else if (first) run_rw(gload, psm, nofetch);

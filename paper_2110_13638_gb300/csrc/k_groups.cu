@@ -128,11 +128,11 @@ void k_mul_relin_rescale_groups(const fhe_ctx* c, const LevelBatch* g, int ng, v
         k_tensor_groups_kernel<<<ew_grid(tg.start[ng]), 256, 0, st>>>(tg, (int)c->logN, c->d_pc);
     }
     launch_ntt<true>(c, m1, st);
-    launch_ntt<false>(c, m2, st);
+    launch_groups_modup_mac(c, m2, st);
     launch_ntt<true>(c, m3, st);
-    launch_ntt<false>(c, m4, st);
+    launch_groups_moddown(c, m4, st);
     launch_ntt<true>(c, m5, st);
-    launch_ntt<false>(c, m6, st);
+    launch_groups_divfwd(c, m6, st);
 }
 
 

@@ -210,4 +210,11 @@ struct OpModDown {
     }
 };
 
+// Grouped (MultiOp) launches of the forward steps, each compiled in a
+// translation unit of its own (k_groups_ks.cu, k_groups_fwd.cu) so the build runs them in
+// parallel.
+void launch_groups_modup_mac(const fhe_ctx* c, const MultiOp<OpModUpMac>& m, cudaStream_t st);
+void launch_groups_moddown(const fhe_ctx* c, const MultiOp<OpModDown>& m, cudaStream_t st);
+void launch_groups_divfwd(const fhe_ctx* c, const MultiOp<OpDivFwd>& m, cudaStream_t st);
+
 }  // namespace fhe
