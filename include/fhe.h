@@ -387,6 +387,12 @@ int fhe_profile_end(fhe_ctx* ctx, double* total_ms, uint64_t* launches, uint64_t
 const char* fhe_profile_families(void);
 /* Number of kernels this library has launched in the process so far. */
 int fhe_launch_count(uint64_t* out);
+/* Health hook (no counterpart in the paper): reads and clears the device
+ * fault flags of the current device.  Bit 0: a tensor-core layer MAC block
+ * gave up waiting for its matrix products (its waits are bounded, well under a
+ * second) and left its outputs unwritten.  Synchronises the device; *out = 0
+ * when no wait gave up since the last call. */
+int fhe_device_faults(uint32_t* out);
 
 const char* fhe_last_error(void);
 

@@ -995,7 +995,7 @@ int fhe_add_const(fhe_ctx* c, uint64_t* ct, const int64_t* h_c, uint32_t n_ct, u
 // ---------------------------------------------------------------- measurement
 static const char* kFamilies =
     "ntt,rescale_intt,rescale_ntt,keyswitch_intt,keyswitch_modup_mac,keyswitch_acc_intt,keyswitch_moddown,"
-    "keygen,encrypt,decrypt,encode_ntt,encode_fft,decode_fft,mac,tensor,elementwise";
+    "keygen,encrypt,decrypt,encode_ntt,encode_fft,decode_fft,mac,mac_tc,tensor,elementwise";
 
 const char* fhe_profile_families(void) { return kFamilies; }
 
@@ -1043,6 +1043,14 @@ int fhe_launch_count(uint64_t* out)
 {
     if (!out) return fail(FHE_EINVAL, "null output");
     *out = launch_count();
+    return FHE_OK;
+}
+
+int fhe_device_faults(uint32_t* out)
+{
+    if (!out) return fail(FHE_EINVAL, "null output");
+    *out = fhe::mac_tc_fault_take();
+    if (*out == 0xFFFFFFFFu) return fail(FHE_ECUDA, "reading the device fault flags failed");
     return FHE_OK;
 }
 

@@ -40,13 +40,13 @@ __global__ void __launch_bounds__(256, 2) k_mac_tiled_kernel(const u64* __restri
                                                            const uint32_t* __restrict__ rows,
                                                            const uint32_t* __restrict__ col,
                                                            const u64* __restrict__ W, u64* __restrict__ Y, int L, int N,
-                                                           const PrimeC* __restrict__ pc)
+                                                           const PrimeC* __restrict__ pc, uint64_t skip_mask)
 {
     const uint4 tl = tiles[blockIdx.x];
     const int j = blockIdx.y * blockDim.x + threadIdx.x;
     const int kr = blockIdx.z;
     const int r = kr % L;
-    if (j >= N) return;
+    if (j >= N || ((skip_mask >> r) & 1u)) return;
     const PrimeC P = pc[r];
     const size_t ct_stride = (size_t)2 * L * N;
     const u64* Xj = X + (size_t)kr * N + j;
@@ -164,14 +164,14 @@ __global__ void __launch_bounds__(256, 2) k_mac_tiled_kernel(const u64* __restri
 }
 
 void k_linear_mac_tiled(const fhe_ctx* c, const u64* X, const uint4* tiles, uint32_t n_tiles, const uint32_t* rows,
-                        const uint32_t* col, const u64* W, uint32_t L, u64* Y, cudaStream_t st)
+                        const uint32_t* col, const u64* W, uint32_t L, u64* Y, cudaStream_t st, uint64_t skip_mask)
 {
-    if (n_tiles == 0) return;
+    if (n_tiles == 0 || (L < 64 && (skip_mask & ((1ull << L) - 1)) == (1ull << L) - 1)) return;
     const int N = (int)c->N;
     const int tpb = N < 256 ? N : 256;
     dim3 grid(n_tiles, (N + tpb - 1) / tpb, 2 * L);
     LaunchScope ls(c, "mac", st);
-    k_mac_tiled_kernel<<<grid, tpb, 0, st>>>(X, tiles, rows, col, W, Y, (int)L, N, c->d_pc);
+    k_mac_tiled_kernel<<<grid, tpb, 0, st>>>(X, tiles, rows, col, W, Y, (int)L, N, c->d_pc, skip_mask);
 }
 
 

@@ -113,6 +113,7 @@ SIGNATURES = {
     "fhe_profile_end": [_P, _P, _P, _P],
     "fhe_profile_families": [],
     "fhe_launch_count": [_P],
+    "fhe_device_faults": [_P],
     "fhe_last_error": [],
 }
 
@@ -168,6 +169,13 @@ def parameterise(cost, log_scale=40, special_mult=1.5):
 def launch_count():
     out = ctypes.c_uint64()
     _check(lib().fhe_launch_count(ctypes.byref(out)))
+    return out.value
+
+
+def device_faults():
+    """Device fault flags (bit 0: a tensor-core MAC wait gave up), cleared by the read."""
+    out = ctypes.c_uint32()
+    _check(lib().fhe_device_faults(ctypes.byref(out)))
     return out.value
 
 

@@ -6,6 +6,8 @@
   (each needs only its 25 input encryptions) and must be bit-exact.
 - The whole CNN and the whole yield MLP: decrypted outputs within 1e-4 of the
   FP64 plaintext forward pass with the same polynomial activations.
+- The dense layers give the same words on the tensor cores as on the integer
+  pipes.
 - Every NTT schedule the autotuner can pick gives bit-exact results."""
 import os
 
@@ -96,6 +98,22 @@ def test_full_network_matches_fp64(ctx, builder):
     (node, r), = ref.items()
     err = float(np.max(np.abs(z - r)))
     assert err < 1e-4, (err, float(np.max(np.abs(r))))
+
+
+@pytest.mark.parametrize("builder", [W.cfg1, W.cfg2])
+def test_tensor_core_mac_equals_integer_mac(ctx, builder, monkeypatch):
+    """The dense layers on the tensor cores give the same words as on the
+    integer pipes, through the whole network.  CNN: 720 -> 100 at L = 5.
+    MLP: 64 -> 128 at L = 8 and 128 -> 32 at L = 5."""
+    g, x = builder()
+    ct = encrypt_all(ctx, x, first=7000)
+    monkeypatch.setenv("FHE_MAC_TC", "0")
+    ref, _, _ = run_graph(ctx, g, ct)
+    monkeypatch.setenv("FHE_MAC_TC", "1")
+    got, _, _ = run_graph(ctx, g, ct)
+    torch.cuda.synchronize()
+    assert torch.equal(got, ref)
+    assert fhe.device_faults() == 0
 
 
 def test_dense_square_full_matches_fp64():

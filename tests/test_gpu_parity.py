@@ -264,6 +264,22 @@ def test_graph_mini_cnn_bit_exact():
     assert err < 1e-4
 
 
+def test_dense_layer_on_tensor_cores_bit_exact():
+    """A dense 150 -> 100 layer, then x^2, at N = 1024, L = 8.  The seven
+    40-bit residues of the layer go through the tensor-core MAC: five 32-term
+    chunks, the last one ragged, and three 48-row tiles, the last one holding
+    4 rows.  The 60-bit residue goes through the integer MAC.  Every output
+    word must equal the oracle's, and no bounded wait may have given up."""
+    g, o = pair(1024, BITS9)
+    rng = np.random.Generator(np.random.PCG64(29))
+    Wm = rng.normal(0.0, 0.2, size=(100, 150))
+    graph = W.chain_graph(150, [W._linear(*W.dense_csr(Wm), rng.normal(0.0, 0.1, 100)), {"kind": "square"}])
+    x = rng.uniform(-1.0, 1.0, size=(150, 512))
+    err = _graph_parity(g, o, graph, [x], [0])
+    assert err < 1e-4
+    assert fhe.device_faults() == 0
+
+
 def test_graph_branches_bit_exact():
     g, o = pair(256, [60, 40, 40, 40, 60])
     graph, xs = W.branch_graph(n_slots=128)
