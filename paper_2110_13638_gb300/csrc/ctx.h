@@ -96,10 +96,13 @@ struct fhe_node_const {
     uint32_t* tile_rows = nullptr;
     uint32_t n_tiles = 0;
     u64* bias = nullptr;       // LINEAR: [n_out][L-1] bias residues
-    uint16_t* tcW = nullptr;   // LINEAR, dense: tensor-core weight limbs (see k_linear_mac_tc)
-    uint32_t* tc_rows = nullptr;
-    uint32_t tc_tiles = 0, tc_K = 0;
-    uint64_t tc_mask = 0;      // residues computed by the tensor-core MAC
+    struct TcPart {            // LINEAR, dense: one limb count of the tensor-core MAC
+        uint16_t* W = nullptr; // weight limbs (see k_linear_mac_tc)
+        uint32_t* rows = nullptr;
+        uint32_t tiles = 0;
+        uint64_t mask = 0;     // its residues
+    } tc[2];                   // five limbs, eight limbs
+    uint32_t tc_K = 0;
     bool tc_on = false;        // the setting the constants were made for
     u64* c3 = nullptr;         // POLY: constant residues (shared by all ciphertexts)
     u64* c2 = nullptr;
@@ -219,14 +222,17 @@ void k_linear_mac_tiled(const fhe_ctx* c, const u64* X, const uint4* tiles, uint
                         const uint32_t* col, const u64* W, uint32_t L, u64* Y, cudaStream_t st,
                         uint64_t skip_mask = 0);
 // tensor-core MAC of a dense layer (every row over the same K input columns),
-// residues r with bit r of tc_mask set (primes below kMacTcPrimeBound):
-//   Wl = bf16 weight limbs [tc residue][tile][chunk][5][48 x 32 core-matrix order],
-//   rows[tile * kMacTcRows + o] = output row (0xFFFFFFFF: none)
+// residues r with bit r of mask set: five limbs for primes below 2^41 (tiles
+// of kMacTcRows rows), eight below 2^61 (tiles of kMacTcRows8 rows):
+//   Wl = bf16 weight limbs [residue of the mask][tile][chunk][limb][rows x 32, core-matrix order],
+//   rows[tile * tile rows + o] = output row (0xFFFFFFFF: none)
 constexpr int kMacTcRows = 48;
+constexpr int kMacTcRows8 = 32;
 constexpr int kMacTcChunk = 32;
-constexpr unsigned long long kMacTcPrimeBound = 1ull << 41;
-int k_linear_mac_tc(const fhe_ctx* c, const u64* X, const uint32_t* col, uint32_t K, const uint16_t* Wl,
-                    const uint32_t* rows, uint32_t n_tiles, uint64_t tc_mask, uint32_t L, u64* Y, cudaStream_t st);
+constexpr unsigned long long kMacTcPrimeBound5 = 1ull << 41;
+constexpr unsigned long long kMacTcPrimeBound8 = 1ull << 61;
+int k_linear_mac_tc(const fhe_ctx* c, int limbs, const u64* X, const uint32_t* col, uint32_t K, const uint16_t* Wl,
+                    const uint32_t* rows, uint32_t n_tiles, uint64_t mask, uint32_t L, u64* Y, cudaStream_t st);
 // reads and clears the tensor-core MAC's fault flag (a wait that gave up); synchronous
 uint32_t mac_tc_fault_take();
 

@@ -71,14 +71,18 @@ static bool mac_tc_enabled()
     return !(e && e[0] == '0');
 }
 
-// balanced base-256 limbs of |v| < 2^40: four digits in [-128, 127] and a top
-// digit of magnitude <= 256 (the split the tensor-core MAC makes on the device)
-static void mac_tc_limbs(int64_t v, int32_t (&d)[5])
+// balanced base-256 limbs of a centred residue (|v| < 2^40 with five limbs,
+// < 2^60 with eight): n - 1 digits in [-128, 127] and a top digit taking the
+// rest (the split the tensor-core MAC makes on the device)
+static void mac_tc_limbs(int64_t v, int n, int32_t (&d)[8])
 {
-    const int64_t u = v + 0x80808080ll;
-    const uint32_t lo = (uint32_t)u;
-    for (int a = 0; a < 4; ++a) d[a] = (int32_t)((lo >> (8 * a)) & 255u) - 128;
-    d[4] = (int32_t)((u - (int64_t)lo) / 4294967296ll);
+    int64_t bias = 0;
+    for (int a = 0; a + 1 < n; ++a) bias += (int64_t)128 << (8 * a);
+    const int64_t u = v + bias;
+    const int64_t span = (int64_t)1 << (8 * (n - 1));
+    const int64_t low = u & (span - 1);
+    for (int a = 0; a + 1 < n; ++a) d[a] = (int32_t)((low >> (8 * a)) & 255) - 128;
+    d[n - 1] = (int32_t)((u - low) / span);
 }
 
 // bf16 bit pattern of a small integer (|v| <= 256: exact)
@@ -142,9 +146,9 @@ struct Exec {
             return off;
         };
         size_t o_rp = 0, o_tr = 0, o_col = 0, o_W = 0, o_b = 0, o_c3 = 0, o_c2 = 0, o_c1 = 0, o_c0 = 0;
-        size_t o_tcW = 0, o_tcr = 0;
-        uint32_t tc_tiles = 0, tc_K = 0;
-        uint64_t tc_mask = 0;
+        size_t o_tcW[2] = {0, 0}, o_tcr[2] = {0, 0};
+        uint32_t tc_tiles[2] = {0, 0}, tc_K = 0;
+        uint64_t tc_mask[2] = {0, 0};
         if (nd.kind == FHE_NODE_LINEAR) {
             const double qd = (double)c->primes[L - 1];
             // group rows with identical column lists, split groups into tiles
@@ -193,48 +197,55 @@ struct Exec {
                 const int64_t b = (int64_t)std::llround(nd.bias[o] * s_out);
                 for (uint32_t r = 0; r + 1 < L; ++r) B[(size_t)o * (L - 1) + r] = mod_signed(b, c->primes[r]);
             }
-            // dense layer (one column list shared by every row): the residues of
-            // primes below 2^41 go to the tensor-core MAC, as bf16 limb tiles
-            // (at most 8192 terms: the 64-bit class sums of the epilogue stay exact)
+            // dense layer (one column list shared by every row): its residues go
+            // to the tensor-core MAC as bf16 limb tiles, five limbs for primes
+            // below 2^41 and eight below 2^61 (at most 8192 terms: the 64-bit
+            // class sums of the epilogue stay exact)
             const bool dense = order.size() == 1 && order[0].size() >= (size_t)kMacTcChunk &&
                                order[0].size() <= 8192 && nd.n_out >= 16 && c->N % 128 == 0 && 2 * L <= 64;
             if (tc_on && dense)
-                for (uint32_t r = 0; r < L; ++r)
-                    if (c->primes[r] < kMacTcPrimeBound) tc_mask |= 1ull << r;
-            if (tc_mask) {
+                for (uint32_t r = 0; r < L; ++r) {
+                    if (c->primes[r] < kMacTcPrimeBound5) tc_mask[0] |= 1ull << r;
+                    else if (c->primes[r] < kMacTcPrimeBound8) tc_mask[1] |= 1ull << r;
+                }
+            for (int part = 0; part < 2; ++part) {
+                if (!tc_mask[part]) continue;
+                const int limbs = part == 0 ? 5 : 8;
+                const size_t NT = part == 0 ? kMacTcRows : kMacTcRows8;
                 const std::vector<uint32_t>& cols = order[0];
                 const std::vector<uint32_t>& rs = groups[cols];
                 tc_K = (uint32_t)cols.size();
-                tc_tiles = (uint32_t)((rs.size() + kMacTcRows - 1) / kMacTcRows);
+                tc_tiles[part] = (uint32_t)((rs.size() + NT - 1) / NT);
                 const size_t n_chunks = (tc_K + kMacTcChunk - 1) / kMacTcChunk;
-                const size_t plane = (size_t)kMacTcRows * kMacTcChunk;
-                const size_t n_tc = (size_t)__builtin_popcountll(tc_mask);
-                std::vector<uint16_t> Wl(n_tc * tc_tiles * n_chunks * 5 * plane, 0);
-                std::vector<uint32_t> trow((size_t)tc_tiles * kMacTcRows, 0xFFFFFFFFu);
+                const size_t plane = NT * kMacTcChunk;
+                const size_t n_res = (size_t)__builtin_popcountll(tc_mask[part]);
+                std::vector<uint16_t> Wl(n_res * tc_tiles[part] * n_chunks * limbs * plane, 0);
+                std::vector<uint32_t> trow((size_t)tc_tiles[part] * NT, 0xFFFFFFFFu);
                 for (size_t idx = 0; idx < rs.size(); ++idx) trow[idx] = rs[idx];
                 size_t ri = 0;
                 for (uint32_t r = 0; r < L; ++r) {
-                    if (!((tc_mask >> r) & 1u)) continue;
+                    if (!((tc_mask[part] >> r) & 1u)) continue;
                     const u64 q = c->primes[r], half = (q - 1) / 2;
                     for (size_t idx = 0; idx < rs.size(); ++idx) {
-                        const size_t t = idx / kMacTcRows, o = idx % kMacTcRows;
+                        const size_t t = idx / NT, o = idx % NT;
                         const uint32_t row = rs[idx];
                         for (uint32_t e = 0; e < tc_K; ++e) {
                             const int64_t w = (int64_t)std::llround(nd.weight[nd.row_ptr[row] + e] * qd);
                             const u64 wr = mod_signed(w, q);
                             const int64_t wc = wr > half ? (int64_t)wr - (int64_t)q : (int64_t)wr;
-                            int32_t d[5];
-                            mac_tc_limbs(wc, d);
+                            int32_t d[8];
+                            mac_tc_limbs(wc, limbs, d);
                             const size_t ch = e / kMacTcChunk, k = e % kMacTcChunk;
                             const size_t pos = ((o >> 3) * (kMacTcChunk / 8) + (k >> 3)) * 64 + (o & 7) * 8 + (k & 7);
-                            for (int b = 0; b < 5; ++b)
-                                Wl[(((ri * tc_tiles + t) * n_chunks + ch) * 5 + b) * plane + pos] = bf16_of_small(d[b]);
+                            for (int b = 0; b < limbs; ++b)
+                                Wl[(((ri * tc_tiles[part] + t) * n_chunks + ch) * limbs + b) * plane + pos] =
+                                    bf16_of_small(d[b]);
                         }
                     }
                     ++ri;
                 }
-                o_tcW = put(Wl.data(), Wl.size() * 2);
-                o_tcr = put(trow.data(), trow.size() * 4);
+                o_tcW[part] = put(Wl.data(), Wl.size() * 2);
+                o_tcr[part] = put(trow.data(), trow.size() * 4);
             }
             nc.n_tiles = (uint32_t)tiles.size();
             o_rp = put(tiles.data(), std::max<size_t>(1, tiles.size()) * sizeof(uint4));
@@ -278,13 +289,14 @@ struct Exec {
         nc.s_in = s_in;
         nc.tc_on = tc_on;
         if (nd.kind == FHE_NODE_LINEAR) {
-            if (tc_mask) {
-                nc.tcW = (uint16_t*)(b + o_tcW);
-                nc.tc_rows = (uint32_t*)(b + o_tcr);
-                nc.tc_tiles = tc_tiles;
-                nc.tc_K = tc_K;
-                nc.tc_mask = tc_mask;
+            for (int part = 0; part < 2; ++part) {
+                if (!tc_mask[part]) continue;
+                nc.tc[part].W = (uint16_t*)(b + o_tcW[part]);
+                nc.tc[part].rows = (uint32_t*)(b + o_tcr[part]);
+                nc.tc[part].tiles = tc_tiles[part];
+                nc.tc[part].mask = tc_mask[part];
             }
+            nc.tc_K = tc_K;
             nc.tiles = (uint4*)(b + o_rp);
             nc.tile_rows = (uint32_t*)(b + o_tr);
             nc.col = (uint32_t*)(b + o_col);
@@ -549,11 +561,15 @@ struct Exec {
         if (!dry && ok()) {
             fhe_node_const* k = node_const(i, L, x.scale);
             if (!k) return y;
-            if (k->tc_mask) {
-                rc = k_linear_mac_tc(c, x.p, k->col, k->tc_K, k->tcW, k->tc_rows, k->tc_tiles, k->tc_mask, L, Y, st);
+            for (int part = 0; part < 2; ++part) {
+                const fhe_node_const::TcPart& tp = k->tc[part];
+                if (!tp.mask) continue;
+                rc = k_linear_mac_tc(c, part == 0 ? 5 : 8, x.p, k->col, k->tc_K, tp.W, tp.rows, tp.tiles, tp.mask, L, Y,
+                                     st);
                 if (rc != FHE_OK) return y;
             }
-            k_linear_mac_tiled(c, x.p, k->tiles, k->n_tiles, k->tile_rows, k->col, k->W, L, Y, st, k->tc_mask);
+            k_linear_mac_tiled(c, x.p, k->tiles, k->n_tiles, k->tile_rows, k->col, k->W, L, Y, st,
+                               k->tc[0].mask | k->tc[1].mask);
             k_rescale(c, Y, out, nd.n_out, 2, L, k->bias, L - 1, sc, st);
         }
         y.p = out;

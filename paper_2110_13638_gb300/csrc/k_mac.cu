@@ -124,6 +124,9 @@ __global__ void __launch_bounds__(256, 2) k_mac_tiled_kernel(const u64* __restri
     for (int o = 0; o < kMacTile; ++o) lo[o] = hi[o] = 0;
     uint32_t e = 0;
     int cnt = 0;
+    // products are below q^2, so a high word is below 2^58 for q < 2^61 and
+    // below 2^60 for q < 2^62: fold before 32 (resp. 16) high words can overflow
+    const int fold = P.q < (1ull << 61) ? 32 : 16;
     for (; e + 4 <= K; e += 4) {
         u64 x[4];
 #pragma unroll
@@ -139,7 +142,7 @@ __global__ void __launch_bounds__(256, 2) k_mac_tiled_kernel(const u64* __restri
             }
         }
         cnt += 4;
-        if (cnt == 32) {                // hi < 32 * 2^58: fold before it can overflow
+        if (cnt == fold) {
 #pragma unroll
             for (int o = 0; o < kMacTile; ++o) {
                 lo[o] = reduce128(hi[o], lo[o], P);

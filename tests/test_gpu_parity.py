@@ -264,17 +264,19 @@ def test_graph_mini_cnn_bit_exact():
     assert err < 1e-4
 
 
-def test_dense_layer_on_tensor_cores_bit_exact():
-    """A dense 150 -> 100 layer, then x^2, at N = 1024, L = 8.  The seven
-    40-bit residues of the layer go through the tensor-core MAC: five 32-term
-    chunks, the last one ragged, and three 48-row tiles, the last one holding
-    4 rows.  The 60-bit residue goes through the integer MAC.  Every output
-    word must equal the oracle's, and no bounded wait may have given up."""
-    g, o = pair(1024, BITS9)
+@pytest.mark.parametrize("N,bits", [(1024, BITS9), (256, [61, 40, 40, 61])])
+def test_dense_layer_on_tensor_cores_bit_exact(N, bits):
+    """A dense 150 -> 100 layer, then x^2.  With [60, 40 x 7, 60] every residue
+    goes through the tensor-core MAC: the 40-bit ones with five limbs
+    (three 48-row tiles, the last holding 4 rows), the 60-bit one with eight
+    (four 32-row tiles); five 32-term chunks, the last one ragged.  With
+    [61, 40, 40, 61] the 61-bit residue is left to the integer MAC.  Every
+    output word must equal the oracle's, and no bounded wait may have given up."""
+    g, o = pair(N, bits)
     rng = np.random.Generator(np.random.PCG64(29))
     Wm = rng.normal(0.0, 0.2, size=(100, 150))
     graph = W.chain_graph(150, [W._linear(*W.dense_csr(Wm), rng.normal(0.0, 0.1, 100)), {"kind": "square"}])
-    x = rng.uniform(-1.0, 1.0, size=(150, 512))
+    x = rng.uniform(-1.0, 1.0, size=(150, N // 2))
     err = _graph_parity(g, o, graph, [x], [0])
     assert err < 1e-4
     assert fhe.device_faults() == 0
