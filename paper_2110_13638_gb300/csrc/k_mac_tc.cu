@@ -39,7 +39,7 @@ namespace fhe {
 namespace {
 constexpr int kTcM = 128;                      // coefficients per tile
 constexpr int kTcK = kMacTcChunk;              // terms per chunk (32)
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 512;             // 16 warps: 4 lane quarters x 4 column quarters
 constexpr uint32_t kTmemCols = 512;
 constexpr int kALimb = kTcM * kTcK * 2;        // bytes of one input limb plane (8 KB)
 constexpr uint32_t kSpinLimit = 1u << 22;      // polls of ~64 ns: well under a second
@@ -63,7 +63,7 @@ struct TcShape {
                                        ((uint32_t)(kTcM >> 4) << 24);
     static_assert(kClasses * NT <= (int)kTmemCols, "tensor memory columns");
     static_assert(kSmem <= 227 * 1024, "shared memory");
-    static_assert(NT % 16 == 0 && (NT / 2) % 8 == 0, "MMA N and epilogue split");
+    static_assert(NT % 16 == 0 && (NT / 4) % 4 == 0, "MMA N and epilogue split");
 };
 }  // namespace
 
@@ -121,20 +121,20 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
     return false;
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* v)
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t* v)
 {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
                  : "r"(taddr)
                  : "memory");
 }
 
 // wait for this thread's tensor-memory loads; the loaded registers pass
 // through the statement, so no use of them can be scheduled before the wait
-__device__ __forceinline__ void tmem_wait8(uint32_t* v)
+__device__ __forceinline__ void tmem_wait4(uint32_t* v)
 {
     asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7])
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3])
                  :
                  : "memory");
 }
@@ -178,7 +178,7 @@ template <int LIMBS>
 __global__ void __launch_bounds__(kTcThreads, 1) k_mac_tc_kernel(const MacTcArgs a)
 {
     using S = TcShape<LIMBS>;
-    constexpr int NT = S::NT, NH = NT / 2;     // outputs per epilogue thread
+    constexpr int NT = S::NT, NQ = NT / 4;     // outputs per epilogue thread
     extern __shared__ __align__(1024) unsigned char sm[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + S::kOffBar);
     uint32_t* tbase_s = reinterpret_cast<uint32_t*>(sm + S::kOffBar + 8);
@@ -207,36 +207,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mac_tc_kernel(const MacTcArgs
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tbase = *tbase_s;
 
-    // producer role: coefficient m, k-groups kh and kh + 2 of each chunk;
+    // producer role: coefficient m, k-group kg (8 terms) of each chunk;
     // xr holds the inputs of the next chunk to stage
-    const int m = tid & (kTcM - 1), kh = tid >> 7;
+    const int m = tid & (kTcM - 1), kg = tid >> 7;
     const u64* Xm = a.X + (size_t)kr * N + j0 + m;
-    u64 xr[16];
+    u64 xr[8];
     auto fetch = [&](uint32_t c) {
 #pragma unroll
-        for (int g = 0; g < 2; ++g)
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const uint32_t term = c * kTcK + (uint32_t)((kh + 2 * g) * 8 + e);
-                xr[g * 8 + e] = term < a.K ? Xm[(size_t)__ldg(&a.col[term]) * ct_stride] : 0ull;
-            }
+        for (int e = 0; e < 8; ++e) {
+            const uint32_t term = c * kTcK + (uint32_t)(kg * 8 + e);
+            xr[e] = term < a.K ? Xm[(size_t)__ldg(&a.col[term]) * ct_stride] : 0ull;
+        }
     };
     // input limbs of xr and the chunk's weight limbs into staging buffer sb
     auto stage = [&](uint32_t c, unsigned char* sb) {
-#pragma unroll
-        for (int g = 0; g < 2; ++g) {
+        {
             uint32_t w[LIMBS][4];
 #pragma unroll
             for (int e2 = 0; e2 < 4; ++e2) {
                 float f0[LIMBS], f1[LIMBS];
-                const u64 x0 = xr[g * 8 + 2 * e2], x1 = xr[g * 8 + 2 * e2 + 1];
+                const u64 x0 = xr[2 * e2], x1 = xr[2 * e2 + 1];
                 limbs_f32<LIMBS>(x0 > P.half ? (i64)(x0 - P.q) : (i64)x0, f0);
                 limbs_f32<LIMBS>(x1 > P.half ? (i64)(x1 - P.q) : (i64)x1, f1);
 #pragma unroll
                 for (int l = 0; l < LIMBS; ++l)
                     w[l][e2] = __byte_perm(__float_as_uint(f0[l]), __float_as_uint(f1[l]), 0x7632);
             }
-            const int kg = kh + 2 * g;
             const int off = ((m >> 3) * (kTcK / 8) + kg) * 128 + (m & 7) * 16;
 #pragma unroll
             for (int l = 0; l < LIMBS; ++l)
@@ -248,14 +244,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mac_tc_kernel(const MacTcArgs
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     };
 
-    // epilogue role: lanes 32 (warp % 4) .. +31, outputs NH (warp / 4) .. +NH-1
+    // epilogue role: lanes 32 (warp % 4) .. +31, outputs NQ (warp / 4) .. +NQ-1
     const int q4 = warp & 3, h = warp >> 2;
-    const uint32_t trow = tbase + ((uint32_t)(32 * q4) << 16) + (uint32_t)(h * NH);
-    i64 acc[S::kAcc][NH];
+    const uint32_t trow = tbase + ((uint32_t)(32 * q4) << 16) + (uint32_t)(h * NQ);
+    i64 acc[S::kAcc][NQ];
 #pragma unroll
     for (int i = 0; i < S::kAcc; ++i)
 #pragma unroll
-        for (int o = 0; o < NH; ++o) acc[i][o] = 0;
+        for (int o = 0; o < NQ; ++o) acc[i][o] = 0;
 
     fetch(0);
     stage(0, sm);
@@ -309,21 +305,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mac_tc_kernel(const MacTcArgs
                 const int s0 = 5 * i + 2 * part;
                 if (s0 >= S::kClasses) continue;
                 const bool pair = part < 2 && s0 + 1 < S::kClasses;
-                uint32_t v0[NH], v1[NH];
+                uint32_t v0[NQ], v1[NQ];
 #pragma unroll
-                for (int p = 0; p < NH / 8; ++p) tmem_ld8(trow + (uint32_t)(s0 * NT + 8 * p), v0 + 8 * p);
+                for (int p = 0; p < NQ / 4; ++p) tmem_ld4(trow + (uint32_t)(s0 * NT + 4 * p), v0 + 4 * p);
                 if (pair) {
 #pragma unroll
-                    for (int p = 0; p < NH / 8; ++p) tmem_ld8(trow + (uint32_t)((s0 + 1) * NT + 8 * p), v1 + 8 * p);
+                    for (int p = 0; p < NQ / 4; ++p) tmem_ld4(trow + (uint32_t)((s0 + 1) * NT + 4 * p), v1 + 4 * p);
                 }
 #pragma unroll
-                for (int p = 0; p < NH / 8; ++p) tmem_wait8(v0 + 8 * p);
+                for (int p = 0; p < NQ / 4; ++p) tmem_wait4(v0 + 4 * p);
                 if (pair) {
 #pragma unroll
-                    for (int p = 0; p < NH / 8; ++p) tmem_wait8(v1 + 8 * p);
+                    for (int p = 0; p < NQ / 4; ++p) tmem_wait4(v1 + 4 * p);
                 }
 #pragma unroll
-                for (int o = 0; o < NH; ++o) {
+                for (int o = 0; o < NQ; ++o) {
                     const uint32_t b0 = __float_as_uint(__uint_as_float(v0[o]) + 12582912.0f);
                     if (!pair) {
                         acc[i][o] += (i64)(int32_t)(b0 - 0x4B400000u) << (16 * part);
@@ -345,8 +341,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mac_tc_kernel(const MacTcArgs
         for (int i = 1; i < S::kAcc; ++i) pw[i] = mul_mod(pw[i - 1], reduce64(1ull << 40, P), P);
         const size_t off = (size_t)kr * N + j0 + 32 * q4 + lane;
 #pragma unroll
-        for (int o = 0; o < NH; ++o) {
-            const uint32_t row = __ldg(&a.rows[t * NT + h * NH + o]);
+        for (int o = 0; o < NQ; ++o) {
+            const uint32_t row = __ldg(&a.rows[t * NT + h * NQ + o]);
             if (row == 0xFFFFFFFFu) continue;
             u64 y = from_signed(acc[0][o], P);
 #pragma unroll
