@@ -24,10 +24,12 @@
 // tensor-memory columns the block allocates), NT = 32 with eight (15 x 32 =
 // 480).  Operands sit in shared memory K-major without swizzle: core matrices
 // of 8 rows x 16 bytes (8 bf16 terms), adjacent along K 128 bytes apart, 8-row
-// groups 512 bytes apart.  The block's threads split the input limbs from the
-// u64 residues (coalesced along the coefficients) into one of two staging
-// buffers while the tensor core works on the other; the weight limbs come
-// pre-split and pre-laid-out from the host.  One thread issues the MMAs of a
+// groups 512 bytes apart.  The block's 16 warps split the input limbs from
+// the u64 residues (coalesced along the coefficients) into one of two staging
+// buffers while the tensor core works on the other, and read the class sums
+// back (warp w: lanes 32 (w % 4) .. +31, a quarter of the tile's rows); the
+// weight limbs come pre-split and pre-laid-out from the host.  Up to 8192
+// terms keep the 64-bit sums exact.  One thread issues the MMAs of a
 // chunk and commits them to an mbarrier; every wait on it is bounded, and a
 // wait that gives up sets g_mac_tc_fault, skips the rest of the block's work
 // and frees its tensor memory.
@@ -375,8 +377,8 @@ int k_linear_mac_tc(const fhe_ctx* c, int limbs, const u64* X, const uint32_t* c
 {
     if (n_tiles == 0 || K == 0 || mask == 0) return FHE_OK;
     const int N = (int)c->N;
-    if (N % kTcM != 0 || 2 * L > 64 || (limbs != 5 && limbs != 8))
-        return fail(FHE_EINVAL, "tensor-core MAC: ring, level or limb count out of range");
+    if (N % kTcM != 0 || 2 * L > 64 || (limbs != 5 && limbs != 8) || K > 8192)
+        return fail(FHE_EINVAL, "tensor-core MAC: ring, level, limb count or term count out of range");
     MacTcArgs a{};
     a.X = X;
     a.col = col;
