@@ -110,3 +110,11 @@ def test_host_errors_are_reported():
     assert e.value.code == -1
     with pytest.raises(fhe.FheError):
         fhe.prime_chain(1024, [70, 40])
+
+
+def test_health_hooks_reject_null_outputs():
+    """fhe_device_faults and fhe_launch_count check their output pointer
+    before touching the device."""
+    lib = fhe.lib()
+    assert lib.fhe_device_faults(None) == -1
+    assert lib.fhe_launch_count(None) == -1
