@@ -22,7 +22,12 @@
  *     first use, so run one batch of a graph that has it before forking;
  *   - growing a workspace or batch area (the first call at a larger size)
  *     synchronises the device before freeing the old buffer; size them with
- *     one call before stream capture or latency-critical use.
+ *     one call before stream capture or latency-critical use;
+ *   - every wait a kernel makes on the device is bounded.  A kernel whose wait
+ *     gives up leaves its outputs unwritten and sets the context's status
+ *     word; FHE_ETIMEOUT then comes from the first of fhe_eval_graph,
+ *     fhe_eval_batch or fhe_ctx_sync on that context to run after that kernel
+ *     has finished (fhe_ctx_sync waits for the stream, so it always sees it).
  *
  * Data layout:
  *   residue polynomial  : N u64 words, every word < its prime
@@ -68,6 +73,9 @@ typedef struct {
     float ntt_variant_us[8];     /* autotuner: microseconds per transform of each schedule */
     uint32_t ntt_variant_ks;     /* schedule of the key-switching inner-product transforms */
     float ntt_variant_ks_us[8];  /* autotuner: microseconds per digit transform of each schedule */
+    uint64_t workspace_bytes;    /* device bytes of this context's call workspace and batch
+                                    area (both grow on demand; 0 before the first call that
+                                    needs them) */
 } fhe_ctx_info;
 
 /* Per-ciphertext metadata returned by graph evaluation. */
@@ -285,9 +293,14 @@ int fhe_relinearise(fhe_ctx* ctx, const uint64_t* d3, uint32_t n_ct, uint32_t le
  * device-wide synchronisation a workspace cudaMalloc/cudaFree can cause).
  * The paper has no counterpart: it is an allocation policy of this library.
  * Scratch comes from a fixed 16 MiB device array that every GPU loading the
- * library holds until exit; nothing is allocated or freed.  The first call on
- * a device (with the context's device current) looks up that array's device
- * address, so make it before any stream capture.  Batches needing more
+ * library holds until exit; the call itself allocates and frees nothing.
+ * The first call on a device (with the context's device current) looks up
+ * that array's device address; under CUDA's lazy module loading (the
+ * default) this is also when the library's module is loaded on that device
+ * and the array is reserved, so that first call can allocate device memory
+ * and fail with FHE_ENOMEM if another allocator already holds all of it.
+ * Make one warm-up call per device before handing device memory to another
+ * allocator and before any stream capture.  Batches needing more
  * scratch than 16 MiB ((L + 2(L+1) + 2) N 8 bytes per ciphertext, aligned)
  * return FHE_EINVAL.  All calls share the array: calls that overlap on the
  * GPU race and must be serialised by the caller. */
@@ -393,6 +406,40 @@ int fhe_launch_count(uint64_t* out);
  * second) and left its outputs unwritten.  Synchronises the device; *out = 0
  * when no wait gave up since the last call. */
 int fhe_device_faults(uint32_t* out);
+
+/* Integer-pipe ceiling microbenchmark (no counterpart in the paper; the
+ * denominators of the ALU roofline).  Enqueues one kernel of `blocks` x
+ * `threads` threads (threads a multiple of 32, at most 1024), each running
+ * `iters` steps of 32 independent operations of one kind held in registers:
+ *   0  32-bit multiply-add (IMAD)
+ *   1  32 x 32 -> 64-bit multiply-add (IMAD.WIDE)
+ *   2  high half of a 64 x 64-bit product
+ *   3  Shoup butterfly of the fused transforms for primes below 2^58:
+ *      T = a w - floor(a w' / 2^64) q, (X, Y) -> (X + T, X + 2q - T)
+ *   4  the same butterfly in Harvey's form (X reduced below 2q first)
+ * so blocks * threads * iters * 32 operations in all.  d_sink (device,
+ * blocks * threads words, caller-owned) receives one word per thread.  Time
+ * it with events on `stream`. */
+int fhe_peak_launch(uint32_t kind, uint32_t blocks, uint32_t threads, uint32_t iters, uint64_t* d_sink,
+                    void* stream);
+
+/* Wait for `stream`, then report the context's health: FHE_ETIMEOUT if a
+ * kernel launched through this context gave up a bounded device wait since
+ * the last report (its outputs are then unspecified), else FHE_OK.  The
+ * report clears the status.  Serving infrastructure: the paper has no
+ * counterpart. */
+int fhe_ctx_sync(fhe_ctx* ctx, void* stream);
+
+/* Test hook (no counterpart in the paper): make a failure happen on purpose,
+ * on the host's side of the device, without faulting anything.
+ * FHE_INJECT_MAC_TC_WITHHOLD: the next tensor-core layer MAC launched through
+ * this context issues none of its matrix products and shortens its waits to
+ * about a millisecond, so every block's bounded wait runs out with no tensor
+ * work in flight; the blocks free their tensor memory and return, the layer's
+ * outputs are left unwritten, and the context reports FHE_ETIMEOUT.  The
+ * context stays usable. */
+#define FHE_INJECT_MAC_TC_WITHHOLD 1u
+int fhe_inject_fault(fhe_ctx* ctx, uint32_t kind);
 
 const char* fhe_last_error(void);
 

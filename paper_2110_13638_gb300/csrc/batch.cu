@@ -114,5 +114,5 @@ extern "C" int fhe_eval_batch(fhe_ctx* c, const fhe_graph* g, const fhe_request*
         off += r.n_samples;
     }
     if (e != cudaSuccess) return cuda_check(e, "batch scatter");
-    return FHE_OK;
+    return status_take(c);
 }

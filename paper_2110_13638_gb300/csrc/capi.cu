@@ -59,6 +59,14 @@ int ws_reserve(fhe_ctx* c, size_t bytes, Arena* a)
     return FHE_OK;
 }
 
+int status_take(const fhe_ctx* c)
+{
+    volatile unsigned int* h = c->h_status;
+    if (!h || *h == 0) return FHE_OK;
+    *h = 0;
+    return fail(FHE_ETIMEOUT, "a kernel's bounded device wait gave up; its outputs were not written");
+}
+
 // llround of a double: round half away from zero (C semantics)
 static int64_t dround(double x) { return (int64_t)std::llround(x); }
 
@@ -283,6 +291,7 @@ int fhe_autoparam(const fhe_graph* g, uint32_t log_scale, double special_mult, u
 static void free_ctx(fhe_ctx* c)
 {
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    cudaFreeHost(c->h_status);
     cudaFree(c->bb);
     if (c->parent) {            // shared tables and keys belong to the parent
         cudaFree(c->ws);
@@ -307,6 +316,25 @@ static void free_ctx(fhe_ctx* c)
     cudaFree(c->ws);
     cudaFree(c->d_ntt2);
     delete c;
+}
+
+// The context's status word: pinned host memory mapped into the device's
+// address space, written by a kernel whose bounded wait gave up
+static int alloc_status(fhe_ctx* c)
+{
+    void* h = nullptr;
+    cudaError_t e = cudaHostAlloc(&h, sizeof(unsigned int), cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+        *(volatile unsigned int*)h = 0;
+        e = cudaHostGetDevicePointer((void**)&c->d_status, h, 0);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (h) cudaFreeHost(h);
+        return cuda_check(e, "status word");
+    }
+    c->h_status = (unsigned int*)h;
+    return FHE_OK;
 }
 
 // Time every NTT schedule on a representative fused step and keep the
@@ -538,6 +566,7 @@ int fhe_ctx_create(uint32_t N, const uint32_t* bits, uint32_t n_bits, uint32_t l
     up((void**)&c->d_enc_tw_q, etw_q.data(), etw_q.size() * sizeof(ulonglong2));
     up((void**)&c->d_enc_twist_q, etwist_q.data(), etwist_q.size() * sizeof(ulonglong2));
     up((void**)&c->d_slot_of, slot_of.data(), slot_of.size() * sizeof(uint32_t));
+    if (rc == FHE_OK) rc = alloc_status(c);
     if (rc == FHE_OK) {
         // two-pass NTT intermediate: 128 MiB (or 64 transforms for small rings)
         c->ntt2_words = std::max<size_t>((size_t)1 << 24, (size_t)64 * N);
@@ -607,6 +636,11 @@ int fhe_ctx_fork(fhe_ctx* parent, fhe_ctx** out)
         delete c;
         return cuda_check(e, "fork scratch");
     }
+    const int rc = alloc_status(c);
+    if (rc != FHE_OK) {
+        free_ctx(c);
+        return rc;
+    }
     *out = c;
     return FHE_OK;
 }
@@ -632,6 +666,7 @@ int fhe_ctx_query(const fhe_ctx* c, fhe_ctx_info* out)
     out->key_bytes = c->key_bytes;
     out->ntt_variant = (uint32_t)c->ntt_variant;
     out->ntt_variant_ks = (uint32_t)c->ntt_variant_ks;
+    out->workspace_bytes = c->ws_bytes + c->bb_bytes;
     for (int v = 0; v < kNttVariants && v < 8; ++v) {
         out->ntt_variant_us[v] = c->ntt_variant_us[v];
         out->ntt_variant_ks_us[v] = c->ntt_variant_ks_us[v];
@@ -1043,6 +1078,22 @@ int fhe_launch_count(uint64_t* out)
 {
     if (!out) return fail(FHE_EINVAL, "null output");
     *out = launch_count();
+    return FHE_OK;
+}
+
+int fhe_ctx_sync(fhe_ctx* c, void* stream)
+{
+    CHECK_CTX(c);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_check(e, "fhe_ctx_sync");
+    return status_take(c);
+}
+
+int fhe_inject_fault(fhe_ctx* c, uint32_t kind)
+{
+    CHECK_CTX(c);
+    if (kind != FHE_INJECT_MAC_TC_WITHHOLD) return fail(FHE_EINVAL, "unknown fault kind");
+    c->inject = (int)kind;
     return FHE_OK;
 }
 

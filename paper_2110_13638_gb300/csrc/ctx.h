@@ -19,7 +19,6 @@ struct fhe_ctx {
     float ntt_variant_us[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // autotuner: us per transform per variant
     int ntt_variant_ks = 0;        // schedule of the key-switching inner-product transforms
     float ntt_variant_ks_us[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    mutable int force_single_pass = 0;   // set while a call must not use the two-pass scratch
     u64* d_ntt2 = nullptr;         // two-pass intermediate (allocated with the context)
     size_t ntt2_words = 0;
 
@@ -55,6 +54,13 @@ struct fhe_ctx {
     size_t ws_bytes = 0;
     void* bb = nullptr;            // fhe_eval_batch's slots / ciphertext area (own per fork)
     size_t bb_bytes = 0;
+
+    // health: a host-mapped word that a kernel sets when one of its bounded
+    // waits gives up (read and cleared by fhe_ctx_sync and the graph calls);
+    // one per context, forks included
+    unsigned int* h_status = nullptr;
+    unsigned int* d_status = nullptr;      // device address of h_status
+    mutable int inject = 0;                // test hook (fhe_inject_fault), consumed by the next launch it names
 
     // measurement hook: CUDA events around every launch of one kernel family
     mutable std::string prof_family;
@@ -150,6 +156,10 @@ struct Arena {
     }
 };
 int ws_reserve(fhe_ctx* c, size_t bytes, Arena* a);
+// Reads and clears the context's status word without synchronising:
+// FHE_ETIMEOUT if a kernel launched through this context gave up one of its
+// bounded waits and has finished since the word was last read, else FHE_OK.
+int status_take(const fhe_ctx* c);
 inline size_t arena_need(std::initializer_list<size_t> parts)
 {
     size_t s = 0;
@@ -181,9 +191,11 @@ size_t relin_scratch_bytes(const fhe_ctx* c, uint32_t n_ct, uint32_t L);
 // device (once per kernel, device and size; thread-safe).
 void ensure_smem(const void* kernel, size_t bytes);
 
-// key: the relinearisation key unless another key of the same layout is given
+// key: the relinearisation key unless another key of the same layout is given;
+// single_pass: no two-pass schedule (scratch is then the only memory used
+// besides d3 and out2)
 void k_relin(const fhe_ctx* c, const u64* d3, u64* out2, uint32_t n_ct, uint32_t L, void* scratch, cudaStream_t st,
-             const ulonglong2* key = nullptr);
+             const ulonglong2* key = nullptr, bool single_pass = false);
 // rotation key for Galois element k into `key` ([L_top][2][L_top + 1][N])
 void k_galois_keygen(fhe_ctx* c, u64 k, ulonglong2* key, cudaStream_t st);
 // d3 = (c0(X^k), 0, c1(X^k)) of ciphertexts [n][2][L][N] in NTT form

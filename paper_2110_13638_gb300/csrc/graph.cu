@@ -1064,7 +1064,7 @@ int fhe_eval_graph(fhe_ctx* c, const fhe_graph* gc, const uint64_t* const* d_in,
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(e, "graph launch");
-    return FHE_OK;
+    return status_take(c);
 }
 
 }  // extern "C"

@@ -30,9 +30,11 @@
 // back (warp w: lanes 32 (w % 4) .. +31, a quarter of the tile's rows); the
 // weight limbs come pre-split and pre-laid-out from the host.  Up to 8192
 // terms keep the 64-bit sums exact.  One thread issues the MMAs of a
-// chunk and commits them to an mbarrier; every wait on it is bounded, and a
-// wait that gives up sets g_mac_tc_fault, skips the rest of the block's work
-// and frees its tensor memory.
+// chunk and commits them to an mbarrier; every wait on it is bounded.  A wait
+// that gives up makes the block skip the rest of its work: it waits once more
+// (bounded) for the products already committed, so that tensor memory is not
+// released under a running MMA, then sets g_mac_tc_fault and the context's
+// status word (the host reports FHE_ETIMEOUT) and frees its tensor memory.
 #include "../../include/fhe.h"
 #include "launch.cuh"
 
@@ -78,6 +80,9 @@ struct MacTcArgs {
     const uint32_t* rows;
     u64* Y;
     const PrimeC* pc;
+    unsigned int* status;  // the context's status word (host-mapped), set when a wait gives up
+    uint32_t spin_limit;   // polls per mbarrier wait
+    uint32_t withhold;     // test hook: issue no MMA, so every wait runs out with nothing in flight
     uint32_t K, n_tiles, n_chunks;
     int L, N;
     uint8_t zkr[64];   // grid z -> component-residue row k L + r
@@ -106,9 +111,9 @@ __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uin
         : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t limit)
 {
-    for (uint32_t i = 0; i < kSpinLimit; ++i) {
+    for (uint32_t i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -262,7 +267,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mac_tc_kernel(const MacTcArgs
 
     bool failed = false;
     for (uint32_t c = 0; c < a.n_chunks; ++c) {
-        if (tid == 0) {
+        if (tid == 0 && !a.withhold) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t sb = smem_u32(sm + (c & 1u) * S::kStage);
             uint32_t seen = 0;
@@ -288,9 +293,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mac_tc_kernel(const MacTcArgs
             if (c + 2 < a.n_chunks) fetch(c + 2);
         }
 
-        const bool ok = mbar_wait(bar_a, c & 1u);
+        const bool ok = mbar_wait(bar_a, c & 1u, a.spin_limit);
         if (__syncthreads_or(!ok)) {
-            if (tid == 0) atomicOr(&g_mac_tc_fault, 1u);
+            // products committed to this phase may still be running: give them
+            // one more bounded wait before tensor memory is released below
+            mbar_wait(bar_a, c & 1u, a.spin_limit);
+            if (tid == 0) {
+                atomicOr(&g_mac_tc_fault, 1u);
+                if (a.status) *(volatile unsigned int*)a.status = 1u;
+            }
             failed = true;
             break;
         }
@@ -386,6 +397,13 @@ int k_linear_mac_tc(const fhe_ctx* c, int limbs, const u64* X, const uint32_t* c
     a.rows = rows;
     a.Y = Y;
     a.pc = c->d_pc;
+    a.status = c->d_status;
+    a.spin_limit = kSpinLimit;
+    if (c->inject == FHE_INJECT_MAC_TC_WITHHOLD) {   // test hook, consumed by this launch
+        c->inject = 0;
+        a.withhold = 1;
+        a.spin_limit = 1024;
+    }
     a.K = K;
     a.n_tiles = n_tiles;
     a.n_chunks = (K + kTcK - 1) / kTcK;

@@ -10,7 +10,7 @@ size_t relin_scratch_bytes(const fhe_ctx* c, uint32_t n_ct, uint32_t L)
 }
 
 void k_relin(const fhe_ctx* c, const u64* d3, u64* out2, uint32_t n_ct, uint32_t L, void* scratch, cudaStream_t st,
-             const ulonglong2* key)
+             const ulonglong2* key, bool single_pass)
 {
     if (n_ct == 0) return;
     const size_t N = c->N;
@@ -22,11 +22,11 @@ void k_relin(const fhe_ctx* c, const u64* d3, u64* out2, uint32_t n_ct, uint32_t
     u64* Vp = (u64*)ar.take((size_t)n_ct * 2 * N * 8);
 
     OpDigitsInv s1{d3, D, (int)n_ct, (int)L, (int)N};
-    launch_ntt<true>(c, s1, st);
+    launch_ntt<true>(c, s1, st, single_pass);
     OpModUpMac s2{d3, D, key ? key : c->d_ksk, acc, (int)n_ct, (int)L, (int)N, (int)c->L_top, modup_red_mask(c, L)};
-    launch_ntt<false>(c, s2, st);
+    launch_ntt<false>(c, s2, st, single_pass);
     OpAccPInv s3{acc, Vp, (int)n_ct, (int)L, (int)N, (int)c->L_top};
-    launch_ntt<true>(c, s3, st);
+    launch_ntt<true>(c, s3, st, single_pass);
     OpModDown s4;
     s4.d3 = d3;
     s4.acc = acc;
@@ -36,7 +36,7 @@ void k_relin(const fhe_ctx* c, const u64* d3, u64* out2, uint32_t n_ct, uint32_t
     s4.L = (int)L;
     s4.N = (int)N;
     s4.d = make_divc(c, c->L_top, L);
-    launch_ntt<false>(c, s4, st);
+    launch_ntt<false>(c, s4, st, single_pass);
 }
 
 

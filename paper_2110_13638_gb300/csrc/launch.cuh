@@ -190,14 +190,17 @@ static void launch_ntt_2pass(const fhe_ctx* c, const Op& op, int count, cudaStre
     }
 }
 
+// single_pass: the caller's scratch must be the only memory the transform
+// touches besides its operands, so the two-pass schedules (whose intermediate
+// is the context's scratch) are replaced by their one-block-per-transform form
 template <bool INV, class Op>
-static void launch_ntt(const fhe_ctx* c, const Op& op, cudaStream_t st)
+static void launch_ntt(const fhe_ctx* c, const Op& op, cudaStream_t st, bool single_pass = false)
 {
     const int count = op.count();
     if (count <= 0) return;
     // the two-pass schedule needs the same number of transforms in every unit
     // (callers refuse single-pass-only work above kMaxSinglePassN)
-    const bool single = c->force_single_pass || !uniform_subs<Op>::value;
+    const bool single = single_pass || !uniform_subs<Op>::value;
     const int base = keyswitch_mac<Op>::value ? c->ntt_variant_ks : c->ntt_variant;
     const int v = single && (base == 2 || base == 3) ? 1 : base;
     switch (v) {

@@ -13,8 +13,11 @@
 // use the array's name as a device address (on the host it names a host-side
 // stand-in), so the first call on each device looks the device address up
 // with cudaGetSymbolAddress while that device is current, and passes that
-// address to the kernels.  That first call should therefore happen before any
-// stream capture.  All calls share the array and it keeps the previous call's
+// address to the kernels.  Under lazy module loading (CUDA's default) that
+// lookup is also what loads the module on the device and reserves the array,
+// so the first call can allocate (and fail for lack of device memory); make
+// one warm-up call per device before another allocator takes the memory and
+// before any stream capture.  All calls share the array and it keeps the previous call's
 // contents; the relinearisation kernels write every scratch word before they
 // read it, so nothing has to be cleared.  Calls whose work overlaps on the GPU
 // (two streams, or two threads) race on the array: serialise them.
@@ -78,9 +81,7 @@ extern "C" int fhe_relinearise_noalloc(fhe_ctx* c, const uint64_t* d3, uint32_t 
     if (rc) return rc;
     // single-pass transforms only: the two-pass schedule would use the
     // context's intermediate buffer in addition to the fixed array
-    c->force_single_pass = 1;
-    k_relin(c, (const u64*)d3, (u64*)d_out, n_ct, level, scratch, (cudaStream_t)stream);
-    c->force_single_pass = 0;
+    k_relin(c, (const u64*)d3, (u64*)d_out, n_ct, level, scratch, (cudaStream_t)stream, nullptr, true);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(e, "relinearise_noalloc launch");
     return FHE_OK;

@@ -37,7 +37,8 @@ class CtxInfo(ctypes.Structure):
     _fields_ = [("N", ctypes.c_uint32), ("slots", ctypes.c_uint32), ("L_top", ctypes.c_uint32),
                 ("log_scale", ctypes.c_uint32), ("primes", ctypes.c_uint64 * 64), ("key_bytes", ctypes.c_uint64),
                 ("ntt_variant", ctypes.c_uint32), ("ntt_variant_us", ctypes.c_float * 8),
-                ("ntt_variant_ks", ctypes.c_uint32), ("ntt_variant_ks_us", ctypes.c_float * 8)]
+                ("ntt_variant_ks", ctypes.c_uint32), ("ntt_variant_ks_us", ctypes.c_float * 8),
+                ("workspace_bytes", ctypes.c_uint64)]
 
 
 class CtMeta(ctypes.Structure):
@@ -114,6 +115,9 @@ SIGNATURES = {
     "fhe_profile_families": [],
     "fhe_launch_count": [_P],
     "fhe_device_faults": [_P],
+    "fhe_ctx_sync": [_P, _P],
+    "fhe_peak_launch": [_U32, _U32, _U32, _U32, _P, _P],
+    "fhe_inject_fault": [_P, _U32],
     "fhe_last_error": [],
 }
 
@@ -177,6 +181,15 @@ def device_faults():
     out = ctypes.c_uint32()
     _check(lib().fhe_device_faults(ctypes.byref(out)))
     return out.value
+
+
+def peak_launch(kind, blocks, threads, iters, sink, stream=None):
+    """Enqueue the integer-pipe ceiling microbenchmark (include/fhe.h):
+    blocks * threads * iters * 32 operations of `kind`; sink: int64 device
+    tensor of at least blocks * threads words."""
+    if sink.numel() < blocks * threads or sink.dtype.itemsize != 8 or not sink.is_cuda:
+        raise ValueError("sink must be a device tensor of blocks * threads 8-byte words")
+    _check(lib().fhe_peak_launch(kind, blocks, threads, iters, _ptr(sink), _stream(stream)))
 
 
 def profile_families():
@@ -339,43 +352,103 @@ class Context:
         import torch
         return torch.empty((n, level, self.N), dtype=torch.int64, device="cuda")
 
+    def workspace_bytes(self):
+        """Device bytes of this context's call workspace and batch area."""
+        info = CtxInfo()
+        _check(lib().fhe_ctx_query(self.h, ctypes.byref(info)))
+        return int(info.workspace_bytes)
+
+    # -- health ---------------------------------------------------------------
+    def sync(self, stream=None):
+        """Wait for the stream; raises FheError (FHE_ETIMEOUT) if a kernel of a
+        call on this context gave up a bounded device wait."""
+        _check(lib().fhe_ctx_sync(self.h, _stream(stream)))
+
+    def inject_fault(self, kind=1):
+        """Test hook: kind 1 = the next tensor-core layer MAC withholds its
+        matrix products, so its bounded waits run out (FHE_ETIMEOUT)."""
+        _check(lib().fhe_inject_fault(self.h, kind))
+
+    # -- argument checks (a wrong-sized buffer would be read or written out of bounds)
+    def _ct(self, t, n, comps, level, name):
+        _dev(t, (n, comps, level, self.N), "int64", name)
+
+    def _level(self, level):
+        if not 1 <= level <= self.L_top:
+            raise ValueError("level %d outside 1..%d" % (level, self.L_top))
+
     # -- keys / encode / encrypt / decrypt / decode ------------------------
     def keygen(self, seed, stream=None):
         _check(lib().fhe_keygen(self.h, seed, _stream(stream)))
 
     def export_secret(self, out, stream=None):
+        _dev(out, (self.L_top + 1, self.N), "int64", "out")
         _check(lib().fhe_export_secret(self.h, _ptr(out), _stream(stream)))
 
     def encode(self, slots, level, scale, out, stream=None):
-        _check(lib().fhe_encode(self.h, _ptr(slots), slots.shape[0], level, scale, _ptr(out), _stream(stream)))
+        self._level(level)
+        n = _rows(slots)
+        _dev(slots, (n, self.N // 2), "float64", "slots")
+        _dev(out, (n, level, self.N), "int64", "out")
+        _check(lib().fhe_encode(self.h, _ptr(slots), n, level, scale, _ptr(out), _stream(stream)))
 
     def encrypt(self, pt, first_ct_id, out, stream=None):
-        _check(lib().fhe_encrypt(self.h, _ptr(pt), pt.shape[0], first_ct_id, _ptr(out), _stream(stream)))
+        n = _rows(pt)
+        _dev(pt, (n, self.L_top, self.N), "int64", "pt")
+        self._ct(out, n, 2, self.L_top, "out")
+        _check(lib().fhe_encrypt(self.h, _ptr(pt), n, first_ct_id, _ptr(out), _stream(stream)))
 
     def encode_encrypt(self, slots, scale, first_ct_id, out, stream=None):
-        _check(lib().fhe_encode_encrypt(self.h, _ptr(slots), slots.shape[0], scale, first_ct_id, _ptr(out),
+        n = _rows(slots)
+        _dev(slots, (n, self.N // 2), "float64", "slots")
+        self._ct(out, n, 2, self.L_top, "out")
+        _check(lib().fhe_encode_encrypt(self.h, _ptr(slots), n, scale, first_ct_id, _ptr(out),
                                         _stream(stream)))
 
     def decrypt(self, ct, level, out, stream=None):
-        _check(lib().fhe_decrypt(self.h, _ptr(ct), ct.shape[0], level, _ptr(out), _stream(stream)))
+        self._level(level)
+        n = _rows(ct)
+        self._ct(ct, n, 2, level, "ct")
+        _dev(out, (n, self.N), "int64", "out")
+        _check(lib().fhe_decrypt(self.h, _ptr(ct), n, level, _ptr(out), _stream(stream)))
 
     def decode(self, m, scale, out, stream=None):
-        _check(lib().fhe_decode(self.h, _ptr(m), m.shape[0], scale, _ptr(out), _stream(stream)))
+        n = _rows(m)
+        _dev(m, (n, self.N), "int64", "m")
+        _dev(out, (n, self.N // 2), "float64", "out")
+        _check(lib().fhe_decode(self.h, _ptr(m), n, scale, _ptr(out), _stream(stream)))
 
     # -- layout ---------------------------------------------------------------
     def ntt(self, polys, rows, forward, stream=None):
-        _check(lib().fhe_ntt(self.h, _ptr(polys), polys.shape[0], rows, 1 if forward else 0, _stream(stream)))
+        if not 1 <= rows <= self.L_top + 1:
+            raise ValueError("rows %d outside 1..%d" % (rows, self.L_top + 1))
+        n = _rows(polys)
+        _dev(polys, (n, rows, self.N), "int64", "polys")
+        _check(lib().fhe_ntt(self.h, _ptr(polys), n, rows, 1 if forward else 0, _stream(stream)))
 
     def ct_convert(self, ct, level, to_coeff, out, stream=None):
-        _check(lib().fhe_ct_convert(self.h, _ptr(ct), ct.shape[0], level, 1 if to_coeff else 0, _ptr(out),
+        self._level(level)
+        n = _rows(ct)
+        self._ct(ct, n, 2, level, "ct")
+        self._ct(out, n, 2, level, "out")
+        _check(lib().fhe_ct_convert(self.h, _ptr(ct), n, level, 1 if to_coeff else 0, _ptr(out),
                                     _stream(stream)))
 
     # -- operations -----------------------------------------------------------
     def add(self, a, b, level, out, stream=None):
-        _check(lib().fhe_add(self.h, _ptr(a), _ptr(b), a.shape[0], level, _ptr(out), _stream(stream)))
+        self._level(level)
+        n = _rows(a)
+        for t, nm in ((a, "a"), (b, "b"), (out, "out")):
+            self._ct(t, n, 2, level, nm)
+        _check(lib().fhe_add(self.h, _ptr(a), _ptr(b), n, level, _ptr(out), _stream(stream)))
 
     def tensor(self, a, b, level, out, stream=None):
-        _check(lib().fhe_tensor(self.h, _ptr(a), _ptr(b), a.shape[0], level, _ptr(out), _stream(stream)))
+        self._level(level)
+        n = _rows(a)
+        self._ct(a, n, 2, level, "a")
+        self._ct(b, n, 2, level, "b")
+        self._ct(out, n, 3, level, "out")
+        _check(lib().fhe_tensor(self.h, _ptr(a), _ptr(b), n, level, _ptr(out), _stream(stream)))
 
     def galois_keygen(self, steps, stream=None):
         """Rotation keys for the given slot steps (parent context)."""
@@ -383,40 +456,101 @@ class Context:
         _check(lib().fhe_galois_keygen(self.h, arr, len(steps), _stream(stream)))
 
     def rotate(self, ct, level, step, out, stream=None):
-        _check(lib().fhe_rotate(self.h, _ptr(ct), ct.shape[0], level, int(step), _ptr(out), _stream(stream)))
+        self._level(level)
+        n = _rows(ct)
+        self._ct(ct, n, 2, level, "ct")
+        self._ct(out, n, 2, level, "out")
+        _check(lib().fhe_rotate(self.h, _ptr(ct), n, level, int(step), _ptr(out), _stream(stream)))
 
     def relinearise(self, d3, level, out, stream=None):
-        _check(lib().fhe_relinearise(self.h, _ptr(d3), d3.shape[0], level, _ptr(out), _stream(stream)))
+        self._level(level)
+        n = _rows(d3)
+        self._ct(d3, n, 3, level, "d3")
+        self._ct(out, n, 2, level, "out")
+        _check(lib().fhe_relinearise(self.h, _ptr(d3), n, level, _ptr(out), _stream(stream)))
 
     def relinearise_noalloc(self, d3, level, out, stream=None):
         """fhe_relinearise without allocating: scratch from the library's fixed
         16 MiB device array (see include/fhe.h)."""
-        _check(lib().fhe_relinearise_noalloc(self.h, _ptr(d3), d3.shape[0], level, _ptr(out), _stream(stream)))
+        self._level(level)
+        n = _rows(d3)
+        self._ct(d3, n, 3, level, "d3")
+        self._ct(out, n, 2, level, "out")
+        _check(lib().fhe_relinearise_noalloc(self.h, _ptr(d3), n, level, _ptr(out), _stream(stream)))
 
     def rescale(self, x, comps, level, out, stream=None):
-        _check(lib().fhe_rescale(self.h, _ptr(x), x.shape[0], comps, level, _ptr(out), _stream(stream)))
+        if not 2 <= level <= self.L_top:
+            raise ValueError("rescale needs level 2..%d" % self.L_top)
+        n = _rows(x)
+        self._ct(x, n, comps, level, "x")
+        self._ct(out, n, comps, level - 1, "out")
+        _check(lib().fhe_rescale(self.h, _ptr(x), n, comps, level, _ptr(out), _stream(stream)))
 
     def mul_relin_rescale(self, a, b, level, out, stream=None):
-        _check(lib().fhe_mul_relin_rescale(self.h, _ptr(a), _ptr(b), a.shape[0], level, _ptr(out),
+        if not 2 <= level <= self.L_top:
+            raise ValueError("mul_relin_rescale needs level 2..%d" % self.L_top)
+        n = _rows(a)
+        self._ct(a, n, 2, level, "a")
+        self._ct(b, n, 2, level, "b")
+        self._ct(out, n, 2, level - 1, "out")
+        _check(lib().fhe_mul_relin_rescale(self.h, _ptr(a), _ptr(b), n, level, _ptr(out),
                                            _stream(stream)))
 
     def mul_relin_rescale_levels(self, batches, stream=None):
         """batches: list of (a, b, out, level) tensors; every step is one
         launch over all batches."""
-        arr = (LevelBatch * len(batches))()
+        arr = (LevelBatch * max(1, len(batches)))()
         for k, (a, b, out, level) in enumerate(batches):
-            arr[k] = LevelBatch(a.data_ptr(), b.data_ptr(), out.data_ptr(), a.shape[0], level)
+            if not 2 <= level <= self.L_top:
+                raise ValueError("batch %d: level %d outside 2..%d" % (k, level, self.L_top))
+            n = _rows(a)
+            self._ct(a, n, 2, level, "a")
+            self._ct(b, n, 2, level, "b")
+            self._ct(out, n, 2, level - 1, "out")
+            arr[k] = LevelBatch(a.data_ptr(), b.data_ptr(), out.data_ptr(), n, level)
         _check(lib().fhe_mul_relin_rescale_levels(self.h, arr, len(batches), _stream(stream)))
 
     def mul_const(self, x, consts, level, out, stream=None):
+        self._level(level)
+        n = _rows(x)
+        self._ct(x, n, 2, level, "x")
+        self._ct(out, n, 2, level, "out")
         c = np.ascontiguousarray(consts, dtype=np.int64)
-        _check(lib().fhe_mul_const(self.h, _ptr(x), c.ctypes.data_as(ctypes.c_void_p), x.shape[0], level,
+        if c.shape != (n,):
+            raise ValueError("one constant per ciphertext expected")
+        _check(lib().fhe_mul_const(self.h, _ptr(x), c.ctypes.data_as(ctypes.c_void_p), n, level,
                                    _ptr(out), _stream(stream)))
 
     def add_const(self, x, consts, level, stream=None):
+        self._level(level)
+        n = _rows(x)
+        self._ct(x, n, 2, level, "x")
         c = np.ascontiguousarray(consts, dtype=np.int64)
-        _check(lib().fhe_add_const(self.h, _ptr(x), c.ctypes.data_as(ctypes.c_void_p), x.shape[0], level,
+        if c.shape != (n,):
+            raise ValueError("one constant per ciphertext expected")
+        _check(lib().fhe_add_const(self.h, _ptr(x), c.ctypes.data_as(ctypes.c_void_p), n, level,
                                    _stream(stream)))
+
+
+def _rows(t):
+    if getattr(t, "dim", None) is None or t.dim() < 1:
+        raise ValueError("a batched tensor is expected")
+    return int(t.shape[0])
+
+
+def _dev(t, shape, dtype, name):
+    """t must be a contiguous CUDA tensor of `dtype` and `shape` on the current device."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch tensor" % name)
+    if t.dtype != getattr(torch, dtype):
+        raise ValueError("%s: dtype %s, expected %s" % (name, t.dtype, dtype))
+    if not t.is_cuda or t.device.index != torch.cuda.current_device():
+        raise ValueError("%s must live on the current CUDA device" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError("%s: shape %s, expected %s" % (name, tuple(t.shape), tuple(shape)))
 
 
 class Graph:
@@ -427,7 +561,9 @@ class Graph:
         h = ctypes.c_void_p()
         _check(lib().fhe_graph_create(ctypes.byref(self._arrays.desc), ctypes.byref(h)))
         self.h = h
-        self.n_inputs = sum(1 for n in graph["nodes"] if n["kind"] == "input")
+        self.in_sizes = [int(n.get("n", 0)) for n in graph["nodes"] if n["kind"] == "input"]
+        self.n_inputs = len(self.in_sizes)
+        self._out_shape = {}
 
     def close(self):
         if getattr(self, "h", None):
@@ -446,9 +582,21 @@ class Graph:
         _check(lib().fhe_graph_outputs(ctx.h, self.h, ctypes.byref(n), ctypes.byref(L)))
         return n.value, L.value
 
+    def _outs(self, ctx):
+        key = (ctx.N, tuple(ctx.primes))
+        if key not in self._out_shape:
+            self._out_shape[key] = self.outputs(ctx)
+        return self._out_shape[key]
+
     def eval(self, ctx, inputs, out, stream=None):
         """inputs: list of ciphertext tensors, one per input node; out: tensor
         [n_out][2][out_level][N].  Returns a list of (level, scale)."""
+        if len(inputs) != self.n_inputs:
+            raise ValueError("%d input tensors for %d input nodes" % (len(inputs), self.n_inputs))
+        for k, (t, n) in enumerate(zip(inputs, self.in_sizes)):
+            ctx._ct(t, n, 2, ctx.L_top, "inputs[%d]" % k)
+        n_out, L_out = self._outs(ctx)
+        ctx._ct(out, n_out, 2, L_out, "out")
         arr = (ctypes.c_void_p * len(inputs))(*[t.data_ptr() for t in inputs])
         cap = out.shape[0]
         meta = (CtMeta * max(1, cap))()
@@ -469,12 +617,19 @@ class Graph:
         (x, y, n) to use only the first n columns.  Packs them into the slots,
         encrypts, evaluates, decrypts and decodes in one call."""
         import torch
+        if self.n_inputs != 1:
+            raise ValueError("eval_batch needs a graph with exactly one input node")
+        n_out, _ = self._outs(ctx)
         arr = (Request * max(1, len(requests)))()
         for k, rq in enumerate(requests):
             x, y = rq[0], rq[1]
             n = rq[2] if len(rq) > 2 else x.shape[1]
+            if x.dim() != 2 or y.dim() != 2 or x.shape[0] != self.in_sizes[0] or y.shape[0] != n_out:
+                raise ValueError("request %d: x must be [%d][>= n], y [%d][>= n]" % (k, self.in_sizes[0], n_out))
             if x.dtype != torch.float64 or y.dtype != torch.float64 or x.stride(1) != 1 or y.stride(1) != 1:
                 raise ValueError("requests take float64 tensors with unit column stride")
+            if not 0 < n <= min(x.shape[1], y.shape[1]):
+                raise ValueError("request %d: %d samples do not fit its buffers" % (k, n))
             arr[k] = Request(x.data_ptr(), n, x.stride(0), y.data_ptr(), y.stride(0))
         _check(lib().fhe_eval_batch(ctx.h, self.h, arr, len(requests), first_ct_id, _stream(stream)))
 

@@ -148,6 +148,7 @@ class Server:
         for slots in self.slots.values():
             for s in slots:
                 if s.done():
+                    s.ctx.sync(s.stream)          # raises if a kernel of the batch gave up a device wait
                     t = now_fn()
                     out = s.host_out.numpy()
                     for req, roff, soff, n in s.batch:

@@ -109,3 +109,82 @@ def test_refusals(small):
         G = fhe.Graph({"nodes": [{"kind": "input", "n": 1}, {"kind": "rotate"}, {"kind": "output"}],
                        "edges": [(0, 1), (1, 2)]})
         G.eval(g, [ct], g.empty_ct(1, L))
+
+
+def test_scale_mismatch_is_refused(small):
+    """An ADD node over inputs whose nominal scales differ by more than 2^-40
+    (x at scale s and x^2 at s^2 / q_{L-1}) is refused with FHE_ESCALE before
+    anything is launched."""
+    g, _ = small
+    graph = {"nodes": [{"kind": "input", "n": 1}, {"kind": "square"}, {"kind": "add"}, {"kind": "output"}],
+             "edges": [(0, 1), (1, 2), (0, 2), (2, 3)]}
+    G = fhe.Graph(graph)
+    before = fhe.launch_count()
+    with pytest.raises(fhe.FheError) as e:
+        G.outputs(g)
+    assert e.value.code == -4
+    with pytest.raises(fhe.FheError) as e:
+        G.eval(g, [g.empty_ct(1, g.L_top)], g.empty_ct(1, g.L_top - 1))
+    assert e.value.code == -4
+    assert fhe.launch_count() == before
+    G.close()
+
+
+def test_tensor_core_wait_that_runs_out_reports_timeout():
+    """A tensor-core layer MAC whose matrix products never arrive (the test
+    hook withholds them, so nothing is in flight on the tensor cores): every
+    block's bounded wait runs out, the blocks free their tensor memory and
+    return, and the context reports FHE_ETIMEOUT.  The context stays usable:
+    the next evaluation gives the same words as before."""
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    N, bits = 256, [60] + [40] * 7 + [60]
+    ctx = fhe.Context(N, bits, 40)
+    ctx.keygen(0)
+    rng = np.random.Generator(np.random.PCG64(31))
+    Wm = rng.normal(0.0, 0.2, size=(16, 40))          # dense 40 -> 16: on the tensor cores
+    graph = W.chain_graph(40, [W._linear(*W.dense_csr(Wm), np.zeros(16)), {"kind": "square"}])
+    x = rng.uniform(-1.0, 1.0, size=(40, N // 2))
+    ct = ctx.empty_ct(40, ctx.L_top)
+    ctx.encode_encrypt(torch.tensor(x, device="cuda"), ctx.delta, 0, ct)
+    G = fhe.Graph(graph)
+    n_out, L_out = G.outputs(ctx)
+    ref = ctx.empty_ct(n_out, L_out)
+    G.eval(ctx, [ct], ref)
+    ctx.sync()
+    assert fhe.device_faults() == 0
+    ctx.inject_fault(1)
+    bad = ctx.empty_ct(n_out, L_out)
+    with pytest.raises(fhe.FheError) as e:
+        G.eval(ctx, [ct], bad)
+        ctx.sync()                                     # reports it if the call returned first
+    assert e.value.code == -6
+    ctx.sync()                                         # the report cleared the status
+    assert fhe.device_faults() == 1                    # the device-wide flag saw it too
+    again = ctx.empty_ct(n_out, L_out)
+    G.eval(ctx, [ct], again)
+    ctx.sync()
+    assert torch.equal(again, ref)
+    assert fhe.device_faults() == 0
+    G.close()
+    ctx.close()
+
+
+def test_binding_refuses_wrong_buffers(small):
+    """The binding checks shape, dtype, contiguity and device before any
+    pointer reaches the library (a short output would be written past)."""
+    g, _ = small
+    L = g.L_top
+    d3 = torch.zeros((2, 3, L, g.N), dtype=torch.int64, device="cuda")
+    with pytest.raises(ValueError):
+        g.relinearise(d3, L, g.empty_ct(1, L))               # too few output ciphertexts
+    with pytest.raises(ValueError):
+        g.relinearise(d3, L, g.empty_ct(2, L - 1))           # wrong level
+    with pytest.raises(ValueError):
+        g.relinearise(d3.to(torch.float64), L, g.empty_ct(2, L))
+    with pytest.raises(ValueError):
+        g.relinearise(d3, L, torch.zeros((2, L, 2, g.N), dtype=torch.int64, device="cuda").transpose(1, 2))
+    with pytest.raises(ValueError):
+        g.relinearise(d3.cpu(), L, g.empty_ct(2, L))
+    with pytest.raises(ValueError):
+        g.rescale(g.empty_ct(2, L), 2, L, g.empty_ct(2, L))

@@ -4,6 +4,11 @@
   ciphertexts, then the degree-3 sigmoid fit over 720 ciphertexts) at
   N = 16384, L = 8: sampled outputs are recomputed one by one by the oracle
   (each needs only its 25 input encryptions) and must be bit-exact.
+- The rest of the CNN at full size: each later block is recomputed by the
+  oracle from the device's own inputs to that block (sampled rows of the
+  720 -> 100 tensor-core layer at L = 5 across its row tiles, two outputs of
+  the second sigmoid fit at L = 4, all ten outputs of the 100 -> 10 layer)
+  and must be bit-exact.
 - The whole CNN and the whole yield MLP: decrypted outputs within 1e-4 of the
   FP64 plaintext forward pass with the same polynomial activations.
 - The dense layers give the same words on the tensor cores as on the integer
@@ -76,6 +81,52 @@ def test_cnn_first_blocks_sampled_bit_exact(ctx, octx):
         torch.cuda.synchronize()
         assert np.array_equal(fhe.raw_u64(got)[0], y.c), k
         assert meta[k][1] == y.scale
+
+
+def _coeff(ctx, t, level):
+    c = t.clone()
+    ctx.ct_convert(c, level, True, c)
+    torch.cuda.synchronize()
+    return fhe.raw_u64(c)
+
+
+def test_cnn_tail_sampled_bit_exact(ctx, octx):
+    """Each block after the first sigmoid fit, recomputed by the oracle from
+    the ciphertexts the device fed it (the device's evaluation is
+    deterministic, so the prefix runs reproduce the inputs of the full run)."""
+    g, x = W.cfg1()
+    nodes = g["nodes"]
+    ct = encrypt_all(ctx, x)
+    runs = {}
+    for k in (2, 3, 4, 5):                   # the first k blocks after the input
+        out, meta, L = run_graph(ctx, W.chain_graph(784, nodes[1:1 + k]), ct)
+        runs[k] = (_coeff(ctx, out, L), meta, L)
+        del out
+    X5, m5, L5 = runs[2]                     # 720 ciphertexts at L = 5
+    Y4, m4, L4 = runs[3]                     # 100 at L = 4 (dense 720 -> 100)
+    Y2, m2, L2 = runs[4]                     # 100 at L = 2 (second sigmoid fit)
+    Y1, m1, L1 = runs[5]                     # 10 at L = 1 (dense 100 -> 10)
+    assert (L5, L4, L2, L1) == (5, 4, 2, 1)
+    # dense 720 -> 100 on the tensor cores: rows at both ends of the 48-row
+    # (five-limb) and 32-row (eight-limb) tiles
+    xs = [ckks.Ciphertext(X5[i], L5, m5[i][1]) for i in range(720)]
+    rows = ckks.csr_rows(nodes[3])
+    for k in (0, 31, 47, 48, 99):
+        y = octx.linear(xs, [rows[k]], [nodes[3]["bias"][k]])[0]
+        assert np.array_equal(Y4[k], y.c), k
+        assert m4[k][1] == y.scale
+    del xs, X5
+    # second sigmoid fit
+    for k in (0, 77):
+        y = octx.poly3(ckks.Ciphertext(Y4[k], L4, m4[k][1]), nodes[4]["coeffs"])
+        assert np.array_equal(Y2[k], y.c), k
+        assert m2[k][1] == y.scale
+    # dense 100 -> 10 on the integer MAC, every output
+    xs = [ckks.Ciphertext(Y2[i], L2, m2[i][1]) for i in range(100)]
+    ys = octx.linear(xs, ckks.csr_rows(nodes[5]), nodes[5]["bias"])
+    for k in range(10):
+        assert np.array_equal(Y1[k], ys[k].c), k
+        assert m1[k][1] == ys[k].scale
 
 
 def _decrypted(ctx, out, meta, L_out):

@@ -19,7 +19,7 @@ def _nets():
     torch.cuda.set_device(0)
     out = []
     ctxs = {}
-    for name, builder in (("dense_square", W.cfg0), ("mlp", W.cfg2)):
+    for name, builder in (("dense_square", W.cfg0), ("cnn", W.cfg1), ("mlp", W.cfg2)):
         g, x = builder()
         gof, gcost = fhe.autohe(g)
         N, bits = fhe.parameterise(max(gcost), 40, 1.5)
@@ -32,7 +32,8 @@ def _nets():
 
 
 def _requests(nets):
-    spec = [(0, 1500, 0), (1, 3000, 10), (0, 2500, 20), (0, 700, 30), (1, 6000, 40), (0, 5000, 50)]
+    spec = [(0, 1500, 0), (2, 3000, 10), (1, 2000, 60), (0, 2500, 20), (0, 700, 30), (2, 6000, 40),
+            (1, 7000, 70), (0, 5000, 50)]
     return [serve.Request(i, nets[k], 0.0, n, nets[k].inputs(off, n)) for i, (k, n, off) in enumerate(spec)]
 
 
@@ -41,17 +42,17 @@ def test_results_alone_equal_results_in_the_mix():
     # alone: one request per run, one slot, no packing
     alone = []
     for r in _requests(nets):
-        srv = serve.Server(nets, {"dense_square": 1, "mlp": 1}, 150e9, pack=False, max_inflight=1)
+        srv = serve.Server(nets, {"dense_square": 1, "cnn": 1, "mlp": 1}, 150e9, pack=False, max_inflight=1)
         done, wall, backlog = srv.run([r])
         assert len(done) == 1 and backlog == 0
         alone.append(done[0].y.copy())
         del srv
     # in the mix: all at once, packing and two slots per network
-    srv = serve.Server(nets, {"dense_square": 2, "mlp": 2}, 150e9, pack=True)
+    srv = serve.Server(nets, {"dense_square": 2, "cnn": 2, "mlp": 2}, 150e9, pack=True)
     reqs = _requests(nets)
     done, wall, backlog = srv.run(reqs)
     assert backlog == 0 and len(done) == len(reqs)
-    assert max(r.issued for r in reqs) >= 2          # the 5000-sample request was split across batches
+    assert max(r.issued for r in reqs) >= 2          # a request was split across batches
     for r, ya in zip(reqs, alone):
         assert np.max(np.abs(r.y - ya)) < 1e-4, r.rid
         ref = ckks.forward_fp64(r.net.graph, W.input_nodes(r.net.graph), [r.x])
@@ -108,3 +109,14 @@ def test_eval_batch_equals_the_separate_calls():
         G.eval_batch(c, [(big, torch.zeros((n_out, N // 2 + 1), dtype=torch.float64, device="cuda"))], 0)
     G.close()
     c.close()
+
+
+def test_admission_cap_binds():
+    """Slots beyond the admission cap are not created: with a cap below one
+    slot's footprint each network keeps only its first slot."""
+    nets = _nets()
+    srv = serve.Server(nets, {"dense_square": 3, "cnn": 3, "mlp": 3}, 1.0, pack=True)
+    assert {k: len(v) for k, v in srv.slots.items()} == {"dense_square": 1, "cnn": 1, "mlp": 1}
+    assert srv.footprint > 1.0
+    roomy = serve.Server(nets[:1], {"dense_square": 3}, 150e9, pack=True)
+    assert len(roomy.slots["dense_square"]) == 3

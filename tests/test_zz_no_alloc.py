@@ -30,14 +30,28 @@ def test_noalloc_relinearise_matches_twice():
     torch.cuda.set_device(0)
     ctx = fhe.Context(16384, BITS9, 40)
     ctx.keygen(0)
-    for call, (n, L) in enumerate([(2, 8), (3, 5)]):
-        d3 = _random_d3(ctx, n, L, 100 + call)
-        ref = ctx.empty_ct(n, L)
-        got = ctx.empty_ct(n, L)
-        ctx.relinearise(d3, L, ref)
+    cases = [(2, 8), (3, 5)]
+    d3s = [_random_d3(ctx, n, L, 100 + k) for k, (n, L) in enumerate(cases)]
+    gots = [ctx.empty_ct(n, L) for n, L in cases]
+    # the first call on a device looks up (and, under lazy loading, reserves)
+    # the fixed array: make it before measuring
+    ctx.relinearise_noalloc(d3s[0], cases[0][1], ctx.empty_ct(*cases[0]))
+    torch.cuda.synchronize()
+    ws0 = ctx.workspace_bytes()
+    free0 = torch.cuda.mem_get_info()[0]
+    # two calls in a row on a context whose workspace has not been used
+    for (n, L), d3, got in zip(cases, d3s, gots):
         ctx.relinearise_noalloc(d3, L, got)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0, "the calls allocated device memory"
+    assert ctx.workspace_bytes() == ws0, "the calls used or grew the context workspace"
+    # only now the ordinary entry point, which grows the workspace
+    for call, ((n, L), d3, got) in enumerate(zip(cases, d3s, gots)):
+        ref = ctx.empty_ct(n, L)
+        ctx.relinearise(d3, L, ref)
         torch.cuda.synchronize()
         assert torch.equal(ref, got), "call %d differs" % call
+    assert ctx.workspace_bytes() > ws0
     too_big = _random_d3(ctx, 5, 8, 7)
     with pytest.raises(fhe.FheError) as e:
         ctx.relinearise_noalloc(too_big, 8, ctx.empty_ct(5, 8))
