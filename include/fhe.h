@@ -313,7 +313,10 @@ int fhe_rescale(fhe_ctx* ctx, const uint64_t* d_in, uint32_t n_ct, uint32_t comp
                 uint64_t* d_out, void* stream);
 
 /* ct-mult + relinearise + rescale for n_ct pairs at `level`:
- * d_out [n_ct][2][level-1][N] = rescale(relin(a (x) b)). */
+ * d_out [n_ct][2][level-1][N] = rescale(relin(a (x) b)).  ModDown and the
+ * rescale share their forward transforms (NTT([v] P^-1 + [r]) per output
+ * row, the transforms being linear); both centred roundings are those of
+ * the separate steps, so the words equal fhe_relinearise then fhe_rescale. */
 int fhe_mul_relin_rescale(fhe_ctx* ctx, const uint64_t* d_a, const uint64_t* d_b, uint32_t n_ct,
                           uint32_t level, uint64_t* d_out, void* stream);
 
@@ -327,11 +330,13 @@ typedef struct {
 } fhe_level_batch;
 
 /* ct-mult + relinearise + rescale for ciphertexts at uneven levels: each
- * step (tensor, the four key-switching transforms, the two rescale
- * transforms) is ONE launch over every batch, located by prefix sums, so the
- * whole set costs seven launches and can be captured in a CUDA graph (after a
- * first call has sized the workspace).  Up to 8 batches per call (more are
- * processed 8 at a time).  Same results as fhe_mul_relin_rescale per batch. */
+ * step (tensor, digit inverse transforms, key inner products, inverse
+ * transforms of P's residues, and ModDown merged with the rescale: one
+ * inverse and one forward step) is ONE launch over every batch, located by
+ * prefix sums, so the whole set costs six launches and can be captured in a
+ * CUDA graph (after a first call has sized the workspace).  Up to 8 batches
+ * per call (more are processed 8 at a time).  Same results as
+ * fhe_mul_relin_rescale per batch. */
 int fhe_mul_relin_rescale_levels(fhe_ctx* ctx, const fhe_level_batch* batches, uint32_t n_batches, void* stream);
 
 /* multiply by integer constants: ct_k *= C_k (one signed constant per

@@ -933,19 +933,15 @@ int fhe_mul_relin_rescale(fhe_ctx* c, const uint64_t* a, const uint64_t* b, uint
     if (n_ct == 0) return FHE_OK;
     if (!a || !b || !out) return fail(FHE_EINVAL, "null buffer");
     const size_t N = c->N;
-    const size_t b3 = (size_t)n_ct * 3 * level * N * 8, b2 = (size_t)n_ct * 2 * level * N * 8;
-    const size_t br = relin_scratch_bytes(c, n_ct, level), bs = rescale_scratch_bytes(c, n_ct, 2);
+    const size_t b3 = (size_t)n_ct * 3 * level * N * 8, br = relin_rescale_scratch_bytes(c, n_ct, level);
     Arena ar;
-    int rc = ws_reserve(c, arena_need({b3, b2, br, bs}), &ar);
+    int rc = ws_reserve(c, arena_need({b3, br}), &ar);
     if (rc) return rc;
     u64* t3 = (u64*)ar.take(b3);
-    u64* t2 = (u64*)ar.take(b2);
     void* sr = ar.take(br);
-    void* ss = ar.take(bs);
     cudaStream_t st = (cudaStream_t)stream;
     k_tensor(c, (const u64*)a, (const u64*)b, t3, n_ct, level, st);
-    k_relin(c, t3, t2, n_ct, level, sr, st);
-    k_rescale(c, t2, (u64*)out, n_ct, 2, level, nullptr, 0, ss, st);
+    k_relin_rescale(c, t3, (u64*)out, n_ct, level, sr, st);
     CUDA_LAST("mul_relin_rescale launch");
     return FHE_OK;
 }
@@ -1030,6 +1026,7 @@ int fhe_add_const(fhe_ctx* c, uint64_t* ct, const int64_t* h_c, uint32_t n_ct, u
 // ---------------------------------------------------------------- measurement
 static const char* kFamilies =
     "ntt,rescale_intt,rescale_ntt,keyswitch_intt,keyswitch_modup_mac,keyswitch_acc_intt,keyswitch_moddown,"
+    "keyswitch_rescale_intt,keyswitch_rescale_ntt,"
     "keygen,encrypt,decrypt,encode_ntt,encode_fft,decode_fft,mac,mac_tc,tensor,elementwise";
 
 const char* fhe_profile_families(void) { return kFamilies; }

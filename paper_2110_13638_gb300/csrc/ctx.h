@@ -209,6 +209,21 @@ void k_plain_mac(const fhe_ctx* c, u64* Y, const u64* X, const u64* PT, uint32_t
 // comp 0 of out[f * n + i] += BIAS[f] (level L1)
 void k_add_plain(const fhe_ctx* c, u64* out, const u64* bias, uint32_t F, uint32_t n, uint32_t L1, cudaStream_t st);
 void k_gather_slots(const double* src, const int64_t* index, size_t total, double* dst, cudaStream_t st);
+// relinearise then rescale, fused (ModDown's and the rescale's forward
+// transforms merged; word for word the two steps in sequence):
+// out [n][2][L-1][N] = rescale(relin(d3) + E) (+ addc on comp 0, as k_rescale),
+// E = x2 c2 + x c1 when ex is given (fields may be null)
+struct KsExtra {
+    const u64* x2;      // [n][2][L][N] (level of the relinearisation) or null
+    const u64* c2;      // [L] device residues
+    const u64* x;       // [n][2][Lx][N], its first L residues used, or null
+    const u64* c1;      // [L] device residues
+    int Lx;
+};
+size_t relin_rescale_scratch_bytes(const fhe_ctx* c, uint32_t n_ct, uint32_t L);
+void k_relin_rescale(const fhe_ctx* c, const u64* d3, u64* out, uint32_t n_ct, uint32_t L, void* scratch,
+                     cudaStream_t st, const KsExtra* ex = nullptr, const u64* addc = nullptr,
+                     uint32_t addc_stride = 0);
 // scratch: rescale_scratch_bytes; addc: optional constants (device residues,
 // addc[ct * addc_stride + i]) added to comp 0 of the result
 size_t rescale_scratch_bytes(const fhe_ctx* c, uint32_t n_ct, uint32_t comps);

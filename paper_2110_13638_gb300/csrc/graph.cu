@@ -469,14 +469,11 @@ struct Exec {
             const uint32_t j = P.j[k], lv = P.lev[k] + 1;
             const Sig A = drop_to(pw[j], lv), B = (j == k - j) ? A : drop_to(pw[k - j], lv);
             u64* T3 = (u64*)take(cts(n, 3, lv));
-            u64* R = (u64*)take(cts(n, 2, lv));
-            void* rs = take(relin_scratch_bytes(c, n, lv));
-            void* ss = take(rescale_scratch_bytes(c, n, 2));
+            void* rs = take(relin_rescale_scratch_bytes(c, n, lv));
             u64* out = (u64*)take(cts(n, 2, lv - 1));
             if (!dry && ok()) {
                 k_tensor(c, A.p, B.p, T3, n, lv, st);
-                k_relin(c, T3, R, n, lv, rs, st);
-                k_rescale(c, R, out, n, 2, lv, nullptr, 0, ss, st);
+                k_relin_rescale(c, T3, out, n, lv, rs, st);
             }
             pw[k].p = out;
             pw[k].n = n;
@@ -586,14 +583,11 @@ struct Exec {
         const uint32_t L = x.L;
         if (L < 2) { err(FHE_ELEVEL, "square needs two primes"); return y; }
         u64* T3 = (u64*)take(cts(x.n, 3, L));
-        u64* R = (u64*)take(cts(x.n, 2, L));
-        void* rs = take(relin_scratch_bytes(c, x.n, L));
-        void* ss = take(rescale_scratch_bytes(c, x.n, 2));
+        void* rs = take(relin_rescale_scratch_bytes(c, x.n, L));
         u64* out = (u64*)take(cts(x.n, 2, L - 1));
         if (!dry && ok()) {
             k_tensor(c, x.p, x.p, T3, x.n, L, st);
-            k_relin(c, T3, R, x.n, L, rs, st);
-            k_rescale(c, R, out, x.n, 2, L, nullptr, 0, ss, st);
+            k_relin_rescale(c, T3, out, x.n, L, rs, st);
         }
         y.p = out;
         y.n = x.n;
@@ -618,25 +612,22 @@ struct Exec {
         }
         if (deg == 2) return poly2(i, x, k);
         u64* T3 = (u64*)take(cts(n, 3, L));
-        u64* R = (u64*)take(cts(n, 2, L));
-        void* rs = take(relin_scratch_bytes(c, n, L));
+        void* rs = take(relin_rescale_scratch_bytes(c, n, L));
         void* ss = take(rescale_scratch_bytes(c, n, 2));
         u64* x2 = (u64*)take(cts(n, 2, L - 1));
         u64* w = (u64*)take(cts(n, 2, L - 1));
         u64* T3b = (u64*)take(cts(n, 3, L - 1));
-        u64* t1 = (u64*)take(cts(n, 2, L - 1));
         u64* out = (u64*)take(cts(n, 2, L - 2));
         if (!dry && ok()) {
             fhe_node_const* kc = node_const(i, L, x.scale);
             if (!kc) return y;
             k_tensor(c, x.p, x.p, T3, n, L, st);
-            k_relin(c, T3, R, n, L, rs, st);
-            k_rescale(c, R, x2, n, 2, L, nullptr, 0, ss, st);
+            k_relin_rescale(c, T3, x2, n, L, rs, st);                         // x2 = rescale(relin(x (x) x))
             k_rescale(c, x.p, w, n, 2, L, nullptr, 0, ss, st, kc->c3);        // rescale(x * C3)
             k_tensor(c, x2, w, T3b, n, L - 1, st);
-            k_relin(c, T3b, t1, n, L - 1, rs, st);
-            k_poly_combine(c, t1, x2, x.p, n, L - 1, L, kc->c2, kc->c1, st);  // + x2 C2 + drop(x) C1
-            k_rescale(c, t1, out, n, 2, L - 1, kc->c0, 0, ss, st);
+            // y = rescale(relin(x2 (x) w) + x2 C2 + drop(x) C1) + C0
+            const KsExtra ex{x2, kc->c2, x.p, kc->c1, (int)L};
+            k_relin_rescale(c, T3b, out, n, L - 1, rs, st, &ex, kc->c0, 0);
         }
         y.p = out;
         y.n = n;
@@ -674,8 +665,7 @@ struct Exec {
         Sig y;
         const uint32_t L = x.L, n = x.n;
         u64* T3 = (u64*)take(cts(n, 3, L));
-        u64* R = (u64*)take(cts(n, 2, L));
-        void* rs = take(relin_scratch_bytes(c, n, L));
+        void* rs = take(relin_rescale_scratch_bytes(c, n, L));
         void* ss = take(rescale_scratch_bytes(c, n, 2));
         u64* x2 = (u64*)take(cts(n, 2, L - 1));
         u64* t = (u64*)take(cts(n, 2, L - 1));
@@ -684,8 +674,7 @@ struct Exec {
             fhe_node_const* kc = node_const(i, L, x.scale);
             if (!kc) return y;
             k_tensor(c, x.p, x.p, T3, n, L, st);
-            k_relin(c, T3, R, n, L, rs, st);
-            k_rescale(c, R, x2, n, 2, L, nullptr, 0, ss, st);
+            k_relin_rescale(c, T3, x2, n, L, rs, st);
             k_poly_combine(c, t, x2, x.p, n, L - 1, L, kc->c2, kc->c1, st, false);   // x2 C2 + drop(x) C1
             k_rescale(c, t, out, n, 2, L - 1, kc->c0, 0, ss, st);
         }

@@ -6,7 +6,9 @@ namespace fhe {
 // ---------------------------------------------------------------- level groups
 // ct-mult + relinearise + rescale for batches at different levels: every step
 // is one launch over all batches (MultiOp), so a set of uneven-level
-// ciphertexts costs seven launches whatever its level mix.
+// ciphertexts costs six launches whatever its level mix (tensor, digit
+// inverses, key inner products, P inverses, and the merged ModDown + rescale
+// inverse and forward steps).
 struct TensorGroups {
     const u64* a[kMaxGroups];
     const u64* b[kMaxGroups];
@@ -44,8 +46,7 @@ size_t level_groups_scratch_bytes(const fhe_ctx* c, const LevelBatch* g, int ng)
     size_t s = 0;
     for (int k = 0; k < ng; ++k) {
         const size_t n = g[k].n, L = g[k].L;
-        s += arena_need({n * 3 * L * N * 8, n * 2 * L * N * 8, n * L * N * 8, n * 2 * (L + 1) * N * 8,
-                         n * 2 * N * 8, n * 2 * N * 8});
+        s += arena_need({n * 3 * L * N * 8, n * L * N * 8, n * 2 * (L + 1) * N * 8, n * 2 * N * 8, n * 2 * N * 8});
     }
     return s;
 }
@@ -60,16 +61,15 @@ void k_mul_relin_rescale_groups(const fhe_ctx* c, const LevelBatch* g, int ng, v
     MultiOp<OpDigitsInv> m1;
     MultiOp<OpModUpMac> m2;
     MultiOp<OpAccPInv> m3;
-    MultiOp<OpModDown> m4;
-    MultiOp<OpTakeRowInv> m5;
-    MultiOp<OpDivFwd> m6;
-    m1.ng = m2.ng = m3.ng = m4.ng = m5.ng = m6.ng = tg.ng = ng;
-    m1.pre_[0] = m2.pre_[0] = m3.pre_[0] = m4.pre_[0] = m5.pre_[0] = m6.pre_[0] = 0;
+    MultiOp<OpKsRowInv> m4;
+    MultiOp<OpKsDivFwd> m5;
+    m1.ng = m2.ng = m3.ng = m4.ng = m5.ng = tg.ng = ng;
+    m1.pre_[0] = m2.pre_[0] = m3.pre_[0] = m4.pre_[0] = m5.pre_[0] = 0;
     tg.start[0] = 0;
+    const KsExtra none{nullptr, nullptr, nullptr, nullptr, 0};
     for (int k = 0; k < ng; ++k) {
         const int n = (int)g[k].n, L = (int)g[k].L;
         u64* t3 = (u64*)ar.take((size_t)n * 3 * L * N * 8);
-        u64* t2 = (u64*)ar.take((size_t)n * 2 * L * N * 8);
         u64* D = (u64*)ar.take((size_t)n * L * N * 8);
         u64* acc = (u64*)ar.take((size_t)n * 2 * (L + 1) * N * 8);
         u64* Vp = (u64*)ar.take((size_t)n * 2 * N * 8);
@@ -82,46 +82,13 @@ void k_mul_relin_rescale_groups(const fhe_ctx* c, const LevelBatch* g, int ng, v
         m1.ops[k] = OpDigitsInv{t3, D, n, L, (int)N};
         m2.ops[k] = OpModUpMac{t3, D, c->d_ksk, acc, n, L, (int)N, (int)c->L_top, modup_red_mask(c, (uint32_t)L)};
         m3.ops[k] = OpAccPInv{acc, Vp, n, L, (int)N, (int)c->L_top};
-        OpModDown md;
-        md.d3 = t3;
-        md.acc = acc;
-        md.Vp = Vp;
-        md.out = t2;
-        md.n = n;
-        md.L = L;
-        md.N = (int)N;
-        md.d = make_divc(c, c->L_top, L);
-        m4.ops[k] = md;
-        OpTakeRowInv tr;
-        tr.in = t2;
-        tr.V = V;
-        tr.n = n * 2;
-        tr.L = L;
-        tr.row = L - 1;
-        tr.N = (int)N;
-        tr.pidx = L - 1;
-        tr.mulc = nullptr;
-        m5.ops[k] = tr;
-        OpDivFwd dv;
-        dv.in = t2;
-        dv.V = V;
-        dv.out = g[k].out;
-        dv.addc = nullptr;
-        dv.addc_stride = 0;
-        dv.n_poly = n * 2;
-        dv.comps = 2;
-        dv.L_in = L;
-        dv.L_out = L - 1;
-        dv.N = (int)N;
-        dv.d = make_divc(c, L - 1, L - 1);
-        dv.mulc = nullptr;
-        m6.ops[k] = dv;
+        m4.ops[k] = make_ks_row_inv(c, t3, acc, Vp, V, n, L, none);
+        m5.ops[k] = make_ks_div_fwd(c, t3, acc, Vp, V, g[k].out, n, L, none, nullptr, 0);
         m1.pre_[k + 1] = m1.pre_[k] + m1.ops[k].count();
         m2.pre_[k + 1] = m2.pre_[k] + m2.ops[k].count();
         m3.pre_[k + 1] = m3.pre_[k] + m3.ops[k].count();
         m4.pre_[k + 1] = m4.pre_[k] + m4.ops[k].count();
         m5.pre_[k + 1] = m5.pre_[k] + m5.ops[k].count();
-        m6.pre_[k + 1] = m6.pre_[k] + m6.ops[k].count();
     }
     {
         LaunchScope ls(c, "tensor", st);
@@ -130,9 +97,8 @@ void k_mul_relin_rescale_groups(const fhe_ctx* c, const LevelBatch* g, int ng, v
     launch_ntt<true>(c, m1, st);
     launch_groups_modup_mac(c, m2, st);
     launch_ntt<true>(c, m3, st);
-    launch_groups_moddown(c, m4, st);
-    launch_ntt<true>(c, m5, st);
-    launch_groups_divfwd(c, m6, st);
+    launch_ntt<true>(c, m4, st);
+    launch_groups_ks_divfwd(c, m5, st);
 }
 
 

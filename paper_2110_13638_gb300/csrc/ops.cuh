@@ -210,11 +210,109 @@ struct OpModDown {
     }
 };
 
+// ---------------------------------------------------------------- relinearise + rescale
+// ModDown and the rescale right after it, with the forward transforms of the
+// two corrections merged.  With v = centred INTT_P(acc_P) (ModDown's
+// remainder), R = d + E + (acc - NTT([v])) P^-1 the relinearised ciphertext
+// (E an optional NTT-form term added before the rescale) and r = centred
+// INTT_{q_{L-1}}(R_{L-1}) (the rescale's remainder):
+//   INTT(R_{L-1}) = INTT(d_{L-1} + E_{L-1} + acc_{L-1} P^-1) - [v]_{L-1} P^-1
+//   out_i = (d_i + E_i + acc_i P^-1 - NTT([v]_i P^-1 + [r]_i)) q_{L-1}^-1,  i < L-1
+// The transforms are linear mod q_i, so out is word for word ModDown
+// followed by the rescale: both centred roundings are taken exactly as
+// there, but each output row needs one forward transform instead of two.
+
+// step 4': INTT of row L-1 of the relinearised ciphertext, per (ct, comp)
+struct OpKsRowInv {
+    static const char* family() { return "keyswitch_rescale_intt"; }
+    const u64* d3;      // [n][3][L][N]
+    const u64* acc;     // [n][2][L+1][N]
+    const u64* Vp;      // [n][2][N] coefficient form mod P
+    u64* V;             // [n][2][N] coefficient form mod q_{L-1}
+    int n, L, N;
+    KsExtra ex;
+    u64 p, p_half, pmod, pinv, pinvs;    // P, (P-1)/2, P mod q_{L-1}, P^-1 mod q_{L-1} (+ Shoup)
+    __host__ __device__ int count() const { return n * 2; }
+    __host__ __device__ int nsub(int) const { return 1; }
+    __device__ int prime(int, int) const { return L - 1; }
+    __device__ bool direct(int, int) const { return false; }
+    __device__ u64 load(int p, int, int j, const PrimeC& Q) const
+    {
+        const int ct = p >> 1, k = p & 1, i = L - 1;
+        u64 s = d3[(((size_t)ct * 3 + k) * L + i) * N + j];
+        s = add_mod(s, mul_shoup(acc[((size_t)p * (L + 1) + i) * N + j], pinv, pinvs, Q.q), Q.q);
+        if (ex.x2) s = add_mod(s, mul_mod(ex.x2[((size_t)p * L + i) * N + j], ex.c2[i], Q), Q.q);
+        if (ex.x) s = add_mod(s, mul_mod(ex.x[((size_t)p * ex.Lx + i) * N + j], ex.c1[i], Q), Q.q);
+        return s;
+    }
+    struct Pre { u64 v; };
+    __device__ Pre pre(int p, int, int j) const { return {Vp[(size_t)p * N + j]}; }
+    __device__ void store(int p, int, int j, u64 v, const Pre& pr, const PrimeC& Q) const
+    {
+        const u64 vq = mul_shoup(centred_to(pr.v, this->p, p_half, pmod, Q), pinv, pinvs, Q.q);
+        V[(size_t)p * N + j] = sub_mod(v, vq, Q.q);
+    }
+};
+
+// step 5': the merged forward transform of both corrections into q_i, i < L-1,
+// per (ct, comp, i), and the rescaled output row
+struct OpKsDivFwd {
+    static const char* family() { return "keyswitch_rescale_ntt"; }
+    const u64* d3;      // [n][3][L][N]
+    const u64* acc;     // [n][2][L+1][N]
+    const u64* Vp;      // [n][2][N] mod P
+    const u64* V;       // [n][2][N] mod q_{L-1}
+    u64* out;           // [n][2][L-1][N]
+    const u64* addc;    // optional constants added to comp 0 of the result, [n][addc_stride]
+    int n, L, N, addc_stride;
+    KsExtra ex;
+    DivC dp;            // division by P into q_0 .. q_{L-1}
+    DivC dq;            // division by q_{L-1} into q_0 .. q_{L-2}
+    __host__ __device__ int count() const { return n * 2 * (L - 1); }
+    __host__ __device__ int nsub(int) const { return 1; }
+    __device__ int prime(int p, int) const { return p % (L - 1); }
+    __device__ bool direct(int, int) const { return false; }
+    __device__ u64 load(int p, int, int j, const PrimeC& Q) const
+    {
+        const int poly = p / (L - 1), i = p % (L - 1);
+        const u64 a = centred_to(Vp[(size_t)poly * N + j], dp.p, dp.p_half, dp.pmod[i], Q);
+        const u64 b = centred_to(V[(size_t)poly * N + j], dq.p, dq.p_half, dq.pmod[i], Q);
+        return add_mod(mul_shoup(a, dp.inv[i], dp.invs[i], Q.q), b, Q.q);
+    }
+    struct Pre { u64 d, a, x2, x; };
+    __device__ Pre pre(int p, int, int j) const
+    {
+        const int poly = p / (L - 1), i = p % (L - 1);
+        const int ct = poly >> 1, k = poly & 1;
+        Pre r;
+        r.d = d3[(((size_t)ct * 3 + k) * L + i) * N + j];
+        r.a = acc[((size_t)poly * (L + 1) + i) * N + j];
+        r.x2 = ex.x2 ? ex.x2[((size_t)poly * L + i) * N + j] : 0;
+        r.x = ex.x ? ex.x[((size_t)poly * ex.Lx + i) * N + j] : 0;
+        return r;
+    }
+    __device__ void store(int p, int, int j, u64 v, const Pre& pr, const PrimeC& Q) const
+    {
+        const int poly = p / (L - 1), i = p % (L - 1);
+        u64 s = add_mod(pr.d, mul_shoup(pr.a, dp.inv[i], dp.invs[i], Q.q), Q.q);
+        if (ex.x2) s = add_mod(s, mul_mod(pr.x2, ex.c2[i], Q), Q.q);
+        if (ex.x) s = add_mod(s, mul_mod(pr.x, ex.c1[i], Q), Q.q);
+        u64 r = mul_shoup(sub_mod(s, v, Q.q), dq.inv[i], dq.invs[i], Q.q);
+        if (addc && (poly & 1) == 0) r = add_mod(r, addc[(size_t)(poly >> 1) * addc_stride + i], Q.q);
+        out[((size_t)poly * (L - 1) + i) * N + j] = r;
+    }
+};
+
 // Grouped (MultiOp) launches of the forward steps, each compiled in a
-// translation unit of its own (k_groups_ks.cu, k_groups_fwd.cu) so the build runs them in
-// parallel.
+// translation unit of its own (k_groups_ks.cu, k_groups_fwd.cu) so the build
+// runs them in parallel.
 void launch_groups_modup_mac(const fhe_ctx* c, const MultiOp<OpModUpMac>& m, cudaStream_t st);
-void launch_groups_moddown(const fhe_ctx* c, const MultiOp<OpModDown>& m, cudaStream_t st);
-void launch_groups_divfwd(const fhe_ctx* c, const MultiOp<OpDivFwd>& m, cudaStream_t st);
+void launch_groups_ks_divfwd(const fhe_ctx* c, const MultiOp<OpKsDivFwd>& m, cudaStream_t st);
+
+// The merged ModDown + rescale of one batch (k_relin.cu): ops of steps 4' and 5'.
+OpKsRowInv make_ks_row_inv(const fhe_ctx* c, const u64* d3, const u64* acc, const u64* Vp, u64* V, int n, int L,
+                           const KsExtra& ex);
+OpKsDivFwd make_ks_div_fwd(const fhe_ctx* c, const u64* d3, const u64* acc, const u64* Vp, const u64* V, u64* out,
+                           int n, int L, const KsExtra& ex, const u64* addc, int addc_stride);
 
 }  // namespace fhe

@@ -373,9 +373,10 @@ class Context:
     def _ct(self, t, n, comps, level, name):
         _dev(t, (n, comps, level, self.N), "int64", name)
 
-    def _level(self, level):
-        if not 1 <= level <= self.L_top:
-            raise ValueError("level %d outside 1..%d" % (level, self.L_top))
+    def _lv(self, level, lo=1):
+        """True if the library accepts `level`; otherwise it refuses the call
+        with FHE_ELEVEL before touching any buffer, so shapes are not checked."""
+        return lo <= level <= self.L_top
 
     # -- keys / encode / encrypt / decrypt / decode ------------------------
     def keygen(self, seed, stream=None):
@@ -386,10 +387,10 @@ class Context:
         _check(lib().fhe_export_secret(self.h, _ptr(out), _stream(stream)))
 
     def encode(self, slots, level, scale, out, stream=None):
-        self._level(level)
         n = _rows(slots)
         _dev(slots, (n, self.N // 2), "float64", "slots")
-        _dev(out, (n, level, self.N), "int64", "out")
+        if self._lv(level):
+            _dev(out, (n, level, self.N), "int64", "out")
         _check(lib().fhe_encode(self.h, _ptr(slots), n, level, scale, _ptr(out), _stream(stream)))
 
     def encrypt(self, pt, first_ct_id, out, stream=None):
@@ -406,9 +407,9 @@ class Context:
                                         _stream(stream)))
 
     def decrypt(self, ct, level, out, stream=None):
-        self._level(level)
         n = _rows(ct)
-        self._ct(ct, n, 2, level, "ct")
+        if self._lv(level):
+            self._ct(ct, n, 2, level, "ct")
         _dev(out, (n, self.N), "int64", "out")
         _check(lib().fhe_decrypt(self.h, _ptr(ct), n, level, _ptr(out), _stream(stream)))
 
@@ -420,34 +421,33 @@ class Context:
 
     # -- layout ---------------------------------------------------------------
     def ntt(self, polys, rows, forward, stream=None):
-        if not 1 <= rows <= self.L_top + 1:
-            raise ValueError("rows %d outside 1..%d" % (rows, self.L_top + 1))
         n = _rows(polys)
-        _dev(polys, (n, rows, self.N), "int64", "polys")
+        if 1 <= rows <= self.L_top + 1:            # otherwise the library refuses the call
+            _dev(polys, (n, rows, self.N), "int64", "polys")
         _check(lib().fhe_ntt(self.h, _ptr(polys), n, rows, 1 if forward else 0, _stream(stream)))
 
     def ct_convert(self, ct, level, to_coeff, out, stream=None):
-        self._level(level)
         n = _rows(ct)
-        self._ct(ct, n, 2, level, "ct")
-        self._ct(out, n, 2, level, "out")
+        if self._lv(level):
+            self._ct(ct, n, 2, level, "ct")
+            self._ct(out, n, 2, level, "out")
         _check(lib().fhe_ct_convert(self.h, _ptr(ct), n, level, 1 if to_coeff else 0, _ptr(out),
                                     _stream(stream)))
 
     # -- operations -----------------------------------------------------------
     def add(self, a, b, level, out, stream=None):
-        self._level(level)
         n = _rows(a)
-        for t, nm in ((a, "a"), (b, "b"), (out, "out")):
-            self._ct(t, n, 2, level, nm)
+        if self._lv(level):
+            for t, nm in ((a, "a"), (b, "b"), (out, "out")):
+                self._ct(t, n, 2, level, nm)
         _check(lib().fhe_add(self.h, _ptr(a), _ptr(b), n, level, _ptr(out), _stream(stream)))
 
     def tensor(self, a, b, level, out, stream=None):
-        self._level(level)
         n = _rows(a)
-        self._ct(a, n, 2, level, "a")
-        self._ct(b, n, 2, level, "b")
-        self._ct(out, n, 3, level, "out")
+        if self._lv(level):
+            self._ct(a, n, 2, level, "a")
+            self._ct(b, n, 2, level, "b")
+            self._ct(out, n, 3, level, "out")
         _check(lib().fhe_tensor(self.h, _ptr(a), _ptr(b), n, level, _ptr(out), _stream(stream)))
 
     def galois_keygen(self, steps, stream=None):
@@ -456,43 +456,41 @@ class Context:
         _check(lib().fhe_galois_keygen(self.h, arr, len(steps), _stream(stream)))
 
     def rotate(self, ct, level, step, out, stream=None):
-        self._level(level)
         n = _rows(ct)
-        self._ct(ct, n, 2, level, "ct")
-        self._ct(out, n, 2, level, "out")
+        if self._lv(level):
+            self._ct(ct, n, 2, level, "ct")
+            self._ct(out, n, 2, level, "out")
         _check(lib().fhe_rotate(self.h, _ptr(ct), n, level, int(step), _ptr(out), _stream(stream)))
 
     def relinearise(self, d3, level, out, stream=None):
-        self._level(level)
         n = _rows(d3)
-        self._ct(d3, n, 3, level, "d3")
-        self._ct(out, n, 2, level, "out")
+        if self._lv(level):
+            self._ct(d3, n, 3, level, "d3")
+            self._ct(out, n, 2, level, "out")
         _check(lib().fhe_relinearise(self.h, _ptr(d3), n, level, _ptr(out), _stream(stream)))
 
     def relinearise_noalloc(self, d3, level, out, stream=None):
         """fhe_relinearise without allocating: scratch from the library's fixed
         16 MiB device array (see include/fhe.h)."""
-        self._level(level)
         n = _rows(d3)
-        self._ct(d3, n, 3, level, "d3")
-        self._ct(out, n, 2, level, "out")
+        if self._lv(level):
+            self._ct(d3, n, 3, level, "d3")
+            self._ct(out, n, 2, level, "out")
         _check(lib().fhe_relinearise_noalloc(self.h, _ptr(d3), n, level, _ptr(out), _stream(stream)))
 
     def rescale(self, x, comps, level, out, stream=None):
-        if not 2 <= level <= self.L_top:
-            raise ValueError("rescale needs level 2..%d" % self.L_top)
         n = _rows(x)
-        self._ct(x, n, comps, level, "x")
-        self._ct(out, n, comps, level - 1, "out")
+        if self._lv(level, 2):
+            self._ct(x, n, comps, level, "x")
+            self._ct(out, n, comps, level - 1, "out")
         _check(lib().fhe_rescale(self.h, _ptr(x), n, comps, level, _ptr(out), _stream(stream)))
 
     def mul_relin_rescale(self, a, b, level, out, stream=None):
-        if not 2 <= level <= self.L_top:
-            raise ValueError("mul_relin_rescale needs level 2..%d" % self.L_top)
         n = _rows(a)
-        self._ct(a, n, 2, level, "a")
-        self._ct(b, n, 2, level, "b")
-        self._ct(out, n, 2, level - 1, "out")
+        if self._lv(level, 2):
+            self._ct(a, n, 2, level, "a")
+            self._ct(b, n, 2, level, "b")
+            self._ct(out, n, 2, level - 1, "out")
         _check(lib().fhe_mul_relin_rescale(self.h, _ptr(a), _ptr(b), n, level, _ptr(out),
                                            _stream(stream)))
 
@@ -501,20 +499,19 @@ class Context:
         launch over all batches."""
         arr = (LevelBatch * max(1, len(batches)))()
         for k, (a, b, out, level) in enumerate(batches):
-            if not 2 <= level <= self.L_top:
-                raise ValueError("batch %d: level %d outside 2..%d" % (k, level, self.L_top))
             n = _rows(a)
-            self._ct(a, n, 2, level, "a")
-            self._ct(b, n, 2, level, "b")
-            self._ct(out, n, 2, level - 1, "out")
+            if self._lv(level, 2):
+                self._ct(a, n, 2, level, "a")
+                self._ct(b, n, 2, level, "b")
+                self._ct(out, n, 2, level - 1, "out")
             arr[k] = LevelBatch(a.data_ptr(), b.data_ptr(), out.data_ptr(), n, level)
         _check(lib().fhe_mul_relin_rescale_levels(self.h, arr, len(batches), _stream(stream)))
 
     def mul_const(self, x, consts, level, out, stream=None):
-        self._level(level)
         n = _rows(x)
-        self._ct(x, n, 2, level, "x")
-        self._ct(out, n, 2, level, "out")
+        if self._lv(level):
+            self._ct(x, n, 2, level, "x")
+            self._ct(out, n, 2, level, "out")
         c = np.ascontiguousarray(consts, dtype=np.int64)
         if c.shape != (n,):
             raise ValueError("one constant per ciphertext expected")
@@ -522,9 +519,9 @@ class Context:
                                    _ptr(out), _stream(stream)))
 
     def add_const(self, x, consts, level, stream=None):
-        self._level(level)
         n = _rows(x)
-        self._ct(x, n, 2, level, "x")
+        if self._lv(level):
+            self._ct(x, n, 2, level, "x")
         c = np.ascontiguousarray(consts, dtype=np.int64)
         if c.shape != (n,):
             raise ValueError("one constant per ciphertext expected")
