@@ -329,14 +329,18 @@ typedef struct {
     uint32_t level;          /* 2 .. L_top */
 } fhe_level_batch;
 
-/* ct-mult + relinearise + rescale for ciphertexts at uneven levels: each
- * step (tensor, digit inverse transforms, key inner products, inverse
- * transforms of P's residues, and ModDown merged with the rescale: one
- * inverse and one forward step) is ONE launch over every batch, located by
- * prefix sums, so the whole set costs six launches and can be captured in a
- * CUDA graph (after a first call has sized the workspace).  Up to 8 batches
- * per call (more are processed 8 at a time).  Same results as
- * fhe_mul_relin_rescale per batch. */
+/* ct-mult + relinearise + rescale for ciphertexts at uneven levels in ONE
+ * persistent kernel launch (plus a memset of its work queue): one block per
+ * SM takes transform units from a device queue -- digit inverse transforms,
+ * key inner products, inverse transforms of P's residues, then ModDown
+ * merged with the rescale -- for every ciphertext of every batch; a unit
+ * waits (bounded, about a second; FHE_ETIMEOUT if it gives up) for its
+ * ciphertext's previous step, and the tensor product is recomputed from the
+ * factors where needed instead of being stored.  Capturable in a CUDA graph
+ * (after a first call has sized the workspace).  N <= 16384.  Up to 8
+ * batches per launch (more are processed 8 at a time).  Same results as
+ * fhe_mul_relin_rescale per batch.  FHE_PERSISTENT=0 in the environment
+ * runs the same steps as six separate launches instead, for comparisons. */
 int fhe_mul_relin_rescale_levels(fhe_ctx* ctx, const fhe_level_batch* batches, uint32_t n_batches, void* stream);
 
 /* multiply by integer constants: ct_k *= C_k (one signed constant per
@@ -444,6 +448,13 @@ int fhe_ctx_sync(fhe_ctx* ctx, void* stream);
  * outputs are left unwritten, and the context reports FHE_ETIMEOUT.  The
  * context stays usable. */
 #define FHE_INJECT_MAC_TC_WITHHOLD 1u
+/* FHE_INJECT_PERSIST_STALL: in the next persistent uneven-level launch
+ * (fhe_mul_relin_rescale_levels) through this context, the first phase's
+ * units never report completion and the waits are shortened to about a
+ * millisecond, so the second phase's bounded waits run out: the launch
+ * aborts its remaining units, leaves the outputs unwritten, and the context
+ * reports FHE_ETIMEOUT.  The context stays usable. */
+#define FHE_INJECT_PERSIST_STALL 2u
 int fhe_inject_fault(fhe_ctx* ctx, uint32_t kind);
 
 const char* fhe_last_error(void);

@@ -968,11 +968,19 @@ int fhe_mul_relin_rescale_levels(fhe_ctx* c, const fhe_level_batch* batches, uin
                                  batches[k].n_ct, batches[k].level};
         }
         if (ng == 0) continue;
-        const size_t need = level_groups_scratch_bytes(c, g, ng);
+        // FHE_PERSISTENT=0 runs the six-launch form instead (for comparisons)
+        const char* env = std::getenv("FHE_PERSISTENT");
+        const bool persistent = !(env && env[0] == '0');
+        const size_t need = persistent ? persist_scratch_bytes(c, g, ng) : level_groups_scratch_bytes(c, g, ng);
         Arena ar;
         int rc = ws_reserve(c, need, &ar);
         if (rc) return rc;
-        k_mul_relin_rescale_groups(c, g, ng, ar.take(need), st);
+        if (persistent) {
+            rc = k_mul_relin_rescale_persistent(c, g, ng, ar.take(need), st);
+            if (rc) return rc;
+        } else {
+            k_mul_relin_rescale_groups(c, g, ng, ar.take(need), st);
+        }
         CUDA_LAST("mul_relin_rescale_levels launch");
     }
     return FHE_OK;
@@ -1027,7 +1035,7 @@ int fhe_add_const(fhe_ctx* c, uint64_t* ct, const int64_t* h_c, uint32_t n_ct, u
 static const char* kFamilies =
     "ntt,rescale_intt,rescale_ntt,keyswitch_intt,keyswitch_modup_mac,keyswitch_acc_intt,keyswitch_moddown,"
     "keyswitch_rescale_intt,keyswitch_rescale_ntt,"
-    "keygen,encrypt,decrypt,encode_ntt,encode_fft,decode_fft,mac,mac_tc,tensor,elementwise";
+    "keygen,encrypt,decrypt,encode_ntt,encode_fft,decode_fft,mac,mac_tc,tensor,elementwise,persistent";
 
 const char* fhe_profile_families(void) { return kFamilies; }
 
@@ -1089,7 +1097,8 @@ int fhe_ctx_sync(fhe_ctx* c, void* stream)
 int fhe_inject_fault(fhe_ctx* c, uint32_t kind)
 {
     CHECK_CTX(c);
-    if (kind != FHE_INJECT_MAC_TC_WITHHOLD) return fail(FHE_EINVAL, "unknown fault kind");
+    if (kind != FHE_INJECT_MAC_TC_WITHHOLD && kind != FHE_INJECT_PERSIST_STALL)
+        return fail(FHE_EINVAL, "unknown fault kind");
     c->inject = (int)kind;
     return FHE_OK;
 }

@@ -272,6 +272,9 @@ struct LevelBatch {
 };
 size_t level_groups_scratch_bytes(const fhe_ctx* c, const LevelBatch* g, int ng);
 void k_mul_relin_rescale_groups(const fhe_ctx* c, const LevelBatch* g, int ng, void* scratch, cudaStream_t st);
+// the same in one persistent launch (N <= 16384; plus one memset of its queue)
+size_t persist_scratch_bytes(const fhe_ctx* c, const LevelBatch* g, int ng);
+int k_mul_relin_rescale_persistent(const fhe_ctx* c, const LevelBatch* g, int ng, void* scratch, cudaStream_t st);
 
 void k_keygen(fhe_ctx* c, cudaStream_t st);
 size_t encrypt_scratch_bytes(const fhe_ctx* c, uint32_t n_ct);

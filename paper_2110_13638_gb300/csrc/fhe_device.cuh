@@ -773,14 +773,15 @@ constexpr int kEpiBatchWide = 8;
 template <int MAXT>
 constexpr int kEpiPrefetch = MAXT <= 512 ? 4 : 0;
 
+// one unit p of a fused-I/O transform step (all its sub-transforms, in
+// order) by the calling block; shared memory sm holds ntt_smem_words(N) words
 template <bool INV, int LOGR, int MAXT, class Op>
-__global__ void __launch_bounds__(MAXT, 1) k_ntt_io(Op op, NttTables T)
+__device__ __forceinline__ void ntt_io_unit(const Op& op, const NttTables& T, int p, u64* sm)
 {
-    extern __shared__ u64 sm[];
     const int logN = T.logN;
     const int N = 1 << logN;
     const int tid = threadIdx.x, nthr = blockDim.x;
-    for (int p = blockIdx.x; p < op.count(); p += gridDim.x) {
+    {
         const int ns = op.nsub(p);
         for (int u = 0; u < ns; ++u) {
             const int pi = op.prime(p, u);
@@ -879,4 +880,11 @@ __global__ void __launch_bounds__(MAXT, 1) k_ntt_io(Op op, NttTables T)
             }
         }
     }
+}
+
+template <bool INV, int LOGR, int MAXT, class Op>
+__global__ void __launch_bounds__(MAXT, 1) k_ntt_io(Op op, NttTables T)
+{
+    extern __shared__ u64 sm[];
+    for (int p = blockIdx.x; p < op.count(); p += gridDim.x) ntt_io_unit<INV, LOGR, MAXT>(op, T, p, sm);
 }

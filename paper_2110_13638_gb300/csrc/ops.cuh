@@ -66,25 +66,61 @@ struct OpDivFwd {
 };
 
 // ---------------------------------------------------------------- relinearise
+// The three components of a tensor product d = (a0 b0, a0 b1 + a1 b0, a1 b1):
+// read from a stored [n][3][L][N] batch (D3Src<false>), or recomputed from
+// the factors a, b ([n][2][L][N]) where they are needed (D3Src<true>: no
+// tensor is written to memory).
+template <bool TENSOR>
+struct D3Src;
+
+template <>
+struct D3Src<false> {
+    const u64* d3 = nullptr;
+    __host__ __device__ D3Src() {}
+    __host__ __device__ D3Src(const u64* t) : d3(t) {}
+    // component k, residue i (prime Q), coefficient j of ciphertext ct
+    __device__ __forceinline__ u64 get(int ct, int k, int L, int N, int i, int j, const PrimeC&) const
+    {
+        return d3[(((size_t)ct * 3 + k) * L + i) * N + j];
+    }
+};
+
+template <>
+struct D3Src<true> {
+    const u64* a = nullptr;
+    const u64* b = nullptr;
+    __host__ __device__ D3Src() {}
+    __host__ __device__ D3Src(const u64* a_, const u64* b_) : a(a_), b(b_) {}
+    __device__ __forceinline__ u64 get(int ct, int k, int L, int N, int i, int j, const PrimeC& Q) const
+    {
+        const size_t o0 = (((size_t)ct * 2) * L + i) * N + j, o1 = o0 + (size_t)L * N;
+        if (k == 0) return mul_mod(a[o0], b[o0], Q);
+        if (k == 2) return mul_mod(a[o1], b[o1], Q);
+        return add_mod(mul_mod(a[o0], b[o1], Q), mul_mod(a[o1], b[o0], Q), Q.q);
+    }
+};
+
 // step 1: digits D_j = INTT(d2_j) in [0, q_j)
-struct OpDigitsInv {
+template <bool TENSOR>
+struct OpDigitsInvT {
     static const char* family() { return "keyswitch_intt"; }
-    const u64* d3;      // [n][3][L][N]
+    D3Src<TENSOR> d3;   // [n][3][L][N]
     u64* D;             // [n][L][N]
     int n, L, N;
     __host__ __device__ int count() const { return n * L; }
     __host__ __device__ int nsub(int) const { return 1; }
     __device__ int prime(int p, int) const { return p % L; }
     __device__ bool direct(int, int) const { return false; }
-    __device__ u64 load(int p, int, int j, const PrimeC&) const
+    __device__ u64 load(int p, int, int j, const PrimeC& Q) const
     {
         const int ct = p / L, r = p % L;
-        return d3[(((size_t)ct * 3 + 2) * L + r) * N + j];
+        return d3.get(ct, 2, L, N, r, j, Q);
     }
     struct Pre {};
     __device__ Pre pre(int, int, int) const { return {}; }
     __device__ void store(int p, int, int j, u64 v, const Pre&, const PrimeC&) const { D[(size_t)p * N + j] = v; }
 };
+using OpDigitsInv = OpDigitsInvT<false>;
 
 // digits u < L whose prime q_u exceeds 4 q_t for some target t in {q_0..q_{L-1}, P}:
 // their lift into q_t must be reduced before the forward transform, which
@@ -102,11 +138,12 @@ inline uint32_t modup_red_mask(const fhe_ctx* c, uint32_t L)
 // step 2: per (ct, target t in 0..L, t = L meaning P): for every digit u,
 // NTT(D_u mod q_t) * ksk_u[k][t], accumulated over u into acc[ct][k][t].
 // Keys carry their Shoup quotients, so each key product is one Shoup product.
-struct OpModUpMac {
+template <bool TENSOR>
+struct OpModUpMacT {
     static const char* family() { return "keyswitch_modup_mac"; }
     static constexpr bool kLazyStore = true;     // the key products reduce any v < 2^64
     static constexpr bool kKeySwitchMac = true;  // scheduled separately (heavy epilogue)
-    const u64* d3;
+    D3Src<TENSOR> d3;
     const u64* D;
     const ulonglong2* ksk;  // [L_top][2][L_top+1][N] (k, floor(k 2^64 / q))
     u64* acc;               // [n][2][L+1][N]
@@ -149,13 +186,14 @@ struct OpModUpMac {
     __device__ void store(int p, int u, int j, u64 v, const Pre& pr, const PrimeC& Q) const
     {
         const int ct = p / (L + 1), t = p % (L + 1);
-        if (t == u) v = d3[(((size_t)ct * 3 + 2) * L + t) * N + j];   // direct: NTT(d2_t) is d2_t
+        if (t == u) v = d3.get(ct, 2, L, N, t, j, Q);                 // direct: NTT(d2_t) is d2_t
         const u64 p0 = mul_shoup(v, pr.k0.x, pr.k0.y, Q.q);
         const u64 p1 = mul_shoup(v, pr.k1.x, pr.k1.y, Q.q);
         acc[(((size_t)ct * 2 + 0) * (L + 1) + t) * N + j] = u == 0 ? p0 : add_mod(pr.a0, p0, Q.q);
         acc[(((size_t)ct * 2 + 1) * (L + 1) + t) * N + j] = u == 0 ? p1 : add_mod(pr.a1, p1, Q.q);
     }
 };
+using OpModUpMac = OpModUpMacT<false>;
 
 // step 3: INTT of the P residue of both accumulators
 struct OpAccPInv {
@@ -223,9 +261,10 @@ struct OpModDown {
 // there, but each output row needs one forward transform instead of two.
 
 // step 4': INTT of row L-1 of the relinearised ciphertext, per (ct, comp)
-struct OpKsRowInv {
+template <bool TENSOR>
+struct OpKsRowInvT {
     static const char* family() { return "keyswitch_rescale_intt"; }
-    const u64* d3;      // [n][3][L][N]
+    D3Src<TENSOR> d3;   // [n][3][L][N]
     const u64* acc;     // [n][2][L+1][N]
     const u64* Vp;      // [n][2][N] coefficient form mod P
     u64* V;             // [n][2][N] coefficient form mod q_{L-1}
@@ -239,7 +278,7 @@ struct OpKsRowInv {
     __device__ u64 load(int p, int, int j, const PrimeC& Q) const
     {
         const int ct = p >> 1, k = p & 1, i = L - 1;
-        u64 s = d3[(((size_t)ct * 3 + k) * L + i) * N + j];
+        u64 s = d3.get(ct, k, L, N, i, j, Q);
         s = add_mod(s, mul_shoup(acc[((size_t)p * (L + 1) + i) * N + j], pinv, pinvs, Q.q), Q.q);
         if (ex.x2) s = add_mod(s, mul_mod(ex.x2[((size_t)p * L + i) * N + j], ex.c2[i], Q), Q.q);
         if (ex.x) s = add_mod(s, mul_mod(ex.x[((size_t)p * ex.Lx + i) * N + j], ex.c1[i], Q), Q.q);
@@ -253,12 +292,15 @@ struct OpKsRowInv {
         V[(size_t)p * N + j] = sub_mod(v, vq, Q.q);
     }
 };
+using OpKsRowInv = OpKsRowInvT<false>;
 
 // step 5': the merged forward transform of both corrections into q_i, i < L-1,
-// per (ct, comp, i), and the rescaled output row
-struct OpKsDivFwd {
+// per (ct, comp, i), and the rescaled output row.  TENSOR: the tensor product
+// is recomputed from its factors (the epilogue then loads the factors)
+template <bool TENSOR>
+struct OpKsDivFwdT {
     static const char* family() { return "keyswitch_rescale_ntt"; }
-    const u64* d3;      // [n][3][L][N]
+    D3Src<TENSOR> d3;   // [n][3][L][N] (TENSOR: the factors)
     const u64* acc;     // [n][2][L+1][N]
     const u64* Vp;      // [n][2][N] mod P
     const u64* V;       // [n][2][N] mod q_{L-1}
@@ -279,29 +321,45 @@ struct OpKsDivFwd {
         const u64 b = centred_to(V[(size_t)poly * N + j], dq.p, dq.p_half, dq.pmod[i], Q);
         return add_mod(mul_shoup(a, dp.inv[i], dp.invs[i], Q.q), b, Q.q);
     }
-    struct Pre { u64 d, a, x2, x; };
+    // d the stored component (or, TENSOR, the factors: d = a0 (b0 | b1), x2 = a1, x = b0)
+    struct Pre { u64 d, a, x2, x, f; };
     __device__ Pre pre(int p, int, int j) const
     {
         const int poly = p / (L - 1), i = p % (L - 1);
         const int ct = poly >> 1, k = poly & 1;
         Pre r;
-        r.d = d3[(((size_t)ct * 3 + k) * L + i) * N + j];
         r.a = acc[((size_t)poly * (L + 1) + i) * N + j];
-        r.x2 = ex.x2 ? ex.x2[((size_t)poly * L + i) * N + j] : 0;
-        r.x = ex.x ? ex.x[((size_t)poly * ex.Lx + i) * N + j] : 0;
+        if constexpr (TENSOR) {
+            const size_t o0 = (((size_t)ct * 2) * L + i) * N + j, o1 = o0 + (size_t)L * N;
+            r.d = d3.a[o0];
+            r.f = d3.b[k ? o1 : o0];
+            r.x2 = k ? d3.a[o1] : 0;
+            r.x = k ? d3.b[o0] : 0;
+        } else {
+            r.d = d3.d3[(((size_t)ct * 3 + k) * L + i) * N + j];
+            r.f = 0;
+            r.x2 = ex.x2 ? ex.x2[((size_t)poly * L + i) * N + j] : 0;
+            r.x = ex.x ? ex.x[((size_t)poly * ex.Lx + i) * N + j] : 0;
+        }
         return r;
     }
     __device__ void store(int p, int, int j, u64 v, const Pre& pr, const PrimeC& Q) const
     {
         const int poly = p / (L - 1), i = p % (L - 1);
-        u64 s = add_mod(pr.d, mul_shoup(pr.a, dp.inv[i], dp.invs[i], Q.q), Q.q);
-        if (ex.x2) s = add_mod(s, mul_mod(pr.x2, ex.c2[i], Q), Q.q);
-        if (ex.x) s = add_mod(s, mul_mod(pr.x, ex.c1[i], Q), Q.q);
+        u64 d = pr.d;
+        if constexpr (TENSOR) {
+            d = mul_mod(pr.d, pr.f, Q);                          // a0 b0, or a0 b1
+            if (poly & 1) d = add_mod(d, mul_mod(pr.x2, pr.x, Q), Q.q);   // + a1 b0
+        }
+        u64 s = add_mod(d, mul_shoup(pr.a, dp.inv[i], dp.invs[i], Q.q), Q.q);
+        if (!TENSOR && ex.x2) s = add_mod(s, mul_mod(pr.x2, ex.c2[i], Q), Q.q);
+        if (!TENSOR && ex.x) s = add_mod(s, mul_mod(pr.x, ex.c1[i], Q), Q.q);
         u64 r = mul_shoup(sub_mod(s, v, Q.q), dq.inv[i], dq.invs[i], Q.q);
         if (addc && (poly & 1) == 0) r = add_mod(r, addc[(size_t)(poly >> 1) * addc_stride + i], Q.q);
         out[((size_t)poly * (L - 1) + i) * N + j] = r;
     }
 };
+using OpKsDivFwd = OpKsDivFwdT<false>;
 
 // Grouped (MultiOp) launches of the forward steps, each compiled in a
 // translation unit of its own (k_groups_ks.cu, k_groups_fwd.cu) so the build

@@ -512,7 +512,7 @@ def test_grouped_rotation_bit_exact_per_group():
     net.close()
 
 
-# ---------------------------------------------------------------- uneven levels, one launch per step
+# ---------------------------------------------------------------- uneven levels, one persistent launch
 def test_mul_relin_rescale_levels_matches_per_batch_and_oracle():
     g, o = pair(1024, BITS9)
     rng = np.random.default_rng(42)
@@ -529,16 +529,78 @@ def test_mul_relin_rescale_levels_matches_per_batch_and_oracle():
         batches.append((ta, tb, out, L))
         ref_outs.append(ref)
         keep[L] = (A, B)
-    g.mul_relin_rescale_levels(batches)
     torch.cuda.synchronize()
+    before = fhe.launch_count()
+    g.mul_relin_rescale_levels(batches)
+    g.sync()
+    assert fhe.launch_count() - before == 1           # one persistent launch for every level
     for (ta, tb, out, L), ref in zip(batches, ref_outs):
         assert torch.equal(out, ref), L
-    # one level against the oracle directly
-    L = 5
-    A, B = keep[L]
-    got = download(g, batches[L - 2][2], L - 1)
-    want = o.rescale(o.relinearise(o.tensor(ckks.Ciphertext(A[0], L, 1.0), ckks.Ciphertext(B[0], L, 1.0)))).c
-    assert np.array_equal(got[0], want)
+    # every level against the oracle directly
+    for L in range(2, 9):
+        A, B = keep[L]
+        got = download(g, batches[L - 2][2], L - 1)
+        for k in range(len(A)):
+            want = o.rescale(o.relinearise(o.tensor(ckks.Ciphertext(A[k], L, 1.0),
+                                                    ckks.Ciphertext(B[k], L, 1.0)))).c
+            assert np.array_equal(got[k], want), (L, k)
+
+
+def test_mul_relin_rescale_levels_persistent_equals_separate_launches(monkeypatch):
+    """The persistent launch and the six-launch form (FHE_PERSISTENT=0) give
+    the same words, on a batch large enough that many units wait for their
+    ciphertext's previous step."""
+    g, o = pair(4096, BITS9)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(9)
+    batches = []
+    for L, n in ((2, 40), (5, 33), (8, 21)):
+        def rnd():
+            t = torch.empty((n, 2, L, g.N), dtype=torch.int64, device="cuda")
+            for r in range(L):
+                t[:, :, r, :] = torch.randint(0, g.primes[r], (n, 2, g.N), device="cuda", generator=gen)
+            return t
+        batches.append((rnd(), rnd(), g.empty_ct(n, L - 1), L))
+    g.mul_relin_rescale_levels(batches)
+    g.sync()
+    want = [b[2].clone() for b in batches]
+    monkeypatch.setenv("FHE_PERSISTENT", "0")
+    for b in batches:
+        b[2].zero_()
+    before = fhe.launch_count()
+    g.mul_relin_rescale_levels(batches)
+    g.sync()
+    assert fhe.launch_count() - before == 6
+    for b, w in zip(batches, want):
+        assert torch.equal(b[2], w), b[3]
+
+
+def test_persistent_wait_that_runs_out_reports_timeout():
+    """The persistent launch's waits are bounded: with the first step's
+    completions withheld (test hook) the second step's waits run out, the
+    launch abandons its remaining units and the context reports
+    FHE_ETIMEOUT; the next call gives the right words again."""
+    g, o = pair(1024, BITS9)
+    rng = np.random.default_rng(44)
+    batches = []
+    for L in (4, 7):
+        A = [rand_ct(o, L, rng) for _ in range(3)]
+        B = [rand_ct(o, L, rng) for _ in range(3)]
+        batches.append((upload(g, A, L), upload(g, B, L), g.empty_ct(3, L - 1), L))
+    g.mul_relin_rescale_levels(batches)
+    g.sync()
+    want = [b[2].clone() for b in batches]
+    g.inject_fault(2)
+    with pytest.raises(fhe.FheError) as e:
+        g.mul_relin_rescale_levels(batches)
+        g.sync()
+    assert e.value.code == -6
+    for b in batches:
+        b[2].zero_()
+    g.mul_relin_rescale_levels(batches)
+    g.sync()
+    for b, w in zip(batches, want):
+        assert torch.equal(b[2], w)
 
 
 def test_mul_relin_rescale_levels_in_cuda_graph():
