@@ -114,6 +114,9 @@ struct fhe_node_const {
     u64* c2 = nullptr;
     u64* c1 = nullptr;
     u64* c0 = nullptr;
+    u64* c3s = nullptr;        // POLY: Shoup quotients of c3, c2, c1
+    u64* c2s = nullptr;
+    u64* c1s = nullptr;
     u64* cpow = nullptr;       // POLY degree > 3: residues of C_1..C_d at l* primes, then C_0 ([d + 1][l*])
     u64* pt = nullptr;         // CONV_PACKED: mask-and-kernel plaintexts [F][k^2][L][N] (NTT form)
     u64* bias_pt = nullptr;    // CONV_PACKED: bias plaintexts [F][L-1][N]
@@ -216,8 +219,10 @@ void k_gather_slots(const double* src, const int64_t* index, size_t total, doubl
 struct KsExtra {
     const u64* x2;      // [n][2][L][N] (level of the relinearisation) or null
     const u64* c2;      // [L] device residues
+    const u64* c2s;     // their Shoup quotients
     const u64* x;       // [n][2][Lx][N], its first L residues used, or null
     const u64* c1;      // [L] device residues
+    const u64* c1s;     // their Shoup quotients
     int Lx;
 };
 size_t relin_rescale_scratch_bytes(const fhe_ctx* c, uint32_t n_ct, uint32_t L);
@@ -228,7 +233,8 @@ void k_relin_rescale(const fhe_ctx* c, const u64* d3, u64* out, uint32_t n_ct, u
 // addc[ct * addc_stride + i]) added to comp 0 of the result
 size_t rescale_scratch_bytes(const fhe_ctx* c, uint32_t n_ct, uint32_t comps);
 void k_rescale(const fhe_ctx* c, const u64* in, u64* out, uint32_t n_ct, uint32_t comps, uint32_t L,
-               const u64* addc, uint32_t addc_stride, void* scratch, cudaStream_t st, const u64* mulc = nullptr);
+               const u64* addc, uint32_t addc_stride, void* scratch, cudaStream_t st, const u64* mulc = nullptr,
+               const u64* mulcs = nullptr);
 // polynomial activation: t1 (+)= x2 * c2 + (first L1 residues of x) * c1
 // (accumulate: add to t1; else overwrite it)
 void k_poly_combine(const fhe_ctx* c, u64* t1, const u64* x2, const u64* x, uint32_t n_ct, uint32_t L1, uint32_t Lx,

@@ -146,6 +146,7 @@ struct Exec {
             return off;
         };
         size_t o_rp = 0, o_tr = 0, o_col = 0, o_W = 0, o_b = 0, o_c3 = 0, o_c2 = 0, o_c1 = 0, o_c0 = 0;
+        size_t o_c3s = 0, o_c2s = 0, o_c1s = 0;
         size_t o_tcW[2] = {0, 0}, o_tcr[2] = {0, 0};
         uint32_t tc_tiles[2] = {0, 0}, tc_K = 0;
         uint64_t tc_mask[2] = {0, 0};
@@ -270,10 +271,19 @@ struct Exec {
                 r1[r] = mod_signed(k.C1, c->primes[r]);
                 r0[r] = mod_signed(k.C0, c->primes[r]);
             }
+            std::vector<u64> r3s(L), r2s(L), r1s(L);              // Shoup quotients of C3..C1
+            for (uint32_t r = 0; r < L; ++r) {
+                r3s[r] = shoup(r3[r], c->primes[r]);
+                r2s[r] = shoup(r2[r], c->primes[r]);
+                r1s[r] = shoup(r1[r], c->primes[r]);
+            }
             o_c3 = put(r3.data(), r3.size() * 8);
             o_c2 = put(r2.data(), r2.size() * 8);
             o_c1 = put(r1.data(), r1.size() * 8);
             o_c0 = put(r0.data(), r0.size() * 8);
+            o_c3s = put(r3s.data(), r3s.size() * 8);
+            o_c2s = put(r2s.data(), r2s.size() * 8);
+            o_c1s = put(r1s.data(), r1s.size() * 8);
         } else {
             return nullptr;
         }
@@ -309,6 +319,9 @@ struct Exec {
             nc.c2 = (u64*)(b + o_c2);
             nc.c1 = (u64*)(b + o_c1);
             nc.c0 = (u64*)(b + o_c0);
+            nc.c3s = (u64*)(b + o_c3s);
+            nc.c2s = (u64*)(b + o_c2s);
+            nc.c1s = (u64*)(b + o_c1s);
         }
         return &nc;
     }
@@ -623,10 +636,10 @@ struct Exec {
             if (!kc) return y;
             k_tensor(c, x.p, x.p, T3, n, L, st);
             k_relin_rescale(c, T3, x2, n, L, rs, st);                         // x2 = rescale(relin(x (x) x))
-            k_rescale(c, x.p, w, n, 2, L, nullptr, 0, ss, st, kc->c3);        // rescale(x * C3)
+            k_rescale(c, x.p, w, n, 2, L, nullptr, 0, ss, st, kc->c3, kc->c3s);   // rescale(x * C3)
             k_tensor(c, x2, w, T3b, n, L - 1, st);
             // y = rescale(relin(x2 (x) w) + x2 C2 + drop(x) C1) + C0
-            const KsExtra ex{x2, kc->c2, x.p, kc->c1, (int)L};
+            const KsExtra ex{x2, kc->c2, kc->c2s, x.p, kc->c1, kc->c1s, (int)L};
             k_relin_rescale(c, T3b, out, n, L - 1, rs, st, &ex, kc->c0, 0);
         }
         y.p = out;
@@ -649,7 +662,7 @@ struct Exec {
         if (!dry && ok()) {
             fhe_node_const* kc = node_const(i, L, x.scale);
             if (!kc) return y;
-            k_rescale(c, x.p, out, n, 2, L, kc->c0, 0, ss, st, kc->c1);
+            k_rescale(c, x.p, out, n, 2, L, kc->c0, 0, ss, st, kc->c1, kc->c1s);
         }
         y.p = out;
         y.n = n;

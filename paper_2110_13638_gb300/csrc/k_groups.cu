@@ -66,7 +66,7 @@ void k_mul_relin_rescale_groups(const fhe_ctx* c, const LevelBatch* g, int ng, v
     m1.ng = m2.ng = m3.ng = m4.ng = m5.ng = tg.ng = ng;
     m1.pre_[0] = m2.pre_[0] = m3.pre_[0] = m4.pre_[0] = m5.pre_[0] = 0;
     tg.start[0] = 0;
-    const KsExtra none{nullptr, nullptr, nullptr, nullptr, 0};
+    const KsExtra none{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0};
     for (int k = 0; k < ng; ++k) {
         const int n = (int)g[k].n, L = (int)g[k].L;
         u64* t3 = (u64*)ar.take((size_t)n * 3 * L * N * 8);
@@ -80,7 +80,8 @@ void k_mul_relin_rescale_groups(const fhe_ctx* c, const LevelBatch* g, int ng, v
         tg.L[k] = L;
         tg.start[k + 1] = tg.start[k] + (unsigned long long)n * L * N;
         m1.ops[k] = OpDigitsInv{t3, D, n, L, (int)N};
-        m2.ops[k] = OpModUpMac{t3, D, c->d_ksk, acc, n, L, (int)N, (int)c->L_top, modup_red_mask(c, (uint32_t)L)};
+        m2.ops[k] = OpModUpMac{t3, D, c->d_ksk, acc, n, L, (int)N, (int)c->L_top, modup_red_mask(c, (uint32_t)L),
+                               modup_lazy_mask(c, (uint32_t)L)};
         m3.ops[k] = OpAccPInv{acc, Vp, n, L, (int)N, (int)c->L_top};
         m4.ops[k] = make_ks_row_inv(c, t3, acc, Vp, V, n, L, none);
         m5.ops[k] = make_ks_div_fwd(c, t3, acc, Vp, V, g[k].out, n, L, none, nullptr, 0);

@@ -178,7 +178,7 @@ int k_mul_relin_rescale_persistent(const fhe_ctx* c, const LevelBatch* g, int ng
         A.wait_polls = 1024;
     }
     unsigned int* cnt = ctl + 2;
-    const KsExtra none{nullptr, nullptr, nullptr, nullptr, 0};
+    const KsExtra none{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0};
     for (int ph = 0; ph < kPhases; ++ph) A.start[ph][0] = 0;
     for (int k = 0; k < ng; ++k) {
         const int n = (int)g[k].n, L = (int)g[k].L;
@@ -193,7 +193,8 @@ int k_mul_relin_rescale_persistent(const fhe_ctx* c, const LevelBatch* g, int ng
         G.cnt = cnt;
         cnt += (size_t)n * 4;
         G.p1 = OpDigitsInvT<true>{src, D, n, L, (int)N};
-        G.p2 = OpModUpMacT<true>{src, D, c->d_ksk, acc, n, L, (int)N, (int)c->L_top, modup_red_mask(c, (uint32_t)L)};
+        G.p2 = OpModUpMacT<true>{src, D, c->d_ksk, acc, n, L, (int)N, (int)c->L_top, modup_red_mask(c, (uint32_t)L),
+                               modup_lazy_mask(c, (uint32_t)L)};
         G.p3 = OpAccPInv{acc, Vp, n, L, (int)N, (int)c->L_top};
         const OpKsRowInv r = make_ks_row_inv(c, nullptr, acc, Vp, V, n, L, none);
         OpKsRowInvT<true>& p4 = G.p4;

@@ -23,7 +23,8 @@ void k_relin(const fhe_ctx* c, const u64* d3, u64* out2, uint32_t n_ct, uint32_t
 
     OpDigitsInv s1{d3, D, (int)n_ct, (int)L, (int)N};
     launch_ntt<true>(c, s1, st, single_pass);
-    OpModUpMac s2{d3, D, key ? key : c->d_ksk, acc, (int)n_ct, (int)L, (int)N, (int)c->L_top, modup_red_mask(c, L)};
+    OpModUpMac s2{d3, D, key ? key : c->d_ksk, acc, (int)n_ct, (int)L, (int)N, (int)c->L_top, modup_red_mask(c, L),
+                  modup_lazy_mask(c, L)};
     launch_ntt<false>(c, s2, st, single_pass);
     OpAccPInv s3{acc, Vp, (int)n_ct, (int)L, (int)N, (int)c->L_top};
     launch_ntt<true>(c, s3, st, single_pass);
@@ -100,12 +101,13 @@ void k_relin_rescale(const fhe_ctx* c, const u64* d3, u64* out, uint32_t n_ct, u
     u64* acc = (u64*)ar.take((size_t)n_ct * 2 * (L + 1) * N * 8);
     u64* Vp = (u64*)ar.take((size_t)n_ct * 2 * N * 8);
     u64* V = (u64*)ar.take((size_t)n_ct * 2 * N * 8);
-    const KsExtra none{nullptr, nullptr, nullptr, nullptr, 0};
+    const KsExtra none{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0};
     const KsExtra& e = ex ? *ex : none;
 
     OpDigitsInv s1{d3, D, (int)n_ct, (int)L, (int)N};
     launch_ntt<true>(c, s1, st);
-    OpModUpMac s2{d3, D, c->d_ksk, acc, (int)n_ct, (int)L, (int)N, (int)c->L_top, modup_red_mask(c, L)};
+    OpModUpMac s2{d3, D, c->d_ksk, acc, (int)n_ct, (int)L, (int)N, (int)c->L_top, modup_red_mask(c, L),
+                  modup_lazy_mask(c, L)};
     launch_ntt<false>(c, s2, st);
     OpAccPInv s3{acc, Vp, (int)n_ct, (int)L, (int)N, (int)c->L_top};
     launch_ntt<true>(c, s3, st);
@@ -118,7 +120,8 @@ void k_relin_rescale(const fhe_ctx* c, const u64* d3, u64* out, uint32_t n_ct, u
 void k_modup_mac_step(const fhe_ctx* c, const u64* d3, const u64* D, const ulonglong2* ksk, u64* acc, uint32_t n_ct,
                       uint32_t L, cudaStream_t st)
 {
-    OpModUpMac op{d3, D, ksk, acc, (int)n_ct, (int)L, (int)c->N, (int)L, modup_red_mask(c, L)};
+    OpModUpMac op{d3, D, ksk, acc, (int)n_ct, (int)L, (int)c->N, (int)L, modup_red_mask(c, L),
+                  modup_lazy_mask(c, L)};
     launch_ntt<false>(c, op, st);
 }
 

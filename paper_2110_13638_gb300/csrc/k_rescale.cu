@@ -9,7 +9,7 @@ size_t rescale_scratch_bytes(const fhe_ctx* c, uint32_t n_ct, uint32_t comps)
 }
 
 void k_rescale(const fhe_ctx* c, const u64* in, u64* out, uint32_t n_ct, uint32_t comps, uint32_t L, const u64* addc,
-               uint32_t addc_stride, void* scratch, cudaStream_t st, const u64* mulc)
+               uint32_t addc_stride, void* scratch, cudaStream_t st, const u64* mulc, const u64* mulcs)
 {
     if (n_ct == 0) return;
     u64* V = (u64*)scratch;
@@ -22,6 +22,7 @@ void k_rescale(const fhe_ctx* c, const u64* in, u64* out, uint32_t n_ct, uint32_
     a.N = (int)c->N;
     a.pidx = (int)L - 1;
     a.mulc = mulc;
+    a.mulcs = mulcs;
     launch_ntt<true>(c, a, st);
     OpDivFwd b;
     b.in = in;
@@ -36,6 +37,7 @@ void k_rescale(const fhe_ctx* c, const u64* in, u64* out, uint32_t n_ct, uint32_
     b.N = (int)c->N;
     b.d = make_divc(c, L - 1, L - 1);
     b.mulc = mulc;
+    b.mulcs = mulcs;
     launch_ntt<false>(c, b, st);
 }
 

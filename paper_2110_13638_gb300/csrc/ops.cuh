@@ -14,6 +14,7 @@ struct OpTakeRowInv {
     u64* V;
     int n, L, row, N, pidx;
     const u64* mulc;    // optional: the input is first multiplied by this per-residue constant
+    const u64* mulcs;   // its Shoup quotients (with mulc)
     __host__ __device__ int count() const { return n; }
     __host__ __device__ int nsub(int) const { return 1; }
     __device__ int prime(int, int) const { return pidx; }
@@ -21,7 +22,7 @@ struct OpTakeRowInv {
     __device__ u64 load(int p, int, int j, const PrimeC& P) const
     {
         const u64 x = in[((size_t)p * L + row) * N + j];
-        return mulc ? mul_mod(x, mulc[row], P) : x;
+        return mulc ? mul_shoup(x, mulc[row], mulcs[row], P.q) : x;
     }
     struct Pre {};
     __device__ Pre pre(int, int, int) const { return {}; }
@@ -37,6 +38,7 @@ struct OpDivFwd {
     const u64* addc;    // optional: residues of a constant added to comp 0, [n_ct][addc_stride]
     int n_poly, comps, L_in, L_out, N, addc_stride;
     const u64* mulc;    // optional: the input is first multiplied by this per-residue constant
+    const u64* mulcs;   // its Shoup quotients (with mulc)
     DivC d;
     __host__ __device__ int count() const { return n_poly * L_out; }
     __host__ __device__ int nsub(int) const { return 1; }
@@ -59,7 +61,7 @@ struct OpDivFwd {
     __device__ void store(int p, int, int j, u64 v, const Pre& pr, const PrimeC& Q) const
     {
         const int poly = p / L_out, i = p % L_out;
-        const u64 x = mulc ? mul_mod(pr.x, mulc[i], Q) : pr.x;
+        const u64 x = mulc ? mul_shoup(pr.x, mulc[i], mulcs[i], Q.q) : pr.x;
         const u64 r = mul_shoup(sub_mod(x, v, Q.q), d.inv[i], d.invs[i], Q.q);
         out[((size_t)poly * L_out + i) * N + j] = add_mod(r, pr.c, Q.q);
     }
@@ -135,6 +137,18 @@ inline uint32_t modup_red_mask(const fhe_ctx* c, uint32_t L)
     return m;
 }
 
+// targets t in 0..L (t = L: the special prime) whose accumulators may stay
+// unreduced: L lazy Shoup products below 2 q_t each sum below 2^64
+inline uint64_t modup_lazy_mask(const fhe_ctx* c, uint32_t L)
+{
+    uint64_t m = 0;
+    for (uint32_t t = 0; t <= L; ++t) {
+        const u64 q = c->primes[t == L ? c->L_top : t];
+        if (q < (1ull << 63) / L) m |= 1ull << t;
+    }
+    return m;
+}
+
 // step 2: per (ct, target t in 0..L, t = L meaning P): for every digit u,
 // NTT(D_u mod q_t) * ksk_u[k][t], accumulated over u into acc[ct][k][t].
 // Keys carry their Shoup quotients, so each key product is one Shoup product.
@@ -150,6 +164,8 @@ struct OpModUpMacT {
     int n, L, N, Ltop;
     uint32_t red_mask;      // digits u whose prime exceeds 4 q_t for some target t:
                             // only these need reducing before the forward transform
+    uint64_t lazy_mask;     // targets t (L = P) whose sums are kept unreduced: the L key
+                            // products, each below 2 q_t, then sum below 2 L q_t < 2^64
     __host__ __device__ int count() const { return n * (L + 1); }
     __host__ __device__ int nsub(int) const { return L; }
     __device__ int prime(int p, int) const
@@ -187,10 +203,19 @@ struct OpModUpMacT {
     {
         const int ct = p / (L + 1), t = p % (L + 1);
         if (t == u) v = d3.get(ct, 2, L, N, t, j, Q);                 // direct: NTT(d2_t) is d2_t
-        const u64 p0 = mul_shoup(v, pr.k0.x, pr.k0.y, Q.q);
-        const u64 p1 = mul_shoup(v, pr.k1.x, pr.k1.y, Q.q);
-        acc[(((size_t)ct * 2 + 0) * (L + 1) + t) * N + j] = u == 0 ? p0 : add_mod(pr.a0, p0, Q.q);
-        acc[(((size_t)ct * 2 + 1) * (L + 1) + t) * N + j] = u == 0 ? p1 : add_mod(pr.a1, p1, Q.q);
+        u64* a0 = acc + (((size_t)ct * 2 + 0) * (L + 1) + t) * N + j;
+        u64* a1 = acc + (((size_t)ct * 2 + 1) * (L + 1) + t) * N + j;
+        if ((lazy_mask >> t) & 1u) {                                   // block-uniform
+            const u64 p0 = mul_shoup_lazy(v, pr.k0.x, pr.k0.y, Q.q);
+            const u64 p1 = mul_shoup_lazy(v, pr.k1.x, pr.k1.y, Q.q);
+            *a0 = u == 0 ? p0 : pr.a0 + p0;
+            *a1 = u == 0 ? p1 : pr.a1 + p1;
+        } else {
+            const u64 p0 = mul_shoup(v, pr.k0.x, pr.k0.y, Q.q);
+            const u64 p1 = mul_shoup(v, pr.k1.x, pr.k1.y, Q.q);
+            *a0 = u == 0 ? p0 : add_mod(pr.a0, p0, Q.q);
+            *a1 = u == 0 ? p1 : add_mod(pr.a1, p1, Q.q);
+        }
     }
 };
 using OpModUpMac = OpModUpMacT<false>;
@@ -205,7 +230,10 @@ struct OpAccPInv {
     __host__ __device__ int nsub(int) const { return 1; }
     __device__ int prime(int, int) const { return Ltop; }
     __device__ bool direct(int, int) const { return false; }
-    __device__ u64 load(int p, int, int j, const PrimeC&) const { return acc[((size_t)p * (L + 1) + L) * N + j]; }
+    __device__ u64 load(int p, int, int j, const PrimeC& Q) const
+    {
+        return reduce64(acc[((size_t)p * (L + 1) + L) * N + j], Q);   // the sum may be unreduced
+    }
     struct Pre {};
     __device__ Pre pre(int, int, int) const { return {}; }
     __device__ void store(int p, int, int j, u64 v, const Pre&, const PrimeC&) const { Vp[(size_t)p * N + j] = v; }
@@ -243,7 +271,7 @@ struct OpModDown {
     {
         const int poly = p / L, t = p % L;
         const int ct = poly >> 1, k = poly & 1;
-        const u64 ks = mul_shoup(sub_mod(pr.a, v, Q.q), d.inv[t], d.invs[t], Q.q);
+        const u64 ks = mul_shoup(sub_mod(reduce64(pr.a, Q), v, Q.q), d.inv[t], d.invs[t], Q.q);
         out[(((size_t)ct * 2 + k) * L + t) * N + j] = add_mod(pr.dk, ks, Q.q);
     }
 };
@@ -280,8 +308,8 @@ struct OpKsRowInvT {
         const int ct = p >> 1, k = p & 1, i = L - 1;
         u64 s = d3.get(ct, k, L, N, i, j, Q);
         s = add_mod(s, mul_shoup(acc[((size_t)p * (L + 1) + i) * N + j], pinv, pinvs, Q.q), Q.q);
-        if (ex.x2) s = add_mod(s, mul_mod(ex.x2[((size_t)p * L + i) * N + j], ex.c2[i], Q), Q.q);
-        if (ex.x) s = add_mod(s, mul_mod(ex.x[((size_t)p * ex.Lx + i) * N + j], ex.c1[i], Q), Q.q);
+        if (ex.x2) s = add_mod(s, mul_shoup(ex.x2[((size_t)p * L + i) * N + j], ex.c2[i], ex.c2s[i], Q.q), Q.q);
+        if (ex.x) s = add_mod(s, mul_shoup(ex.x[((size_t)p * ex.Lx + i) * N + j], ex.c1[i], ex.c1s[i], Q.q), Q.q);
         return s;
     }
     struct Pre { u64 v; };
@@ -352,8 +380,8 @@ struct OpKsDivFwdT {
             if (poly & 1) d = add_mod(d, mul_mod(pr.x2, pr.x, Q), Q.q);   // + a1 b0
         }
         u64 s = add_mod(d, mul_shoup(pr.a, dp.inv[i], dp.invs[i], Q.q), Q.q);
-        if (!TENSOR && ex.x2) s = add_mod(s, mul_mod(pr.x2, ex.c2[i], Q), Q.q);
-        if (!TENSOR && ex.x) s = add_mod(s, mul_mod(pr.x, ex.c1[i], Q), Q.q);
+        if (!TENSOR && ex.x2) s = add_mod(s, mul_shoup(pr.x2, ex.c2[i], ex.c2s[i], Q.q), Q.q);
+        if (!TENSOR && ex.x) s = add_mod(s, mul_shoup(pr.x, ex.c1[i], ex.c1s[i], Q.q), Q.q);
         u64 r = mul_shoup(sub_mod(s, v, Q.q), dq.inv[i], dq.invs[i], Q.q);
         if (addc && (poly & 1) == 0) r = add_mod(r, addc[(size_t)(poly >> 1) * addc_stride + i], Q.q);
         out[((size_t)poly * (L - 1) + i) * N + j] = r;
