@@ -677,9 +677,12 @@ constexpr u64 kInvNoRedBound = 1ull << 46;
 // behind the group's loads and butterflies; put(R, j0, lsh, x, fetched).
 struct NoFetch {};
 
+// sh, goff (forward only): the pass works on one half of a larger transform
+// (k_ntt_half_io): its local stage s is global stage s + sh, and its local
+// group g is global group g + goff at the pass's first stage.
 template <bool INV, int K, bool RED, class Get, class Put, class Fetch>
 __device__ __forceinline__ void pass_io(int logN, int s0, const ulonglong2* __restrict__ tw, u64 q, u64 q2, int tid,
-                                        int nthr, Get& get, Put& put, Fetch& fetch)
+                                        int nthr, Get& get, Put& put, Fetch& fetch, int sh = 0, int goff = 0)
 {
     constexpr int R = 1 << K;
     const int N = 1 << logN;
@@ -696,7 +699,7 @@ __device__ __forceinline__ void pass_io(int logN, int s0, const ulonglong2* __re
 #pragma unroll
             for (int l = 0; l < K; ++l) {
                 const int h = R >> (l + 1);
-                const ulonglong2* twl = tw + (1 << (s0 + l)) + (g << l);
+                const ulonglong2* twl = tw + (1 << (s0 + l + sh)) + ((g + goff) << l);
 #pragma unroll
                 for (int m = 0; m < (1 << l); ++m) {
                     const ulonglong2 w = __ldg(&twl[m]);
@@ -738,14 +741,14 @@ __device__ __forceinline__ void pass_io(int logN, int s0, const ulonglong2* __re
 
 template <bool INV, int KMAX, bool RED, class Get, class Put, class Fetch>
 __device__ __forceinline__ void pass_io_k(int k, int logN, int s0, const ulonglong2* tw, u64 q, u64 q2, int tid, int nthr,
-                                          Get& get, Put& put, Fetch& fetch)
+                                          Get& get, Put& put, Fetch& fetch, int sh = 0, int goff = 0)
 {
     if constexpr (KMAX >= 1) {
         if (k == KMAX) {
-            pass_io<INV, KMAX, RED>(logN, s0, tw, q, q2, tid, nthr, get, put, fetch);
+            pass_io<INV, KMAX, RED>(logN, s0, tw, q, q2, tid, nthr, get, put, fetch, sh, goff);
             return;
         }
-        pass_io_k<INV, KMAX - 1, RED>(k, logN, s0, tw, q, q2, tid, nthr, get, put, fetch);
+        pass_io_k<INV, KMAX - 1, RED>(k, logN, s0, tw, q, q2, tid, nthr, get, put, fetch, sh, goff);
     }
 }
 
@@ -887,4 +890,132 @@ __global__ void __launch_bounds__(MAXT, 1) k_ntt_io(Op op, NttTables T)
 {
     extern __shared__ u64 sm[];
     for (int p = blockIdx.x; p < op.count(); p += gridDim.x) ntt_io_unit<INV, LOGR, MAXT>(op, T, p, sm);
+}
+
+// ---------------------------------------------------------------- half transforms
+// A forward transform split over two blocks, one per half of the output.  The
+// first stage pairs j with j + N/2; after it the halves [0, N/2) and
+// [N/2, N) are independent N/2-point problems that keep the full transform's
+// twiddles (local stage s is global stage s + 1, local group g of half h is
+// global group g + h 2^s).  Each block reads both halves of the input for
+// that first stage and keeps only its own outputs (the stage's twiddle
+// product is made by both blocks: 1/(2 log2 N) more multiplies), so a block
+// holds N/2 words of shared memory and two blocks share an SM: one block's
+// loads and epilogue overlap the other's butterflies.  The epilogue of each
+// half is independent (the key-switching digit transforms).
+template <int MAXT, class Op>
+__global__ void __launch_bounds__(MAXT, 2) k_ntt_half_io(Op op, NttTables T)
+{
+    constexpr int LOGR = 4;
+    extern __shared__ u64 sm[];
+    const int logN = T.logN;
+    const int N = 1 << logN, logNh = logN - 1, Nh = N >> 1;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int b = blockIdx.x; b < 2 * op.count(); b += gridDim.x) {
+        const int p = b >> 1, hh = b & 1;
+        const int jb = hh * Nh;                      // this half's first coefficient
+        const int ns = op.nsub(p);
+        for (int u = 0; u < ns; ++u) {
+            const int pi = op.prime(p, u);
+            const PrimeC P = T.pc[pi];
+            if (op.direct(p, u)) {
+                for (int j = tid; j < Nh; j += nthr) op.store(p, u, jb + j, 0, op.pre(p, u, jb + j), P);
+                __syncthreads();
+                continue;
+            }
+            const u64 q = P.q, q2 = 2 * q;
+            const bool wide = !cold_path<Op>::value && q < kFwdNoRedBound;  // block-uniform
+            const ulonglong2* tw = T.tw_fwd + (size_t)pi * N;
+            const ulonglong2 w1 = __ldg(&tw[1]);    // the first stage's twiddle
+            int s = 0;
+            bool first = true;
+            while (s < logNh) {
+                // radix-16 passes, but never a last pass of one stage (its
+                // epilogue would wait for its loads two elements at a time)
+                const int rem = logNh - s;
+                const int k = rem <= LOGR ? rem : (rem - LOGR == 1 ? LOGR - 1 : LOGR);
+                const bool last = s + k >= logNh;
+                const int goff = hh << s;
+                // first pass: global stage 0 for this half's outputs from both input halves
+                auto gload = [&](auto Rc, int j0, int lsh, u64* x) {
+                    constexpr int R = decltype(Rc)::value;
+                    u64 top[R], bot[R];
+#pragma unroll
+                    for (int i = 0; i < R; ++i) {
+                        top[i] = op.load(p, u, j0 + (i << lsh), P);
+                        bot[i] = op.load(p, u, Nh + j0 + (i << lsh), P);
+                    }
+#pragma unroll
+                    for (int i = 0; i < R; ++i) {
+                        u64 X = top[i];
+                        if (!wide) X = X >= q2 ? X - q2 : X;
+                        const u64 Tv = mul_shoup_lazy(bot[i], w1.x, w1.y, q);
+                        x[i] = hh ? X + q2 - Tv : X + Tv;
+                    }
+                };
+                auto gsm = [&](auto Rc, int j0, int lsh, u64* x) {
+                    constexpr int R = decltype(Rc)::value;
+#pragma unroll
+                    for (int i = 0; i < R; ++i) x[i] = sm[spad(j0 + (i << lsh))];
+                };
+                auto psm = [&](auto Rc, int j0, int lsh, u64* x, NoFetch) {
+                    constexpr int R = decltype(Rc)::value;
+#pragma unroll
+                    for (int i = 0; i < R; ++i) sm[spad(j0 + (i << lsh))] = x[i];
+                };
+                constexpr int EB = MAXT <= 512 ? kEpiBatchWide : kEpiBatch;
+                auto nofetch = [&](auto, int, int) { return NoFetch{}; };
+                auto efetch = [&](auto Rc, int j0, int lsh) {
+                    constexpr int R = decltype(Rc)::value;
+                    constexpr int PF = R < kEpiPrefetch<MAXT> ? R : kEpiPrefetch<MAXT>;
+                    if constexpr (PF == 0) {
+                        return NoFetch{};
+                    } else {
+                        PreBatch<typename Op::Pre, PF> f;
+#pragma unroll
+                        for (int i = 0; i < PF; ++i) f.v[i] = op.pre(p, u, jb + j0 + (i << lsh));
+                        return f;
+                    }
+                };
+                auto pepi = [&](auto Rc, int j0, int lsh, u64* x, const auto& f) {
+                    constexpr int R = decltype(Rc)::value;
+                    constexpr int PF = R < kEpiPrefetch<MAXT> ? R : kEpiPrefetch<MAXT>;
+                    constexpr int B = R < EB ? R : EB;
+                    auto out = [&](int i, const typename Op::Pre& pr) {
+                        op.store(p, u, jb + j0 + (i << lsh), wide ? fwd_out_wide<Op>(x[i], P) : fwd_out<Op>(x[i], q),
+                                 pr, P);
+                    };
+                    if constexpr (PF > 0) {
+#pragma unroll
+                        for (int i = 0; i < PF; ++i) out(i, f.v[i]);
+                    }
+#pragma unroll
+                    for (int i0 = PF; i0 < R; i0 += B) {
+                        typename Op::Pre pr[B];
+#pragma unroll
+                        for (int i = 0; i < B; ++i)
+                            if (i0 + i < R) pr[i] = op.pre(p, u, jb + j0 + ((i0 + i) << lsh));
+#pragma unroll
+                        for (int i = 0; i < B; ++i)
+                            if (i0 + i < R) out(i0 + i, pr[i]);
+                    }
+                };
+                auto run = [&](auto redc, auto& get, auto& put, auto& fetch) {
+                    pass_io_k<false, LOGR, decltype(redc)::value>(k, logNh, s, tw, q, q2, tid, nthr, get, put, fetch, 1,
+                                                                  goff);
+                };
+                auto run_rw = [&](auto& get, auto& put, auto& fetch) {
+                    if (wide) run(std::false_type{}, get, put, fetch);
+                    else run(std::true_type{}, get, put, fetch);
+                };
+                if (first && last) run_rw(gload, pepi, efetch);
+                else if (first) run_rw(gload, psm, nofetch);
+                else if (last) run_rw(gsm, pepi, efetch);
+                else run_rw(gsm, psm, nofetch);
+                __syncthreads();
+                first = false;
+                s += k;
+            }
+        }
+    }
 }

@@ -155,6 +155,20 @@ struct MultiOp {
     }
 };
 
+// forward transforms split over two blocks per residue polynomial (schedule 6,
+// key-switching digit transforms)
+template <class Op>
+static void launch_ntt_half(const fhe_ctx* c, const Op& op, int count, cudaStream_t st)
+{
+    const int N = (int)c->N;
+    const int thr = std::min(256, std::max(32, (N / 2) >> 4));
+    const size_t smem = (size_t)ntt_smem_words(N / 2) * sizeof(u64);
+    auto fn = k_ntt_half_io<256, Op>;
+    ensure_smem((const void*)fn, smem);
+    LaunchScope ls(c, Op::family(), st);
+    fn<<<2 * count, thr, smem, st>>>(op, c->tabs());
+}
+
 template <class Op> struct uniform_subs { static constexpr bool value = true; };
 template <class Op> struct uniform_subs<MultiOp<Op>> { static constexpr bool value = false; };
 
@@ -209,6 +223,17 @@ static void launch_ntt(const fhe_ctx* c, const Op& op, cudaStream_t st, bool sin
     case 3: launch_ntt_2pass<INV, 3>(c, op, count, st); break;
     case 4: launch_ntt_v<INV, 3, 1024, Op, true>(c, op, count, st); break;
     case 5: launch_ntt_v<INV, 4, 512, Op, true>(c, op, count, st); break;
+    case 6:
+        // half transforms: forward key-switching digit transforms only; the
+        // rest run as schedule 5
+        if constexpr (!INV && keyswitch_mac<Op>::value) {
+            if (c->N >= 64) {
+                launch_ntt_half(c, op, count, st);
+                break;
+            }
+        }
+        launch_ntt_v<INV, 4, 512, Op, true>(c, op, count, st);
+        break;
     default: launch_ntt_v<INV, 4, 512>(c, op, count, st); break;
     }
 }

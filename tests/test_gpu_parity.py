@@ -403,7 +403,7 @@ def test_masquerade_cnn_bit_exact_per_group():
     net.close()
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("N", [256, 4096])
 def test_every_schedule_at_small_rings(N, variant):
     """Rings whose last register pass is a full radix-16 pass (log2 N a
@@ -425,6 +425,38 @@ def test_every_schedule_at_small_rings(N, variant):
     ta, tb = upload(g, [A], L), upload(g, [B], L)
     out = g.empty_ct(1, L - 1)
     g.mul_relin_rescale(ta, tb, L, out)
+    want = o.rescale(o.relinearise(o.tensor(ckks.Ciphertext(A, L, 1.0), ckks.Ciphertext(B, L, 1.0)))).c
+    assert np.array_equal(download(g, out, L - 1)[0], want)
+    g.close()
+
+
+@pytest.mark.parametrize("N", [64, 128, 1024, 2048])
+def test_half_transform_schedule_every_pass_split(N):
+    """Schedule 6 (key-switching digit transforms split over two blocks per
+    polynomial) on rings whose halves take every pass split (log2 N - 1 =
+    5, 6, 9, 10 stages): relinearisation and mul + relinearise + rescale
+    equal the oracle's."""
+    import os
+    bits = [60, 40, 40, 40, 60]
+    os.environ["FHE_NTT_VARIANT"] = "6"
+    try:
+        g = fhe.Context(N, bits, 40)
+    finally:
+        del os.environ["FHE_NTT_VARIANT"]
+    assert g.ntt_variant_ks == 6
+    g.keygen(0)
+    o = ckks.Context(N, bits, 40)
+    o.keygen(0)
+    rng = np.random.default_rng(N)
+    L = 4
+    D3 = rand_ct(o, L, rng, comps=3)
+    t3 = upload(g, [D3], L)
+    r = g.empty_ct(1, L)
+    g.relinearise(t3, L, r)
+    assert np.array_equal(download(g, r, L)[0], o.relinearise(ckks.Ciphertext(D3, L, 1.0)).c)
+    A, B = rand_ct(o, L, rng), rand_ct(o, L, rng)
+    out = g.empty_ct(1, L - 1)
+    g.mul_relin_rescale(upload(g, [A], L), upload(g, [B], L), L, out)
     want = o.rescale(o.relinearise(o.tensor(ckks.Ciphertext(A, L, 1.0), ckks.Ciphertext(B, L, 1.0)))).c
     assert np.array_equal(download(g, out, L - 1)[0], want)
     g.close()
