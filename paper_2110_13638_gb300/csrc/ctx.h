@@ -298,7 +298,9 @@ void k_encode_encrypt(const fhe_ctx* c, const double* slots, uint32_t n_ct, doub
 
 uint64_t stream_key(uint64_t seed, uint64_t domain, uint64_t object);
 const char* ntt_variant_name(int v);
-constexpr int kNttVariants = 7;   // schedule 6 applies to the key-switching digit transforms only
+// the ModUp cluster schedule (7) handles this ring
+bool modup_cluster_fits(const fhe_ctx* c);
+constexpr int kNttVariants = 8;   // schedules 6 and 7 apply to the key-switching digit transforms only
 inline bool ntt_two_pass(int v) { return v == 2 || v == 3; }
 constexpr uint32_t kMaxSinglePassN = 16384;   // one transform per block in shared memory
 

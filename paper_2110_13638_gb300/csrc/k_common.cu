@@ -52,6 +52,8 @@ const char* ntt_variant_name(int v)
     case 4: return "one block per transform, radix-8, loads and stores fused into the first and last pass";
     case 5: return "one block per transform, radix-16, loads and stores fused into the first and last pass";
     case 6: return "key-switching digit transforms split over two blocks (one per output half), radix-16";
+    case 7: return "key-switching digit transforms on a cluster of four blocks (one per coefficient quarter), "
+                   "accumulators in shared memory";
     default: return "one block per transform, radix-16 passes, 512 threads";
     }
 }

@@ -226,6 +226,7 @@ int k_mul_relin_rescale_persistent(const fhe_ctx* c, const LevelBatch* g, int ng
         p5.ex = none;
         p5.dp = f.dp;
         p5.dq = f.dq;
+        p5.small_mask = f.small_mask;
         for (int ph = 0; ph < kPhases; ++ph) A.start[ph][k + 1] = A.start[ph][k] + n * phase_units(ph, L);
     }
     A.phase0[0] = 0;

@@ -25,7 +25,7 @@ void k_relin(const fhe_ctx* c, const u64* d3, u64* out2, uint32_t n_ct, uint32_t
     launch_ntt<true>(c, s1, st, single_pass);
     OpModUpMac s2{d3, D, key ? key : c->d_ksk, acc, (int)n_ct, (int)L, (int)N, (int)c->L_top, modup_red_mask(c, L),
                   modup_lazy_mask(c, L)};
-    launch_ntt<false>(c, s2, st, single_pass);
+    launch_modup(c, s2, st, single_pass);
     OpAccPInv s3{acc, Vp, (int)n_ct, (int)L, (int)N, (int)c->L_top};
     launch_ntt<true>(c, s3, st, single_pass);
     OpModDown s4;
@@ -79,6 +79,7 @@ OpKsDivFwd make_ks_div_fwd(const fhe_ctx* c, const u64* d3, const u64* acc, cons
     op.ex = ex;
     op.dp = make_divc(c, c->L_top, (uint32_t)L);
     op.dq = make_divc(c, (uint32_t)L - 1, (uint32_t)L - 1);
+    op.small_mask = small_div_mask(c, c->primes[L - 1], (uint32_t)L - 1);
     return op;
 }
 
@@ -108,7 +109,7 @@ void k_relin_rescale(const fhe_ctx* c, const u64* d3, u64* out, uint32_t n_ct, u
     launch_ntt<true>(c, s1, st);
     OpModUpMac s2{d3, D, c->d_ksk, acc, (int)n_ct, (int)L, (int)N, (int)c->L_top, modup_red_mask(c, L),
                   modup_lazy_mask(c, L)};
-    launch_ntt<false>(c, s2, st);
+    launch_modup(c, s2, st);
     OpAccPInv s3{acc, Vp, (int)n_ct, (int)L, (int)N, (int)c->L_top};
     launch_ntt<true>(c, s3, st);
     launch_ntt<true>(c, make_ks_row_inv(c, d3, acc, Vp, V, (int)n_ct, (int)L, e), st);
@@ -122,7 +123,7 @@ void k_modup_mac_step(const fhe_ctx* c, const u64* d3, const u64* D, const ulong
 {
     OpModUpMac op{d3, D, ksk, acc, (int)n_ct, (int)L, (int)c->N, (int)L, modup_red_mask(c, L),
                   modup_lazy_mask(c, L)};
-    launch_ntt<false>(c, op, st);
+    launch_modup(c, op, st);
 }
 
 }  // namespace fhe

@@ -36,6 +36,7 @@ void k_rescale(const fhe_ctx* c, const u64* in, u64* out, uint32_t n_ct, uint32_
     b.L_out = (int)L - 1;
     b.N = (int)c->N;
     b.d = make_divc(c, L - 1, L - 1);
+    b.small_mask = small_div_mask(c, c->primes[L - 1], L - 1);
     b.mulc = mulc;
     b.mulcs = mulcs;
     launch_ntt<false>(c, b, st);

@@ -224,8 +224,10 @@ static void launch_ntt(const fhe_ctx* c, const Op& op, cudaStream_t st, bool sin
     case 4: launch_ntt_v<INV, 3, 1024, Op, true>(c, op, count, st); break;
     case 5: launch_ntt_v<INV, 4, 512, Op, true>(c, op, count, st); break;
     case 6:
+    case 7:
         // half transforms: forward key-switching digit transforms only; the
-        // rest run as schedule 5
+        // rest run as schedule 5 (schedule 7, the ModUp cluster kernel, is
+        // launched by launch_modup; other key-switching ops take 6 under it)
         if constexpr (!INV && keyswitch_mac<Op>::value) {
             if (c->N >= 64) {
                 launch_ntt_half(c, op, count, st);

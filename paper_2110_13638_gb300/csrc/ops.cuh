@@ -40,6 +40,7 @@ struct OpDivFwd {
     const u64* mulc;    // optional: the input is first multiplied by this per-residue constant
     const u64* mulcs;   // its Shoup quotients (with mulc)
     DivC d;
+    uint32_t small_mask;   // targets i with p < 2 q_i (centred remainder by one conditional add)
     __host__ __device__ int count() const { return n_poly * L_out; }
     __host__ __device__ int nsub(int) const { return 1; }
     __device__ int prime(int p, int) const { return p % L_out; }
@@ -47,7 +48,10 @@ struct OpDivFwd {
     __device__ u64 load(int p, int, int j, const PrimeC& Q) const
     {
         const int poly = p / L_out, i = p % L_out;
-        return centred_to(V[(size_t)poly * N + j], d.p, d.p_half, d.pmod[i], Q);
+        const u64 v = V[(size_t)poly * N + j];
+        // p < 2 q_i: v and v - p + q_i (for the negative lift) are below 2 q_i
+        if ((small_mask >> i) & 1u) return v > d.p_half ? v + Q.q - d.p : v;
+        return centred_to(v, d.p, d.p_half, d.pmod[i], Q);
     }
     struct Pre { u64 x, c; };
     __device__ Pre pre(int p, int, int j) const
@@ -338,15 +342,28 @@ struct OpKsDivFwdT {
     KsExtra ex;
     DivC dp;            // division by P into q_0 .. q_{L-1}
     DivC dq;            // division by q_{L-1} into q_0 .. q_{L-2}
+    uint32_t small_mask;   // targets i with q_{L-1} < 2 q_i
     __host__ __device__ int count() const { return n * 2 * (L - 1); }
     __host__ __device__ int nsub(int) const { return 1; }
     __device__ int prime(int p, int) const { return p % (L - 1); }
     __device__ bool direct(int, int) const { return false; }
+    // the transform input [v]_i P^-1 + [r]_i, in [0, 4 q_i) (the forward
+    // transforms accept that range)
     __device__ u64 load(int p, int, int j, const PrimeC& Q) const
     {
         const int poly = p / (L - 1), i = p % (L - 1);
-        const u64 a = centred_to(Vp[(size_t)poly * N + j], dp.p, dp.p_half, dp.pmod[i], Q);
-        const u64 b = centred_to(V[(size_t)poly * N + j], dq.p, dq.p_half, dq.pmod[i], Q);
+        const u64 vp = Vp[(size_t)poly * N + j], vq = V[(size_t)poly * N + j];
+        if ((small_mask >> i) & 1u) {
+            // [v]_i P^-1 = v P^-1 - [v > P/2] (mod q_i) because P P^-1 = 1: a lazy
+            // Shoup product of the unreduced v, less one, in [0, 2 q_i)
+            u64 a = mul_shoup_lazy(vp, dp.inv[i], dp.invs[i], Q.q);
+            if (vp > dp.p_half) a = a ? a - 1 : Q.q2 - 1;
+            // [r]_i: r or r - q_{L-1} + q_i, both in [0, 2 q_i)
+            const u64 b = vq > dq.p_half ? vq + Q.q - dq.p : vq;
+            return a + b;
+        }
+        const u64 a = centred_to(vp, dp.p, dp.p_half, dp.pmod[i], Q);
+        const u64 b = centred_to(vq, dq.p, dq.p_half, dq.pmod[i], Q);
         return add_mod(mul_shoup(a, dp.inv[i], dp.invs[i], Q.q), b, Q.q);
     }
     // d the stored component (or, TENSOR, the factors: d = a0 (b0 | b1), x2 = a1, x = b0)
@@ -389,11 +406,32 @@ struct OpKsDivFwdT {
 };
 using OpKsDivFwd = OpKsDivFwdT<false>;
 
+// targets i < n with p < 2 q_i: there the centred lift of a residue mod p
+// needs one conditional add instead of a reduction
+inline uint32_t small_div_mask(const fhe_ctx* c, u64 p, uint32_t n)
+{
+    uint32_t m = 0;
+    for (uint32_t i = 0; i < n && i < 32; ++i)
+        if (p / 2 < c->primes[i]) m |= 1u << i;
+    return m;
+}
+
 // Grouped (MultiOp) launches of the forward steps, each compiled in a
 // translation unit of its own (k_groups_ks.cu, k_groups_fwd.cu) so the build
 // runs them in parallel.
 void launch_groups_modup_mac(const fhe_ctx* c, const MultiOp<OpModUpMac>& m, cudaStream_t st);
 void launch_groups_ks_divfwd(const fhe_ctx* c, const MultiOp<OpKsDivFwd>& m, cudaStream_t st);
+
+// Schedule 7 of the ModUp step (k_modup_cluster.cu): a cluster of four blocks
+// per (ciphertext, target), accumulators in shared memory.
+void launch_modup_cluster(const fhe_ctx* c, const OpModUpMac& op, cudaStream_t st);
+
+// The ModUp step with the schedule the autotuner picked for it
+inline void launch_modup(const fhe_ctx* c, const OpModUpMac& op, cudaStream_t st, bool single_pass = false)
+{
+    if (c->ntt_variant_ks == 7 && modup_cluster_fits(c)) launch_modup_cluster(c, op, st);
+    else launch_ntt<false>(c, op, st, single_pass);
+}
 
 // The merged ModDown + rescale of one batch (k_relin.cu): ops of steps 4' and 5'.
 OpKsRowInv make_ks_row_inv(const fhe_ctx* c, const u64* d3, const u64* acc, const u64* Vp, u64* V, int n, int L,
