@@ -101,6 +101,7 @@ struct fhe_node_const {
     uint4* tiles = nullptr;    // LINEAR: row tiles {col_off, K, n_rows, w_off}
     uint32_t* tile_rows = nullptr;
     uint32_t n_tiles = 0;
+    uint32_t max_tile_rows = 0;   // LINEAR: the most rows a tile holds
     u64* bias = nullptr;       // LINEAR: [n_out][L-1] bias residues
     struct TcPart {            // LINEAR, dense: one limb count of the tensor-core MAC
         uint16_t* W = nullptr; // weight limbs (see k_linear_mac_tc)
@@ -250,10 +251,11 @@ void k_add_const(const fhe_ctx* c, u64* ct, uint32_t n_ct, uint32_t L, const u64
 constexpr int kMacTile = 6;
 // primes below this bound store MAC weights as 21-bit limbs (wL | wH << 32)
 constexpr unsigned long long kLimbPrimeBound = 1ull << 42;
-// skip_mask: residues r with bit r set are left to the tensor-core MAC
+// skip_mask: residues r with bit r set are left to the tensor-core MAC;
+// max_tile_rows: the most rows any tile holds (five or fewer: a cheaper kernel)
 void k_linear_mac_tiled(const fhe_ctx* c, const u64* X, const uint4* tiles, uint32_t n_tiles, const uint32_t* rows,
                         const uint32_t* col, const u64* W, uint32_t L, u64* Y, cudaStream_t st,
-                        uint64_t skip_mask = 0);
+                        uint64_t skip_mask = 0, uint32_t max_tile_rows = kMacTile);
 // tensor-core MAC of a dense layer (every row over the same K input columns),
 // residues r with bit r of mask set: five limbs for primes below 2^41 (tiles
 // of kMacTcRows rows), eight below 2^61 (tiles of kMacTcRows8 rows):

@@ -249,6 +249,8 @@ struct Exec {
                 o_tcr[part] = put(trow.data(), trow.size() * 4);
             }
             nc.n_tiles = (uint32_t)tiles.size();
+            nc.max_tile_rows = 0;
+            for (const uint4& tl : tiles) nc.max_tile_rows = std::max(nc.max_tile_rows, tl.z);
             o_rp = put(tiles.data(), std::max<size_t>(1, tiles.size()) * sizeof(uint4));
             o_tr = put(trows.data(), std::max<size_t>(1, trows.size()) * 4);
             o_col = put(tcol.data(), std::max<size_t>(1, tcol.size()) * 4);
@@ -579,7 +581,7 @@ struct Exec {
                 if (rc != FHE_OK) return y;
             }
             k_linear_mac_tiled(c, x.p, k->tiles, k->n_tiles, k->tile_rows, k->col, k->W, L, Y, st,
-                               k->tc[0].mask | k->tc[1].mask);
+                               k->tc[0].mask | k->tc[1].mask, k->max_tile_rows);
             k_rescale(c, Y, out, nd.n_out, 2, L, k->bias, L - 1, sc, st);
         }
         y.p = out;

@@ -52,8 +52,8 @@ struct OpEncrypt {
     {
         const int ci = p / Ltop;
         i64 v = (i64)S[((size_t)ci * 3 + u) * N + j];
-        if (u == 1 && M) v += M[(size_t)ci * N + j];
-        return from_signed(v, P);
+        if (u == 1 && M) return from_signed(v + M[(size_t)ci * N + j], P);
+        return v >= 0 ? (u64)v : P.q - (u64)(-v);        // a sample, |v| <= 19 < q
     }
     struct Pre { u64 a, b, bs, c, cs; };
     __device__ Pre pre(int p, int u, int j) const

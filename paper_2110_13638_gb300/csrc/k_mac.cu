@@ -36,6 +36,10 @@ __device__ __forceinline__ u64 limb_combine(u64 s0, u64 s1, u64 s2, const PrimeC
     return reduce128(hi, lo, P);
 }
 
+// NR: rows computed per thread (<= kMacTile); a layer whose tiles hold at most
+// five rows (the convolution: five filters over one receptive field) skips
+// the sixth row's products
+template <int NR>
 __global__ void __launch_bounds__(256, 2) k_mac_tiled_kernel(const u64* __restrict__ X, const uint4* __restrict__ tiles,
                                                            const uint32_t* __restrict__ rows,
                                                            const uint32_t* __restrict__ col,
@@ -84,9 +88,10 @@ __global__ void __launch_bounds__(256, 2) k_mac_tiled_kernel(const u64* __restri
                     const ulonglong2 wv = __ldg(&we[o2]);
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
+                        const int o = 2 * o2 + h;
+                        if (o >= NR) continue;
                         const u64 wd = h ? wv.y : wv.x;
                         const uint32_t wl = (uint32_t)wd, wh = (uint32_t)(wd >> 32);
-                        const int o = 2 * o2 + h;
                         s0[o] += (u64)xl * wl;
                         s1[o] += (u64)xs * (wl + wh);
                         s2[o] += (u64)xh * wh;
@@ -103,9 +108,10 @@ __global__ void __launch_bounds__(256, 2) k_mac_tiled_kernel(const u64* __restri
                 const ulonglong2 wv = __ldg(&we[o2]);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
+                    const int o = 2 * o2 + h;
+                    if (o >= NR) continue;
                     const u64 wd = h ? wv.y : wv.x;
                     const uint32_t wl = (uint32_t)wd, wh = (uint32_t)(wd >> 32);
-                    const int o = 2 * o2 + h;
                     s0[o] += (u64)xl * wl;
                     s1[o] += (u64)xs * (wl + wh);
                     s2[o] += (u64)xh * wh;
@@ -113,7 +119,7 @@ __global__ void __launch_bounds__(256, 2) k_mac_tiled_kernel(const u64* __restri
             }
         }
 #pragma unroll
-        for (int o = 0; o < kMacTile; ++o)
+        for (int o = 0; o < NR; ++o)
             if (o < (int)tl.z)
                 Y[(size_t)rows[blockIdx.x * kMacTile + o] * ct_stride + off] =
                     limb_combine(s0[o], s1[o] - s0[o] - s2[o], s2[o], P);
@@ -138,7 +144,7 @@ __global__ void __launch_bounds__(256, 2) k_mac_tiled_kernel(const u64* __restri
             for (int o2 = 0; o2 < kMacTile / 2; ++o2) {
                 const ulonglong2 wv = __ldg(&we[o2]);
                 mac128(lo[2 * o2], hi[2 * o2], x[u], wv.x);
-                mac128(lo[2 * o2 + 1], hi[2 * o2 + 1], x[u], wv.y);
+                if (2 * o2 + 1 < NR) mac128(lo[2 * o2 + 1], hi[2 * o2 + 1], x[u], wv.y);
             }
         }
         cnt += 4;
@@ -158,23 +164,27 @@ __global__ void __launch_bounds__(256, 2) k_mac_tiled_kernel(const u64* __restri
         for (int o2 = 0; o2 < kMacTile / 2; ++o2) {
             const ulonglong2 wv = __ldg(&we[o2]);
             mac128(lo[2 * o2], hi[2 * o2], x, wv.x);
-            mac128(lo[2 * o2 + 1], hi[2 * o2 + 1], x, wv.y);
+            if (2 * o2 + 1 < NR) mac128(lo[2 * o2 + 1], hi[2 * o2 + 1], x, wv.y);
         }
     }
 #pragma unroll
-    for (int o = 0; o < kMacTile; ++o)
+    for (int o = 0; o < NR; ++o)
         if (o < (int)tl.z) Y[(size_t)rows[blockIdx.x * kMacTile + o] * ct_stride + off] = reduce128(hi[o], lo[o], P);
 }
 
 void k_linear_mac_tiled(const fhe_ctx* c, const u64* X, const uint4* tiles, uint32_t n_tiles, const uint32_t* rows,
-                        const uint32_t* col, const u64* W, uint32_t L, u64* Y, cudaStream_t st, uint64_t skip_mask)
+                        const uint32_t* col, const u64* W, uint32_t L, u64* Y, cudaStream_t st, uint64_t skip_mask,
+                        uint32_t max_tile_rows)
 {
     if (n_tiles == 0 || (L < 64 && (skip_mask & ((1ull << L) - 1)) == (1ull << L) - 1)) return;
     const int N = (int)c->N;
     const int tpb = N < 256 ? N : 256;
     dim3 grid(n_tiles, (N + tpb - 1) / tpb, 2 * L);
     LaunchScope ls(c, "mac", st);
-    k_mac_tiled_kernel<<<grid, tpb, 0, st>>>(X, tiles, rows, col, W, Y, (int)L, N, c->d_pc, skip_mask);
+    if (max_tile_rows <= 5)
+        k_mac_tiled_kernel<5><<<grid, tpb, 0, st>>>(X, tiles, rows, col, W, Y, (int)L, N, c->d_pc, skip_mask);
+    else
+        k_mac_tiled_kernel<kMacTile><<<grid, tpb, 0, st>>>(X, tiles, rows, col, W, Y, (int)L, N, c->d_pc, skip_mask);
 }
 
 
