@@ -36,10 +36,10 @@ PEAK_KINDS = {0: "IMAD (32-bit multiply-add)", 1: "IMAD.WIDE (32x32->64 multiply
 BUTTERFLY = 3
 # DRAM bytes (read + write) of the key-switching ModUp + key-product kernel
 # per (ciphertext, target prime, digit) unit, from one ncu capture of that
-# kernel (schedule 5) on 64 ciphertexts at L = 7 (--workload relin):
-# 226.9 MB read + 111.3 MB written over 64 * 8 * 7 units.  Scaled by units
-# to the bench's launches.
-KS_DRAM_BYTES_PER_UNIT = (226.922496e6 + 111.259904e6) / (64 * 8 * 7)
+# kernel (schedule 6, two blocks per polynomial) on 64 ciphertexts at L = 7
+# (--workload relin): 241.3 MB read + 133.4 MB written over 64 * 8 * 7 units.
+# Scaled by units to the bench's launches.
+KS_DRAM_BYTES_PER_UNIT = (241.323008e6 + 133.441280e6) / (64 * 8 * 7)
 
 
 def _env_rank():
