@@ -70,9 +70,9 @@ typedef struct {
     uint64_t primes[64]; /* q_0 .. q_{L_top-1}, then the special prime P */
     uint64_t key_bytes;  /* device bytes held for keys and tables */
     uint32_t ntt_variant;        /* NTT schedule the autotuner picked (0..5) */
-    float ntt_variant_us[8];     /* autotuner: microseconds per transform of each schedule */
-    uint32_t ntt_variant_ks;     /* schedule of the key-switching inner-product transforms (0..7) */
-    float ntt_variant_ks_us[8];  /* autotuner: microseconds per digit transform of each schedule */
+    float ntt_variant_us[16];    /* autotuner: microseconds per transform of each schedule (0 = not timed) */
+    uint32_t ntt_variant_ks;     /* schedule of the key-switching inner-product transforms (0..8) */
+    float ntt_variant_ks_us[16]; /* autotuner: microseconds per digit transform of each schedule */
     uint64_t workspace_bytes;    /* device bytes of this context's call workspace and batch
                                     area (both grow on demand; 0 before the first call that
                                     needs them) */

@@ -347,7 +347,7 @@ static int autotune_ntt(fhe_ctx* c)
         const char* env_ks = std::getenv("FHE_NTT_VARIANT_KS");
         const int v = std::atoi(env), vk = (env_ks && *env_ks) ? std::atoi(env_ks) : v;
         for (int x : {v, vk}) {
-            if (x < 0 || x >= kNttVariants) return fail(FHE_EINVAL, "FHE_NTT_VARIANT(_KS) out of range (0..7)");
+            if (x < 0 || x >= kNttVariants) return fail(FHE_EINVAL, "FHE_NTT_VARIANT(_KS) out of range (0..8)");
             if (c->N > kMaxSinglePassN && !ntt_two_pass(x))
                 return fail(FHE_EINVAL, "N > 16384 needs a two-pass NTT schedule (2 or 3)");
         }
@@ -611,7 +611,7 @@ int fhe_ctx_fork(fhe_ctx* parent, fhe_ctx** out)
     c->device = parent->device;
     c->ntt_variant = parent->ntt_variant;
     c->ntt_variant_ks = parent->ntt_variant_ks;
-    for (int v = 0; v < 8; ++v) {
+    for (int v = 0; v < 16; ++v) {
         c->ntt_variant_us[v] = parent->ntt_variant_us[v];
         c->ntt_variant_ks_us[v] = parent->ntt_variant_ks_us[v];
     }
@@ -669,7 +669,7 @@ int fhe_ctx_query(const fhe_ctx* c, fhe_ctx_info* out)
     out->ntt_variant = (uint32_t)c->ntt_variant;
     out->ntt_variant_ks = (uint32_t)c->ntt_variant_ks;
     out->workspace_bytes = c->ws_bytes + c->bb_bytes;
-    for (int v = 0; v < kNttVariants && v < 8; ++v) {
+    for (int v = 0; v < kNttVariants && v < 16; ++v) {
         out->ntt_variant_us[v] = c->ntt_variant_us[v];
         out->ntt_variant_ks_us[v] = c->ntt_variant_ks_us[v];
     }

@@ -16,9 +16,9 @@ struct fhe_ctx {
     double delta = 0.0;
     int device = 0;
     int ntt_variant = 0;           // NTT schedule (see ntt_variant_name), autotuned
-    float ntt_variant_us[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // autotuner: us per transform per variant
+    float ntt_variant_us[16] = {};   // autotuner: us per transform per variant
     int ntt_variant_ks = 0;        // schedule of the key-switching inner-product transforms
-    float ntt_variant_ks_us[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    float ntt_variant_ks_us[16] = {};
     u64* d_ntt2 = nullptr;         // two-pass intermediate (allocated with the context)
     size_t ntt2_words = 0;
 
@@ -302,7 +302,7 @@ uint64_t stream_key(uint64_t seed, uint64_t domain, uint64_t object);
 const char* ntt_variant_name(int v);
 // the ModUp cluster schedule (7) handles this ring
 bool modup_cluster_fits(const fhe_ctx* c);
-constexpr int kNttVariants = 8;   // schedules 6 and 7 apply to the key-switching digit transforms only
+constexpr int kNttVariants = 9;   // schedules 6, 7 and 8 apply to the key-switching digit transforms only
 inline bool ntt_two_pass(int v) { return v == 2 || v == 3; }
 constexpr uint32_t kMaxSinglePassN = 16384;   // one transform per block in shared memory
 

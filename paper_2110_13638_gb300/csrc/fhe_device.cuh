@@ -903,10 +903,12 @@ __global__ void __launch_bounds__(MAXT, 1) k_ntt_io(Op op, NttTables T)
 // holds N/2 words of shared memory and two blocks share an SM: one block's
 // loads and epilogue overlap the other's butterflies.  The epilogue of each
 // half is independent (the key-switching digit transforms).
-template <int MAXT, class Op>
-__global__ void __launch_bounds__(MAXT, 2) k_ntt_half_io(Op op, NttTables T)
+// LOGR: radix of the register passes; MINB: blocks per SM the registers are
+// budgeted for (2 at radix 16, 3 at radix 8; the shared memory of a half
+// polynomial at N = 16384 allows three)
+template <int MAXT, int LOGR, int MINB, class Op>
+__global__ void __launch_bounds__(MAXT, MINB) k_ntt_half_io(Op op, NttTables T)
 {
-    constexpr int LOGR = 4;
     extern __shared__ u64 sm[];
     const int logN = T.logN;
     const int N = 1 << logN, logNh = logN - 1, Nh = N >> 1;
@@ -930,8 +932,8 @@ __global__ void __launch_bounds__(MAXT, 2) k_ntt_half_io(Op op, NttTables T)
             int s = 0;
             bool first = true;
             while (s < logNh) {
-                // radix-16 passes, but never a last pass of one stage (its
-                // epilogue would wait for its loads two elements at a time)
+                // radix-2^LOGR passes, but never a last pass of one stage
+                // (its epilogue would wait for its loads two elements at a time)
                 const int rem = logNh - s;
                 const int k = rem <= LOGR ? rem : (rem - LOGR == 1 ? LOGR - 1 : LOGR);
                 const bool last = s + k >= logNh;

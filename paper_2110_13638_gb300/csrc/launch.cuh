@@ -155,15 +155,16 @@ struct MultiOp {
     }
 };
 
-// forward transforms split over two blocks per residue polynomial (schedule 6,
-// key-switching digit transforms)
-template <class Op>
+// forward transforms split over two blocks per residue polynomial (schedules
+// 6 and 8, key-switching digit transforms): radix 16 with two blocks per SM,
+// or radix 8 with three
+template <class Op, int LOGR = 4, int MINB = 2>
 static void launch_ntt_half(const fhe_ctx* c, const Op& op, int count, cudaStream_t st)
 {
     const int N = (int)c->N;
-    const int thr = std::min(256, std::max(32, (N / 2) >> 4));
+    const int thr = std::min(256, std::max(32, (N / 2) >> LOGR));
     const size_t smem = (size_t)ntt_smem_words(N / 2) * sizeof(u64);
-    auto fn = k_ntt_half_io<256, Op>;
+    auto fn = k_ntt_half_io<256, LOGR, MINB, Op>;
     ensure_smem((const void*)fn, smem);
     LaunchScope ls(c, Op::family(), st);
     fn<<<2 * count, thr, smem, st>>>(op, c->tabs());
@@ -225,12 +226,14 @@ static void launch_ntt(const fhe_ctx* c, const Op& op, cudaStream_t st, bool sin
     case 5: launch_ntt_v<INV, 4, 512, Op, true>(c, op, count, st); break;
     case 6:
     case 7:
+    case 8:
         // half transforms: forward key-switching digit transforms only; the
         // rest run as schedule 5 (schedule 7, the ModUp cluster kernel, is
         // launched by launch_modup; other key-switching ops take 6 under it)
         if constexpr (!INV && keyswitch_mac<Op>::value) {
             if (c->N >= 64) {
-                launch_ntt_half(c, op, count, st);
+                if (v == 8) launch_ntt_half<Op, 3, 3>(c, op, count, st);
+                else launch_ntt_half<Op, 4, 2>(c, op, count, st);
                 break;
             }
         }

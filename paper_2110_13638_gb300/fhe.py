@@ -36,8 +36,8 @@ class FheError(RuntimeError):
 class CtxInfo(ctypes.Structure):
     _fields_ = [("N", ctypes.c_uint32), ("slots", ctypes.c_uint32), ("L_top", ctypes.c_uint32),
                 ("log_scale", ctypes.c_uint32), ("primes", ctypes.c_uint64 * 64), ("key_bytes", ctypes.c_uint64),
-                ("ntt_variant", ctypes.c_uint32), ("ntt_variant_us", ctypes.c_float * 8),
-                ("ntt_variant_ks", ctypes.c_uint32), ("ntt_variant_ks_us", ctypes.c_float * 8),
+                ("ntt_variant", ctypes.c_uint32), ("ntt_variant_us", ctypes.c_float * 16),
+                ("ntt_variant_ks", ctypes.c_uint32), ("ntt_variant_ks_us", ctypes.c_float * 16),
                 ("workspace_bytes", ctypes.c_uint64)]
 
 
@@ -291,6 +291,8 @@ NTT_SCHEDULES = (
     "key-switching digit transforms split over two blocks per polynomial (one per output half), 256 threads",
     "key-switching digit transforms on a cluster of four blocks (one per coefficient quarter), accumulators in "
     "shared memory",
+    "key-switching digit transforms split over two blocks per polynomial (one per output half), radix-8, three "
+    "blocks per SM",
 )
 
 
@@ -314,9 +316,9 @@ class Context:
         self.primes = [int(info.primes[i]) for i in range(info.L_top + 1)]
         self.key_bytes = int(info.key_bytes)
         self.ntt_variant = int(info.ntt_variant)
-        self.ntt_variant_us = [float(info.ntt_variant_us[i]) for i in range(8)]
+        self.ntt_variant_us = [float(info.ntt_variant_us[i]) for i in range(9)]
         self.ntt_variant_ks = int(info.ntt_variant_ks)
-        self.ntt_variant_ks_us = [float(info.ntt_variant_ks_us[i]) for i in range(8)]
+        self.ntt_variant_ks_us = [float(info.ntt_variant_ks_us[i]) for i in range(9)]
         self.delta = float(2 ** log_scale)
 
     def fork(self):
