@@ -11,6 +11,9 @@
   and must be bit-exact.
 - The whole CNN and the whole yield MLP: decrypted outputs within 1e-4 of the
   FP64 plaintext forward pass with the same polynomial activations.
+- The yield MLP block by block the same way, and the uneven-level batching
+  workload (4096 pairs, one persistent launch in a CUDA graph) with one
+  sampled pair per level recomputed by the oracle.
 - The dense layers give the same words on the tensor cores as on the integer
   pipes.
 - Every NTT schedule the autotuner can pick gives bit-exact results."""
@@ -206,3 +209,84 @@ def test_every_ntt_schedule_bit_exact(octx, variant):
     want = octx.rescale(octx.relinearise(octx.tensor(ckks.Ciphertext(A, L, 1.0), ckks.Ciphertext(B, L, 1.0)))).c
     assert np.array_equal(fhe.raw_u64(out)[0], want)
     c.close()
+
+
+def test_mlp_blocks_sampled_bit_exact(ctx, octx):
+    """The yield MLP (config 2) at full size, block by block: each block is
+    recomputed by the oracle from the ciphertexts the device fed it (rows at both ends
+    of the 64 -> 128 and 128 -> 32 tensor-core layers' tiles, outputs of both
+    sigmoid fits, the 32 -> 1 integer-MAC layer), bit-exact with equal
+    nominal scales."""
+    g, x = W.cfg2()
+    nodes = g["nodes"]
+    ct = encrypt_all(ctx, x, first=900)
+    X = _coeff(ctx, ct, ctx.L_top)
+    runs = {}
+    for k in (1, 2, 3, 4, 5):
+        out, meta, L = run_graph(ctx, W.chain_graph(64, nodes[1:1 + k]), ct)
+        runs[k] = (_coeff(ctx, out, L), meta, L)
+        del out
+    (Y1, m1, L1), (Y2, m2, L2), (Y3, m3, L3), (Y4, m4, L4), (Y5, m5, L5) = (runs[k] for k in (1, 2, 3, 4, 5))
+    assert (L1, L2, L3, L4, L5) == (7, 5, 4, 2, 1)
+    xs = [ckks.Ciphertext(X[i], ctx.L_top, ctx.delta) for i in range(64)]
+    rows = ckks.csr_rows(nodes[1])
+    for k in (0, 31, 47, 48, 127):
+        y = octx.linear(xs, [rows[k]], [nodes[1]["bias"][k]])[0]
+        assert np.array_equal(Y1[k], y.c), k
+        assert m1[k][1] == y.scale
+    for k in (0, 100):
+        y = octx.poly3(ckks.Ciphertext(Y1[k], L1, m1[k][1]), nodes[2]["coeffs"])
+        assert np.array_equal(Y2[k], y.c), k
+        assert m2[k][1] == y.scale
+    xs = [ckks.Ciphertext(Y2[i], L2, m2[i][1]) for i in range(128)]
+    rows = ckks.csr_rows(nodes[3])
+    for k in (0, 31):
+        y = octx.linear(xs, [rows[k]], [nodes[3]["bias"][k]])[0]
+        assert np.array_equal(Y3[k], y.c), k
+    y = octx.poly3(ckks.Ciphertext(Y3[5], L3, m3[5][1]), nodes[4]["coeffs"])
+    assert np.array_equal(Y4[5], y.c)
+    xs = [ckks.Ciphertext(Y4[i], L4, m4[i][1]) for i in range(32)]
+    y = octx.linear(xs, ckks.csr_rows(nodes[5]), nodes[5]["bias"])[0]
+    assert np.array_equal(Y5[0], y.c)
+    assert m5[0][1] == y.scale
+
+
+def test_uneven_level_batch_full_size_sampled_bit_exact(ctx, octx):
+    """The batching workload at full size in the launch configuration the
+    bench times: 4096 ciphertext pairs at levels 1 + U{1..7} (seed 3) in one
+    persistent launch captured in a CUDA graph; one sampled pair per level is
+    recomputed by the oracle (tensor, relinearise, rescale), bit-exact."""
+    levels = 1 + np.random.Generator(np.random.PCG64(3)).integers(1, 8, size=4096)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(11)
+    batches = []
+    for L in range(2, 9):
+        n = int((levels == L).sum())
+        def rnd():
+            t = torch.empty((n, 2, L, 16384), dtype=torch.int64, device="cuda")
+            for r in range(L):
+                t[:, :, r, :] = torch.randint(0, ctx.primes[r], (n, 2, 16384), device="cuda", generator=gen)
+            return t
+        batches.append((rnd(), rnd(), ctx.empty_ct(n, L - 1), L))
+    ctx.mul_relin_rescale_levels(batches)           # sizes the workspace
+    ctx.sync()
+    for b in batches:
+        b[2].zero_()
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            ctx.mul_relin_rescale_levels(batches)
+    torch.cuda.current_stream().wait_stream(s)
+    graph.replay()
+    ctx.sync()
+    rng = np.random.default_rng(12)
+    for a, b, out, L in batches:
+        k = int(rng.integers(0, a.shape[0]))
+        A = _coeff(ctx, a[k:k + 1].clone(), L)[0]
+        B = _coeff(ctx, b[k:k + 1].clone(), L)[0]
+        got = _coeff(ctx, out[k:k + 1].clone(), L - 1)[0]
+        want = octx.rescale(octx.relinearise(octx.tensor(ckks.Ciphertext(A, L, 1.0),
+                                                         ckks.Ciphertext(B, L, 1.0)))).c
+        assert np.array_equal(got, want), (L, k)
