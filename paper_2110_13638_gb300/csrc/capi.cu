@@ -512,6 +512,12 @@ int fhe_ctx_create(uint32_t N, const uint32_t* bits, uint32_t n_bits, uint32_t l
             P.p21[k] = hpow(2, 21ull * (k + 1), q);
             P.p21s[k] = shoup(P.p21[k], q);
         }
+        {
+            int b = 0;
+            while (b < 64 && (q >> b)) ++b;                  // bit length of q (q < 2^62)
+            P.bsh = (u64)(b - 1);
+            P.bmu = (u64)((((u128)1 << (2 * b)) / q) << (63 - b));
+        }
         const u64 psi = primitive_root_2n(q, N);
         const u64 psi_inv = hinv(psi, q);
         for (uint32_t i = 0; i < N; ++i) {

@@ -35,6 +35,8 @@ struct PrimeC {
     u64 ub;      // floor(2^64 / q) * q (rejection bound of the uniform sampler)
     u64 p21[4];  // 2^21, 2^42, 2^63, 2^84 mod q (limb positions of the MAC)
     u64 p21s[4]; // their Shoup quotients
+    u64 bmu;     // Barrett constant floor(2^(2b) / q) << (63 - b), b = bit length of q
+    u64 bsh;     // b - 1
 };
 
 // ---------------------------------------------------------------- scalar ops
@@ -81,6 +83,21 @@ __device__ __forceinline__ u64 reduce128(u64 hi, u64 lo, const PrimeC& P)
 __device__ __forceinline__ u64 mul_mod(u64 a, u64 b, const PrimeC& P)
 {
     return reduce128(__umul64hi(a, b), a * b, P);
+}
+
+// a * b mod q for REDUCED a, b < q < 2^62 (Barrett): with x = a b < 2^(2b),
+// t = floor(floor(x / 2^(b-1)) floor(2^(2b) / q) / 2^(b+1)) lies within 2 of
+// floor(x / q), so x - t q is in [0, 3q) and two conditional subtractions
+// finish it; two 64-bit products and two high products instead of mul_mod's
+// four high products
+__device__ __forceinline__ u64 mul_mod_r(u64 a, u64 b, const PrimeC& P)
+{
+    const u64 lo = a * b, hi = __umul64hi(a, b);
+    const u64 xh = (hi << (64 - P.bsh)) | (lo >> P.bsh);
+    const u64 t = __umul64hi(xh, P.bmu);
+    u64 r = lo - t * P.q;
+    r = r >= P.q ? r - P.q : r;
+    return r >= P.q ? r - P.q : r;
 }
 
 // signed 64-bit integer -> residue mod q

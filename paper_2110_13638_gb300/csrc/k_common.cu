@@ -144,16 +144,16 @@ __global__ void k_tensor_kernel(const u64* __restrict__ a, const u64* __restrict
         u64* O = out + (size_t)ct * 3 * per_comp;
         const u64 a0 = A[w], a1 = A[per_comp + w];
         if constexpr (SQUARE) {
-            const u64 m = mul_mod(a0, a1, P);
-            O[w] = mul_mod(a0, a0, P);
+            const u64 m = mul_mod_r(a0, a1, P);
+            O[w] = mul_mod_r(a0, a0, P);
             O[per_comp + w] = add_mod(m, m, P.q);
-            O[2 * per_comp + w] = mul_mod(a1, a1, P);
+            O[2 * per_comp + w] = mul_mod_r(a1, a1, P);
         } else {
             const u64* B = b + (size_t)ct * 2 * per_comp;
             const u64 b0 = B[w], b1 = B[per_comp + w];
-            O[w] = mul_mod(a0, b0, P);
-            O[per_comp + w] = add_mod(mul_mod(a0, b1, P), mul_mod(a1, b0, P), P.q);
-            O[2 * per_comp + w] = mul_mod(a1, b1, P);
+            O[w] = mul_mod_r(a0, b0, P);
+            O[per_comp + w] = add_mod(mul_mod_r(a0, b1, P), mul_mod_r(a1, b0, P), P.q);
+            O[2 * per_comp + w] = mul_mod_r(a1, b1, P);
         }
     }
 }
@@ -183,7 +183,7 @@ __global__ void k_mul_const_kernel(const u64* __restrict__ in, u64* __restrict__
         const uint32_t ct = poly / (uint32_t)comps;
         const PrimeC P = pc[r];
         const u64 x = in[(((size_t)poly * L_in + r) << logN) + (i & Nm)];
-        out[i] = mul_mod(x, cres[(size_t)ct * cstride + r], P);
+        out[i] = mul_mod_r(x, cres[(size_t)ct * cstride + r], P);
     }
 }
 
@@ -229,9 +229,9 @@ __global__ void k_poly_combine_kernel(u64* __restrict__ t1, const u64* __restric
         const uint32_t poly = row / (uint32_t)L1, r = row - poly * (uint32_t)L1;
         const PrimeC P = pc[r];
         const u64 xv = x[(((size_t)poly * Lx + r) << logN) + (i & Nm)];
-        u64 a = mul_mod(x2[i], c2[r], P);
+        u64 a = mul_mod_r(x2[i], c2[r], P);
         if (accumulate) a = add_mod(t1[i], a, P.q);
-        t1[i] = add_mod(a, mul_mod(xv, c1[r], P), P.q);
+        t1[i] = add_mod(a, mul_mod_r(xv, c1[r], P), P.q);
     }
 }
 
@@ -276,7 +276,7 @@ __global__ void k_plain_mac_kernel(u64* __restrict__ Y, const u64* __restrict__ 
         const PrimeC P = pc[r];
         const u64 x = X[((((size_t)ct * 2 + comp) * L + r) << logN) + j];
         const u64 w = PT[((((size_t)f * k2 + p) * L + r) << logN) + j];
-        u64 v = mul_mod(x, w, P);
+        u64 v = mul_mod_r(x, w, P);
         if (accumulate) v = add_mod(Y[i], v, P.q);
         Y[i] = v;
     }

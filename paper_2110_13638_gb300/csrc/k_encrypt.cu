@@ -144,7 +144,7 @@ struct OpDecrypt {
     {
         const u64 c0 = ct[(((size_t)p * 2 + 0) * L) * N + j];
         const u64 c1 = ct[(((size_t)p * 2 + 1) * L) * N + j];
-        return add_mod(c0, mul_mod(c1, s[j], P), P.q);
+        return add_mod(c0, mul_mod_r(c1, s[j], P), P.q);
     }
     struct Pre {};
     __device__ Pre pre(int, int, int) const { return {}; }

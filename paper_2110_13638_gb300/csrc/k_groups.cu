@@ -34,9 +34,9 @@ __global__ void k_tensor_groups_kernel(TensorGroups G, int logN, const PrimeC* _
         const u64* B = G.b[g] + ct * 2 * per_comp;
         const u64 a0 = A[w], a1 = A[per_comp + w], b0 = B[w], b1 = B[per_comp + w];
         u64* O = G.out[g] + ct * 3 * per_comp;
-        O[w] = mul_mod(a0, b0, P);
-        O[per_comp + w] = add_mod(mul_mod(a0, b1, P), mul_mod(a1, b0, P), P.q);
-        O[2 * per_comp + w] = mul_mod(a1, b1, P);
+        O[w] = mul_mod_r(a0, b0, P);
+        O[per_comp + w] = add_mod(mul_mod_r(a0, b1, P), mul_mod_r(a1, b0, P), P.q);
+        O[2 * per_comp + w] = mul_mod_r(a1, b1, P);
     }
 }
 

@@ -100,9 +100,9 @@ struct D3Src<true> {
     __device__ __forceinline__ u64 get(int ct, int k, int L, int N, int i, int j, const PrimeC& Q) const
     {
         const size_t o0 = (((size_t)ct * 2) * L + i) * N + j, o1 = o0 + (size_t)L * N;
-        if (k == 0) return mul_mod(a[o0], b[o0], Q);
-        if (k == 2) return mul_mod(a[o1], b[o1], Q);
-        return add_mod(mul_mod(a[o0], b[o1], Q), mul_mod(a[o1], b[o0], Q), Q.q);
+        if (k == 0) return mul_mod_r(a[o0], b[o0], Q);
+        if (k == 2) return mul_mod_r(a[o1], b[o1], Q);
+        return add_mod(mul_mod_r(a[o0], b[o1], Q), mul_mod_r(a[o1], b[o0], Q), Q.q);
     }
 };
 
@@ -393,8 +393,8 @@ struct OpKsDivFwdT {
         const int poly = p / (L - 1), i = p % (L - 1);
         u64 d = pr.d;
         if constexpr (TENSOR) {
-            d = mul_mod(pr.d, pr.f, Q);                          // a0 b0, or a0 b1
-            if (poly & 1) d = add_mod(d, mul_mod(pr.x2, pr.x, Q), Q.q);   // + a1 b0
+            d = mul_mod_r(pr.d, pr.f, Q);                        // a0 b0, or a0 b1
+            if (poly & 1) d = add_mod(d, mul_mod_r(pr.x2, pr.x, Q), Q.q); // + a1 b0
         }
         u64 s = add_mod(d, mul_shoup(pr.a, dp.inv[i], dp.invs[i], Q.q), Q.q);
         if (!TENSOR && ex.x2) s = add_mod(s, mul_shoup(pr.x2, ex.c2[i], ex.c2s[i], Q.q), Q.q);
