@@ -239,6 +239,17 @@ static void launch_ntt(const fhe_ctx* c, const Op& op, cudaStream_t st, bool sin
         }
         launch_ntt_v<INV, 4, 512, Op, true>(c, op, count, st);
         break;
+    case 9:
+        // every forward transform split over two blocks (radix 16, two
+        // blocks per SM), inverse transforms as schedule 4
+        if constexpr (!INV) {
+            if (c->N >= 64) {
+                launch_ntt_half<Op, 4, 2>(c, op, count, st);
+                break;
+            }
+        }
+        launch_ntt_v<INV, 3, 1024, Op, true>(c, op, count, st);
+        break;
     default: launch_ntt_v<INV, 4, 512>(c, op, count, st); break;
     }
 }
