@@ -110,9 +110,9 @@ void k_relin_rescale(const fhe_ctx* c, const u64* d3, u64* out, uint32_t n_ct, u
     OpModUpMac s2{d3, D, c->d_ksk, acc, (int)n_ct, (int)L, (int)N, (int)c->L_top, modup_red_mask(c, L),
                   modup_lazy_mask(c, L)};
     launch_modup(c, s2, st);
-    OpAccPInv s3{acc, Vp, (int)n_ct, (int)L, (int)N, (int)c->L_top};
-    launch_ntt<true>(c, s3, st);
-    launch_ntt<true>(c, make_ks_row_inv(c, d3, acc, Vp, V, (int)n_ct, (int)L, e), st);
+    // the P residues' and row L-1's inverse transforms in one launch
+    OpKsPRowInv s34{make_ks_row_inv(c, d3, acc, Vp, V, (int)n_ct, (int)L, e), Vp, (int)c->L_top};
+    launch_ntt<true>(c, s34, st);
     launch_ntt<false>(c, make_ks_div_fwd(c, d3, acc, Vp, V, out, (int)n_ct, (int)L, e, addc, (int)addc_stride), st);
 }
 

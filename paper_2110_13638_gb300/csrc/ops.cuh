@@ -326,6 +326,35 @@ struct OpKsRowInvT {
 };
 using OpKsRowInv = OpKsRowInvT<false>;
 
+// steps 3 and 4' in one unit per (ct, comp): sub 0 is the inverse transform of
+// the accumulator's P residue (into Vp), sub 1 that of row L-1 (into V), whose
+// epilogue reads the Vp words sub 0 wrote (the same block, after its barrier)
+struct OpKsPRowInv {
+    static const char* family() { return "keyswitch_rescale_intt"; }
+    OpKsRowInv row;     // its acc, V, constants; row.Vp is the array below
+    u64* Vp;            // [n][2][N] written by sub 0
+    int Ltop;
+    __host__ __device__ int count() const { return row.n * 2; }
+    __host__ __device__ int nsub(int) const { return 2; }
+    __device__ int prime(int, int u) const { return u == 0 ? Ltop : row.L - 1; }
+    __device__ bool direct(int, int) const { return false; }
+    __device__ u64 load(int p, int u, int j, const PrimeC& Q) const
+    {
+        if (u == 0) return reduce64(row.acc[((size_t)p * (row.L + 1) + row.L) * row.N + j], Q);
+        return row.load(p, 0, j, Q);
+    }
+    struct Pre { u64 v; };
+    __device__ Pre pre(int p, int u, int j) const
+    {
+        return {u == 0 ? 0ull : Vp[(size_t)p * row.N + j]};
+    }
+    __device__ void store(int p, int u, int j, u64 v, const Pre& pr, const PrimeC& Q) const
+    {
+        if (u == 0) Vp[(size_t)p * row.N + j] = v;
+        else row.store(p, 0, j, v, OpKsRowInv::Pre{pr.v}, Q);
+    }
+};
+
 // step 5': the merged forward transform of both corrections into q_i, i < L-1,
 // per (ct, comp, i), and the rescaled output row.  TENSOR: the tensor product
 // is recomputed from its factors (the epilogue then loads the factors)
