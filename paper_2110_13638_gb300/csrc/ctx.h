@@ -236,6 +236,12 @@ size_t rescale_scratch_bytes(const fhe_ctx* c, uint32_t n_ct, uint32_t comps);
 void k_rescale(const fhe_ctx* c, const u64* in, u64* out, uint32_t n_ct, uint32_t comps, uint32_t L,
                const u64* addc, uint32_t addc_stride, void* scratch, cudaStream_t st, const u64* mulc = nullptr,
                const u64* mulcs = nullptr);
+// (x2 (x) rescale(x * C)) into out3 [n][3][L-1][N]: the rescale's forward
+// transforms with the tensor product in their epilogue (x at level L, x2 at
+// L-1; C: per-residue constants with their Shoup quotients)
+size_t rescale_tensor_scratch_bytes(const fhe_ctx* c, uint32_t n_ct, uint32_t L);
+void k_rescale_tensor(const fhe_ctx* c, const u64* x, const u64* mulc, const u64* mulcs, const u64* x2, u64* out3,
+                      uint32_t n_ct, uint32_t L, void* scratch, cudaStream_t st);
 // polynomial activation: t1 (+)= x2 * c2 + (first L1 residues of x) * c1
 // (accumulate: add to t1; else overwrite it)
 void k_poly_combine(const fhe_ctx* c, u64* t1, const u64* x2, const u64* x, uint32_t n_ct, uint32_t L1, uint32_t Lx,

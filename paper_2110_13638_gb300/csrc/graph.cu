@@ -628,9 +628,8 @@ struct Exec {
         if (deg == 2) return poly2(i, x, k);
         u64* T3 = (u64*)take(cts(n, 3, L));
         void* rs = take(relin_rescale_scratch_bytes(c, n, L));
-        void* ss = take(rescale_scratch_bytes(c, n, 2));
+        void* ts = take(rescale_tensor_scratch_bytes(c, n, L));
         u64* x2 = (u64*)take(cts(n, 2, L - 1));
-        u64* w = (u64*)take(cts(n, 2, L - 1));
         u64* T3b = (u64*)take(cts(n, 3, L - 1));
         u64* out = (u64*)take(cts(n, 2, L - 2));
         if (!dry && ok()) {
@@ -638,8 +637,8 @@ struct Exec {
             if (!kc) return y;
             k_tensor(c, x.p, x.p, T3, n, L, st);
             k_relin_rescale(c, T3, x2, n, L, rs, st);                         // x2 = rescale(relin(x (x) x))
-            k_rescale(c, x.p, w, n, 2, L, nullptr, 0, ss, st, kc->c3, kc->c3s);   // rescale(x * C3)
-            k_tensor(c, x2, w, T3b, n, L - 1, st);
+            // x2 (x) w with w = rescale(x * C3), the tensor formed in the rescale's epilogue
+            k_rescale_tensor(c, x.p, kc->c3, kc->c3s, x2, T3b, n, L, ts, st);
             // y = rescale(relin(x2 (x) w) + x2 C2 + drop(x) C1) + C0
             const KsExtra ex{x2, kc->c2, kc->c2s, x.p, kc->c1, kc->c1s, (int)L};
             k_relin_rescale(c, T3b, out, n, L - 1, rs, st, &ex, kc->c0, 0);

@@ -71,6 +71,62 @@ struct OpDivFwd {
     }
 };
 
+// rescale of x C (per-residue constant C) fused with the tensor product of the
+// result w and a second ciphertext x2 at the output level: unit (ct, i) runs
+// the forward transforms of both components (sub k = 0, 1); sub 0 keeps w_0
+// in scratch, sub 1 forms (x2_0 w_0, x2_0 w_1 + x2_1 w_0, x2_1 w_1) at residue
+// i.  The element-to-thread mapping of both subs' epilogues is the same, so
+// the w_0 word sub 1 reads was written by the same thread.
+struct OpDivFwdTensor {
+    static const char* family() { return "rescale_ntt"; }
+    const u64* in;      // [n][2][L_in][N]: x
+    const u64* V;       // [n][2][N] coefficient form mod q_{L_in-1} (of x C)
+    const u64* mulc;    // C residues and their Shoup quotients
+    const u64* mulcs;
+    const u64* x2;      // [n][2][L_out][N]
+    u64* W0;            // [n][L_out][N] scratch: w_0
+    u64* out3;          // [n][3][L_out][N]
+    int n, L_in, L_out, N;
+    DivC d;
+    uint32_t small_mask;
+    __host__ __device__ int count() const { return n * L_out; }
+    __host__ __device__ int nsub(int) const { return 2; }
+    __device__ int prime(int p, int) const { return p % L_out; }
+    __device__ bool direct(int, int) const { return false; }
+    __device__ u64 load(int p, int k, int j, const PrimeC& Q) const
+    {
+        const int ct = p / L_out, i = p % L_out;
+        const u64 v = V[((size_t)ct * 2 + k) * N + j];
+        if ((small_mask >> i) & 1u) return v > d.p_half ? v + Q.q - d.p : v;
+        return centred_to(v, d.p, d.p_half, d.pmod[i], Q);
+    }
+    struct Pre { u64 x, w0, a0, a1; };
+    __device__ Pre pre(int p, int k, int j) const
+    {
+        const int ct = p / L_out, i = p % L_out;
+        Pre r;
+        r.x = in[(((size_t)ct * 2 + k) * L_in + i) * N + j];
+        r.w0 = k ? W0[((size_t)ct * L_out + i) * N + j] : 0;
+        r.a0 = k ? x2[(((size_t)ct * 2 + 0) * L_out + i) * N + j] : 0;
+        r.a1 = k ? x2[(((size_t)ct * 2 + 1) * L_out + i) * N + j] : 0;
+        return r;
+    }
+    __device__ void store(int p, int k, int j, u64 v, const Pre& pr, const PrimeC& Q) const
+    {
+        const int ct = p / L_out, i = p % L_out;
+        const u64 x = mul_shoup(pr.x, mulc[i], mulcs[i], Q.q);
+        const u64 w = mul_shoup(sub_mod(x, v, Q.q), d.inv[i], d.invs[i], Q.q);
+        if (k == 0) {
+            W0[((size_t)ct * L_out + i) * N + j] = w;
+            return;
+        }
+        const size_t o = (((size_t)ct * 3) * L_out + i) * N + j, st3 = (size_t)L_out * N;
+        out3[o] = mul_mod_r(pr.a0, pr.w0, Q);
+        out3[o + st3] = add_mod(mul_mod_r(pr.a0, w, Q), mul_mod_r(pr.a1, pr.w0, Q), Q.q);
+        out3[o + 2 * st3] = mul_mod_r(pr.a1, w, Q);
+    }
+};
+
 // ---------------------------------------------------------------- relinearise
 // The three components of a tensor product d = (a0 b0, a0 b1 + a1 b0, a1 b1):
 // read from a stored [n][3][L][N] batch (D3Src<false>), or recomputed from
