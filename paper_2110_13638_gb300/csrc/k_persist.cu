@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_persist_kernel(const __g
         while (g + 1 < A.ng && w >= A.start[ph][g + 1]) ++g;
         const int q = w - A.start[ph][g];
         const PersistGroup& G = A.g[g];
-        const int ct = q / phase_units(ph, G.L);
+        const int ct = ph == 1 ? G.p2.ct_of(q) : q / phase_units(ph, G.L);
         if (threadIdx.x == 0) {
             bool go = true;
             if (ph > 0) {

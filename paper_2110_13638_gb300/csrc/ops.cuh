@@ -228,15 +228,20 @@ struct OpModUpMacT {
                             // products, each below 2 q_t, then sum below 2 L q_t < 2^64
     __host__ __device__ int count() const { return n * (L + 1); }
     __host__ __device__ int nsub(int) const { return L; }
+    // unit p: the n L units of the data-prime targets first, then the n units
+    // of the special prime, so a launch runs the (reduced-butterfly) P units
+    // together at its end instead of interleaved with the others
+    __host__ __device__ __forceinline__ int ct_of(int p) const { return p < n * L ? p / L : p - n * L; }
+    __host__ __device__ __forceinline__ int t_of(int p) const { return p < n * L ? p % L : L; }
     __device__ int prime(int p, int) const
     {
-        const int t = p % (L + 1);
+        const int t = t_of(p);
         return t == L ? Ltop : t;
     }
-    __device__ bool direct(int p, int u) const { return (p % (L + 1)) == u; }
+    __device__ bool direct(int p, int u) const { return t_of(p) == u; }
     __device__ u64 load(int p, int u, int j, const PrimeC& Q) const
     {
-        const int ct = p / (L + 1);
+        const int ct = ct_of(p);
         const u64 d = D[((size_t)ct * L + u) * N + j];       // in [0, q_u)
         return ((red_mask >> u) & 1u) ? reduce64(d, Q) : d;
     }
@@ -246,7 +251,7 @@ struct OpModUpMacT {
     };
     __device__ Pre pre(int p, int u, int j) const
     {
-        const int ct = p / (L + 1), t = p % (L + 1);
+        const int ct = ct_of(p), t = t_of(p);
         const int tk = t == L ? Ltop : t;
         Pre r;
         r.k0 = __ldg(&ksk[(((size_t)u * 2 + 0) * (Ltop + 1) + tk) * N + j]);
@@ -261,7 +266,7 @@ struct OpModUpMacT {
     }
     __device__ void store(int p, int u, int j, u64 v, const Pre& pr, const PrimeC& Q) const
     {
-        const int ct = p / (L + 1), t = p % (L + 1);
+        const int ct = ct_of(p), t = t_of(p);
         if (t == u) v = d3.get(ct, 2, L, N, t, j, Q);                 // direct: NTT(d2_t) is d2_t
         u64* a0 = acc + (((size_t)ct * 2 + 0) * (L + 1) + t) * N + j;
         u64* a1 = acc + (((size_t)ct * 2 + 1) * (L + 1) + t) * N + j;
