@@ -69,9 +69,9 @@ typedef struct {
     uint32_t log_scale;  /* scale = 2^log_scale */
     uint64_t primes[64]; /* q_0 .. q_{L_top-1}, then the special prime P */
     uint64_t key_bytes;  /* device bytes held for keys and tables */
-    uint32_t ntt_variant;        /* NTT schedule the autotuner picked (0..5, 9) */
+    uint32_t ntt_variant;        /* NTT schedule the autotuner picked (0..5) */
     float ntt_variant_us[16];    /* autotuner: microseconds per transform of each schedule (0 = not timed) */
-    uint32_t ntt_variant_ks;     /* schedule of the key-switching inner-product transforms (0..9) */
+    uint32_t ntt_variant_ks;     /* schedule of the key-switching inner-product transforms (0..7) */
     float ntt_variant_ks_us[16]; /* autotuner: microseconds per digit transform of each schedule */
     uint64_t workspace_bytes;    /* device bytes of this context's call workspace and batch
                                     area (both grow on demand; 0 before the first call that
@@ -178,15 +178,13 @@ int fhe_gauss_table(uint64_t* out38);
  * here by timing each candidate on a rescale of 64 ciphertexts, and again
  * separately for the key-switching digit transforms (whose epilogue holds the
  * key inner product) on that step alone; the environment variable
- * FHE_NTT_VARIANT=0..9 fixes both instead (and FHE_NTT_VARIANT_KS, when set
- * with it, the key-switching one).  Schedules 6 and 8 split each
- * key-switching digit transform over two blocks (one per output half; radix
- * 16 with two blocks per SM, radix 8 with three); schedule 7 runs the
- * key-switching inner-product step on a cluster of four blocks per
- * (ciphertext, target prime), one per quarter of the coefficients, with the
- * accumulators in shared memory (N >= 256); the other transforms run as
- * schedule 5 under 6, 7 and 8.  Schedule 9 splits every forward transform
- * over two blocks and runs the inverse ones as schedule 4.  bits: coefficient-modulus bit sizes, the
+ * FHE_NTT_VARIANT=0..7 fixes both instead (and FHE_NTT_VARIANT_KS, when set
+ * with it, the key-switching one).  Schedule 6 splits each key-switching
+ * digit transform over two blocks (one per output half, two blocks per SM);
+ * schedule 7 runs the key-switching inner-product step on a cluster of four
+ * blocks per (ciphertext, target prime), one per quarter of the
+ * coefficients, with the accumulators in shared memory (N >= 256); the
+ * other transforms run as schedule 5 under either.  bits: coefficient-modulus bit sizes, the
  * last one being the special prime; log_scale: scale 2^log_scale.
  * N must be a power of two in [16, 65536]; above 16384 only the two-pass
  * NTT schedules exist and the grouped (uneven-level) calls are refused. */

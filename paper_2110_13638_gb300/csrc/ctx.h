@@ -308,7 +308,7 @@ uint64_t stream_key(uint64_t seed, uint64_t domain, uint64_t object);
 const char* ntt_variant_name(int v);
 // the ModUp cluster schedule (7) handles this ring
 bool modup_cluster_fits(const fhe_ctx* c);
-constexpr int kNttVariants = 10;  // schedules 6, 7 and 8 apply to the key-switching digit transforms only
+constexpr int kNttVariants = 8;   // schedules 6 and 7 apply to the key-switching digit transforms only
 inline bool ntt_two_pass(int v) { return v == 2 || v == 3; }
 constexpr uint32_t kMaxSinglePassN = 16384;   // one transform per block in shared memory
 

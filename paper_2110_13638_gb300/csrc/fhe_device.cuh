@@ -921,8 +921,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_ntt_io(Op op, NttTables T)
 // loads and epilogue overlap the other's butterflies.  The epilogue of each
 // half is independent (the key-switching digit transforms).
 // LOGR: radix of the register passes; MINB: blocks per SM the registers are
-// budgeted for (2 at radix 16, 3 at radix 8; the shared memory of a half
-// polynomial at N = 16384 allows three)
+// budgeted for
 template <int MAXT, int LOGR, int MINB, class Op>
 __global__ void __launch_bounds__(MAXT, MINB) k_ntt_half_io(Op op, NttTables T)
 {

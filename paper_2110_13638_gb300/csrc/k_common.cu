@@ -54,9 +54,6 @@ const char* ntt_variant_name(int v)
     case 6: return "key-switching digit transforms split over two blocks (one per output half), radix-16";
     case 7: return "key-switching digit transforms on a cluster of four blocks (one per coefficient quarter), "
                    "accumulators in shared memory";
-    case 8: return "key-switching digit transforms split over two blocks (one per output half), radix-8, three blocks "
-                   "per SM";
-    case 9: return "forward transforms split over two blocks (one per output half), radix-16; inverse as schedule 4";
     default: return "one block per transform, radix-16 passes, 512 threads";
     }
 }

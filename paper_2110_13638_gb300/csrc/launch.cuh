@@ -155,9 +155,8 @@ struct MultiOp {
     }
 };
 
-// forward transforms split over two blocks per residue polynomial (schedules
-// 6 and 8, key-switching digit transforms): radix 16 with two blocks per SM,
-// or radix 8 with three
+// forward transforms split over two blocks per residue polynomial (schedule
+// 6, key-switching digit transforms): radix 16 with two blocks per SM
 template <class Op, int LOGR = 4, int MINB = 2>
 static void launch_ntt_half(const fhe_ctx* c, const Op& op, int count, cudaStream_t st)
 {
@@ -226,29 +225,16 @@ static void launch_ntt(const fhe_ctx* c, const Op& op, cudaStream_t st, bool sin
     case 5: launch_ntt_v<INV, 4, 512, Op, true>(c, op, count, st); break;
     case 6:
     case 7:
-    case 8:
         // half transforms: forward key-switching digit transforms only; the
         // rest run as schedule 5 (schedule 7, the ModUp cluster kernel, is
         // launched by launch_modup; other key-switching ops take 6 under it)
         if constexpr (!INV && keyswitch_mac<Op>::value) {
             if (c->N >= 64) {
-                if (v == 8) launch_ntt_half<Op, 3, 3>(c, op, count, st);
-                else launch_ntt_half<Op, 4, 2>(c, op, count, st);
-                break;
-            }
-        }
-        launch_ntt_v<INV, 4, 512, Op, true>(c, op, count, st);
-        break;
-    case 9:
-        // every forward transform split over two blocks (radix 16, two
-        // blocks per SM), inverse transforms as schedule 4
-        if constexpr (!INV) {
-            if (c->N >= 64) {
                 launch_ntt_half<Op, 4, 2>(c, op, count, st);
                 break;
             }
         }
-        launch_ntt_v<INV, 3, 1024, Op, true>(c, op, count, st);
+        launch_ntt_v<INV, 4, 512, Op, true>(c, op, count, st);
         break;
     default: launch_ntt_v<INV, 4, 512>(c, op, count, st); break;
     }

@@ -517,11 +517,8 @@ void launch_groups_ks_divfwd(const fhe_ctx* c, const MultiOp<OpKsDivFwd>& m, cud
 void launch_modup_cluster(const fhe_ctx* c, const OpModUpMac& op, cudaStream_t st);
 
 // The ModUp step with the schedule the autotuner picked for it
-inline void launch_modup(const fhe_ctx* c, const OpModUpMac& op, cudaStream_t st, bool single_pass = false)
-{
-    if (c->ntt_variant_ks == 7 && modup_cluster_fits(c)) launch_modup_cluster(c, op, st);
-    else launch_ntt<false>(c, op, st, single_pass);
-}
+// (k_relin_modup.cu, the only unit that instantiates the ModUp kernels)
+void launch_modup(const fhe_ctx* c, const OpModUpMac& op, cudaStream_t st, bool single_pass = false);
 
 // The merged ModDown + rescale of one batch (k_relin.cu): ops of steps 4' and 5'.
 OpKsRowInv make_ks_row_inv(const fhe_ctx* c, const u64* d3, const u64* acc, const u64* Vp, u64* V, int n, int L,

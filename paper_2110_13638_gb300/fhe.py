@@ -291,9 +291,6 @@ NTT_SCHEDULES = (
     "key-switching digit transforms split over two blocks per polynomial (one per output half), 256 threads",
     "key-switching digit transforms on a cluster of four blocks (one per coefficient quarter), accumulators in "
     "shared memory",
-    "key-switching digit transforms split over two blocks per polynomial (one per output half), radix-8, three "
-    "blocks per SM",
-    "forward transforms split over two blocks per polynomial (one per output half), radix-16; inverse as schedule 4",
 )
 
 
@@ -317,9 +314,9 @@ class Context:
         self.primes = [int(info.primes[i]) for i in range(info.L_top + 1)]
         self.key_bytes = int(info.key_bytes)
         self.ntt_variant = int(info.ntt_variant)
-        self.ntt_variant_us = [float(info.ntt_variant_us[i]) for i in range(10)]
+        self.ntt_variant_us = [float(info.ntt_variant_us[i]) for i in range(8)]
         self.ntt_variant_ks = int(info.ntt_variant_ks)
-        self.ntt_variant_ks_us = [float(info.ntt_variant_ks_us[i]) for i in range(10)]
+        self.ntt_variant_ks_us = [float(info.ntt_variant_ks_us[i]) for i in range(8)]
         self.delta = float(2 ** log_scale)
 
     def fork(self):
