@@ -178,13 +178,16 @@ int fhe_gauss_table(uint64_t* out38);
  * here by timing each candidate on a rescale of 64 ciphertexts, and again
  * separately for the key-switching digit transforms (whose epilogue holds the
  * key inner product) on that step alone; the environment variable
- * FHE_NTT_VARIANT=0..7 fixes both instead (and FHE_NTT_VARIANT_KS, when set
+ * FHE_NTT_VARIANT=0..8 fixes both instead (and FHE_NTT_VARIANT_KS, when set
  * with it, the key-switching one).  Schedule 6 splits each key-switching
  * digit transform over two blocks (one per output half, two blocks per SM);
  * schedule 7 runs the key-switching inner-product step on a cluster of four
  * blocks per (ciphertext, target prime), one per quarter of the
  * coefficients, with the accumulators in shared memory (N >= 256); the
- * other transforms run as schedule 5 under either.  bits: coefficient-modulus bit sizes, the
+ * other transforms run as schedule 5 under either.  Schedule 8 (1024 <= N
+ * <= 16384, else schedule 5) runs each transform on N/32 threads: the first
+ * log2 N - 10 stages block-wide, then each warp a 1024-point sub-transform
+ * with warp-level synchronisation only.  bits: coefficient-modulus bit sizes, the
  * last one being the special prime; log_scale: scale 2^log_scale.
  * N must be a power of two in [16, 65536]; above 16384 only the two-pass
  * NTT schedules exist and the grouped (uneven-level) calls are refused. */

@@ -347,7 +347,7 @@ static int autotune_ntt(fhe_ctx* c)
         const char* env_ks = std::getenv("FHE_NTT_VARIANT_KS");
         const int v = std::atoi(env), vk = (env_ks && *env_ks) ? std::atoi(env_ks) : v;
         for (int x : {v, vk}) {
-            if (x < 0 || x >= kNttVariants) return fail(FHE_EINVAL, "FHE_NTT_VARIANT(_KS) out of range (0..7)");
+            if (x < 0 || x >= kNttVariants) return fail(FHE_EINVAL, "FHE_NTT_VARIANT(_KS) out of range (0..8)");
             if (c->N > kMaxSinglePassN && !ntt_two_pass(x))
                 return fail(FHE_EINVAL, "N > 16384 needs a two-pass NTT schedule (2 or 3)");
         }
@@ -391,7 +391,8 @@ static int autotune_ntt(fhe_ctx* c)
     float best = 1e30f;
     for (int v = 0; v < kNttVariants; ++v) {
         if (c->N > kMaxSinglePassN && !ntt_two_pass(v)) continue;   // one block per transform needs N <= 16384
-        if (v >= 6) continue;                                       // key-switching transforms only
+        if (ntt_ks_only(v)) continue;                               // key-switching transforms only
+        if (v == 8 && !ntt_wl_fits(c->logN)) continue;
         c->ntt_variant = v;
         work();                                                     // warm-up
         float us_best = 1e30f;
@@ -442,6 +443,7 @@ static int autotune_ntt(fhe_ctx* c)
             for (int v = 0; v < kNttVariants && e == cudaSuccess; ++v) {
                 if ((c->N > kMaxSinglePassN) != ntt_two_pass(v)) continue;
                 if (v == 7 && !modup_cluster_fits(c)) continue;
+                if (v == 8 && !ntt_wl_fits(c->logN)) continue;
                 c->ntt_variant_ks = v;
                 k_modup_mac_step(c, d3, D, ksk, acc, nk, Lk, nullptr);       // warm-up
                 float us_best = 1e30f;

@@ -308,8 +308,11 @@ uint64_t stream_key(uint64_t seed, uint64_t domain, uint64_t object);
 const char* ntt_variant_name(int v);
 // the ModUp cluster schedule (7) handles this ring
 bool modup_cluster_fits(const fhe_ctx* c);
-constexpr int kNttVariants = 8;   // schedules 6 and 7 apply to the key-switching digit transforms only
+constexpr int kNttVariants = 9;   // schedules 6 and 7 apply to the key-switching digit transforms only
 inline bool ntt_two_pass(int v) { return v == 2 || v == 3; }
+inline bool ntt_ks_only(int v) { return v == 6 || v == 7; }
+// the warp-local schedule (8) needs 1024 <= N <= 16384; below, schedule 5 stands in
+inline bool ntt_wl_fits(uint32_t logN) { return logN >= 10 && logN <= 14; }
 constexpr uint32_t kMaxSinglePassN = 16384;   // one transform per block in shared memory
 
 }  // namespace fhe

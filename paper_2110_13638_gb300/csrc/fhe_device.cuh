@@ -694,6 +694,116 @@ constexpr u64 kInvNoRedBound = 1ull << 46;
 // behind the group's loads and butterflies; put(R, j0, lsh, x, fetched).
 struct NoFetch {};
 
+// The butterflies of one group: the 2^K values x[i] = a[j0 + i 2^lsh] of a
+// pass starting at global stage s0, g being the group's index at that stage
+// (forward: j >> (logN - s0); inverse: j >> (s0 + K)).
+//  - forward, stage s0 + l: pairs (i, i + h), h = 2^(K-1-l), i = m 2h + t,
+//    twiddle psi_rev[2^(s0+l) + g 2^l + m];
+//  - inverse, stage s0 + l: pairs (i, i + h), h = 2^l, i = m 2h + t,
+//    twiddle psi_rev^-1[N / 2^(s0+l+1) + g 2^(K-1-l) + m].
+// Each stage is its own instantiation (bfly_*_from<K, RED, l>), so every loop
+// has a constant trip count and x stays in registers (with the stage index a
+// loop variable the inverse kept x in local memory).
+template <int K, bool RED, int l>
+__device__ __forceinline__ void bfly_fwd_from(u64* x, const ulonglong2* __restrict__ tw, int s0, int g, u64 q, u64 q2)
+{
+    if constexpr (l < K) {
+        constexpr int R = 1 << K, h = R >> (l + 1);
+        const ulonglong2* twl = tw + (1 << (s0 + l)) + (g << l);
+#pragma unroll
+        for (int m = 0; m < (1 << l); ++m) {
+            const ulonglong2 w = __ldg(&twl[m]);
+#pragma unroll
+            for (int t = 0; t < h; ++t) {
+                const int i = m * 2 * h + t;
+                u64 X = x[i];
+                if (RED) X = X >= q2 ? X - q2 : X;
+                const u64 T = mul_shoup_lazy(x[i + h], w.x, w.y, q);
+                x[i] = X + T;
+                x[i + h] = X + q2 - T;
+            }
+        }
+        bfly_fwd_from<K, RED, l + 1>(x, tw, s0, g, q, q2);
+    }
+}
+
+template <int K, bool RED>
+__device__ __forceinline__ void bfly_fwd(u64* x, const ulonglong2* __restrict__ tw, int s0, int g, u64 q, u64 q2)
+{
+    bfly_fwd_from<K, RED, 0>(x, tw, s0, g, q, q2);
+}
+
+template <int K, bool RED, int l>
+__device__ __forceinline__ void bfly_inv_from(u64* x, const ulonglong2* __restrict__ tw, int N, int s0, int g, u64 q,
+                                              u64 q2)
+{
+    if constexpr (l < K) {
+        constexpr int R = 1 << K, h = 1 << l;
+        const ulonglong2* twl = tw + (N >> (s0 + l + 1)) + (g << (K - l - 1));
+        const u64 c = RED ? q2 : (q2 << (s0 + l));       // bound of Y at this stage
+#pragma unroll
+        for (int m = 0; m < (R >> (l + 1)); ++m) {
+            const ulonglong2 w = __ldg(&twl[m]);
+#pragma unroll
+            for (int t = 0; t < h; ++t) {
+                const int i = m * 2 * h + t;
+                const u64 X = x[i], Y = x[i + h];
+                u64 S = X + Y;
+                if (RED) S = S >= q2 ? S - q2 : S;
+                x[i] = S;
+                x[i + h] = mul_shoup_lazy(X + c - Y, w.x, w.y, q);
+            }
+        }
+        bfly_inv_from<K, RED, l + 1>(x, tw, N, s0, g, q, q2);
+    }
+}
+
+template <int K, bool RED>
+__device__ __forceinline__ void bfly_inv(u64* x, const ulonglong2* __restrict__ tw, int logN, int s0, int g, u64 q,
+                                         u64 q2)
+{
+    bfly_inv_from<K, RED, 0>(x, tw, 1 << logN, s0, g, q, q2);
+}
+
+// Five stages on 32 values as one stage over all of them and two independent
+// 16-value groups (forward; the inverse in the opposite order), so fewer
+// twiddles are live at once than in one 32-value group (less spilling).
+template <bool RED>
+__device__ __forceinline__ void bfly_fwd32(u64* x, const ulonglong2* __restrict__ tw, int s0, int g, u64 q, u64 q2)
+{
+    {
+        const ulonglong2 w = __ldg(&tw[(1 << s0) + g]);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            u64 X = x[i];
+            if (RED) X = X >= q2 ? X - q2 : X;
+            const u64 T = mul_shoup_lazy(x[i + 16], w.x, w.y, q);
+            x[i] = X + T;
+            x[i + 16] = X + q2 - T;
+        }
+    }
+    bfly_fwd<4, RED>(x, tw, s0 + 1, 2 * g, q, q2);
+    bfly_fwd<4, RED>(x + 16, tw, s0 + 1, 2 * g + 1, q, q2);
+}
+
+template <bool RED>
+__device__ __forceinline__ void bfly_inv32(u64* x, const ulonglong2* __restrict__ tw, int logN, int s0, int g, u64 q,
+                                           u64 q2)
+{
+    bfly_inv<4, RED>(x, tw, logN, s0, 2 * g, q, q2);
+    bfly_inv<4, RED>(x + 16, tw, logN, s0, 2 * g + 1, q, q2);
+    const ulonglong2 w = __ldg(&tw[((1 << logN) >> (s0 + 5)) + g]);
+    const u64 c = RED ? q2 : (q2 << (s0 + 4));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const u64 X = x[i], Y = x[i + 16];
+        u64 S = X + Y;
+        if (RED) S = S >= q2 ? S - q2 : S;
+        x[i] = S;
+        x[i + 16] = mul_shoup_lazy(X + c - Y, w.x, w.y, q);
+    }
+}
+
 // sh, goff (forward only): the pass works on one half of a larger transform
 // (k_ntt_half_io): its local stage s is global stage s + sh, and its local
 // group g is global group g + goff at the pass's first stage.
@@ -712,46 +822,8 @@ __device__ __forceinline__ void pass_io(int logN, int s0, const ulonglong2* __re
         auto fetched = fetch(std::integral_constant<int, R>{}, j0, lsh);
         u64 x[R];
         get(std::integral_constant<int, R>{}, j0, lsh, x);
-        if (!INV) {
-#pragma unroll
-            for (int l = 0; l < K; ++l) {
-                const int h = R >> (l + 1);
-                const ulonglong2* twl = tw + (1 << (s0 + l + sh)) + ((g + goff) << l);
-#pragma unroll
-                for (int m = 0; m < (1 << l); ++m) {
-                    const ulonglong2 w = __ldg(&twl[m]);
-#pragma unroll
-                    for (int t = 0; t < h; ++t) {
-                        const int i = m * 2 * h + t;
-                        u64 X = x[i];
-                        if (RED) X = X >= q2 ? X - q2 : X;
-                        const u64 T = mul_shoup_lazy(x[i + h], w.x, w.y, q);
-                        x[i] = X + T;
-                        x[i + h] = X + q2 - T;
-                    }
-                }
-            }
-        } else {
-#pragma unroll
-            for (int l = 0; l < K; ++l) {
-                const int h = 1 << l;
-                const ulonglong2* twl = tw + (N >> (s0 + l + 1)) + (g << (K - l - 1));
-                const u64 c = RED ? q2 : (q2 << (s0 + l));       // bound of Y at this stage
-#pragma unroll
-                for (int m = 0; m < (R >> (l + 1)); ++m) {
-                    const ulonglong2 w = __ldg(&twl[m]);
-#pragma unroll
-                    for (int t = 0; t < h; ++t) {
-                        const int i = m * 2 * h + t;
-                        const u64 X = x[i], Y = x[i + h];
-                        u64 S = X + Y;
-                        if (RED) S = S >= q2 ? S - q2 : S;
-                        x[i] = S;
-                        x[i + h] = mul_shoup_lazy(X + c - Y, w.x, w.y, q);
-                    }
-                }
-            }
-        }
+        if (!INV) bfly_fwd<K, RED>(x, tw, s0 + sh, g + goff, q, q2);
+        else bfly_inv<K, RED>(x, tw, logN, s0, g, q, q2);
         put(std::integral_constant<int, R>{}, j0, lsh, x, fetched);
     }
 }
@@ -907,6 +979,201 @@ __global__ void __launch_bounds__(MAXT, 1) k_ntt_io(Op op, NttTables T)
 {
     extern __shared__ u64 sm[];
     for (int p = blockIdx.x; p < op.count(); p += gridDim.x) ntt_io_unit<INV, LOGR, MAXT>(op, T, p, sm);
+}
+
+// ---------------------------------------------------------------- warp-local transforms
+// One block of N/32 threads per residue polynomial, 1024 <= N <= 16384.
+// After the first logN - 10 stages (distances N/2 .. 1024, forward) the
+// array falls apart into N/1024 independent 1024-point problems on
+// contiguous blocks; warp w owns block [1024 w, 1024 w + 1024), 32 values
+// per lane, and runs its ten stages with warp-level synchronisation only:
+//   five stages with lane l holding elements 1024 w + l + 32 i (i = 0..31:
+//   the pairs at distances 512 .. 32 are in one lane), then, after a
+//   transpose through shared memory, five with lane l holding 1024 w + 32 l
+//   + i (distances 16 .. 1).
+// So a forward transform takes one block-wide barrier (after the first
+// logN - 10 stages, done by the whole block on groups of 2^(logN-10) values
+// at stride 1024) instead of one per register pass, and every global access
+// (the prologue's loads, the epilogue's loads and stores, which go through
+// shared memory once more) is coalesced.  The inverse runs the same steps in
+// the opposite order (warp stages 0..9, barrier, block stages 10..logN-1).
+// Shared-memory word j sits at j + j/32: conflict-free for lanes reading
+// consecutive words and for lanes reading words 32 apart.
+__device__ __forceinline__ int wpad(int j) { return j + (j >> 5); }
+
+__host__ __device__ constexpr int ntt_wl_smem_words(int N) { return N + (N >> 5); }
+
+constexpr int kWlEpiBatch = 8;
+
+// the block stages of a forward transform (0 .. KA-1, KA = logN - 10):
+// group gi in [0, 1024) is the 2^KA values gi + 1024 i, read by the prologue
+template <int KA, bool RED, class Op>
+__device__ __forceinline__ void wl_fwd_block(const Op& op, int p, int u, const PrimeC& P,
+                                             const ulonglong2* __restrict__ tw, u64* sm, int tid, int nthr)
+{
+    constexpr int R = 1 << KA;
+#pragma unroll 1
+    for (int gi = tid; gi < 1024; gi += nthr) {
+        u64 x[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) x[i] = op.load(p, u, gi + (i << 10), P);
+        bfly_fwd<KA, RED>(x, tw, 0, 0, P.q, P.q2);
+#pragma unroll
+        for (int i = 0; i < R; ++i) sm[wpad(gi + (i << 10))] = x[i];
+    }
+}
+
+// the block stages of an inverse transform (10 .. logN-1) from shared memory,
+// each group's outputs (times N^-1) handed to the epilogue
+template <int KA, bool RED, class Op>
+__device__ __forceinline__ void wl_inv_block(const Op& op, int p, int u, const PrimeC& P,
+                                             const ulonglong2* __restrict__ tw, const u64* sm, int logN, int tid,
+                                             int nthr)
+{
+    constexpr int R = 1 << KA;
+    constexpr int B = R < kWlEpiBatch ? R : kWlEpiBatch;
+#pragma unroll 1
+    for (int gi = tid; gi < 1024; gi += nthr) {
+        u64 x[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) x[i] = sm[wpad(gi + (i << 10))];
+        bfly_inv<KA, RED>(x, tw, logN, 10, 0, P.q, P.q2);
+#pragma unroll
+        for (int i0 = 0; i0 < R; i0 += B) {
+            typename Op::Pre pr[B];
+#pragma unroll
+            for (int i = 0; i < B; ++i) pr[i] = op.pre(p, u, gi + ((i0 + i) << 10));
+#pragma unroll
+            for (int i = 0; i < B; ++i) op.store(p, u, gi + ((i0 + i) << 10), inv_final(x[i0 + i], P), pr[i], P);
+        }
+    }
+}
+
+// sub-transform u of unit p
+template <bool INV, bool RED, class Op>
+__device__ __forceinline__ void wl_transform(const Op& op, int p, int u, const PrimeC& P,
+                                             const ulonglong2* __restrict__ tw, u64* sm, int logN)
+{
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int w = tid >> 5, l = tid & 31, b = w << 10;
+    const int KA = logN - 10;
+    const u64 q = P.q, q2 = P.q2;
+    u64 x[32];
+    if (!INV) {
+        if (KA == 0) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) x[i] = op.load(p, u, l + 32 * i, P);
+        } else {
+            switch (KA) {
+            case 1: wl_fwd_block<1, RED>(op, p, u, P, tw, sm, tid, nthr); break;
+            case 2: wl_fwd_block<2, RED>(op, p, u, P, tw, sm, tid, nthr); break;
+            case 3: wl_fwd_block<3, RED>(op, p, u, P, tw, sm, tid, nthr); break;
+            default: wl_fwd_block<4, RED>(op, p, u, P, tw, sm, tid, nthr); break;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < 32; ++i) x[i] = sm[wpad(b + l + 32 * i)];
+        }
+        // stages KA .. KA+4 (distances 512 .. 32 within the block of warp w)
+        bfly_fwd32<RED>(x, tw, KA, w, q, q2);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) sm[wpad(b + l + 32 * i)] = x[i];
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 32; ++i) x[i] = sm[wpad(b + 32 * l + i)];
+        // stages KA+5 .. logN-1 (distances 16 .. 1)
+        bfly_fwd32<RED>(x, tw, KA + 5, 32 * w + l, q, q2);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) sm[wpad(b + 32 * l + i)] = x[i];
+        __syncwarp();
+        // epilogue, coalesced: element b + l + 32 i
+#pragma unroll 1
+        for (int i0 = 0; i0 < 32; i0 += kWlEpiBatch) {
+            typename Op::Pre pr[kWlEpiBatch];
+#pragma unroll
+            for (int i = 0; i < kWlEpiBatch; ++i) pr[i] = op.pre(p, u, b + l + 32 * (i0 + i));
+#pragma unroll
+            for (int i = 0; i < kWlEpiBatch; ++i) {
+                const int j = b + l + 32 * (i0 + i);
+                const u64 v = sm[wpad(j)];
+                op.store(p, u, j, RED ? fwd_out<Op>(v, q) : fwd_out_wide<Op>(v, P), pr[i], P);
+            }
+        }
+    } else {
+        // coalesced loads, transposed through shared memory
+#pragma unroll
+        for (int i = 0; i < 32; ++i) x[i] = op.load(p, u, b + l + 32 * i, P);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) sm[wpad(b + l + 32 * i)] = x[i];
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 32; ++i) x[i] = sm[wpad(b + 32 * l + i)];
+        // stages 0 .. 4 (distances 1 .. 16)
+        bfly_inv32<RED>(x, tw, logN, 0, 32 * w + l, q, q2);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) sm[wpad(b + 32 * l + i)] = x[i];
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 32; ++i) x[i] = sm[wpad(b + l + 32 * i)];
+        // stages 5 .. 9 (distances 32 .. 512)
+        bfly_inv32<RED>(x, tw, logN, 5, w, q, q2);
+        if (KA == 0) {
+#pragma unroll
+            for (int i0 = 0; i0 < 32; i0 += kWlEpiBatch) {
+                typename Op::Pre pr[kWlEpiBatch];
+#pragma unroll
+                for (int i = 0; i < kWlEpiBatch; ++i) pr[i] = op.pre(p, u, l + 32 * (i0 + i));
+#pragma unroll
+                for (int i = 0; i < kWlEpiBatch; ++i)
+                    op.store(p, u, l + 32 * (i0 + i), inv_final(x[i0 + i], P), pr[i], P);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) sm[wpad(b + l + 32 * i)] = x[i];
+            __syncthreads();
+            switch (KA) {
+            case 1: wl_inv_block<1, RED>(op, p, u, P, tw, sm, logN, tid, nthr); break;
+            case 2: wl_inv_block<2, RED>(op, p, u, P, tw, sm, logN, tid, nthr); break;
+            case 3: wl_inv_block<3, RED>(op, p, u, P, tw, sm, logN, tid, nthr); break;
+            default: wl_inv_block<4, RED>(op, p, u, P, tw, sm, logN, tid, nthr); break;
+            }
+        }
+    }
+}
+
+// one unit p (all its sub-transforms) by the calling block of N/32 threads;
+// shared memory sm holds ntt_wl_smem_words(N) words
+template <bool INV, class Op>
+__device__ __forceinline__ void ntt_wl_unit(const Op& op, const NttTables& T, int p, u64* sm)
+{
+    const int logN = T.logN;
+    const int N = 1 << logN;
+    const int ns = op.nsub(p);
+    for (int u = 0; u < ns; ++u) {
+        const int pi = op.prime(p, u);
+        const PrimeC& P = T.pc[pi];
+        if (op.direct(p, u)) {
+            for (int j = threadIdx.x; j < N; j += blockDim.x) op.store(p, u, j, 0, op.pre(p, u, j), P);
+        } else {
+            const ulonglong2* tw = (INV ? T.tw_inv : T.tw_fwd) + (size_t)pi * N;
+            const bool wide = !cold_path<Op>::value && P.q < (INV ? kInvNoRedBound : kFwdNoRedBound);  // block-uniform
+            if constexpr (cold_path<Op>::value) {
+                wl_transform<INV, true>(op, p, u, P, tw, sm, logN);
+            } else {
+                if (wide) wl_transform<INV, false>(op, p, u, P, tw, sm, logN);
+                else wl_transform<INV, true>(op, p, u, P, tw, sm, logN);
+            }
+        }
+        // the next sub-transform rewrites shared memory
+        __syncthreads();
+    }
+}
+
+template <bool INV, class Op>
+__global__ void __launch_bounds__(512, 1) k_ntt_wl(Op op, NttTables T)
+{
+    extern __shared__ u64 sm[];
+    for (int p = blockIdx.x; p < op.count(); p += gridDim.x) ntt_wl_unit<INV>(op, T, p, sm);
 }
 
 // ---------------------------------------------------------------- half transforms

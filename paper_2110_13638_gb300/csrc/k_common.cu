@@ -54,6 +54,8 @@ const char* ntt_variant_name(int v)
     case 6: return "key-switching digit transforms split over two blocks (one per output half), radix-16";
     case 7: return "key-switching digit transforms on a cluster of four blocks (one per coefficient quarter), "
                    "accumulators in shared memory";
+    case 8: return "one block of N/32 threads per transform: the first log2 N - 10 stages block-wide, then each "
+                   "warp runs a 1024-point sub-transform, 32 values per lane (one block barrier per transform)";
     default: return "one block per transform, radix-16 passes, 512 threads";
     }
 }

@@ -169,6 +169,18 @@ static void launch_ntt_half(const fhe_ctx* c, const Op& op, int count, cudaStrea
     fn<<<2 * count, thr, smem, st>>>(op, c->tabs());
 }
 
+// warp-local transforms (schedule 8): one block of N/32 threads per unit
+template <bool INV, class Op>
+static void launch_ntt_wl(const fhe_ctx* c, const Op& op, int count, cudaStream_t st)
+{
+    const int N = (int)c->N;
+    const size_t smem = (size_t)ntt_wl_smem_words(N) * sizeof(u64);
+    auto fn = k_ntt_wl<INV, Op>;
+    ensure_smem((const void*)fn, smem);
+    LaunchScope ls(c, Op::family(), st);
+    fn<<<count, N / 32, smem, st>>>(op, c->tabs());
+}
+
 template <class Op> struct uniform_subs { static constexpr bool value = true; };
 template <class Op> struct uniform_subs<MultiOp<Op>> { static constexpr bool value = false; };
 
@@ -235,6 +247,10 @@ static void launch_ntt(const fhe_ctx* c, const Op& op, cudaStream_t st, bool sin
             }
         }
         launch_ntt_v<INV, 4, 512, Op, true>(c, op, count, st);
+        break;
+    case 8:
+        if (ntt_wl_fits(c->logN)) launch_ntt_wl<INV>(c, op, count, st);
+        else launch_ntt_v<INV, 4, 512, Op, true>(c, op, count, st);
         break;
     default: launch_ntt_v<INV, 4, 512>(c, op, count, st); break;
     }

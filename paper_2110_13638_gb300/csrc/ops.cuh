@@ -228,11 +228,10 @@ struct OpModUpMacT {
                             // products, each below 2 q_t, then sum below 2 L q_t < 2^64
     __host__ __device__ int count() const { return n * (L + 1); }
     __host__ __device__ int nsub(int) const { return L; }
-    // unit p: the n L units of the data-prime targets first, then the n units
-    // of the special prime, so a launch runs the (reduced-butterfly) P units
-    // together at its end instead of interleaved with the others
-    __host__ __device__ __forceinline__ int ct_of(int p) const { return p < n * L ? p / L : p - n * L; }
-    __host__ __device__ __forceinline__ int t_of(int p) const { return p < n * L ? p % L : L; }
+    // unit p = ct (L + 1) + t: the L + 1 targets of one ciphertext run side
+    // by side and share its digits' reads from L2
+    __host__ __device__ __forceinline__ int ct_of(int p) const { return p / (L + 1); }
+    __host__ __device__ __forceinline__ int t_of(int p) const { return p % (L + 1); }
     __device__ int prime(int p, int) const
     {
         const int t = t_of(p);

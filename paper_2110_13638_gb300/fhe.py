@@ -291,6 +291,8 @@ NTT_SCHEDULES = (
     "key-switching digit transforms split over two blocks per polynomial (one per output half), 256 threads",
     "key-switching digit transforms on a cluster of four blocks (one per coefficient quarter), accumulators in "
     "shared memory",
+    "warp-local: the first log2 N - 10 stages block-wide, then one 1024-point sub-transform per warp, 32 values "
+    "per lane",
 )
 
 

@@ -184,7 +184,7 @@ def test_dense_square_full_matches_fp64():
     c.close()
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8])
 def test_every_ntt_schedule_bit_exact(octx, variant):
     __graft_entry__.build()
     os.environ["FHE_NTT_VARIANT"] = str(variant)

@@ -403,7 +403,7 @@ def test_masquerade_cnn_bit_exact_per_group():
     net.close()
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8])
 @pytest.mark.parametrize("N", [256, 4096])
 def test_every_schedule_at_small_rings(N, variant):
     """Rings whose last register pass is a full radix-16 pass (log2 N a
@@ -455,6 +455,38 @@ def test_split_transform_schedules_every_pass_split(N, variant):
     t3 = upload(g, [D3], L)
     r = g.empty_ct(1, L)
     g.relinearise(t3, L, r)
+    assert np.array_equal(download(g, r, L)[0], o.relinearise(ckks.Ciphertext(D3, L, 1.0)).c)
+    A, B = rand_ct(o, L, rng), rand_ct(o, L, rng)
+    out = g.empty_ct(1, L - 1)
+    g.mul_relin_rescale(upload(g, [A], L), upload(g, [B], L), L, out)
+    want = o.rescale(o.relinearise(o.tensor(ckks.Ciphertext(A, L, 1.0), ckks.Ciphertext(B, L, 1.0)))).c
+    assert np.array_equal(download(g, out, L - 1)[0], want)
+    g.close()
+
+
+@pytest.mark.parametrize("N", [512, 1024, 2048, 8192])
+def test_warp_local_schedule_every_block_stage_count(N):
+    """Schedule 8 (warp-local transforms) with 0, 1 and 3 block-wide stages
+    before the per-warp 1024-point sub-transforms, and below 1024 its
+    stand-in: relinearisation and mul + relinearise + rescale equal the
+    oracle's (forward and inverse transforms, both butterfly forms: the
+    60-bit primes take the reduced one)."""
+    import os
+    bits = [60, 40, 40, 40, 60]
+    os.environ["FHE_NTT_VARIANT"] = "8"
+    try:
+        g = fhe.Context(N, bits, 40)
+    finally:
+        del os.environ["FHE_NTT_VARIANT"]
+    assert g.ntt_variant == 8 and g.ntt_variant_ks == 8
+    g.keygen(0)
+    o = ckks.Context(N, bits, 40)
+    o.keygen(0)
+    rng = np.random.default_rng(N + 8)
+    L = 4
+    D3 = rand_ct(o, L, rng, comps=3)
+    r = g.empty_ct(1, L)
+    g.relinearise(upload(g, [D3], L), L, r)
     assert np.array_equal(download(g, r, L)[0], o.relinearise(ckks.Ciphertext(D3, L, 1.0)).c)
     A, B = rand_ct(o, L, rng), rand_ct(o, L, rng)
     out = g.empty_ct(1, L - 1)
