@@ -1049,7 +1049,9 @@ __device__ __forceinline__ void wl_inv_block(const Op& op, int p, int u, const P
     }
 }
 
-// sub-transform u of unit p
+// sub-transform u of unit p; warps beyond the N/1024 that own a
+// sub-transform (a block larger than N/32 threads) only take part in the
+// block stages and barriers
 template <bool INV, bool RED, class Op>
 __device__ __forceinline__ void wl_transform(const Op& op, int p, int u, const PrimeC& P,
                                              const ulonglong2* __restrict__ tw, u64* sm, int logN)
@@ -1057,13 +1059,11 @@ __device__ __forceinline__ void wl_transform(const Op& op, int p, int u, const P
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int w = tid >> 5, l = tid & 31, b = w << 10;
     const int KA = logN - 10;
+    const bool owner = w < (1 << KA);
     const u64 q = P.q, q2 = P.q2;
     u64 x[32];
     if (!INV) {
-        if (KA == 0) {
-#pragma unroll
-            for (int i = 0; i < 32; ++i) x[i] = op.load(p, u, l + 32 * i, P);
-        } else {
+        if (KA > 0) {
             switch (KA) {
             case 1: wl_fwd_block<1, RED>(op, p, u, P, tw, sm, tid, nthr); break;
             case 2: wl_fwd_block<2, RED>(op, p, u, P, tw, sm, tid, nthr); break;
@@ -1071,6 +1071,12 @@ __device__ __forceinline__ void wl_transform(const Op& op, int p, int u, const P
             default: wl_fwd_block<4, RED>(op, p, u, P, tw, sm, tid, nthr); break;
             }
             __syncthreads();
+        }
+        if (!owner) return;
+        if (KA == 0) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) x[i] = op.load(p, u, l + 32 * i, P);
+        } else {
 #pragma unroll
             for (int i = 0; i < 32; ++i) x[i] = sm[wpad(b + l + 32 * i)];
         }
@@ -1100,36 +1106,40 @@ __device__ __forceinline__ void wl_transform(const Op& op, int p, int u, const P
             }
         }
     } else {
-        // coalesced loads, transposed through shared memory
+        if (owner) {
+            // coalesced loads, transposed through shared memory
 #pragma unroll
-        for (int i = 0; i < 32; ++i) x[i] = op.load(p, u, b + l + 32 * i, P);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) sm[wpad(b + l + 32 * i)] = x[i];
-        __syncwarp();
-#pragma unroll
-        for (int i = 0; i < 32; ++i) x[i] = sm[wpad(b + 32 * l + i)];
-        // stages 0 .. 4 (distances 1 .. 16)
-        bfly_inv32<RED>(x, tw, logN, 0, 32 * w + l, q, q2);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) sm[wpad(b + 32 * l + i)] = x[i];
-        __syncwarp();
-#pragma unroll
-        for (int i = 0; i < 32; ++i) x[i] = sm[wpad(b + l + 32 * i)];
-        // stages 5 .. 9 (distances 32 .. 512)
-        bfly_inv32<RED>(x, tw, logN, 5, w, q, q2);
-        if (KA == 0) {
-#pragma unroll
-            for (int i0 = 0; i0 < 32; i0 += kWlEpiBatch) {
-                typename Op::Pre pr[kWlEpiBatch];
-#pragma unroll
-                for (int i = 0; i < kWlEpiBatch; ++i) pr[i] = op.pre(p, u, l + 32 * (i0 + i));
-#pragma unroll
-                for (int i = 0; i < kWlEpiBatch; ++i)
-                    op.store(p, u, l + 32 * (i0 + i), inv_final(x[i0 + i], P), pr[i], P);
-            }
-        } else {
+            for (int i = 0; i < 32; ++i) x[i] = op.load(p, u, b + l + 32 * i, P);
 #pragma unroll
             for (int i = 0; i < 32; ++i) sm[wpad(b + l + 32 * i)] = x[i];
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 32; ++i) x[i] = sm[wpad(b + 32 * l + i)];
+            // stages 0 .. 4 (distances 1 .. 16)
+            bfly_inv32<RED>(x, tw, logN, 0, 32 * w + l, q, q2);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) sm[wpad(b + 32 * l + i)] = x[i];
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 32; ++i) x[i] = sm[wpad(b + l + 32 * i)];
+            // stages 5 .. 9 (distances 32 .. 512)
+            bfly_inv32<RED>(x, tw, logN, 5, w, q, q2);
+            if (KA == 0) {
+#pragma unroll
+                for (int i0 = 0; i0 < 32; i0 += kWlEpiBatch) {
+                    typename Op::Pre pr[kWlEpiBatch];
+#pragma unroll
+                    for (int i = 0; i < kWlEpiBatch; ++i) pr[i] = op.pre(p, u, l + 32 * (i0 + i));
+#pragma unroll
+                    for (int i = 0; i < kWlEpiBatch; ++i)
+                        op.store(p, u, l + 32 * (i0 + i), inv_final(x[i0 + i], P), pr[i], P);
+                }
+                return;
+            }
+#pragma unroll
+            for (int i = 0; i < 32; ++i) sm[wpad(b + l + 32 * i)] = x[i];
+        }
+        if (KA > 0) {
             __syncthreads();
             switch (KA) {
             case 1: wl_inv_block<1, RED>(op, p, u, P, tw, sm, logN, tid, nthr); break;
@@ -1141,8 +1151,8 @@ __device__ __forceinline__ void wl_transform(const Op& op, int p, int u, const P
     }
 }
 
-// one unit p (all its sub-transforms) by the calling block of N/32 threads;
-// shared memory sm holds ntt_wl_smem_words(N) words
+// one unit p (all its sub-transforms) by the calling block of at least N/32
+// threads (a multiple of 32); shared memory sm holds ntt_wl_smem_words(N) words
 template <bool INV, class Op>
 __device__ __forceinline__ void ntt_wl_unit(const Op& op, const NttTables& T, int p, u64* sm)
 {

@@ -36,6 +36,7 @@ __global__ void k_sample_enc_kernel(int8_t* __restrict__ S, int n, int N, u64 se
 // per (ct, r): sub 0 = u, sub 1 = e0, sub 2 = e1
 struct OpEncrypt {
     static const char* family() { return "encrypt"; }
+    static constexpr bool kTransformBound = true;   // int8 samples in; three transforms per output pair
     const u64* pt;      // [n][Ltop][N]
     const u64* pk;      // [2][Ltop][N]
     const u64* pks;     // their Shoup quotients

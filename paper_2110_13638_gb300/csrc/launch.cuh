@@ -100,11 +100,21 @@ struct keyswitch_mac : std::false_type {};
 template <class Op>
 struct keyswitch_mac<Op, std::void_t<decltype(Op::kKeySwitchMac)>> : std::integral_constant<bool, Op::kKeySwitchMac> {};
 
+// Ops that declare  static constexpr bool kTransformBound = true  (prologue
+// and epilogue light on HBM: encryption's samples, the digit inverses) also
+// run with the key-switching pick, whose probe is transform-bound too.
+template <class Op, class = void>
+struct transform_bound : std::false_type {};
+template <class Op>
+struct transform_bound<Op, std::void_t<decltype(Op::kTransformBound)>>
+    : std::integral_constant<bool, Op::kTransformBound> {};
+
 template <class Op>
 struct MultiOp {
     static const char* family() { return Op::family(); }
     static constexpr bool kLazyStore = lazy_store<Op>::value;
     static constexpr bool kKeySwitchMac = keyswitch_mac<Op>::value;
+    static constexpr bool kTransformBound = transform_bound<Op>::value;
     typedef typename Op::Pre Pre;
     Op ops[kMaxGroups];
     int pre_[kMaxGroups + 1];
@@ -227,7 +237,7 @@ static void launch_ntt(const fhe_ctx* c, const Op& op, cudaStream_t st, bool sin
     // the two-pass schedule needs the same number of transforms in every unit
     // (callers refuse single-pass-only work above kMaxSinglePassN)
     const bool single = single_pass || !uniform_subs<Op>::value;
-    const int base = keyswitch_mac<Op>::value ? c->ntt_variant_ks : c->ntt_variant;
+    const int base = keyswitch_mac<Op>::value || transform_bound<Op>::value ? c->ntt_variant_ks : c->ntt_variant;
     const int v = single && (base == 2 || base == 3) ? 1 : base;
     switch (v) {
     case 1: launch_ntt_v<INV, 3, 1024>(c, op, count, st); break;

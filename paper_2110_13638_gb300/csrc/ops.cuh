@@ -166,6 +166,7 @@ struct D3Src<true> {
 template <bool TENSOR>
 struct OpDigitsInvT {
     static const char* family() { return "keyswitch_intt"; }
+    static constexpr bool kTransformBound = true;   // one row in, one row out
     D3Src<TENSOR> d3;   // [n][3][L][N]
     u64* D;             // [n][L][N]
     int n, L, N;
