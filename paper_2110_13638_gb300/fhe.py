@@ -316,9 +316,9 @@ class Context:
         self.primes = [int(info.primes[i]) for i in range(info.L_top + 1)]
         self.key_bytes = int(info.key_bytes)
         self.ntt_variant = int(info.ntt_variant)
-        self.ntt_variant_us = [float(info.ntt_variant_us[i]) for i in range(8)]
+        self.ntt_variant_us = [float(info.ntt_variant_us[i]) for i in range(len(NTT_SCHEDULES))]
         self.ntt_variant_ks = int(info.ntt_variant_ks)
-        self.ntt_variant_ks_us = [float(info.ntt_variant_ks_us[i]) for i in range(8)]
+        self.ntt_variant_ks_us = [float(info.ntt_variant_ks_us[i]) for i in range(len(NTT_SCHEDULES))]
         self.delta = float(2 ** log_scale)
 
     def fork(self):
