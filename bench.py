@@ -36,10 +36,10 @@ PEAK_KINDS = {0: "IMAD (32-bit multiply-add)", 1: "IMAD.WIDE (32x32->64 multiply
 BUTTERFLY = 3
 # DRAM bytes (read + write) of the key-switching ModUp + key-product kernel
 # per (ciphertext, target prime, digit) unit, from one ncu capture of that
-# kernel (schedule 6, two blocks per polynomial) on 64 ciphertexts at L = 7
-# (--workload relin): 241.3 MB read + 133.4 MB written over 64 * 8 * 7 units.
+# kernel (schedule 8, warp-local transforms) on 64 ciphertexts at L = 7
+# (--workload relin): 249.6 MB read + 157.9 MB written over 64 * 8 * 7 units.
 # Scaled by units to the bench's launches.
-KS_DRAM_BYTES_PER_UNIT = (241.323008e6 + 133.441280e6) / (64 * 8 * 7)
+KS_DRAM_BYTES_PER_UNIT = (249.621504e6 + 157.850624e6) / (64 * 8 * 7)
 
 
 def _env_rank():
@@ -512,6 +512,61 @@ def run_relin(args):
                       "clocks": clk, "roofline": roof}), flush=True)
 
 
+def run_mrr(args):
+    """ct-mult + relinearise + rescale of --batch-cts random ciphertext pairs at
+    --level, N = 16384, [60, 40 x 7, 60]: one level per call (the merged
+    ModDown + rescale path the graph takes after an activation's square; also
+    the small case of the ncu captures of the rescale-type transforms)."""
+    import torch
+    import __graft_entry__
+    from paper_2110_13638_gb300 import fhe
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    N = 16384
+    ctx = fhe.Context(N, [60] + [40] * 7 + [60], 40)
+    ctx.keygen(0)
+    n, L = args.batch_cts, args.level
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1)
+    a = torch.empty((n, 2, L, N), dtype=torch.int64, device="cuda")
+    b = torch.empty((n, 2, L, N), dtype=torch.int64, device="cuda")
+    for r in range(L):
+        a[:, :, r, :] = torch.randint(0, ctx.primes[r], (n, 2, N), device="cuda", generator=gen)
+        b[:, :, r, :] = torch.randint(0, ctx.primes[r], (n, 2, N), device="cuda", generator=gen)
+    out = ctx.empty_ct(n, L - 1)
+    peak = alu_peaks()[BUTTERFLY]
+    for _ in range(args.warmup):
+        ctx.mul_relin_rescale(a, b, L, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0.record()
+    for _ in range(args.steps):
+        ctx.mul_relin_rescale(a, b, L, out)
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ctx.sync()
+    ms = e0.elapsed_time(e1)
+    work = n * mul_relin_rescale_shoup(N, L) * args.steps
+    achieved = work / (ms / 1000.0) / 1e9
+    roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak / 1e9, 2),
+            "unit": "G Shoup products/s", "frac": round(achieved / (peak / 1e9), 4), "traffic": None,
+            "kernel": "whole step (every launch of the call)",
+            "work_per_step": "per op at level L: (L + L*L + 2 + 2L + 2 + 2(L-1)) transforms x (N/2) log2 N "
+                             "butterflies + 2 L (L+1) N key products (the merged path executes 2L fewer "
+                             "transforms; tensor and element-wise products not counted)"}
+    roof.update(peak_desc(peak, clk))
+    print(json.dumps({"metric": "ct-mult+relin+rescale/s at N=16384", "value": round(n * args.steps / (ms / 1000.0), 1),
+                      "unit": "ops/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True, "dtype": "u64",
+                      "data": "synthetic (uniform residues, seed 1)",
+                      "config": {"workload": "mul + relinearise + rescale %d ciphertext pairs at L=%d" % (n, L),
+                                 "ntt_schedule": ctx.ntt_variant, "ntt_schedule_keyswitch": ctx.ntt_variant_ks},
+                      "clocks": clk, "roofline": roof}), flush=True)
+
+
 def run_batch(args):
     """4096 ciphertext pairs at uneven levels (L = 1 + U{1..7}, seed 3), each
     getting ct-mult + relinearise + rescale: all levels in one call (one
@@ -909,7 +964,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cnn", choices=["cnn", "mlp", "dense_square", "cnn_relu", "deep", "cnn_rotate",
                                                           "cnn_masquerade", "batch", "relin", "ntt_sweep", "serve",
-                                                          "int_peak"])
+                                                          "int_peak", "mrr"])
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--batch-cts", type=int, default=4096)
@@ -927,6 +982,8 @@ def main():
         run_batch(args)
     elif args.workload == "relin":
         run_relin(args)
+    elif args.workload == "mrr":
+        run_mrr(args)
     elif args.workload == "ntt_sweep":
         run_ntt_sweep(args)
     elif args.workload == "serve":
