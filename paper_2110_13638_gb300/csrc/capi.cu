@@ -302,6 +302,8 @@ static void free_ctx(fhe_ctx* c)
     cudaFree(c->d_pc);
     cudaFree(c->d_tw_fwd);
     cudaFree(c->d_tw_inv);
+    cudaFree(c->d_tw_fwd_wl);
+    cudaFree(c->d_tw_inv_wl);
     cudaFree(c->d_cdt);
     cudaFree(c->d_enc_tw);
     cudaFree(c->d_enc_twist);
@@ -529,6 +531,26 @@ int fhe_ctx_create(uint32_t N, const uint32_t* bits, uint32_t n_bits, uint32_t l
             twi[(size_t)r * N + i] = make_ulonglong2(wi, shoup(wi, q));
         }
     }
+    // warp-local layouts: the stages whose twiddles vary per lane (forward:
+    // the last five, 2^t entries per lane at stage log2 N - 5 + t; inverse:
+    // the first five, 2^(4-s) per lane at stage s) transposed by wl_perm
+    std::vector<ulonglong2> twf_wl, twi_wl;
+    if (ntt_wl_fits(c->logN)) {
+        twf_wl = twf;
+        twi_wl = twi;
+        const int lg = (int)c->logN;
+        for (uint32_t r = 0; r < np; ++r) {
+            const size_t o = (size_t)r * N;
+            for (int t = 0; t < 5; ++t) {
+                const uint32_t base = 1u << (lg - 5 + t);
+                for (uint32_t k = 0; k < base; ++k) twf_wl[o + base + wl_perm(k, t)] = twf[o + base + k];
+            }
+            for (int st = 0; st < 5; ++st) {
+                const uint32_t base = N >> (st + 1);
+                for (uint32_t k = 0; k < base; ++k) twi_wl[o + base + wl_perm(k, 4 - st)] = twi[o + base + k];
+            }
+        }
+    }
     std::vector<u64> cdt = gauss_cdt();
     // encoder tables: zeta^{-4k} (k < N/4), zeta^{-k} (k < N/2), slot positions
     std::vector<double4> etw(N / 4), etwist(N / 2);
@@ -570,6 +592,10 @@ int fhe_ctx_create(uint32_t N, const uint32_t* bits, uint32_t n_bits, uint32_t l
     up((void**)&c->d_pc, c->pc.data(), np * sizeof(PrimeC));
     up((void**)&c->d_tw_fwd, twf.data(), twf.size() * sizeof(ulonglong2));
     up((void**)&c->d_tw_inv, twi.data(), twi.size() * sizeof(ulonglong2));
+    if (!twf_wl.empty()) {
+        up((void**)&c->d_tw_fwd_wl, twf_wl.data(), twf_wl.size() * sizeof(ulonglong2));
+        up((void**)&c->d_tw_inv_wl, twi_wl.data(), twi_wl.size() * sizeof(ulonglong2));
+    }
     up((void**)&c->d_cdt, cdt.data(), cdt.size() * sizeof(u64));
     up((void**)&c->d_enc_tw, etw.data(), etw.size() * sizeof(double4));
     up((void**)&c->d_enc_twist, etwist.data(), etwist.size() * sizeof(double4));
@@ -590,7 +616,7 @@ int fhe_ctx_create(uint32_t N, const uint32_t* bits, uint32_t n_bits, uint32_t l
         free_ctx(c);
         return rc;
     }
-    c->key_bytes = np * sizeof(PrimeC) + 2 * twf.size() * sizeof(ulonglong2) + cdt.size() * 8 +
+    c->key_bytes = np * sizeof(PrimeC) + 2 * (twf.size() + twf_wl.size()) * sizeof(ulonglong2) + cdt.size() * 8 +
                    (etw.size() + etwist.size()) * sizeof(double4) +
                    (etw_q.size() + etwist_q.size()) * sizeof(ulonglong2) + slot_of.size() * 4;
     rc = autotune_ntt(c);
@@ -626,6 +652,8 @@ int fhe_ctx_fork(fhe_ctx* parent, fhe_ctx** out)
     c->d_pc = parent->d_pc;
     c->d_tw_fwd = parent->d_tw_fwd;
     c->d_tw_inv = parent->d_tw_inv;
+    c->d_tw_fwd_wl = parent->d_tw_fwd_wl;
+    c->d_tw_inv_wl = parent->d_tw_inv_wl;
     c->d_cdt = parent->d_cdt;
     c->d_enc_tw = parent->d_enc_tw;
     c->d_enc_twist = parent->d_enc_twist;

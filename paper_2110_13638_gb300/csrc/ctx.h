@@ -26,6 +26,8 @@ struct fhe_ctx {
     PrimeC* d_pc = nullptr;
     ulonglong2* d_tw_fwd = nullptr;
     ulonglong2* d_tw_inv = nullptr;
+    ulonglong2* d_tw_fwd_wl = nullptr;   // warp-local layouts (NttTables::tw_fwd_wl)
+    ulonglong2* d_tw_inv_wl = nullptr;
     u64* d_cdt = nullptr;          // 38 Gaussian thresholds
     double4* d_enc_tw = nullptr;   // [N/4] zeta^{-4k} as (re.hi, re.lo, im.hi, im.lo)
     double4* d_enc_twist = nullptr;// [N/2] zeta^{-k}
@@ -73,6 +75,8 @@ struct fhe_ctx {
         NttTables t;
         t.tw_fwd = d_tw_fwd;
         t.tw_inv = d_tw_inv;
+        t.tw_fwd_wl = d_tw_fwd_wl;
+        t.tw_inv_wl = d_tw_inv_wl;
         t.pc = d_pc;
         t.logN = (int)logN;
         return t;

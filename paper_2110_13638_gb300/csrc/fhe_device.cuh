@@ -278,6 +278,13 @@ __device__ __forceinline__ u64 fwd_out(u64 x, u64 q)
 struct NttTables {
     const ulonglong2* tw_fwd;   // [nprimes][N] (w, w') psi^{bitrev(i)}
     const ulonglong2* tw_inv;   // [nprimes][N] (w, w') psi^{-bitrev(i)}
+    // the same tables with the five stages whose twiddles vary per lane in
+    // the warp-local transform (forward: the last five, inverse: the first
+    // five) transposed so that the 32 lanes of a warp read 32 consecutive
+    // entries (wl_perm); the other stages as in tw_fwd / tw_inv.  Null when
+    // the ring is outside the warp-local schedule's range
+    const ulonglong2* tw_fwd_wl;
+    const ulonglong2* tw_inv_wl;
     const PrimeC* pc;           // [nprimes]
     int logN;
 };
@@ -1049,6 +1056,110 @@ __device__ __forceinline__ void wl_inv_block(const Op& op, int p, int u, const P
     }
 }
 
+// Position, within a stage's block of a warp-local twiddle table, of the
+// entry at natural offset k, for a stage at which each lane of a warp needs
+// 2^u consecutive entries: k = (w 32 + lane) 2^u + m (m < 2^u) is stored at
+// (w 2^u + m) 32 + lane, so lanes read consecutive entries for each m.
+__host__ __device__ constexpr uint32_t wl_perm(uint32_t k, int u)
+{
+    return ((k >> (u + 5)) << (u + 5)) | ((k & ((1u << u) - 1)) << 5) | ((k >> u) & 31u);
+}
+
+// The five lane-varying stages of the warp-local forward transform (global
+// stages sb .. sb+4, sb = log2 N - 5) on lane `lane` of warp w, its 32 values
+// x[i] = a[1024 w + 32 lane + i], twiddles from the transposed table: one
+// stage over all 32 values, then two independent 16-value halves h.
+template <int K, bool RED, int l>
+__device__ __forceinline__ void bfly_fwd_lanes_from(u64* x, const ulonglong2* __restrict__ tw, int sb, int w, int lane,
+                                                    int h, u64 q, u64 q2)
+{
+    if constexpr (l < K) {
+        constexpr int R = 1 << K, hh = R >> (l + 1), t = l + 1;   // global stage sb + t
+        const ulonglong2* twl = tw + (1 << (sb + t)) + ((((w << t) + (h << l))) << 5) + lane;
+#pragma unroll
+        for (int m = 0; m < (1 << l); ++m) {
+            const ulonglong2 wv = __ldg(&twl[m << 5]);
+#pragma unroll
+            for (int tt = 0; tt < hh; ++tt) {
+                const int i = m * 2 * hh + tt;
+                u64 X = x[i];
+                if (RED) X = X >= q2 ? X - q2 : X;
+                const u64 T = mul_shoup_lazy(x[i + hh], wv.x, wv.y, q);
+                x[i] = X + T;
+                x[i + hh] = X + q2 - T;
+            }
+        }
+        bfly_fwd_lanes_from<K, RED, l + 1>(x, tw, sb, w, lane, h, q, q2);
+    }
+}
+
+template <bool RED>
+__device__ __forceinline__ void bfly_fwd32_lanes(u64* x, const ulonglong2* __restrict__ tw, int sb, int w, int lane,
+                                                 u64 q, u64 q2)
+{
+    {
+        const ulonglong2 wv = __ldg(&tw[(1 << sb) + (w << 5) + lane]);    // 2^0 entries per lane: natural order
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            u64 X = x[i];
+            if (RED) X = X >= q2 ? X - q2 : X;
+            const u64 T = mul_shoup_lazy(x[i + 16], wv.x, wv.y, q);
+            x[i] = X + T;
+            x[i + 16] = X + q2 - T;
+        }
+    }
+    bfly_fwd_lanes_from<4, RED, 0>(x, tw, sb, w, lane, 0, q, q2);
+    bfly_fwd_lanes_from<4, RED, 0>(x + 16, tw, sb, w, lane, 1, q, q2);
+}
+
+// The five lane-varying stages of the warp-local inverse transform (global
+// stages 0 .. 4) in the same layout: two independent 16-value halves h
+// (stages 0 .. 3, 2^(4-s) entries per lane at stage s), then one stage over
+// all 32 values.
+template <int K, bool RED, int l>
+__device__ __forceinline__ void bfly_inv_lanes_from(u64* x, const ulonglong2* __restrict__ tw, int N, int w, int lane,
+                                                    int h, u64 q, u64 q2)
+{
+    if constexpr (l < K) {
+        constexpr int R = 1 << K, hh = 1 << l, u = K - l;            // global stage l
+        const ulonglong2* twl = tw + (N >> (l + 1)) + ((((w << u) + (h << (K - l - 1)))) << 5) + lane;
+        const u64 c = RED ? q2 : (q2 << l);
+#pragma unroll
+        for (int m = 0; m < (R >> (l + 1)); ++m) {
+            const ulonglong2 wv = __ldg(&twl[m << 5]);
+#pragma unroll
+            for (int tt = 0; tt < hh; ++tt) {
+                const int i = m * 2 * hh + tt;
+                const u64 X = x[i], Y = x[i + hh];
+                u64 S = X + Y;
+                if (RED) S = S >= q2 ? S - q2 : S;
+                x[i] = S;
+                x[i + hh] = mul_shoup_lazy(X + c - Y, wv.x, wv.y, q);
+            }
+        }
+        bfly_inv_lanes_from<K, RED, l + 1>(x, tw, N, w, lane, h, q, q2);
+    }
+}
+
+template <bool RED>
+__device__ __forceinline__ void bfly_inv32_lanes(u64* x, const ulonglong2* __restrict__ tw, int logN, int w, int lane,
+                                                 u64 q, u64 q2)
+{
+    const int N = 1 << logN;
+    bfly_inv_lanes_from<4, RED, 0>(x, tw, N, w, lane, 0, q, q2);
+    bfly_inv_lanes_from<4, RED, 0>(x + 16, tw, N, w, lane, 1, q, q2);
+    const ulonglong2 wv = __ldg(&tw[(N >> 5) + (w << 5) + lane]);         // natural order
+    const u64 c = RED ? q2 : (q2 << 4);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const u64 X = x[i], Y = x[i + 16];
+        u64 S = X + Y;
+        if (RED) S = S >= q2 ? S - q2 : S;
+        x[i] = S;
+        x[i + 16] = mul_shoup_lazy(X + c - Y, wv.x, wv.y, q);
+    }
+}
+
 // sub-transform u of unit p; warps beyond the N/1024 that own a
 // sub-transform (a block larger than N/32 threads) only take part in the
 // block stages and barriers
@@ -1087,8 +1198,8 @@ __device__ __forceinline__ void wl_transform(const Op& op, int p, int u, const P
         __syncwarp();
 #pragma unroll
         for (int i = 0; i < 32; ++i) x[i] = sm[wpad(b + 32 * l + i)];
-        // stages KA+5 .. logN-1 (distances 16 .. 1)
-        bfly_fwd32<RED>(x, tw, KA + 5, 32 * w + l, q, q2);
+        // stages KA+5 .. logN-1 (distances 16 .. 1), twiddles per lane
+        bfly_fwd32_lanes<RED>(x, tw, KA + 5, w, l, q, q2);
 #pragma unroll
         for (int i = 0; i < 32; ++i) sm[wpad(b + 32 * l + i)] = x[i];
         __syncwarp();
@@ -1115,8 +1226,8 @@ __device__ __forceinline__ void wl_transform(const Op& op, int p, int u, const P
             __syncwarp();
 #pragma unroll
             for (int i = 0; i < 32; ++i) x[i] = sm[wpad(b + 32 * l + i)];
-            // stages 0 .. 4 (distances 1 .. 16)
-            bfly_inv32<RED>(x, tw, logN, 0, 32 * w + l, q, q2);
+            // stages 0 .. 4 (distances 1 .. 16), twiddles per lane
+            bfly_inv32_lanes<RED>(x, tw, logN, w, l, q, q2);
 #pragma unroll
             for (int i = 0; i < 32; ++i) sm[wpad(b + 32 * l + i)] = x[i];
             __syncwarp();
@@ -1165,7 +1276,7 @@ __device__ __forceinline__ void ntt_wl_unit(const Op& op, const NttTables& T, in
         if (op.direct(p, u)) {
             for (int j = threadIdx.x; j < N; j += blockDim.x) op.store(p, u, j, 0, op.pre(p, u, j), P);
         } else {
-            const ulonglong2* tw = (INV ? T.tw_inv : T.tw_fwd) + (size_t)pi * N;
+            const ulonglong2* tw = (INV ? T.tw_inv_wl : T.tw_fwd_wl) + (size_t)pi * N;
             const bool wide = !cold_path<Op>::value && P.q < (INV ? kInvNoRedBound : kFwdNoRedBound);  // block-uniform
             if constexpr (cold_path<Op>::value) {
                 wl_transform<INV, true>(op, p, u, P, tw, sm, logN);

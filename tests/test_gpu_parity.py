@@ -581,9 +581,8 @@ def test_grouped_rotation_bit_exact_per_group():
 # ---------------------------------------------------------------- uneven levels, one persistent launch
 @pytest.mark.parametrize("N", [512, 1024])
 def test_mul_relin_rescale_levels_matches_per_batch_and_oracle(N):
-    """One persistent launch over levels 2..8, below and at the smallest
-    ring of the warp-local schedule: equal to the per-level calls and to the
-    oracle."""
+    """One persistent launch over levels 2..8 at two ring degrees: equal to
+    the per-level calls and to the oracle."""
     g, o = pair(N, BITS9)
     rng = np.random.default_rng(42)
     batches, ref_outs = [], []
