@@ -324,7 +324,10 @@ int fhe_rescale(fhe_ctx* ctx, const uint64_t* d_in, uint32_t n_ct, uint32_t comp
  * d_out [n_ct][2][level-1][N] = rescale(relin(a (x) b)).  ModDown and the
  * rescale share their forward transforms (NTT([v] P^-1 + [r]) per output
  * row, the transforms being linear); both centred roundings are those of
- * the separate steps, so the words equal fhe_relinearise then fhe_rescale. */
+ * the separate steps, so the words equal fhe_relinearise then fhe_rescale.
+ * The tensor product is not stored: each step recomputes the component it
+ * needs from d_a and d_b.  d_out may overlap d_a or d_b (the tensor is then
+ * formed in the workspace first). */
 int fhe_mul_relin_rescale(fhe_ctx* ctx, const uint64_t* d_a, const uint64_t* d_b, uint32_t n_ct,
                           uint32_t level, uint64_t* d_out, void* stream);
 

@@ -17,7 +17,7 @@ SO = os.path.join(BUILD, "libfhe.so")
 ROOT = os.path.dirname(HERE)
 
 # the transform-heavy units first, so the parallel build starts them earliest
-SOURCES = ["k_relin_modup.cu", "k_persist.cu", "k_modup_cluster.cu", "k_keys.cu", "k_encrypt.cu", "k_groups_ks.cu", "k_groups.cu", "k_groups_fwd.cu", "k_relin.cu",
+SOURCES = ["k_relin_modup.cu", "k_relin_tensor.cu", "k_persist.cu", "k_modup_cluster.cu", "k_keys.cu", "k_encrypt.cu", "k_groups_ks.cu", "k_groups.cu", "k_groups_fwd.cu", "k_relin.cu",
            "k_rescale.cu", "k_common.cu", "k_encode.cu", "k_mac.cu", "k_mac_tc.cu", "capi.cu", "graph.cu", "batch.cu", "noalloc.cu", "k_peak.cu",
            "host_math.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

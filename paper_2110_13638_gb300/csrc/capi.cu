@@ -971,15 +971,24 @@ int fhe_mul_relin_rescale(fhe_ctx* c, const uint64_t* a, const uint64_t* b, uint
     if (n_ct == 0) return FHE_OK;
     if (!a || !b || !out) return fail(FHE_EINVAL, "null buffer");
     const size_t N = c->N;
-    const size_t b3 = (size_t)n_ct * 3 * level * N * 8, br = relin_rescale_scratch_bytes(c, n_ct, level);
+    const size_t wa = (size_t)n_ct * 2 * level * N, wo = (size_t)n_ct * 2 * (level - 1) * N;
+    auto overlaps = [&](const uint64_t* x) { return x < out + wo && out < x + wa; };
+    // the factors are read until the last step, which writes d_out: when
+    // d_out overlaps them, the tensor is formed first
+    const bool fused = !overlaps(a) && !overlaps(b);
+    const size_t b3 = fused ? 0 : (size_t)n_ct * 3 * level * N * 8, br = relin_rescale_scratch_bytes(c, n_ct, level);
     Arena ar;
     int rc = ws_reserve(c, arena_need({b3, br}), &ar);
     if (rc) return rc;
-    u64* t3 = (u64*)ar.take(b3);
+    u64* t3 = fused ? nullptr : (u64*)ar.take(b3);
     void* sr = ar.take(br);
     cudaStream_t st = (cudaStream_t)stream;
-    k_tensor(c, (const u64*)a, (const u64*)b, t3, n_ct, level, st);
-    k_relin_rescale(c, t3, (u64*)out, n_ct, level, sr, st);
+    if (fused) {
+        k_mul_relin_rescale(c, (const u64*)a, (const u64*)b, (u64*)out, n_ct, level, sr, st);
+    } else {
+        k_tensor(c, (const u64*)a, (const u64*)b, t3, n_ct, level, st);
+        k_relin_rescale(c, t3, (u64*)out, n_ct, level, sr, st);
+    }
     CUDA_LAST("mul_relin_rescale launch");
     return FHE_OK;
 }

@@ -234,6 +234,10 @@ size_t relin_rescale_scratch_bytes(const fhe_ctx* c, uint32_t n_ct, uint32_t L);
 void k_relin_rescale(const fhe_ctx* c, const u64* d3, u64* out, uint32_t n_ct, uint32_t L, void* scratch,
                      cudaStream_t st, const KsExtra* ex = nullptr, const u64* addc = nullptr,
                      uint32_t addc_stride = 0);
+// the same for the tensor product of a and b ([n][2][L][N] each, NTT form,
+// reduced) without storing it (k_relin_tensor.cu); same scratch
+void k_mul_relin_rescale(const fhe_ctx* c, const u64* a, const u64* b, u64* out, uint32_t n_ct, uint32_t L,
+                         void* scratch, cudaStream_t st);
 // scratch: rescale_scratch_bytes; addc: optional constants (device residues,
 // addc[ct * addc_stride + i]) added to comp 0 of the result
 size_t rescale_scratch_bytes(const fhe_ctx* c, uint32_t n_ct, uint32_t comps);

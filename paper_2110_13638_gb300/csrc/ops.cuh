@@ -390,9 +390,10 @@ using OpKsRowInv = OpKsRowInvT<false>;
 // steps 3 and 4' in one unit per (ct, comp): sub 0 is the inverse transform of
 // the accumulator's P residue (into Vp), sub 1 that of row L-1 (into V), whose
 // epilogue reads the Vp words sub 0 wrote (the same block, after its barrier)
-struct OpKsPRowInv {
+template <bool TENSOR>
+struct OpKsPRowInvT {
     static const char* family() { return "keyswitch_rescale_intt"; }
-    OpKsRowInv row;     // its acc, V, constants; row.Vp is the array below
+    OpKsRowInvT<TENSOR> row;    // its acc, V, constants; row.Vp is the array below
     u64* Vp;            // [n][2][N] written by sub 0
     int Ltop;
     __host__ __device__ int count() const { return row.n * 2; }
@@ -412,9 +413,10 @@ struct OpKsPRowInv {
     __device__ void store(int p, int u, int j, u64 v, const Pre& pr, const PrimeC& Q) const
     {
         if (u == 0) Vp[(size_t)p * row.N + j] = v;
-        else row.store(p, 0, j, v, OpKsRowInv::Pre{pr.v}, Q);
+        else row.store(p, 0, j, v, typename OpKsRowInvT<TENSOR>::Pre{pr.v}, Q);
     }
 };
+using OpKsPRowInv = OpKsPRowInvT<false>;
 
 // step 5': the merged forward transform of both corrections into q_i, i < L-1,
 // per (ct, comp, i), and the rescaled output row.  TENSOR: the tensor product
@@ -517,8 +519,10 @@ void launch_groups_ks_divfwd(const fhe_ctx* c, const MultiOp<OpKsDivFwd>& m, cud
 void launch_modup_cluster(const fhe_ctx* c, const OpModUpMac& op, cudaStream_t st);
 
 // The ModUp step with the schedule the autotuner picked for it
-// (k_relin_modup.cu, the only unit that instantiates the ModUp kernels)
+// (k_relin_modup.cu, the only unit that instantiates the ModUp kernels of a
+// stored tensor; k_relin_tensor.cu those of a recomputed one)
 void launch_modup(const fhe_ctx* c, const OpModUpMac& op, cudaStream_t st, bool single_pass = false);
+void launch_modup(const fhe_ctx* c, const OpModUpMacT<true>& op, cudaStream_t st);
 
 // The merged ModDown + rescale of one batch (k_relin.cu): ops of steps 4' and 5'.
 OpKsRowInv make_ks_row_inv(const fhe_ctx* c, const u64* d3, const u64* acc, const u64* Vp, u64* V, int n, int L,

@@ -403,6 +403,29 @@ def test_masquerade_cnn_bit_exact_per_group():
     net.close()
 
 
+def test_mul_relin_rescale_output_overlapping_an_input():
+    """fhe_mul_relin_rescale recomputes the tensor from its factors in every
+    step, unless the output overlaps a factor (then the tensor is formed
+    first): both give the oracle's words."""
+    g, o = pair(1024, BITS5)
+    rng = np.random.default_rng(11)
+    L, n = 4, 3
+    A = [rand_ct(o, L, rng) for _ in range(n)]
+    B = [rand_ct(o, L, rng) for _ in range(n)]
+    ta, tb = upload(g, A, L), upload(g, B, L)
+    out = g.empty_ct(n, L - 1)
+    g.mul_relin_rescale(ta, tb, L, out)
+    got = download(g, out, L - 1)
+    for k in range(n):
+        want = o.rescale(o.relinearise(o.tensor(ckks.Ciphertext(A[k], L, 1.0), ckks.Ciphertext(B[k], L, 1.0)))).c
+        assert np.array_equal(got[k], want), k
+    # the output over the front of a's storage
+    ta2 = ta.clone()
+    alias = ta2.view(-1)[: n * 2 * (L - 1) * g.N].view(n, 2, L - 1, g.N)
+    g.mul_relin_rescale(ta2, tb, L, alias)
+    assert torch.equal(alias, out)
+
+
 @pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8])
 @pytest.mark.parametrize("N", [256, 4096])
 def test_every_schedule_at_small_rings(N, variant):
