@@ -989,7 +989,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_ntt_io(Op op, NttTables T)
 }
 
 // ---------------------------------------------------------------- warp-local transforms
-// One block of N/32 threads per residue polynomial, 1024 <= N <= 16384.
+// One block of N/32 threads per residue polynomial, 1024 <= N <= 16384 (a
+// larger block works too: its extra warps take part in the block stages and
+// barriers only).
 // After the first logN - 10 stages (distances N/2 .. 1024, forward) the
 // array falls apart into N/1024 independent 1024-point problems on
 // contiguous blocks; warp w owns block [1024 w, 1024 w + 1024), 32 values
@@ -1004,6 +1006,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_ntt_io(Op op, NttTables T)
 // (the prologue's loads, the epilogue's loads and stores, which go through
 // shared memory once more) is coalesced.  The inverse runs the same steps in
 // the opposite order (warp stages 0..9, barrier, block stages 10..logN-1).
+// The five stages whose twiddles differ per lane (forward: the last five,
+// inverse: the first five) read them from tables transposed by wl_perm, so
+// the lanes of a warp read consecutive entries.
 // Shared-memory word j sits at j + j/32: conflict-free for lanes reading
 // consecutive words and for lanes reading words 32 apart.
 __device__ __forceinline__ int wpad(int j) { return j + (j >> 5); }
