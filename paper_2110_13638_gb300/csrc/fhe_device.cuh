@@ -1030,8 +1030,9 @@ __device__ __forceinline__ void wl_fwd_block(const Op& op, int p, int u, const P
 #pragma unroll
         for (int i = 0; i < R; ++i) x[i] = op.load(p, u, gi + (i << 10), P);
         bfly_fwd<KA, RED>(x, tw, 0, 0, P.q, P.q2);
+        u64* const g = sm + wpad(gi);         // element gi + 1024 i at g[1056 i]
 #pragma unroll
-        for (int i = 0; i < R; ++i) sm[wpad(gi + (i << 10))] = x[i];
+        for (int i = 0; i < R; ++i) g[1056 * i] = x[i];
     }
 }
 
@@ -1047,8 +1048,9 @@ __device__ __forceinline__ void wl_inv_block(const Op& op, int p, int u, const P
 #pragma unroll 1
     for (int gi = tid; gi < 1024; gi += nthr) {
         u64 x[R];
+        const u64* const g = sm + wpad(gi);   // element gi + 1024 i at g[1056 i]
 #pragma unroll
-        for (int i = 0; i < R; ++i) x[i] = sm[wpad(gi + (i << 10))];
+        for (int i = 0; i < R; ++i) x[i] = g[1056 * i];
         bfly_inv<KA, RED>(x, tw, logN, 10, 0, P.q, P.q2);
 #pragma unroll
         for (int i0 = 0; i0 < R; i0 += B) {
@@ -1177,6 +1179,10 @@ __device__ __forceinline__ void wl_transform(const Op& op, int p, int u, const P
     const int KA = logN - 10;
     const bool owner = w < (1 << KA);
     const u64 q = P.q, q2 = P.q2;
+    // the warp's two layouts in shared memory (index j + j/32, l < 32):
+    // element b + l + 32 i at smA[33 i], element b + 32 l + i at smB[i]
+    u64* const smA = sm + wpad(b + l);
+    u64* const smB = sm + wpad(b + 32 * l);
     u64 x[32];
     if (!INV) {
         if (KA > 0) {
@@ -1194,19 +1200,19 @@ __device__ __forceinline__ void wl_transform(const Op& op, int p, int u, const P
             for (int i = 0; i < 32; ++i) x[i] = op.load(p, u, l + 32 * i, P);
         } else {
 #pragma unroll
-            for (int i = 0; i < 32; ++i) x[i] = sm[wpad(b + l + 32 * i)];
+            for (int i = 0; i < 32; ++i) x[i] = smA[33 * i];
         }
         // stages KA .. KA+4 (distances 512 .. 32 within the block of warp w)
         bfly_fwd32<RED>(x, tw, KA, w, q, q2);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) sm[wpad(b + l + 32 * i)] = x[i];
+        for (int i = 0; i < 32; ++i) smA[33 * i] = x[i];
         __syncwarp();
 #pragma unroll
-        for (int i = 0; i < 32; ++i) x[i] = sm[wpad(b + 32 * l + i)];
+        for (int i = 0; i < 32; ++i) x[i] = smB[i];
         // stages KA+5 .. logN-1 (distances 16 .. 1), twiddles per lane
         bfly_fwd32_lanes<RED>(x, tw, KA + 5, w, l, q, q2);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) sm[wpad(b + 32 * l + i)] = x[i];
+        for (int i = 0; i < 32; ++i) smB[i] = x[i];
         __syncwarp();
         // epilogue, coalesced: element b + l + 32 i
 #pragma unroll 1
@@ -1217,7 +1223,7 @@ __device__ __forceinline__ void wl_transform(const Op& op, int p, int u, const P
 #pragma unroll
             for (int i = 0; i < kWlEpiBatch; ++i) {
                 const int j = b + l + 32 * (i0 + i);
-                const u64 v = sm[wpad(j)];
+                const u64 v = smA[33 * (i0 + i)];
                 op.store(p, u, j, RED ? fwd_out<Op>(v, q) : fwd_out_wide<Op>(v, P), pr[i], P);
             }
         }
@@ -1227,17 +1233,17 @@ __device__ __forceinline__ void wl_transform(const Op& op, int p, int u, const P
 #pragma unroll
             for (int i = 0; i < 32; ++i) x[i] = op.load(p, u, b + l + 32 * i, P);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) sm[wpad(b + l + 32 * i)] = x[i];
+            for (int i = 0; i < 32; ++i) smA[33 * i] = x[i];
             __syncwarp();
 #pragma unroll
-            for (int i = 0; i < 32; ++i) x[i] = sm[wpad(b + 32 * l + i)];
+            for (int i = 0; i < 32; ++i) x[i] = smB[i];
             // stages 0 .. 4 (distances 1 .. 16), twiddles per lane
             bfly_inv32_lanes<RED>(x, tw, logN, w, l, q, q2);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) sm[wpad(b + 32 * l + i)] = x[i];
+            for (int i = 0; i < 32; ++i) smB[i] = x[i];
             __syncwarp();
 #pragma unroll
-            for (int i = 0; i < 32; ++i) x[i] = sm[wpad(b + l + 32 * i)];
+            for (int i = 0; i < 32; ++i) x[i] = smA[33 * i];
             // stages 5 .. 9 (distances 32 .. 512)
             bfly_inv32<RED>(x, tw, logN, 5, w, q, q2);
             if (KA == 0) {
@@ -1253,7 +1259,7 @@ __device__ __forceinline__ void wl_transform(const Op& op, int p, int u, const P
                 return;
             }
 #pragma unroll
-            for (int i = 0; i < 32; ++i) sm[wpad(b + l + 32 * i)] = x[i];
+            for (int i = 0; i < 32; ++i) smA[33 * i] = x[i];
         }
         if (KA > 0) {
             __syncthreads();
