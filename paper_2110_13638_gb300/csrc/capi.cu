@@ -355,6 +355,7 @@ static int autotune_ntt(fhe_ctx* c)
         }
         c->ntt_variant = v;
         c->ntt_variant_ks = vk;
+        c->ntt_forced = true;
         return FHE_OK;
     }
     // Timed workload: a rescale (inverse transform of the last residue, then
@@ -496,6 +497,10 @@ int fhe_ctx_create(uint32_t N, const uint32_t* bits, uint32_t n_bits, uint32_t l
     c->primes = ch;
     c->delta = std::ldexp(1.0, (int)log_scale);
     cudaGetDevice(&c->device);
+    if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        cudaGetLastError();
+        c->sms = 0;
+    }
 
     const uint32_t np = n_bits;
     c->pc.resize(np);
@@ -645,6 +650,8 @@ int fhe_ctx_fork(fhe_ctx* parent, fhe_ctx** out)
     c->device = parent->device;
     c->ntt_variant = parent->ntt_variant;
     c->ntt_variant_ks = parent->ntt_variant_ks;
+    c->ntt_forced = parent->ntt_forced;
+    c->sms = parent->sms;
     for (int v = 0; v < 16; ++v) {
         c->ntt_variant_us[v] = parent->ntt_variant_us[v];
         c->ntt_variant_ks_us[v] = parent->ntt_variant_ks_us[v];

@@ -18,6 +18,8 @@ struct fhe_ctx {
     int ntt_variant = 0;           // NTT schedule (see ntt_variant_name), autotuned
     float ntt_variant_us[16] = {};   // autotuner: us per transform per variant
     int ntt_variant_ks = 0;        // schedule of the key-switching inner-product transforms
+    bool ntt_forced = false;       // the schedules were fixed by FHE_NTT_VARIANT (no launch-time change)
+    int sms = 0;                   // SMs of the device
     float ntt_variant_ks_us[16] = {};
     u64* d_ntt2 = nullptr;         // two-pass intermediate (allocated with the context)
     size_t ntt2_words = 0;

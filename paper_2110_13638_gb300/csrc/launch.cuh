@@ -238,7 +238,11 @@ static void launch_ntt(const fhe_ctx* c, const Op& op, cudaStream_t st, bool sin
     // (callers refuse single-pass-only work above kMaxSinglePassN)
     const bool single = single_pass || !uniform_subs<Op>::value;
     const int base = keyswitch_mac<Op>::value || transform_bound<Op>::value ? c->ntt_variant_ks : c->ntt_variant;
-    const int v = single && (base == 2 || base == 3) ? 1 : base;
+    int v = single && (base == 2 || base == 3) ? 1 : base;
+    // fewer units than SMs: each unit's latency sets the launch's time, and a
+    // 1024-thread block (schedule 4) works on a unit with twice the warps of
+    // a warp-local one (schedules fixed by FHE_NTT_VARIANT are kept as given)
+    if (v == 8 && !c->ntt_forced && count < c->sms) v = 4;
     switch (v) {
     case 1: launch_ntt_v<INV, 3, 1024>(c, op, count, st); break;
     case 2: launch_ntt_2pass<INV, 4>(c, op, count, st); break;
