@@ -37,9 +37,9 @@ BUTTERFLY = 3
 # DRAM bytes (read + write) of the key-switching ModUp + key-product kernel
 # per (ciphertext, target prime, digit) unit, from one ncu capture of that
 # kernel (schedule 8, warp-local transforms) on 64 ciphertexts at L = 7
-# (--workload relin): 260.2 MB read + 169.3 MB written over 64 * 8 * 7 units.
+# (--workload relin): 245.1 MB read + 152.1 MB written over 64 * 8 * 7 units.
 # Scaled by units to the bench's launches.
-KS_DRAM_BYTES_PER_UNIT = (260.232192e6 + 169.301760e6) / (64 * 8 * 7)
+KS_DRAM_BYTES_PER_UNIT = (245.089024e6 + 152.088064e6) / (64 * 8 * 7)
 
 
 def _env_rank():
