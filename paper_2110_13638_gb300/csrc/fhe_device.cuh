@@ -814,15 +814,20 @@ __device__ __forceinline__ void bfly_inv32(u64* x, const ulonglong2* __restrict_
 // sh, goff (forward only): the pass works on one half of a larger transform
 // (k_ntt_half_io): its local stage s is global stage s + sh, and its local
 // group g is global group g + goff at the pass's first stage.
+// tail: the last pass of the warp-local tail of a 16384-point forward
+// transform on 1024 threads (4096 groups of 4): warp w takes the groups of
+// [256 w + 8192 h, 256 w + 8192 h + 256), h = 0, 1, the elements it wrote in
+// the pass before (see ntt_io_unit).
 template <bool INV, int K, bool RED, class Get, class Put, class Fetch>
 __device__ __forceinline__ void pass_io(int logN, int s0, const ulonglong2* __restrict__ tw, u64 q, u64 q2, int tid,
-                                        int nthr, Get& get, Put& put, Fetch& fetch, int sh = 0, int goff = 0)
+                                        int nthr, Get& get, Put& put, Fetch& fetch, int sh = 0, int goff = 0,
+                                        bool tail = false)
 {
     constexpr int R = 1 << K;
     const int N = 1 << logN;
     const int lsh = INV ? s0 : (logN - s0 - K);
     const int ngroups = N >> K;
-    for (int gi = tid; gi < ngroups; gi += nthr) {
+    auto group = [&](int gi) {
         const int g = gi >> lsh;
         const int r = gi & ((1 << lsh) - 1);
         const int j0 = (g << (lsh + K)) + r;
@@ -832,19 +837,24 @@ __device__ __forceinline__ void pass_io(int logN, int s0, const ulonglong2* __re
         if (!INV) bfly_fwd<K, RED>(x, tw, s0 + sh, g + goff, q, q2);
         else bfly_inv<K, RED>(x, tw, logN, s0, g, q, q2);
         put(std::integral_constant<int, R>{}, j0, lsh, x, fetched);
+    };
+    if (tail) {
+        for (int it = 0; it < 4; ++it) group(((it >> 1) << 11) + ((tid >> 5) << 6) + ((it & 1) << 5) + (tid & 31));
+    } else {
+        for (int gi = tid; gi < ngroups; gi += nthr) group(gi);
     }
 }
 
 template <bool INV, int KMAX, bool RED, class Get, class Put, class Fetch>
 __device__ __forceinline__ void pass_io_k(int k, int logN, int s0, const ulonglong2* tw, u64 q, u64 q2, int tid, int nthr,
-                                          Get& get, Put& put, Fetch& fetch, int sh = 0, int goff = 0)
+                                          Get& get, Put& put, Fetch& fetch, int sh = 0, int goff = 0, bool tail = false)
 {
     if constexpr (KMAX >= 1) {
         if (k == KMAX) {
-            pass_io<INV, KMAX, RED>(logN, s0, tw, q, q2, tid, nthr, get, put, fetch, sh, goff);
+            pass_io<INV, KMAX, RED>(logN, s0, tw, q, q2, tid, nthr, get, put, fetch, sh, goff, tail);
             return;
         }
-        pass_io_k<INV, KMAX - 1, RED>(k, logN, s0, tw, q, q2, tid, nthr, get, put, fetch, sh, goff);
+        pass_io_k<INV, KMAX - 1, RED>(k, logN, s0, tw, q, q2, tid, nthr, get, put, fetch, sh, goff, tail);
     }
 }
 
@@ -893,6 +903,12 @@ __device__ __forceinline__ void ntt_io_unit(const Op& op, const NttTables& T, in
             const u64 q = P.q, q2 = 2 * P.q;
             const bool wide = !cold_path<Op>::value && q < (INV ? kInvNoRedBound : kFwdNoRedBound);  // block-uniform
             const ulonglong2* tw = (INV ? T.tw_inv : T.tw_fwd) + (size_t)pi * N;
+            // 16384 points on 1024 threads, radix 8: the forward passes at
+            // stages 6, 9 and 12 stay within 256-element blocks that one warp
+            // writes and reads (the last one with its groups assigned to match,
+            // pass_io's tail), and so do the inverse passes at stages 0 and 3,
+            // so those passes are separated by warp barriers only
+            const bool warp_tail = LOGR == 3 && MAXT == 1024 && logN == 14 && nthr == 1024;
             int s = 0;
             bool first = true;
             while (s < logN) {
@@ -958,8 +974,10 @@ __device__ __forceinline__ void ntt_io_unit(const Op& op, const NttTables& T, in
                             if (i0 + i < R) out(i0 + i, pr[i]);
                     }
                 };
+                const bool tail = !INV && warp_tail && last;
                 auto run = [&](auto redc, auto& get, auto& put, auto& fetch) {
-                    pass_io_k<INV, LOGR, decltype(redc)::value>(k, logN, s, tw, q, q2, tid, nthr, get, put, fetch);
+                    pass_io_k<INV, LOGR, decltype(redc)::value>(k, logN, s, tw, q, q2, tid, nthr, get, put, fetch, 0, 0,
+                                                                tail);
                 };
                 auto run_rw = [&](auto& get, auto& put, auto& fetch) {
                     if constexpr (cold_path<Op>::value) {
@@ -973,7 +991,10 @@ __device__ __forceinline__ void ntt_io_unit(const Op& op, const NttTables& T, in
                 else if (first) run_rw(gload, psm, nofetch);
                 else if (last) run_rw(gsm, pepi, efetch);
                 else run_rw(gsm, psm, nofetch);
-                __syncthreads();
+                // the next pass reads only what this warp wrote: forward after
+                // stages 6 and 9, inverse after stage 0
+                if (warp_tail && !last && (INV ? s == 0 : (s == 6 || s == 9))) __syncwarp();
+                else __syncthreads();
                 first = false;
                 s += k;
             }
