@@ -815,9 +815,9 @@ __device__ __forceinline__ void bfly_inv32(u64* x, const ulonglong2* __restrict_
 // (k_ntt_half_io): its local stage s is global stage s + sh, and its local
 // group g is global group g + goff at the pass's first stage.
 // tail: the last pass of the warp-local tail of a 16384-point forward
-// transform on 1024 threads (4096 groups of 4): warp w takes the groups of
-// [256 w + 8192 h, 256 w + 8192 h + 256), h = 0, 1, the elements it wrote in
-// the pass before (see ntt_io_unit).
+// transform (4096 groups of 4): with per = 4096 / (2 nthr) groups per lane in
+// each half, warp w takes the groups of [32 per 4 w + 8192 h, + 32 per 4),
+// h = 0, 1: the elements it wrote in the pass before (see ntt_io_unit).
 template <bool INV, int K, bool RED, class Get, class Put, class Fetch>
 __device__ __forceinline__ void pass_io(int logN, int s0, const ulonglong2* __restrict__ tw, u64 q, u64 q2, int tid,
                                         int nthr, Get& get, Put& put, Fetch& fetch, int sh = 0, int goff = 0,
@@ -839,7 +839,10 @@ __device__ __forceinline__ void pass_io(int logN, int s0, const ulonglong2* __re
         put(std::integral_constant<int, R>{}, j0, lsh, x, fetched);
     };
     if (tail) {
-        for (int it = 0; it < 4; ++it) group(((it >> 1) << 11) + ((tid >> 5) << 6) + ((it & 1) << 5) + (tid & 31));
+        const int per = ngroups / (2 * nthr);
+        const int base = (tid >> 5) * 32 * per + (tid & 31);
+        for (int h = 0; h < 2; ++h)
+            for (int k = 0; k < per; ++k) group(h * (ngroups >> 1) + base + k * 32);
     } else {
         for (int gi = tid; gi < ngroups; gi += nthr) group(gi);
     }
@@ -903,12 +906,17 @@ __device__ __forceinline__ void ntt_io_unit(const Op& op, const NttTables& T, in
             const u64 q = P.q, q2 = 2 * P.q;
             const bool wide = !cold_path<Op>::value && q < (INV ? kInvNoRedBound : kFwdNoRedBound);  // block-uniform
             const ulonglong2* tw = (INV ? T.tw_inv : T.tw_fwd) + (size_t)pi * N;
-            // 16384 points on 1024 threads, radix 8: the forward passes at
-            // stages 6, 9 and 12 stay within 256-element blocks that one warp
-            // writes and reads (the last one with its groups assigned to match,
-            // pass_io's tail), and so do the inverse passes at stages 0 and 3,
-            // so those passes are separated by warp barriers only
-            const bool warp_tail = LOGR == 3 && MAXT == 1024 && logN == 14 && nthr == 1024;
+            // 16384 points, radix 8 on 1024 threads or radix 16 on 512: the
+            // inverse passes at stages 0 and 3 (radix 8) or 4 (radix 16), and
+            // with radix 8 the forward passes at stages 6, 9 and 12 (the last
+            // with its groups assigned to match, pass_io's tail), stay within
+            // blocks of 256 or 512 elements that one warp writes and reads, so
+            // those passes are separated by warp barriers only (a radix-16
+            // forward tail would add a second copy of the last pass and its
+            // epilogue, which doubled the spills of the persistent kernel's
+            // forward units)
+            const bool warp_tail = logN == 14 && ((LOGR == 3 && MAXT == 1024 && nthr == 1024) ||
+                                                  (LOGR == 4 && MAXT == 512 && nthr == 512));
             int s = 0;
             bool first = true;
             while (s < logN) {
@@ -974,7 +982,7 @@ __device__ __forceinline__ void ntt_io_unit(const Op& op, const NttTables& T, in
                             if (i0 + i < R) out(i0 + i, pr[i]);
                     }
                 };
-                const bool tail = !INV && warp_tail && last;
+                const bool tail = !INV && LOGR == 3 && warp_tail && last;
                 auto run = [&](auto redc, auto& get, auto& put, auto& fetch) {
                     pass_io_k<INV, LOGR, decltype(redc)::value>(k, logN, s, tw, q, q2, tid, nthr, get, put, fetch, 0, 0,
                                                                 tail);
@@ -992,8 +1000,9 @@ __device__ __forceinline__ void ntt_io_unit(const Op& op, const NttTables& T, in
                 else if (last) run_rw(gsm, pepi, efetch);
                 else run_rw(gsm, psm, nofetch);
                 // the next pass reads only what this warp wrote: forward after
-                // stages 6 and 9, inverse after stage 0
-                if (warp_tail && !last && (INV ? s == 0 : (s == 6 || s == 9))) __syncwarp();
+                // stages 6 and 9 (radix 8) or 8 (radix 16), inverse after stage 0
+                const bool wsync = INV ? s == 0 : (LOGR == 3 && (s == 6 || s == 9));
+                if (warp_tail && !last && wsync) __syncwarp();
                 else __syncthreads();
                 first = false;
                 s += k;
