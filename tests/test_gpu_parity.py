@@ -638,11 +638,21 @@ def test_mul_relin_rescale_levels_matches_per_batch_and_oracle(N):
             assert np.array_equal(got[k], want), (L, k)
 
 
-def test_mul_relin_rescale_levels_persistent_equals_separate_launches(monkeypatch):
+@pytest.mark.parametrize("N", [4096, 16384])
+def test_mul_relin_rescale_levels_persistent_equals_separate_launches(monkeypatch, N):
     """The persistent launch and the six-launch form (FHE_PERSISTENT=0) give
     the same words, on a batch large enough that many units wait for their
-    ciphertext's previous step."""
-    g, o = pair(4096, BITS9)
+    ciphertext's previous step; at N = 16384 the six-launch form runs the
+    grouped radix-8 transforms whose later passes use warp barriers."""
+    if N == 4096:
+        g, o = pair(N, BITS9)
+    else:
+        monkeypatch.setenv("FHE_NTT_VARIANT", "4")
+        monkeypatch.setenv("FHE_NTT_VARIANT_KS", "8")
+        g = fhe.Context(N, BITS9, 40)
+        monkeypatch.delenv("FHE_NTT_VARIANT")
+        monkeypatch.delenv("FHE_NTT_VARIANT_KS")
+        g.keygen(0)
     gen = torch.Generator(device="cuda")
     gen.manual_seed(9)
     batches = []
@@ -665,6 +675,8 @@ def test_mul_relin_rescale_levels_persistent_equals_separate_launches(monkeypatc
     assert fhe.launch_count() - before == 6
     for b, w in zip(batches, want):
         assert torch.equal(b[2], w), b[3]
+    if N != 4096:
+        g.close()
 
 
 def test_persistent_wait_that_runs_out_reports_timeout():
